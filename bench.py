@@ -1,0 +1,391 @@
+"""Benchmark of the fused wave-propagation step on GB300.
+
+Default workload: 2D shallow water (Roe + Harten-Hyman entropy fix), radial
+dam break on a 4096 x 4096 grid, FP32, reflecting walls, MC limiter,
+transverse splits, CFL 0.9 with the device-side variable dt rule.  One bench
+"step" is one time step of that problem (ghost fill + fused step + dt rule),
+all of them launched as CUDA graphs by one mc_advance call; the timed region
+is exactly K steps.  Each state array is 201 MB, larger than the 129 MB L2, so
+every step streams its input from HBM.
+
+Printed (rank 0): one JSON line with the metric (cell-updates/s), the kernel
+roofline of the fused step (algorithmic bytes / CUDA-event duration against
+the measured HBM copy bandwidth), the end-to-end rate through the host-buffer
+C-ABI call, the FP64 CPU oracle timed on this machine's cores as a baseline,
+and SM clocks sampled during the timed region.
+
+``--impl reference`` times the oracle itself (the only reference there is:
+the paper publishes no code), on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "swe32": dict(solver="swe", dtype="f32", n=4096, cfl=0.9, bc="wall",
+                  desc="shallow-water Roe+HH dam break 4096x4096 fp32, walls, MC, CFL 0.9"),
+    "swe64": dict(solver="swe", dtype="f64", n=4096, cfl=0.9, bc="wall",
+                  desc="shallow-water Roe+HH dam break 4096x4096 fp64, walls, MC, CFL 0.9"),
+    "euler32": dict(solver="euler", dtype="f32", n=4096, cfl=0.8, bc="extrap",
+                    desc="Euler Roe+HH four-quadrant 4096x4096 fp32, extrapolation, MC, CFL 0.8"),
+    "acoustics": dict(solver="acoustics", dtype="f64", n=128, cfl=0.9, bc="periodic",
+                      desc="acoustics Gaussian pulse 128x128 fp64, periodic, MC, CFL 0.9"),
+}
+G, GAMMA = 9.81, 1.4
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def make_problem(mc, wl):
+    from paper_1308_1464_gb300 import workloads
+    n = wl["n"]
+    if wl["solver"] == "swe":
+        g = workloads.swe_dambreak(n, n)
+        sid, param, bc = mc.SWE_ROE, (G, 0, 0, 0), mc.BC_WALL
+    elif wl["solver"] == "euler":
+        g = workloads.euler_quadrants(n, n)
+        sid, param, bc = mc.EULER_ROE, (GAMMA, 0, 0, 0), mc.BC_EXTRAP
+    else:
+        g = workloads.acoustics_pulse(n, n)
+        sid, param, bc = mc.ACOUSTICS, (1.0, 4.0, 0, 0), mc.BC_PERIODIC
+    dtype = mc.F64 if wl["dtype"] == "f64" else mc.F32
+    p = mc.Problem.make(sid, n, n, g.dx, g.dy, dtype=dtype, bc=(bc,) * 4, param=param)
+    return p, g
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while a region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [r.strip().split(", ") for r in f if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1308_1464_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.startswith("mc_sweep") or name in ("mc_riemann.cuh", "mc_device.cuh", "mc_tile.h"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """DRAM bytes per launch of the fused step from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("source_hash") == sweep_source_hash():
+            return e["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """The FP64 oracle, as it stands, timed on this machine's cores on a bounded
+    sample of the workload: steps of the same problem on an n x n grid."""
+    import oracle
+    from paper_1308_1464_gb300 import workloads
+    cores = len(os.sched_getaffinity(0))
+    n = 1024 if wl["solver"] != "acoustics" else 128
+    if wl["solver"] == "swe":
+        g = workloads.swe_dambreak(n, n)
+        op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
+                            param=(G, 0, 0, 0))
+    elif wl["solver"] == "euler":
+        g = workloads.euler_quadrants(n, n)
+        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
+                            param=(GAMMA, 0, 0, 0))
+    else:
+        g = workloads.acoustics_pulse(n, n)
+        op = oracle.Problem(oracle.ACOUSTICS, n, n, g.dx, g.dy, param=(1.0, 4.0, 0, 0))
+    q = np.zeros(op.shape)
+    q[:, 2:-2, 2:-2] = g.q
+    dt = wl["cfl"] / oracle.max_cell_speed(op, oracle.bc_fill(op, q))
+    oracle.step(op, q, dt, nthreads=cores)   # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        q, smax, _ = oracle.step(op, q, dt, nthreads=cores)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 200:
+            break
+    return {"value": n * n * steps / el, "unit": "cell-updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the same problem on a {n}x{n} grid "
+                      f"(OpenMP over rows, {cores} threads), {el:.1f} s"}
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    # size each step's sample so that warmup + steps fit in about two minutes
+    per_step_budget = 120.0 / max(1, args.steps + args.warmup)
+    probe = cpu_baseline(wl, budget_s=1.0)
+    rate = probe["value"]
+    n = int(max(16, min(wl["n"], (rate * per_step_budget) ** 0.5)))
+    from paper_1308_1464_gb300 import workloads
+    if wl["solver"] == "swe":
+        g = workloads.swe_dambreak(n, n)
+        op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
+                            param=(G, 0, 0, 0))
+    elif wl["solver"] == "euler":
+        g = workloads.euler_quadrants(n, n)
+        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
+                            param=(GAMMA, 0, 0, 0))
+    else:
+        g = workloads.acoustics_pulse(n, n)
+        op = oracle.Problem(oracle.ACOUSTICS, n, n, g.dx, g.dy, param=(1.0, 4.0, 0, 0))
+    q = np.zeros(op.shape)
+    q[:, 2:-2, 2:-2] = g.q
+    dt = wl["cfl"] / oracle.max_cell_speed(op, oracle.bc_fill(op, q))
+    for _ in range(args.warmup):
+        q, smax, _ = oracle.step(op, q, dt, nthreads=cores)
+        dt = wl["cfl"] / smax
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q, smax, _ = oracle.step(op, q, dt, nthreads=cores)
+        dt = wl["cfl"] / smax
+    el = time.perf_counter() - t0
+    value = n * n * args.steps / el
+    sample = f"each step: one FP64 oracle step on a {n}x{n} grid of the same problem"
+    print(json.dumps({
+        "impl": "reference", "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample_grid": n},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    import paper_1308_1464_gb300 as mc
+    from paper_1308_1464_gb300 import _build
+    from paper_1308_1464_gb300.state import DeviceState
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+
+    p, g = make_problem(mc, wl)
+    n_cells = p.mx * p.my
+    ctx = mc.Context(p)
+    lay = ctx.layout
+    a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+    npdt = np.float64 if p.dtype == mc.F64 else np.float32
+    q0 = np.ascontiguousarray(g.q.astype(npdt))
+    a.upload(q0)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    smax0 = ctx.max_cell_speed(a.ptr, sh)
+    dt0 = wl["cfl"] / smax0
+
+    # warm-up (also builds the cached step graphs)
+    t_sim, dt, inb, _ = ctx.advance(a.ptr, b.ptr, args.warmup, wl["cfl"], 1.0, 0.0, dt0, sh)
+    qa, qb = (b, a) if inb else (a, b)
+    ctx.advance(qa.ptr, qb.ptr, min(args.steps, 50), wl["cfl"], 1.0, t_sim, dt, sh)  # graph build
+    a.upload(q0)
+    qa, qb = a, b
+    t_sim, dt, inb, _ = ctx.advance(qa.ptr, qb.ptr, args.warmup, wl["cfl"], 1.0, 0.0, dt0, sh)
+    if inb:
+        qa, qb = qb, qa
+
+    # timed region: exactly K steps
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device() if world == 1 else local) as clk:
+        ev0.record(stream)
+        t_sim2, dt2, inb2, nrej = ctx.advance(qa.ptr, qb.ptr, args.steps, wl["cfl"], 1.0, t_sim,
+                                              dt, sh)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    clocks = clk.summary()
+    value = world * n_cells * args.steps / (ms * 1e-3)
+    solves = world * ((p.mx + 1) * p.my + p.mx * (p.my + 1)) * args.steps / (ms * 1e-3)
+
+    # kernel roofline: the fused step alone, CUDA events on its stream
+    if inb2:
+        qa, qb = qb, qa
+    ctx.bc_fill(qa.ptr, sh)
+    reps = 50
+    for _ in range(3):
+        ctx.sweep(qa.ptr, qb.ptr, dt2, sh)
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        ctx.sweep(qa.ptr, qb.ptr, dt2, sh)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    alg_bytes = 2 * n_cells * p.meqn * lay.elem_bytes
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.workload),
+                "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
+                "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        host0 = torch.from_numpy(q0).pin_memory()
+        hostq = torch.empty_like(host0).pin_memory()
+        nsteps_e2e = 100
+        ctx.advance_host(host0.data_ptr(), hostq.data_ptr(), a.ptr, b.ptr, nsteps_e2e,
+                         wl["cfl"], 1.0, 0.0, dt0, sh)
+        reps_e2e = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps_e2e):
+            ctx.advance_host(host0.data_ptr(), hostq.data_ptr(), a.ptr, b.ptr, nsteps_e2e,
+                             wl["cfl"], 1.0, 0.0, dt0, sh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        nbytes = host0.numel() * host0.element_size()
+        e2e = {"value": world * n_cells * nsteps_e2e * reps_e2e / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes / nsteps_e2e, "d2h_bytes_per_step": nbytes / nsteps_e2e,
+               "steps_per_call": nsteps_e2e,
+               "note": "mc_advance_host: dense host state in, 100 steps, dense host state out"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+            "config": {"workload": wl["desc"], "mx": p.mx, "my": p.my,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (%.0f MB per state)" % (lay.bytes / 1e6),
+                       "rejected_steps": nrej},
+            "riemann_solves_per_s": solves,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * (args.steps + nrej), "clocks": clocks,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * manyclaw.h -- C ABI of the GB300 wave-propagation library.
+ *
+ * What it computes.  arXiv 1308.1464 (ManyClaw) decomposes an explicit
+ * finite-volume step for hyperbolic PDEs into kernels by arithmetic intensity
+ * (§1.2, Table 1): a Riemann kernel that maps the states of adjacent cell
+ * centres to values at their common edge, and a limiter kernel that maps edge
+ * values back to cell centres; the Riemann kernel is pointwise and unaware of
+ * the parallelism around it (§1.1, §2).  This library runs both kernels, for
+ * every x- and y-edge of a 2D uniform grid, fused in one pass per tile on an
+ * sm_103a GPU: the 2D unsplit wave-propagation step with limited second-order
+ * corrections and transverse (corner-transport) splits.  Solvers: constant-
+ * coefficient acoustics (§3, Table 2), shallow water and Euler with Roe's
+ * linearisation and the Harten-Hyman entropy fix.
+ *
+ * Conventions, for every entry point:
+ *  - Plain pointers and sizes only.  A "device" pointer is CUDA global memory
+ *    of the current device; a "host" pointer is ordinary (pageable or pinned)
+ *    host memory.  Streams are cudaStream_t passed as void* (NULL = legacy
+ *    default stream).
+ *  - The caller owns every state, aux and I/O buffer.  The library owns only
+ *    what its *_create calls allocate (contexts, small device scratch, CUDA
+ *    graphs, tensor maps) and frees it in the matching *_destroy.
+ *  - Every call returns an mc_status (0 = MC_OK).  Nothing throws.  Calls that
+ *    take a stream enqueue work asynchronously unless they say they
+ *    synchronise; errors raised by device code (non-physical states, bounded
+ *    waits that gave up) are latched in a device status word and reported by
+ *    the next call that synchronises.  mc_last_error() gives a message for the
+ *    last failing call on the calling host thread.
+ *  - The library holds no global mutable state except the per-thread error
+ *    message; contexts are not thread-safe (one host thread per context).
+ *
+ * State layout (device).  q is planar: field m, cell (i, j), with
+ * i in [-mbc, mx + mbc) and j in [-mbc, my + mbc) (ghost cells included), is
+ * element   m * ld_field + (j + mbc) * ld_x + x_offset + i   of an array of
+ * float (MC_F32) or double (MC_F64).  mc_layout_of() gives x_offset, ld_x,
+ * ld_field: the interior of every row starts 16-byte aligned and rows are
+ * padded to 128 bytes, so tiles can be moved by the tensor-memory accelerator.
+ * The base pointer must be 16-byte aligned.
+ */
+#ifndef MANYCLAW_H
+#define MANYCLAW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MC_OK = 0,
+    MC_EINVAL = -1,     /* invalid argument (size, pointer, alignment, enum) */
+    MC_ECUDA = -2,      /* a CUDA runtime/driver call failed */
+    MC_ENOMEM = -3,     /* allocation failed */
+    MC_ECFL = -4,       /* a step was rejected (Courant number above the limit) */
+    MC_ENONPHYS = -5,   /* non-physical state met (depth/density/pressure <= 0, NaN) */
+    MC_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+    MC_ENOTSUP = -7     /* combination not supported */
+} mc_status;
+
+enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3 };
+/* limiter numbering as in Clawpack: 0 none (Lax-Wendroff), 1 minmod, 4 MC */
+enum { MC_LIM_NONE = 0, MC_LIM_MINMOD = 1, MC_LIM_MC = 4 };
+enum { MC_BC_PERIODIC = 0, MC_BC_EXTRAP = 1, MC_BC_WALL = 2 };
+enum { MC_F32 = 0, MC_F64 = 1 };
+
+/* A 2D problem.  meqn follows from the solver (acoustics (p, u, v): 3;
+ * shallow water (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4). */
+typedef struct mc_problem {
+    int32_t solver;      /* MC_ACOUSTICS | MC_SWE_ROE | MC_EULER_ROE */
+    int32_t dtype;       /* MC_F32 | MC_F64: storage and arithmetic precision */
+    int32_t mx, my;      /* interior cells, each >= 1 */
+    int32_t mbc;         /* ghost layers; must be 2 */
+    int32_t limiter;     /* MC_LIM_* */
+    int32_t order;       /* 1: first order, 2: limited second-order corrections */
+    int32_t transverse;  /* 0: none, 1: transverse split of the fluctuations */
+    int32_t efix;        /* 1: Harten-Hyman entropy fix (shallow water, Euler) */
+    int32_t bc[4];       /* boundary kinds at xlo, xhi, ylo, yhi (MC_BC_*) */
+    double dx, dy;       /* cell sizes, > 0 */
+    double param[4];     /* acoustics: rho, K | shallow water: g | Euler: gamma */
+} mc_problem;
+
+typedef struct mc_layout {
+    int64_t x_offset;    /* element offset of cell i = 0 within a row */
+    int64_t ld_x;        /* row pitch, elements */
+    int64_t ld_field;    /* field-plane pitch, elements */
+    int64_t elem_bytes;  /* 4 or 8 */
+    int64_t meqn;        /* fields */
+    int64_t bytes;       /* bytes of one state array */
+} mc_layout;
+
+typedef struct mc_ctx mc_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char* mc_status_string(int status);
+
+/* Copies the message of the last failing call on this host thread into buf
+ * (NUL-terminated, truncated to n bytes).  Returns the status of that call. */
+int mc_last_error(char* buf, size_t n);
+
+/* Validates p and fills *out with the state layout.  Host only; no GPU. */
+mc_status mc_layout_of(const mc_problem* p, mc_layout* out);
+
+/* Creates a context for problem p on the current device: validates p,
+ * allocates a few hundred bytes of device scratch (time-step scalars, the
+ * device status word) and picks the tile shape.  *out is owned by the
+ * caller and released with mc_destroy. */
+mc_status mc_create(const mc_problem* p, mc_ctx** out);
+mc_status mc_destroy(mc_ctx* ctx);
+
+/* Rows of cells each warp sweeps per task (the tile height); 0 restores the
+ * default.  Used by the autotuner; results do not depend on it. */
+mc_status mc_set_tile_rows(mc_ctx* ctx, int rows);
+
+/* Host <-> device copies between a dense interior array (meqn x my x mx,
+ * x fastest, the problem's dtype) and a device state in the library layout.
+ * Asynchronous on stream. */
+mc_status mc_upload(mc_ctx* ctx, const void* host_dense, void* q_dev, void* stream);
+mc_status mc_download(mc_ctx* ctx, const void* q_dev, void* host_dense, void* stream);
+
+/* Fills the ghost layers of the device state q from its interior: periodic
+ * wrap, zero-order extrapolation, or a reflecting wall (mirror with the
+ * wall-normal momentum negated), per side (LeVeque 2002, ch. 7 and §21.8).
+ * Corners take the values of filling x ghosts of the interior rows first and
+ * then y ghosts over the full width. */
+mc_status mc_bc_fill(mc_ctx* ctx, void* q, void* stream);
+
+/* One unsplit step with explicit dt: fills q_in's ghosts, then writes the
+ * updated interior of q_out (q_out's ghosts are left untouched; q_in and
+ * q_out must not overlap).  The fused kernel performs, per tile, the normal
+ * Riemann solves at every x- and y-edge (paper Table 1, Riemann row), the
+ * limited corrections and transverse splits (Table 1, limiter row) and the
+ * flux-difference update.  If smax_out is not NULL the call synchronises the
+ * stream and stores max over the interior edges of |s|/dx (x-edges) and
+ * |s|/dy (y-edges), so the Courant number of the step is dt * smax; it then
+ * also reports MC_ENONPHYS if the device flagged a non-physical state. */
+mc_status mc_step(mc_ctx* ctx, void* q_in, void* q_out, double dt, double* smax_out, void* stream);
+
+/* The fused step alone: like mc_step but q_in's ghost layers must already be
+ * filled (mc_bc_fill) and nothing is synchronised; smax is accumulated
+ * (running maximum) into the context's device scalar, which mc_step resets. */
+mc_status mc_sweep(mc_ctx* ctx, const void* q_in, void* q_out, double dt, void* stream);
+
+/* max over interior cells of max((|u|+c)/dx, (|v|+c)/dy), synchronising. */
+mc_status mc_max_cell_speed(mc_ctx* ctx, const void* q, double* smax_out, void* stream);
+
+/* Advances nsteps accepted steps with the variable time step rule of
+ * dynamic time stepping (paper §1.2, Table 1, "dynamic time stepping"): the
+ * Courant number of an attempt is dt * smax over its edges; an attempt above
+ * cfl_max is rejected and retaken with dt = cfl_desired / smax; an accepted
+ * one advances *t_inout and proposes dt = cfl_desired / smax.  The state
+ * starts in qa; the result ends in qa (*result_in_b = 0) or qb (= 1).  The
+ * whole attempt sequence runs as one CUDA graph with dt, t and the buffer
+ * index kept on the device; the call synchronises once at the end.
+ * nrejected (nullable) receives the number of rejected attempts. */
+mc_status mc_advance(mc_ctx* ctx, void* qa, void* qb, int nsteps, double cfl_desired,
+                     double cfl_max, double* t_inout, double* dt_inout, int* result_in_b,
+                     int* nrejected, void* stream);
+
+/* End-to-end form with host buffers: uploads host_q0 (dense interior) into
+ * qa, runs mc_advance, downloads the result into host_q (dense interior),
+ * synchronising. */
+mc_status mc_advance_host(mc_ctx* ctx, const void* host_q0, void* host_q, void* qa, void* qb,
+                          int nsteps, double cfl_desired, double cfl_max, double* t_inout,
+                          double* dt_inout, int* nrejected, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -29,7 +29,7 @@ _LIBDIR = os.path.join(_HERE, "_lib")
 
 ACOUSTICS, SWE, EULER = 1, 2, 3
 LIM_NONE, LIM_MINMOD, LIM_MC = 0, 1, 4
-BC_PERIODIC, BC_EXTRAP, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_EXTRAP, BC_WALL, BC_GIVEN = 0, 1, 2, 3
 SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_GIVEN = range(6)
 RS_OK, RS_VACUUM, RS_NOCONV, RS_FALLBACK = 0, 1, 2, 4
 NIN, KIN, NH = 10, 16, 64

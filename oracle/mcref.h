@@ -29,7 +29,9 @@ extern "C" {
 
 enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3 };
 enum { MCREF_LIM_NONE = 0, MCREF_LIM_MINMOD = 1, MCREF_LIM_MC = 4 };
-enum { MCREF_BC_PERIODIC = 0, MCREF_BC_EXTRAP = 1, MCREF_BC_WALL = 2 };
+/* MCREF_BC_GIVEN leaves that side's ghost layers as the caller set them: the
+ * step of a window cut out of a larger grid then uses the true neighbours. */
+enum { MCREF_BC_PERIODIC = 0, MCREF_BC_EXTRAP = 1, MCREF_BC_WALL = 2, MCREF_BC_GIVEN = 3 };
 
 /* Flags raised by the oracle (bitmask). */
 enum { MCREF_F_NONPHYS = 1 };

@@ -63,11 +63,13 @@ void mcref_bc_fill(const mcref_problem* p, double* q)
             switch (p->bc[0]) {
             case MCREF_BC_PERIODIC: bc_copy(p, q, -k, j, mx - k, j, -1); break;
             case MCREF_BC_EXTRAP:   bc_copy(p, q, -k, j, 0, j, -1); break;
+            case MCREF_BC_GIVEN:    break;
             default:                bc_copy(p, q, -k, j, k - 1, j, 1); break;
             }
             switch (p->bc[1]) {
             case MCREF_BC_PERIODIC: bc_copy(p, q, mx - 1 + k, j, k - 1, j, -1); break;
             case MCREF_BC_EXTRAP:   bc_copy(p, q, mx - 1 + k, j, mx - 1, j, -1); break;
+            case MCREF_BC_GIVEN:    break;
             default:                bc_copy(p, q, mx - 1 + k, j, mx - k, j, 1); break;
             }
         }
@@ -78,11 +80,13 @@ void mcref_bc_fill(const mcref_problem* p, double* q)
             switch (p->bc[2]) {
             case MCREF_BC_PERIODIC: bc_copy(p, q, i, -k, i, my - k, -1); break;
             case MCREF_BC_EXTRAP:   bc_copy(p, q, i, -k, i, 0, -1); break;
+            case MCREF_BC_GIVEN:    break;
             default:                bc_copy(p, q, i, -k, i, k - 1, 2); break;
             }
             switch (p->bc[3]) {
             case MCREF_BC_PERIODIC: bc_copy(p, q, i, my - 1 + k, i, k - 1, -1); break;
             case MCREF_BC_EXTRAP:   bc_copy(p, q, i, my - 1 + k, i, my - 1, -1); break;
+            case MCREF_BC_GIVEN:    break;
             default:                bc_copy(p, q, i, my - 1 + k, i, my - k, 2); break;
             }
         }

@@ -1,0 +1,204 @@
+"""GB300-native wave-propagation library: thin Python binding of include/manyclaw.h.
+
+The compute path lives in the CUDA library ``_lib/libmanyclaw.so`` (built by
+``__graft_entry__.build()`` or ``python -m paper_1308_1464_gb300._build``);
+this module only marshals arguments to its C ABI.  It never falls back to a
+CPU implementation: if the library is missing, ``lib()`` raises.
+
+Device buffers are passed as integer addresses (e.g. ``tensor.data_ptr()``)
+and streams as integer handles (``torch.cuda.current_stream().cuda_stream``);
+PyTorch is only used by callers for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmanyclaw.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "manyclaw.h")
+
+MC_OK, MC_EINVAL, MC_ECUDA, MC_ENOMEM, MC_ECFL, MC_ENONPHYS, MC_ETIMEOUT, MC_ENOTSUP = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+ACOUSTICS, SWE_ROE, EULER_ROE = 1, 2, 3
+LIM_NONE, LIM_MINMOD, LIM_MC = 0, 1, 4
+BC_PERIODIC, BC_EXTRAP, BC_WALL = 0, 1, 2
+F32, F64 = 0, 1
+
+
+class McError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int32), ("dtype", ctypes.c_int32), ("mx", ctypes.c_int32),
+                ("my", ctypes.c_int32), ("mbc", ctypes.c_int32), ("limiter", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("transverse", ctypes.c_int32), ("efix", ctypes.c_int32),
+                ("bc", ctypes.c_int32 * 4), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("param", ctypes.c_double * 4)]
+
+    @classmethod
+    def make(cls, solver, mx, my, dx, dy, dtype=F32, limiter=LIM_MC, order=2, transverse=1,
+             efix=1, bc=(BC_PERIODIC,) * 4, param=(1.0, 4.0, 0.0, 0.0)):
+        p = cls()
+        p.solver, p.dtype, p.mx, p.my, p.mbc = solver, dtype, mx, my, 2
+        p.limiter, p.order, p.transverse, p.efix = limiter, order, transverse, efix
+        for k in range(4):
+            p.bc[k] = int(bc[k])
+            p.param[k] = float(param[k]) if k < len(param) else 0.0
+        p.dx, p.dy = float(dx), float(dy)
+        return p
+
+    @property
+    def meqn(self) -> int:
+        return 4 if self.solver == EULER_ROE else 3
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("x_offset", ctypes.c_int64), ("ld_x", ctypes.c_int64),
+                ("ld_field", ctypes.c_int64), ("elem_bytes", ctypes.c_int64),
+                ("meqn", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(Problem)
+        L.mc_status_string.restype = ctypes.c_char_p
+        L.mc_status_string.argtypes = [ctypes.c_int]
+        L.mc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        L.mc_layout_of.argtypes = [P, ctypes.POINTER(Layout)]
+        L.mc_create.argtypes = [P, ctypes.POINTER(_VP)]
+        L.mc_destroy.argtypes = [_VP]
+        L.mc_set_tile_rows.argtypes = [_VP, ctypes.c_int]
+        L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
+        L.mc_download.argtypes = [_VP, _VP, _VP, _VP]
+        L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
+        L.mc_step.argtypes = [_VP, _VP, _VP, ctypes.c_double, _DP, _VP]
+        L.mc_sweep.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP]
+        L.mc_max_cell_speed.argtypes = [_VP, _VP, _DP, _VP]
+        L.mc_advance.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 _DP, _DP, _IP, _IP, _VP]
+        L.mc_advance_host.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, _DP, _DP, _IP, _VP]
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().mc_status_string(int(status)).decode()
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib().mc_last_error(buf, 512)
+    return buf.value.decode()
+
+
+def check(status: int) -> None:
+    if status != MC_OK:
+        raise McError(status, last_error())
+
+
+def layout_of(p: Problem) -> Layout:
+    lay = Layout()
+    check(lib().mc_layout_of(ctypes.byref(p), ctypes.byref(lay)))
+    return lay
+
+
+class Context:
+    """A problem bound to the current CUDA device (mc_create / mc_destroy)."""
+
+    def __init__(self, problem: Problem):
+        self.problem = problem
+        self.layout = layout_of(problem)
+        h = _VP()
+        check(lib().mc_create(ctypes.byref(problem), ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tile_rows(self, rows: int) -> None:
+        check(lib().mc_set_tile_rows(self._h, int(rows)))
+
+    def upload(self, host_dense_ptr: int, q_dev: int, stream: int = 0) -> None:
+        check(lib().mc_upload(self._h, _VP(host_dense_ptr), _VP(q_dev), _VP(stream)))
+
+    def download(self, q_dev: int, host_dense_ptr: int, stream: int = 0) -> None:
+        check(lib().mc_download(self._h, _VP(q_dev), _VP(host_dense_ptr), _VP(stream)))
+
+    def bc_fill(self, q_dev: int, stream: int = 0) -> None:
+        check(lib().mc_bc_fill(self._h, _VP(q_dev), _VP(stream)))
+
+    def step(self, q_in: int, q_out: int, dt: float, want_smax: bool = True, stream: int = 0):
+        smax = ctypes.c_double(0.0)
+        check(lib().mc_step(self._h, _VP(q_in), _VP(q_out), float(dt),
+                            ctypes.byref(smax) if want_smax else None, _VP(stream)))
+        return smax.value if want_smax else None
+
+    def sweep(self, q_in: int, q_out: int, dt: float, stream: int = 0) -> None:
+        check(lib().mc_sweep(self._h, _VP(q_in), _VP(q_out), float(dt), _VP(stream)))
+
+    def max_cell_speed(self, q: int, stream: int = 0) -> float:
+        s = ctypes.c_double(0.0)
+        check(lib().mc_max_cell_speed(self._h, _VP(q), ctypes.byref(s), _VP(stream)))
+        return s.value
+
+    def advance(self, qa: int, qb: int, nsteps: int, cfl_desired: float, cfl_max: float,
+                t: float, dt: float, stream: int = 0):
+        """-> (t, dt, result_in_b, nrejected)"""
+        tt, dd = ctypes.c_double(t), ctypes.c_double(dt)
+        inb, nrej = ctypes.c_int(0), ctypes.c_int(0)
+        check(lib().mc_advance(self._h, _VP(qa), _VP(qb), int(nsteps), float(cfl_desired),
+                               float(cfl_max), ctypes.byref(tt), ctypes.byref(dd),
+                               ctypes.byref(inb), ctypes.byref(nrej), _VP(stream)))
+        return tt.value, dd.value, bool(inb.value), nrej.value
+
+    def advance_host(self, host_q0: int, host_q: int, qa: int, qb: int, nsteps: int,
+                     cfl_desired: float, cfl_max: float, t: float, dt: float, stream: int = 0):
+        """-> (t, dt, nrejected)"""
+        tt, dd, nrej = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
+        check(lib().mc_advance_host(self._h, _VP(host_q0), _VP(host_q), _VP(qa), _VP(qb),
+                                    int(nsteps), float(cfl_desired), float(cfl_max),
+                                    ctypes.byref(tt), ctypes.byref(dd), ctypes.byref(nrej),
+                                    _VP(stream)))
+        return tt.value, dd.value, nrej.value
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions include/manyclaw.h declares."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(mc_[a-z0-9_]+)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))

@@ -1,0 +1,111 @@
+// mc_device.cuh -- device helpers shared by the library's kernels: status
+// bits, ordered-bit maxima, mbarrier and tensor-memory-accelerator (TMA)
+// copies in inline PTX for sm_103a, and bounded waits.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mc {
+
+// bits of the device status word
+enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2, ST_CFL = 4 };
+
+// A bounded wait gives up after this many SM clock cycles (about 1 s at
+// the GB300 boost clock); nothing in a healthy run comes near it.
+constexpr long long WAIT_CYCLES = 2000000000LL;
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v)
+{
+    // non-negative doubles order like their bit patterns
+    if (v > 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; returns false if
+// the wait ran past WAIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// 3D tiled TMA load of one box into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_down1(T v)
+{
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v)
+{
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+
+}  // namespace mc

@@ -1,0 +1,56 @@
+// mc_internal.h -- host-side declarations shared by the library's
+// translation units (not part of the public C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/manyclaw.h"
+
+namespace mc {
+
+struct DevState;
+
+// One launch of the fused step (and its companions) for one problem.
+struct SweepLaunch {
+    mc_problem prob;
+    mc_layout lay;
+    const CUtensorMap* map_a;
+    const CUtensorMap* map_b;
+    void* qa;
+    void* qb;
+    const int* cur_dev;        // device buffer index, or null (qa -> qb)
+    const double* dt_dev;      // device dt, or null (use dt)
+    double dt;
+    unsigned long long* smax_bits;
+    int* status;
+    int tile_rows;
+    int max_blocks;            // 0: one warp per task
+    cudaStream_t stream;
+};
+
+// per-solver launchers (mc_sweep_<solver>.cu), dispatching on dtype
+cudaError_t sweep_launch_acoustics(const SweepLaunch& L);
+cudaError_t sweep_launch_swe(const SweepLaunch& L);
+cudaError_t sweep_launch_euler(const SweepLaunch& L);
+cudaError_t sweep_prepare_acoustics(int dtype);
+cudaError_t sweep_prepare_swe(int dtype);
+cudaError_t sweep_prepare_euler(int dtype);
+cudaError_t maxspeed_launch_acoustics(const mc_problem& p, const mc_layout& lay, const void* q,
+                                      unsigned long long* out, cudaStream_t s);
+cudaError_t maxspeed_launch_swe(const mc_problem& p, const mc_layout& lay, const void* q,
+                                unsigned long long* out, cudaStream_t s);
+cudaError_t maxspeed_launch_euler(const mc_problem& p, const mc_layout& lay, const void* q,
+                                  unsigned long long* out, cudaStream_t s);
+
+// ghost fill (mc_capi.cu)
+cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
+                      const int* cur_dev, cudaStream_t s);
+
+int ntasks_for(const mc_problem& p, int tile_rows, int* nbands);
+
+// error reporting
+mc_status set_error(mc_status st, const char* fmt, ...);
+mc_status cuda_error(cudaError_t e, const char* what);
+
+}  // namespace mc

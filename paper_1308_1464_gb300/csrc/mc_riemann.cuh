@@ -1,0 +1,332 @@
+// mc_riemann.cuh -- pointwise Riemann solvers of the GPU path.
+//
+// The paper (§1.1, §2) keeps the Riemann solver pointwise and unaware of the
+// parallelism around it; Table 1 gives its data flow (cell-centre states in,
+// edge values out).  Each solver here maps the two states adjacent to one
+// edge to waves W^p, speeds s^p and the fluctuations A-dQ, A+dQ, and keeps the
+// linearised (Roe) state of the edge so the transverse split can reuse it.
+// Mathematics: LeVeque (2002) §3.9 (acoustics), §15.3.3-15.3.5 (Roe solvers
+// for shallow water and Euler, Harten-Hyman entropy fix), §21.2 (transverse
+// split).  Template parameter DIR is the edge normal: 0 = x, 1 = y; the
+// normal momentum is component 1 + DIR and the tangential one 2 - DIR.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mc {
+
+template <typename T>
+__device__ __forceinline__ T tmin0(T a) { return a < T(0) ? a : T(0); }
+template <typename T>
+__device__ __forceinline__ T tmax0(T a) { return a > T(0) ? a : T(0); }
+
+// ---------------------------------------------------------------- acoustics
+template <typename T>
+struct AcousticsRP {
+    using real = T;
+    static constexpr int NEQ = 3, NW = 2;
+    static constexpr bool POSITIVE = false;   // no positivity constraint on (p, u, v)
+    T c, Z, inv2Z;
+    bool efix;  // unused: linear system
+    struct Lin {};
+
+    __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
+
+    __host__ void setup(const double* param, int /*efix*/)
+    {
+        double rho = param[0], K = param[1];
+        double cc = sqrt(K / rho);
+        c = T(cc);
+        Z = T(rho * cc);
+        inv2Z = T(0.5 / (rho * cc));
+        efix = false;
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin&, bool&) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        T dp = qr[0] - ql[0], du = qr[un] - ql[un];
+        T a1 = (Z * du - dp) * inv2Z;
+        T a2 = (dp + Z * du) * inv2Z;
+        W[0][0] = -Z * a1; W[0][un] = a1; W[0][ut] = T(0);
+        W[1][0] = Z * a2;  W[1][un] = a2; W[1][ut] = T(0);
+        s[0] = -c;
+        s[1] = c;
+#pragma unroll
+        for (int m = 0; m < NEQ; m++) {
+            amdq[m] = -c * W[0][m];
+            apdq[m] = c * W[1][m];
+        }
+    }
+
+    // split a fluctuation of a DIR-normal edge in direction 1 - DIR
+    template <int DIR>
+    __device__ __forceinline__ void transverse(const Lin&, const T* a, T* bm, T* bp) const
+    {
+        constexpr int vn = 2 - DIR, vt = 1 + DIR;
+        T b1 = (Z * a[vn] - a[0]) * inv2Z;
+        T b2 = (a[0] + Z * a[vn]) * inv2Z;
+        bm[0] = c * Z * b1;  bm[vn] = -c * b1; bm[vt] = T(0);
+        bp[0] = c * Z * b2;  bp[vn] = c * b2;  bp[vt] = T(0);
+    }
+};
+
+// ---------------------------------------------------------------- shallow water
+template <typename T>
+struct SweRP {
+    using real = T;
+    static constexpr int NEQ = 3, NW = 3;
+    static constexpr bool POSITIVE = true;    // depth h > 0
+    T g;
+    bool efix;
+    struct Lin { T u, v, c, r2c; };
+
+    __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const
+    {
+        const T c = sqrt(g * q[0]);
+        sx = fabs(q[1] / q[0]) + c;
+        sy = fabs(q[2] / q[0]) + c;
+    }
+
+    __host__ void setup(const double* param, int ef)
+    {
+        g = T(param[0]);
+        efix = ef != 0;
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin& L, bool& bad) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        const T hl = ql[0], hr = qr[0];
+        if (!(hl > T(0) && hr > T(0))) {
+            bad = true;
+#pragma unroll
+            for (int p = 0; p < NW; p++) {
+                s[p] = T(0);
+#pragma unroll
+                for (int m = 0; m < NEQ; m++) W[p][m] = T(0);
+            }
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) amdq[m] = apdq[m] = T(0);
+            L.u = L.v = T(0); L.c = T(1); L.r2c = T(0.5);
+            return;
+        }
+        const T sl = sqrt(hl), sr = sqrt(hr);
+        const T w = T(1) / (sl + sr);
+        const T u = (ql[un] / sl + qr[un] / sr) * w;
+        const T v = (ql[ut] / sl + qr[ut] / sr) * w;
+        const T c = sqrt(g * T(0.5) * (hl + hr));
+        const T r2c = T(0.5) / c;
+        const T d0 = hr - hl, dn = qr[un] - ql[un], dt = qr[ut] - ql[ut];
+        const T a1 = ((u + c) * d0 - dn) * r2c;
+        const T a2 = dt - v * d0;
+        const T a3 = (dn - (u - c) * d0) * r2c;
+        W[0][0] = a1; W[0][un] = a1 * (u - c); W[0][ut] = a1 * v;
+        W[1][0] = T(0); W[1][un] = T(0); W[1][ut] = a2;
+        W[2][0] = a3; W[2][un] = a3 * (u + c); W[2][ut] = a3 * v;
+        s[0] = u - c;
+        s[1] = u;
+        s[2] = u + c;
+        L.u = u; L.v = v; L.c = c; L.r2c = r2c;
+
+        T k0 = tmin0(s[0]), k2 = tmin0(s[2]);
+        if (efix) {
+            // 1-wave: speeds of the left state and of ql + W1
+            T lam_l = ql[un] / hl - sqrt(g * hl);
+            T hm = hl + W[0][0];
+            if (hm > T(0)) {
+                T lam_r = (ql[un] + W[0][un]) / hm - sqrt(g * hm);
+                if (lam_l < T(0) && lam_r > T(0)) k0 = (lam_r - s[0]) / (lam_r - lam_l) * lam_l;
+            } else {
+                bad = true;
+            }
+            // 3-wave: speeds of qr - W3 and of the right state
+            T hm3 = hr - W[2][0];
+            T lr = qr[un] / hr + sqrt(g * hr);
+            if (hm3 > T(0)) {
+                T ll = (qr[un] - W[2][un]) / hm3 + sqrt(g * hm3);
+                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) / (lr - ll) * ll;
+            } else {
+                bad = true;
+            }
+        }
+        const T k1 = tmin0(s[1]);
+#pragma unroll
+        for (int m = 0; m < NEQ; m++) {
+            amdq[m] = k0 * W[0][m] + k1 * W[1][m] + k2 * W[2][m];
+            apdq[m] = s[0] * W[0][m] + s[1] * W[1][m] + s[2] * W[2][m] - amdq[m];
+        }
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void transverse(const Lin& L, const T* a, T* bm, T* bp) const
+    {
+        // eigenvectors of the direction 1 - DIR at the edge's Roe state: the
+        // edge-tangential velocity L.v is the normal one there
+        constexpr int vn = 2 - DIR, vt = 1 + DIR;
+        const T u = L.v, v = L.u, c = L.c;
+        const T b1 = ((u + c) * a[0] - a[vn]) * L.r2c;
+        const T b2 = a[vt] - v * a[0];
+        const T b3 = (a[vn] - (u - c) * a[0]) * L.r2c;
+        const T l1 = u - c, l2 = u, l3 = u + c;
+        const T m1 = tmin0(l1) * b1, m2 = tmin0(l2) * b2, m3 = tmin0(l3) * b3;
+        const T p1 = tmax0(l1) * b1, p2 = tmax0(l2) * b2, p3 = tmax0(l3) * b3;
+        bm[0] = m1 + m3;
+        bm[vn] = m1 * (u - c) + m3 * (u + c);
+        bm[vt] = (m1 + m3) * v + m2;
+        bp[0] = p1 + p3;
+        bp[vn] = p1 * (u - c) + p3 * (u + c);
+        bp[vt] = (p1 + p3) * v + p2;
+    }
+};
+
+// ---------------------------------------------------------------- Euler
+template <typename T>
+struct EulerRP {
+    using real = T;
+    static constexpr int NEQ = 4, NW = 3;
+    static constexpr bool POSITIVE = true;    // density rho > 0
+    T gamma, gm1;
+    bool efix;
+    struct Lin { T u, v, H, c, gc2; };
+
+    __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const
+    {
+        const T r1 = T(1) / q[0];
+        const T u = q[1] * r1, v = q[2] * r1;
+        const T p = gm1 * (q[3] - T(0.5) * q[0] * (u * u + v * v));
+        const T c = sqrt(gamma * p * r1);
+        sx = fabs(u) + c;
+        sy = fabs(v) + c;
+    }
+
+    __host__ void setup(const double* param, int ef)
+    {
+        gamma = T(param[0]);
+        gm1 = T(param[0] - 1.0);
+        efix = ef != 0;
+    }
+
+    // speed u_n -+ c of a conserved state; false if not physical
+    template <int DIR>
+    __device__ __forceinline__ bool cspeed(const T* q, T sgn, T& lam) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        if (!(q[0] > T(0))) return false;
+        T r1 = T(1) / q[0];
+        T u = q[un] * r1, v = q[ut] * r1;
+        T p = gm1 * (q[3] - T(0.5) * q[0] * (u * u + v * v));
+        if (!(p > T(0))) return false;
+        lam = u + sgn * sqrt(gamma * p * r1);
+        return true;
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin& L, bool& bad) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        const T rl = ql[0], rr = qr[0];
+        bool ok = rl > T(0) && rr > T(0);
+        T u = T(0), v = T(0), H = T(0), c2 = T(0);
+        if (ok) {
+            const T il = T(1) / rl, ir = T(1) / rr;
+            const T ul = ql[un] * il, vl = ql[ut] * il, ur = qr[un] * ir, vr = qr[ut] * ir;
+            const T pl = gm1 * (ql[3] - T(0.5) * rl * (ul * ul + vl * vl));
+            const T pr = gm1 * (qr[3] - T(0.5) * rr * (ur * ur + vr * vr));
+            const T Hl = (ql[3] + pl) * il, Hr = (qr[3] + pr) * ir;
+            const T sl = sqrt(rl), sr = sqrt(rr);
+            const T w = T(1) / (sl + sr);
+            u = (sl * ul + sr * ur) * w;
+            v = (sl * vl + sr * vr) * w;
+            H = (sl * Hl + sr * Hr) * w;
+            c2 = gm1 * (H - T(0.5) * (u * u + v * v));
+            ok = c2 > T(0);
+        }
+        if (!ok) {
+            bad = true;
+#pragma unroll
+            for (int p = 0; p < NW; p++) {
+                s[p] = T(0);
+#pragma unroll
+                for (int m = 0; m < NEQ; m++) W[p][m] = T(0);
+            }
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) amdq[m] = apdq[m] = T(0);
+            L.u = L.v = L.H = T(0); L.c = T(1); L.gc2 = T(0);
+            return;
+        }
+        const T c = sqrt(c2);
+        const T gc2 = gm1 / c2;
+        const T d0 = qr[0] - ql[0], dn = qr[un] - ql[un], dt = qr[ut] - ql[ut], dE = qr[3] - ql[3];
+        const T a_sh = dt - v * d0;
+        const T a_en = gc2 * ((H - u * u - v * v) * d0 + u * dn + v * dt - dE);
+        const T x = (dn - u * d0) / c;
+        const T a4 = T(0.5) * (d0 - a_en + x);
+        const T a1 = T(0.5) * (d0 - a_en - x);
+        W[0][0] = a1; W[0][un] = a1 * (u - c); W[0][ut] = a1 * v; W[0][3] = a1 * (H - u * c);
+        W[1][0] = a_en; W[1][un] = a_en * u; W[1][ut] = a_en * v + a_sh;
+        W[1][3] = a_en * T(0.5) * (u * u + v * v) + a_sh * v;
+        W[2][0] = a4; W[2][un] = a4 * (u + c); W[2][ut] = a4 * v; W[2][3] = a4 * (H + u * c);
+        s[0] = u - c;
+        s[1] = u;
+        s[2] = u + c;
+        L.u = u; L.v = v; L.H = H; L.c = c; L.gc2 = gc2;
+
+        T k0 = tmin0(s[0]), k2 = tmin0(s[2]);
+        if (efix) {
+            T qm[NEQ];
+            T ll, lr;
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) qm[m] = ql[m] + W[0][m];
+            if (cspeed<DIR>(ql, T(-1), ll) && cspeed<DIR>(qm, T(-1), lr)) {
+                if (ll < T(0) && lr > T(0)) k0 = (lr - s[0]) / (lr - ll) * ll;
+            } else {
+                bad = true;
+            }
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) qm[m] = qr[m] - W[2][m];
+            if (cspeed<DIR>(qm, T(1), ll) && cspeed<DIR>(qr, T(1), lr)) {
+                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) / (lr - ll) * ll;
+            } else {
+                bad = true;
+            }
+        }
+        const T k1 = tmin0(s[1]);
+#pragma unroll
+        for (int m = 0; m < NEQ; m++) {
+            amdq[m] = k0 * W[0][m] + k1 * W[1][m] + k2 * W[2][m];
+            apdq[m] = s[0] * W[0][m] + s[1] * W[1][m] + s[2] * W[2][m] - amdq[m];
+        }
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void transverse(const Lin& L, const T* a, T* bm, T* bp) const
+    {
+        constexpr int vn = 2 - DIR, vt = 1 + DIR;
+        const T u = L.v, v = L.u, c = L.c, H = L.H;   // u: normal to the split direction
+        const T b_sh = a[vt] - v * a[0];
+        const T b_en = L.gc2 * ((H - u * u - v * v) * a[0] + u * a[vn] + v * a[vt] - a[3]);
+        const T x = (a[vn] - u * a[0]) / c;
+        const T b4 = T(0.5) * (a[0] - b_en + x);
+        const T b1 = T(0.5) * (a[0] - b_en - x);
+        const T l1 = u - c, l2 = u, l4 = u + c;
+        const T ke = T(0.5) * (u * u + v * v);
+        const T m1 = tmin0(l1) * b1, me = tmin0(l2) * b_en, ms = tmin0(l2) * b_sh, m4 = tmin0(l4) * b4;
+        const T p1 = tmax0(l1) * b1, pe = tmax0(l2) * b_en, ps = tmax0(l2) * b_sh, p4 = tmax0(l4) * b4;
+        bm[0] = m1 + me + m4;
+        bm[vn] = m1 * (u - c) + me * u + m4 * (u + c);
+        bm[vt] = (m1 + me + m4) * v + ms;
+        bm[3] = m1 * (H - u * c) + me * ke + ms * v + m4 * (H + u * c);
+        bp[0] = p1 + pe + p4;
+        bp[vn] = p1 * (u - c) + pe * u + p4 * (u + c);
+        bp[vt] = (p1 + pe + p4) * v + ps;
+        bp[3] = p1 * (H - u * c) + pe * ke + ps * v + p4 * (H + u * c);
+    }
+};
+
+}  // namespace mc

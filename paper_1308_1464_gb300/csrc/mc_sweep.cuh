@@ -1,0 +1,431 @@
+// mc_sweep.cuh -- the fused wave-propagation step and its companions
+// (ghost fill, time-step rule, cell-speed reduction), templated on the
+// Riemann solver.
+//
+// Paper mapping.  Table 1 (§1.2) splits an explicit step into a Riemann
+// kernel (cell centres -> edge values) and a limiter kernel (edge values ->
+// cell centres); §2 keeps edge results in work arrays "that in practice
+// will cause bandwidth bottlenecks" and finds that computing both directions
+// per cell ("cell-wise") with tiling is fastest on CPUs.  Here both kernels
+// are fused: edge results live only in registers and are exchanged between
+// neighbouring columns with warp shuffles, so HBM sees one read and one
+// write of the state per step.
+//
+// The arithmetic is the 2D unsplit wave-propagation step (LeVeque 2002,
+// eq. 21.8 with §6.13 limited corrections and §21.2 transverse splits):
+//   Q' = Q - nu_x (A+dQ_{i-1/2} + A-dQ_{i+1/2}) - nu_y (B+dQ_{j-1/2} + B-dQ_{j+1/2})
+//          - nu_x (F_{i+1/2} - F_{i-1/2}) - nu_y (G_{j+1/2} - G_{j-1/2}),
+// F = 1/2 sum_p |s^p| (1 - nu_x |s^p|) phi(theta^p) W^p
+//     - nu_y/2 (transverse splits of the y-fluctuations entering the two
+//       cells of the edge), G likewise with x and y exchanged.
+//
+// Work decomposition.  A warp owns a band of 32 columns c = i0-1 .. i0+30
+// (lane l <-> column i0-1+l) and marches up the rows j0 .. j0+TY-1 of a
+// task.  At iteration k lane l:
+//   1. takes row k+2 of its column (and of column c-1) from a shared-memory
+//      ring filled by TMA (one 3D box = all fields of RS rows per stage);
+//   2. solves the y-edge between rows k+1 and k+2 and splits both of its
+//      fluctuations in x;
+//   3. solves the x-edge c-1/2 of row k+1 and splits both fluctuations in y;
+//   4. completes F at x-edge (c-1/2, k+1): the limiter reads the upwind
+//      neighbour edge's waves from lane l-1 or l+1, the transverse part the
+//      A+ pieces of column c-1 from lane l-1;
+//   5. completes G at y-edge (c, k+1/2): limiter from the three y-edges it
+//      holds in registers, transverse pieces of x-edge c+1/2 from lane l+1;
+//   6. writes cell (c, k).
+// Lanes 1..29 see every neighbour they need; lanes 0, 30, 31 only feed them.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mc_device.cuh"
+#include "mc_riemann.cuh"
+#include "mc_tile.h"
+
+namespace mc {
+
+template <class RP>
+struct SweepArgs {
+    using T = typename RP::real;
+    RP rp;
+    T* qa;
+    T* qb;
+    const int* cur;          // device buffer index (0: a -> b, 1: b -> a), or null: a -> b
+    const double* dt_dev;    // device time step, or null: use dt
+    double dt;
+    double dx, dy;
+    int mx, my;
+    long long ld_x, ld_field, x_offset;
+    int limiter, order, transverse;
+    int nbands, ntasks, tile_rows;
+    unsigned long long* smax_bits;
+    int* status;
+};
+
+template <typename T>
+__device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
+{
+    if (!(dr > T(0))) return T(0);
+    const T th = dl / dr;
+    if (lim == 1) return fmax(T(0), fmin(T(1), th));
+    if (lim == 4) return fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
+    return T(1);
+}
+
+template <class RP>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32)
+    ctu_sweep_kernel(const __grid_constant__ CUtensorMap map_a,
+                     const __grid_constant__ CUtensorMap map_b, const SweepArgs<RP> a)
+{
+    using T = typename RP::real;
+    constexpr int N = RP::NEQ, NW = RP::NW;
+    constexpr int ES = sizeof(T);
+    constexpr int AL = align_elems(ES);
+    constexpr int BW = box_w(ES);
+    constexpr int RS = stage_rows(ES);
+    constexpr int SB = stage_bytes(ES, N);
+    constexpr int TB = box_bytes(ES, N);
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * NSTAGE;
+    unsigned char* ring = smem + 128 + warp * NSTAGE * SB;
+
+    const int cur = a.cur ? *a.cur : 0;
+    const CUtensorMap* map = cur ? &map_b : &map_a;
+    const T* __restrict__ qin = cur ? a.qb : a.qa;
+    T* __restrict__ qout = cur ? a.qa : a.qb;
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+    const T nux = T(dt / a.dx), nuy = T(dt / a.dy);
+    const T hnux = T(0.5) * nux, hnuy = T(0.5) * nuy;
+    const bool second = a.order >= 2, trans = a.transverse != 0;
+
+    if (lane == 0) {
+        for (int s = 0; s < NSTAGE; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        prefetch_tensormap(map);
+    }
+    __syncwarp();
+
+    uint32_t phase = 0;   // per-stage completion parity
+    bool failed = false;
+    bool bad = false;     // non-physical input seen by a valid lane
+    T smx = T(0), smy = T(0);
+
+    for (int task = blockIdx.x * SWEEP_WARPS + warp; task < a.ntasks && !failed;
+         task += gridDim.x * SWEEP_WARPS) {
+        const int band = task % a.nbands;
+        const int i0 = band * BAND_W;
+        const int j0 = (task / a.nbands) * a.tile_rows;
+        const int jend = min(j0 + a.tile_rows, a.my);
+        const int c = i0 - 1 + lane;
+        const bool out_lane = lane >= 1 && lane <= BAND_W && c < a.mx;
+        const bool xe_lane = c >= 0 && c <= a.mx;      // x-edge c-1/2 is an interior edge
+        const bool ye_lane = c >= 0 && c < a.mx;       // y-edges of column c are interior
+        const long long gx = a.x_offset + i0 - 2;
+        const int box_x = int(gx - ((gx % AL) + AL) % AL);
+        const int sx = lane + 1 + int(gx - box_x);     // smem column of c; c-1 is sx-1
+        const int rbase = j0 - 2;
+        const int nfill = (jend + 1 - rbase + RS) / RS;
+
+        // start the ring
+        if (lane == 0) {
+            for (int f = 0; f < NSTAGE && f < nfill; f++) {
+                mbar_arrive_expect_tx(&bars[f], TB);
+                tma_load_3d(ring + f * SB, map, &bars[f], box_x, rbase + f * RS + 2, 0);
+            }
+        }
+
+        // fetch row r of columns c and c-1 into registers
+        auto fetch = [&](int r, T* qc, T* ql) -> bool {
+            const int rel = r - rbase, f = rel / RS, rr = rel - f * RS, st = f % NSTAGE;
+            if (rr == 0) {
+                const bool ok = mbar_wait_bounded(&bars[st], (phase >> st) & 1u);
+                if (!__all_sync(0xffffffffu, ok)) return false;
+                phase ^= 1u << st;
+            }
+            const T* row = reinterpret_cast<const T*>(ring + st * SB) + rr * BW;
+#pragma unroll
+            for (int m = 0; m < N; m++) {
+                qc[m] = row[m * RS * BW + sx];
+                ql[m] = row[m * RS * BW + sx - 1];
+            }
+            if (rr == RS - 1) {
+                __syncwarp();
+                const int fn = f + NSTAGE;
+                if (lane == 0 && fn < nfill) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&bars[st], TB);
+                    tma_load_3d(ring + st * SB, map, &bars[st], box_x, rbase + fn * RS + 2, 0);
+                }
+            }
+            return true;
+        };
+
+        // carried state (see the header comment for the schedule)
+        T qc0[N], qc1[N], ql1[N];
+        T Wy0[NW][N], Wy1[NW][N], sy0[NW], sy1[NW];
+        T Gprev[N], dqy[N], bp_pend[N], tyP_m[N], tyP_p[N];
+        T apdq0[N], amdq0[N], BpAp0[N], BpAm0[N], F0[N];
+#pragma unroll
+        for (int m = 0; m < N; m++) {
+            qc0[m] = Gprev[m] = dqy[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
+            apdq0[m] = amdq0[m] = BpAp0[m] = BpAm0[m] = F0[m] = T(0);
+        }
+#pragma unroll
+        for (int p = 0; p < NW; p++) {
+            sy0[p] = sy1[p] = T(0);
+#pragma unroll
+            for (int m = 0; m < N; m++) Wy0[p][m] = Wy1[p][m] = T(0);
+        }
+        if (!fetch(rbase, qc1, ql1)) { failed = true; break; }
+
+        for (int k = j0 - 3; k < jend; k++) {
+            T qc2[N], ql2[N];
+            if (!fetch(k + 2, qc2, ql2)) { failed = true; break; }
+
+            // ---- y-edge between rows k+1 and k+2 of column c
+            T Wy2[NW][N], sy2[NW], bm2[N], bp2[N];
+            typename RP::Lin Ly;
+            bool bady = false;
+            a.rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
+            T TAm[N], TAp[N];   // x-splits of the y-fluctuations entering row k+1
+            T nPm[N], nPp[N];   // ... entering row k+2
+            if (trans) {
+                T t1[N], t2[N];
+                a.rp.template transverse<1>(Ly, bm2, t1, t2);
+                a.rp.template transverse<1>(Ly, bp2, nPm, nPp);
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    TAm[m] = tyP_m[m] + t1[m];
+                    TAp[m] = tyP_p[m] + t2[m];
+                }
+            }
+            T dqy_n[N];
+#pragma unroll
+            for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
+            if (ye_lane && k + 2 >= 0 && k + 2 <= a.my) {
+                bad |= bady;
+#pragma unroll
+                for (int p = 0; p < NW; p++) smy = fmax(smy, fabs(sy2[p]));
+            }
+
+            // ---- x-edge c-1/2 of row k+1
+            T Wx[NW][N], sxw[NW], amdq1[N], apdq1[N];
+            T BmAp1[N], BpAp1[N], BmAm1[N], BpAm1[N];
+            if (k >= j0 - 2) {
+                typename RP::Lin Lx;
+                bool badx = false;
+                a.rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+                if (trans) {
+                    a.rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
+                    a.rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
+                }
+                if (xe_lane && k + 1 >= 0 && k + 1 < a.my) {
+                    bad |= badx;
+#pragma unroll
+                    for (int p = 0; p < NW; p++) smx = fmax(smx, fabs(sxw[p]));
+                }
+            }
+
+            T Fn[N], Gn[N];
+            if (k >= j0 - 1) {
+                // ---- F at x-edge (c-1/2, k+1)
+#pragma unroll
+                for (int m = 0; m < N; m++) Fn[m] = T(0);
+                if (second) {
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
+                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
+                        T dl = T(0), dr = T(0);
+#pragma unroll
+                        for (int m = 0; m < N; m++) {
+                            const T wu = shfl(Wx[p][m], src);
+                            dl += wu * Wx[p][m];
+                            dr += Wx[p][m] * Wx[p][m];
+                        }
+                        const T as = fabs(sxw[p]);
+                        const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(a.limiter, dl, dr);
+#pragma unroll
+                        for (int m = 0; m < N; m++) Fn[m] += cf * Wx[p][m];
+                    }
+                }
+                if (trans) {
+#pragma unroll
+                    for (int m = 0; m < N; m++) Fn[m] -= hnuy * (TAm[m] + shfl_up1(TAp[m]));
+                }
+                // ---- G at y-edge (c, k+1/2)
+#pragma unroll
+                for (int m = 0; m < N; m++) Gn[m] = T(0);
+                if (second) {
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
+                        const bool upl = sy1[p] > T(0);
+                        T dl = T(0), dr = T(0);
+#pragma unroll
+                        for (int m = 0; m < N; m++) {
+                            const T wu = upl ? Wy0[p][m] : Wy2[p][m];
+                            dl += wu * Wy1[p][m];
+                            dr += Wy1[p][m] * Wy1[p][m];
+                        }
+                        const T as = fabs(sy1[p]);
+                        const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(a.limiter, dl, dr);
+#pragma unroll
+                        for (int m = 0; m < N; m++) Gn[m] += cf * Wy1[p][m];
+                    }
+                }
+                if (trans) {
+#pragma unroll
+                    for (int m = 0; m < N; m++)
+                        Gn[m] -= hnux * (BpAp0[m] + BmAp1[m] + shfl_down1(BpAm0[m] + BmAm1[m]));
+                }
+            }
+
+            // ---- cell (c, k)
+            if (k >= j0) {
+                T xr[N];
+#pragma unroll
+                for (int m = 0; m < N; m++) xr[m] = shfl_down1(amdq0[m] + F0[m]);
+                if (out_lane) {
+                    T* o = qout + (long long)(k + 2) * a.ld_x + a.x_offset + c;
+                    T qn[N];
+#pragma unroll
+                    for (int m = 0; m < N; m++) {
+                        qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) -
+                                nuy * (dqy[m] + Gn[m] - Gprev[m]);
+                        o[m * a.ld_field] = qn[m];
+                    }
+                    if (RP::POSITIVE) bad |= !(qn[0] > T(0));
+                    else bad |= qn[0] != qn[0];
+                }
+            }
+
+            // ---- rotate
+#pragma unroll
+            for (int m = 0; m < N; m++) {
+                qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
+                Gprev[m] = Gn[m];
+                dqy[m] = dqy_n[m];
+                bp_pend[m] = bp2[m];
+                if (trans) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
+                apdq0[m] = apdq1[m]; amdq0[m] = amdq1[m];
+                if (trans) { BpAp0[m] = BpAp1[m]; BpAm0[m] = BpAm1[m]; }
+                F0[m] = Fn[m];
+            }
+#pragma unroll
+            for (int p = 0; p < NW; p++) {
+                sy0[p] = sy1[p]; sy1[p] = sy2[p];
+#pragma unroll
+                for (int m = 0; m < N; m++) { Wy0[p][m] = Wy1[p][m]; Wy1[p][m] = Wy2[p][m]; }
+            }
+        }
+        __syncwarp();
+    }
+
+    if (failed) {
+        // give the copies still in flight a bounded chance to land
+        for (int s = 0; s < NSTAGE; s++) (void)mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
+        if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);
+    double v = fmax(double(smx) / a.dx, double(smy) / a.dy);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomic_max_nonneg(a.smax_bits, v);
+}
+
+// ------------------------------------------------------------------ ghosts
+
+template <typename T>
+struct BcArgs {
+    T* qa;
+    T* qb;
+    const int* cur;   // fill qa (cur == 0 or null) or qb (cur == 1)
+    int mx, my, meqn;
+    long long ld_x, ld_field, x_offset;
+    int bc[4];
+};
+
+__device__ __forceinline__ int bc_map(int i, int n, int lo_kind, int hi_kind, bool& flip)
+{
+    for (int it = 0; it < 4 && (i < 0 || i >= n); it++) {
+        const int kind = i < 0 ? lo_kind : hi_kind;
+        if (kind == 0) {
+            i = ((i % n) + n) % n;
+        } else if (kind == 1) {
+            i = i < 0 ? 0 : n - 1;
+        } else {
+            i = i < 0 ? -i - 1 : 2 * n - 1 - i;
+            flip = !flip;
+        }
+    }
+    return i;
+}
+
+template <typename T>
+__global__ void bc_fill_kernel(const BcArgs<T> a)
+{
+    const int W = a.mx + 4;
+    const long long total = 4LL * W + 4LL * a.my;
+    T* q = (a.cur && *a.cur) ? a.qb : a.qa;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, j;
+        if (t < 4LL * W) {
+            const int jr = int(t / W);
+            j = jr < 2 ? jr - 2 : a.my + jr - 2;
+            i = int(t % W) - 2;
+        } else {
+            const long long u = t - 4LL * W;
+            j = int(u / 4);
+            const int ir = int(u % 4);
+            i = ir < 2 ? ir - 2 : a.mx + ir - 2;
+        }
+        bool fx = false, fy = false;
+        const int si = bc_map(i, a.mx, a.bc[0], a.bc[1], fx);
+        const int sj = bc_map(j, a.my, a.bc[2], a.bc[3], fy);
+        const long long dst = (long long)(j + 2) * a.ld_x + a.x_offset + i;
+        const long long src = (long long)(sj + 2) * a.ld_x + a.x_offset + si;
+        for (int m = 0; m < a.meqn; m++) {
+            T v = q[m * a.ld_field + src];
+            if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
+            q[m * a.ld_field + dst] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ time step
+
+struct DevState {
+    unsigned long long smax_bits;
+    double dt, t, cfl_last, cfl_maxseen;
+    int cur, nacc, nrej, status;
+};
+
+// ------------------------------------------------------------------ cell speeds
+
+template <class RP>
+__global__ void max_cell_speed_kernel(const RP rp, const typename RP::real* q, int mx, int my,
+                                      long long ld_x, long long ld_field, long long x_offset,
+                                      double dx, double dy, unsigned long long* out)
+{
+    using T = typename RP::real;
+    double v = 0.0;
+    const long long n = (long long)mx * my;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = int(t % mx), j = int(t / mx);
+        T qq[RP::NEQ];
+        for (int m = 0; m < RP::NEQ; m++) qq[m] = q[m * ld_field + (j + 2) * ld_x + x_offset + i];
+        T sx, sy;
+        rp.cell_speeds(qq, sx, sy);
+        v = fmax(v, fmax(double(sx) / dx, double(sy) / dy));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, v);
+}
+
+}  // namespace mc

@@ -1,0 +1,105 @@
+"""GPU parity of the time-step loop (mc_advance: ghost fill, fused step and
+the device-side dt rule inside one CUDA graph) against the oracle's driver."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1308_1464_gb300 as mc
+from paper_1308_1464_gb300 import workloads
+from gpu_util import TOL, embed, initial_state, problems, scaled_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1308_1464_gb300.state import DeviceState  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1308_1464_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def test_acoustics_pulse_ten_steps():
+    """Acoustics, 128 x 128, FP64, periodic, MC, CFL 0.9, 10 steps."""
+    g = workloads.acoustics_pulse(128, 128)
+    P = mc.BC_PERIODIC
+    p, op = problems("acoustics", 128, 128, g.dx, g.dy, mc.F64, (P, P, P, P))
+    dt0 = 0.9 * g.dx / 2.0
+    assert dt0 == 0.003515625
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(g.q)
+        t, dt, inb, nrej = ctx.advance(a.ptr, b.ptr, 10, 0.9, 1.0, 0.0, dt0)
+        got = (b if inb else a).download()
+    want, t_ref, dt_ref, nrej_ref, _ = oracle.advance(op, embed(op, g.q), 10, 0.9, 1.0, 0.0, dt0)
+    assert nrej == nrej_ref == 0
+    assert t == pytest.approx(t_ref, rel=1e-14) and t == pytest.approx(10 * dt0, rel=1e-14)
+    assert dt == pytest.approx(dt_ref, rel=1e-14)
+    assert scaled_error("acoustics", got, want[:, 2:-2, 2:-2]) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [mc.F64, mc.F32])
+def test_rejection_and_retake(dtype):
+    """An initial dt three times too large is rejected and retaken; the
+    accepted sequence matches the oracle's driver."""
+    mx, my = 64, 48
+    q, dx, dy = initial_state("swe", mx, my, seed=2)
+    W = mc.BC_WALL
+    p, op = problems("swe", mx, my, dx, dy, dtype, (W, W, W, W))
+    npdt = np.float64 if dtype == mc.F64 else np.float32
+    qin = q.astype(npdt)
+    qo = embed(op, qin.astype(np.float64))
+    dt0 = 3.0 * 0.9 / oracle.max_cell_speed(op, oracle.bc_fill(op, qo))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin)
+        t, dt, inb, nrej = ctx.advance(a.ptr, b.ptr, 6, 0.9, 1.0, 0.0, dt0)
+        got = (b if inb else a).download().astype(np.float64)
+    want, t_ref, dt_ref, nrej_ref, _ = oracle.advance(op, qo, 6, 0.9, 1.0, 0.0, dt0)
+    assert nrej == nrej_ref >= 1
+    rel = 1e-12 if dtype == mc.F64 else 1e-5
+    assert t == pytest.approx(t_ref, rel=rel)
+    # FP32: dt follows the FP32 speeds, so states differ by more than one step's rounding
+    assert scaled_error("swe", got, want[:, 2:-2, 2:-2]) <= (1e-11 if dtype == mc.F64 else 1e-4)
+
+
+def test_advance_host_matches_device_path():
+    g = workloads.swe_dambreak(96, 80)
+    W = mc.BC_WALL
+    p, _ = problems("swe", 96, 80, g.dx, g.dy, mc.F32, (W, W, W, W))
+    q32 = g.q.astype(np.float32)
+    dt0 = 0.9 * g.dx / (2.0 + np.sqrt(9.81 * 2.0))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(q32)
+        t1, dt1, inb, _ = ctx.advance(a.ptr, b.ptr, 7, 0.9, 1.0, 0.0, dt0)
+        dev = (b if inb else a).download()
+        a2, b2 = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        host = np.zeros_like(q32)
+        t2, dt2, _ = ctx.advance_host(q32.ctypes.data, host.ctypes.data, a2.ptr, b2.ptr, 7, 0.9,
+                                      1.0, 0.0, dt0)
+    assert t1 == t2 and dt1 == dt2
+    np.testing.assert_array_equal(dev, host)
+
+
+def test_nonphysical_state_is_reported():
+    """A negative depth in the input is flagged by the device status word."""
+    q, dx, dy = initial_state("swe", 40, 30, seed=1)
+    q[0, 10, 10] = -1.0
+    W = mc.BC_WALL
+    p, _ = problems("swe", 40, 30, dx, dy, mc.F32, (W, W, W, W))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(q)
+        with pytest.raises(mc.McError) as ei:
+            ctx.step(a.ptr, b.ptr, 1e-4)
+        assert ei.value.status == mc.MC_ENONPHYS
+        # the status word was cleared: a good state steps cleanly afterwards
+        q2, _, _ = initial_state("swe", 40, 30, seed=1)
+        a.upload(q2)
+        ctx.step(a.ptr, b.ptr, 1e-4)

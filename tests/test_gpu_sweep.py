@@ -1,0 +1,156 @@
+"""GPU parity of the fused step (K1) and ghost fill (K2) against the oracle.
+
+Every case calls the CUDA library through its C ABI (mc_step) and compares
+with the FP64 oracle run on the same (precision-rounded) input with the same
+dt.  The tolerance is the field-scaled max error of one step: 1e-12 for FP64,
+2e-5 for FP32.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1308_1464_gb300 as mc
+from paper_1308_1464_gb300 import workloads
+from gpu_util import (TOL, embed, field_scales, initial_state, problems, scaled_error,
+                      window_step)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1308_1464_gb300.state import DeviceState  # noqa: E402
+
+W, X, P = mc.BC_WALL, mc.BC_EXTRAP, mc.BC_PERIODIC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1308_1464_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def run_step(p, op, q_interior, cfl=0.9, tile_rows=None):
+    """One GPU step and the oracle's step on the same rounded input."""
+    npdt = np.float64 if p.dtype == mc.F64 else np.float32
+    qin = q_interior.astype(npdt)
+    qo = embed(op, qin.astype(np.float64))
+    dt = cfl / oracle.max_cell_speed(op, oracle.bc_fill(op, qo))
+    with mc.Context(p) as ctx:
+        if tile_rows:
+            ctx.set_tile_rows(tile_rows)
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin)
+        smax = ctx.step(a.ptr, b.ptr, dt)
+        got = b.download().astype(np.float64)
+        ghosts = a.with_ghosts().astype(np.float64)
+    want, smax_ref, _ = oracle.step(op, qo, dt)
+    return got, want[:, 2:-2, 2:-2], smax, smax_ref, ghosts, oracle.bc_fill(op, qo)
+
+
+CASES = [
+    ("acoustics", mc.F64, (P, P, P, P), 4, 1),
+    ("acoustics", mc.F32, (W, X, P, P), 1, 1),
+    ("swe", mc.F32, (W, W, W, W), 4, 1),
+    ("swe", mc.F64, (W, W, W, W), 4, 1),
+    ("swe", mc.F32, (X, X, P, P), 1, 1),
+    ("swe", mc.F64, (P, P, X, W), 0, 1),
+    ("swe", mc.F32, (W, X, X, W), 4, 0),
+    ("euler", mc.F32, (X, X, X, X), 4, 1),
+    ("euler", mc.F64, (X, X, X, X), 4, 1),
+    ("euler", mc.F32, (W, W, P, P), 1, 1),
+    ("euler", mc.F64, (P, P, W, X), 4, 0),
+]
+
+
+@pytest.mark.parametrize("solver,dtype,bc,lim,trans", CASES)
+def test_step_parity(solver, dtype, bc, lim, trans):
+    mx, my = 70, 45   # 3 bands (29 + 29 + 12 columns), several row tiles, ragged tails
+    q, dx, dy = initial_state(solver, mx, my, seed=3)
+    p, op = problems(solver, mx, my, dx, dy, dtype, bc, limiter=lim, transverse=trans)
+    got, want, smax, smax_ref, ghosts, ghosts_ref = run_step(p, op, q, tile_rows=8)
+    err = scaled_error(solver, got, want)
+    assert err <= TOL[dtype], f"field-scaled error {err:.3e}"
+    assert smax == pytest.approx(smax_ref, rel=1e-13 if dtype == mc.F64 else 2e-6)
+    # ghost layers of the input filled like the oracle's
+    np.testing.assert_array_equal(ghosts, ghosts_ref.astype(np.float32 if dtype == mc.F32 else np.float64)
+                                  .astype(np.float64))
+
+
+def test_first_order_and_no_limiter():
+    for order, lim in ((1, 4), (2, 0)):
+        q, dx, dy = initial_state("swe", 40, 33, seed=5)
+        p, op = problems("swe", 40, 33, dx, dy, mc.F64, (W, X, X, W), limiter=lim, order=order)
+        got, want, *_ = run_step(p, op, q, tile_rows=16)
+        assert scaled_error("swe", got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("mx,my", [(1, 1), (1, 7), (7, 1), (2, 3), (29, 2), (30, 31), (59, 5),
+                                   (58, 9), (87, 3)])
+@pytest.mark.parametrize("solver,dtype,bc", [("swe", mc.F64, (W, W, W, W)),
+                                             ("euler", mc.F32, (X, X, P, P)),
+                                             ("acoustics", mc.F64, (P, P, W, W))])
+def test_tiny_and_odd_grids(mx, my, solver, dtype, bc):
+    q, _, _ = initial_state(solver, max(mx, 4), max(my, 4), seed=mx * 100 + my)
+    q = np.ascontiguousarray(q[:, :my, :mx])
+    p, op = problems(solver, mx, my, 0.01, 0.013, dtype, bc)
+    got, want, smax, smax_ref, ghosts, ghosts_ref = run_step(p, op, q, cfl=0.5)
+    assert scaled_error(solver, got, want) <= TOL[dtype]
+    assert smax == pytest.approx(smax_ref, rel=1e-12 if dtype == mc.F64 else 2e-6)
+
+
+@pytest.mark.parametrize("solver,dtype", [("swe", mc.F32), ("euler", mc.F64)])
+def test_tile_shape_invariance(solver, dtype):
+    """Results do not depend on the tile height: bitwise equal outputs."""
+    mx, my = 100, 130
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, op = problems(solver, mx, my, dx, dy, dtype, (W, X, X, W))
+    outs = [run_step(p, op, q, tile_rows=t)[0] for t in (8, 17, 64, 256)]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+FULL = [
+    ("swe", mc.F32, 4096, 4096, (W, W, W, W)),     # shallow-water dam break, bench configuration
+    ("swe", mc.F64, 4096, 4096, (W, W, W, W)),
+    ("euler", mc.F32, 4096, 4096, (X, X, X, X)),   # four-quadrant Euler
+]
+
+
+@pytest.mark.parametrize("solver,dtype,mx,my,bc", FULL)
+def test_full_size_windows(solver, dtype, mx, my, bc):
+    """Full-size grid, default launch configuration: 40 windows of 8 x 8 cells
+    (corners, edges, random interior) recomputed by the oracle from the GPU
+    step's filled input, plus conservation of mass across the walls/extrapolation."""
+    if solver == "swe":
+        g = workloads.swe_dambreak(mx, my)
+    else:
+        g = workloads.euler_quadrants(mx, my)
+    p, op = problems(solver, mx, my, g.dx, g.dy, dtype, bc)
+    npdt = np.float64 if dtype == mc.F64 else np.float32
+    qin = g.q.astype(npdt)
+    # dt from the oracle's cell-speed rule on the same rounded input
+    dt = 0.9 / oracle.max_cell_speed(op, embed(op, qin.astype(np.float64)))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin)
+        ctx.step(a.ptr, b.ptr, dt)
+        full_in = a.with_ghosts().astype(np.float64)
+        out = b.download().astype(np.float64)
+    S = field_scales(solver, full_in[:, 2:-2, 2:-2])
+    rng = np.random.default_rng(17)
+    w = h = 8
+    spots = [(0, 0), (mx - w, 0), (0, my - h), (mx - w, my - h), (mx // 2 - 4, 0), (0, my // 2)]
+    spots += [(int(rng.integers(0, mx - w)), int(rng.integers(0, my - h))) for _ in range(34)]
+    for (i0, j0) in spots:
+        want = window_step(op, full_in, dt, i0, j0, w, h)
+        got = out[:, j0: j0 + h, i0: i0 + w]
+        err = max(np.abs(got[m] - want[m]).max() / S[m] for m in range(want.shape[0]))
+        assert err <= TOL[dtype], (i0, j0, err)
+    # mass is conserved by walls exactly; with extrapolation it changes only by boundary fluxes
+    if solver == "swe":
+        m0, m1 = qin[0].astype(np.float64).sum(), out[0].sum()
+        rel = abs(m1 - m0) / m0
+        assert rel <= (1e-13 if dtype == mc.F64 else 1e-6), rel

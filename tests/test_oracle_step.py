@@ -461,3 +461,19 @@ def test_closed_box_conserves_mass(oracle_mod, solver):
     qi = interior(prob, q)
     assert abs(qi[0].sum() - mass0) <= 400 * np.finfo(float).eps * mass0
     assert np.abs(qi[0] - q0[0]).max() > 1e-2   # the flow moved
+
+
+def test_given_ghosts_window_equals_full_grid(oracle_mod):
+    """A window cut out of a grid, stepped with its true neighbours as given
+    ghosts, reproduces the full-grid step on its cells exactly."""
+    n = 24
+    g = workloads.euler_quadrants(n, n, seed=4)
+    prob = make(oracle_mod, "euler", n, n, g.dx, g.dy, (oracle_mod.BC_EXTRAP,) * 4)
+    q = oracle_mod.bc_fill(prob, embed(prob, g.q))
+    dt = 0.8 / oracle_mod.max_cell_speed(prob, q)
+    full, _, _ = oracle_mod.step(prob, q, dt)
+    for (i0, j0, w, h) in [(0, 0, 6, 5), (7, 3, 8, 8), (18, 19, 6, 5)]:
+        win = make(oracle_mod, "euler", w, h, g.dx, g.dy, (oracle_mod.BC_GIVEN,) * 4)
+        qw = q[:, j0: j0 + h + 4, i0: i0 + w + 4].copy()
+        out, _, _ = oracle_mod.step(win, qw, dt)
+        np.testing.assert_array_equal(out[:, 2:-2, 2:-2], full[:, j0 + 2: j0 + h + 2, i0 + 2: i0 + w + 2])
