@@ -165,6 +165,96 @@ mc_status mc_advance_host(mc_ctx* ctx, const void* host_q0, void* host_q, void* 
                           int nsteps, double cfl_desired, double cfl_max, double* t_inout,
                           double* dt_inout, int* nrejected, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Exact Euler Riemann solver with a learned pressure seed.
+ *
+ * The paper lists Euler among its Riemann kernels (§3, Tables 2-3) and keeps
+ * each solve pointwise (§2).  mc_riemann_exact solves n independent 1D Euler
+ * Riemann problems exactly (Toro, ch. 4): the star pressure p* is the root of
+ * f(p) = f_L(p) + f_R(p) + u_R - u_L, found by Newton's method in FP64 from a
+ * seed, stopping when |p_{k+1} - p_k| / p_{k+1} < tol; u* follows from p*.
+ * Inputs and outputs are FP32 structure-of-arrays device buffers of length n.
+ * Seeds: Toro's adaptive choice between the primitive-variable (PV),
+ * two-rarefaction (TR) and two-shock (TS) guesses, each of them alone, PV/TR
+ * only, or the seed network (MC_SEED_MLP), whose proposal is used only if it
+ * is finite and within [1e-6 min(pL,pR), 1e6 max(pL,pR)] and Newton from it
+ * converges within max_iter; otherwise Newton restarts from the adaptive
+ * seed (flag MC_RS_FALLBACK) and iters counts the wasted updates too.
+ * Interfaces that generate vacuum (2 (cL + cR) / (gamma - 1) <= uR - uL) get
+ * p* = 0, u* = NaN, flag MC_RS_VACUUM and no iterations.
+ * ------------------------------------------------------------------------ */
+enum { MC_SEED_ADAPTIVE = 0, MC_SEED_PV = 1, MC_SEED_TR = 2, MC_SEED_TS = 3, MC_SEED_PVTR = 4,
+       MC_SEED_MLP = 5 };
+enum { MC_RS_OK = 0, MC_RS_VACUUM = 1, MC_RS_NOCONV = 2, MC_RS_FALLBACK = 4 };
+
+/* Seed network: 10 features -> 64 -> 64 -> 1 (ReLU), BF16 weights and FP32
+ * accumulation on the tensor cores.  Parameters travel as one FP32 vector
+ * ("master" copy) in the order W1[16][64] (input-major; rows 10..15 are
+ * padding and must be zero), b1[64], W2[64][64], b2[64], W3[64], b3[1],
+ * followed by the feature standardisation mu[10], sigma[10]:
+ * MC_MLP_NPARAM values.  Features of an interface, before standardisation:
+ * ln rhoL, ln rhoR, ln pL, ln pR, ln cL, ln cR, uR - uL, (uR - uL)/(cL + cR),
+ * ln p_TR, ln max(p_PV, 1e-6); the output is ln p* - ln p_TR. */
+#define MC_MLP_NWEIGHT (16 * 64 + 64 + 64 * 64 + 64 + 64 + 1)
+#define MC_MLP_NPARAM (MC_MLP_NWEIGHT + 20)
+typedef struct mc_mlp mc_mlp;
+
+/* Allocates the network's device storage (zero weights) on the current device. */
+mc_status mc_mlp_create(mc_mlp** out);
+mc_status mc_mlp_destroy(mc_mlp* net);
+/* Host FP32 parameter vector of MC_MLP_NPARAM values in / out; set_params
+ * also rounds the weights to the BF16 copy the kernels use.  Synchronous. */
+mc_status mc_mlp_set_params(mc_mlp* net, const float* host_params);
+mc_status mc_mlp_get_params(const mc_mlp* net, float* host_params);
+
+/* Raw features (n x 10, row-major, FP32) of n interfaces given as device
+ * SoA states; rows of vacuum-generating interfaces are NaN.  If p_star is
+ * not NULL, target[i] = ln p_star[i] - ln p_TR[i] (the network's training
+ * target), NaN where p_star is not positive.  Asynchronous. */
+mc_status mc_mlp_features(int64_t n, double gamma, const float* rho_l, const float* u_l,
+                          const float* p_l, const float* rho_r, const float* u_r,
+                          const float* p_r, const float* p_star, float* features, float* target,
+                          void* stream);
+
+/* Network forward over n raw feature rows (device, n x 10): standardised by
+ * the network's mu/sigma, BF16 tensor-core layers, out[n] on the device. */
+mc_status mc_mlp_forward(const mc_mlp* net, int64_t n, const float* features, float* out,
+                         void* stream);
+
+/* Gradient of L = (1/n) sum (out_i - y_i)^2 over n rows (device features n x
+ * 10, targets n) with the precision model of training: BF16 operands of
+ * every product of activations, weights and back-propagated activation
+ * gradients, FP32 accumulation.  grads: device, MC_MLP_NWEIGHT floats in the
+ * parameter order, overwritten; loss: device float, overwritten.  Rows with a
+ * non-finite target contribute nothing.  Asynchronous. */
+mc_status mc_mlp_grad(mc_mlp* net, int64_t n, const float* features, const float* target,
+                      float* grads, float* loss, void* stream);
+
+typedef struct mc_train_cfg {
+    int64_t batch;          /* rows per Adam step */
+    int32_t epochs;
+    float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba 2015) */
+    uint64_t seed;          /* per-epoch row order */
+    int32_t fit_norm;       /* 1: set mu/sigma from the features first */
+} mc_train_cfg;
+
+/* Trains the network on n rows (device features n x 10, targets n) with
+ * minibatch Adam on the GPU (the same kernels as mc_mlp_grad).  Rows with a
+ * non-finite feature or target are skipped.  Each epoch visits the rows in
+ * the order i -> (a i + b) mod n with a coprime to n drawn from seed.
+ * loss_per_epoch (host, nullable): mean loss of each epoch.  Synchronous. */
+mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const float* target,
+                       const mc_train_cfg* cfg, float* loss_per_epoch, void* stream);
+
+/* stats (nullable): device int64[6], accumulated (the caller zeroes it):
+ * interfaces, vacuum, fallback, not converged, total Newton updates,
+ * largest per-interface count. */
+mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const float* u_l,
+                           const float* p_l, const float* rho_r, const float* u_r,
+                           const float* p_r, float* p_star, float* u_star, uint8_t* iters,
+                           uint8_t* flags, int seed_mode, const mc_mlp* net, double tol,
+                           int max_iter, int64_t* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

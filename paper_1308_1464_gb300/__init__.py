@@ -95,6 +95,17 @@ def lib():
                                  _DP, _DP, _IP, _IP, _VP]
         L.mc_advance_host.argtypes = [_VP, _VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, _DP, _DP, _IP, _VP]
+        L.mc_mlp_create.argtypes = [ctypes.POINTER(_VP)]
+        L.mc_mlp_destroy.argtypes = [_VP]
+        L.mc_mlp_set_params.argtypes = [_VP, _VP]
+        L.mc_mlp_get_params.argtypes = [_VP, _VP]
+        L.mc_mlp_features.argtypes = [ctypes.c_int64, ctypes.c_double] + [_VP] * 9 + [_VP]
+        L.mc_mlp_forward.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP]
+        L.mc_mlp_grad.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP]
+        L.mc_mlp_train.argtypes = [_VP, ctypes.c_int64, _VP, _VP, ctypes.POINTER(TrainCfg),
+                                   _VP, _VP]
+        L.mc_riemann_exact.argtypes = [ctypes.c_int64, ctypes.c_double] + [_VP] * 10 + [
+            ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int, _VP, _VP]
         _lib = L
     return _lib
 
@@ -202,3 +213,80 @@ def header_functions(path: str = HEADER) -> list[str]:
     names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(mc_[a-z0-9_]+)\s*\(",
                        text, flags=re.M)
     return sorted(set(names))
+
+
+# ---------------------------------------------------------------- exact solver
+
+SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_MLP = range(6)
+RS_OK, RS_VACUUM, RS_NOCONV, RS_FALLBACK = 0, 1, 2, 4
+MLP_NWEIGHT = 16 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+MLP_NPARAM = MLP_NWEIGHT + 20
+
+
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("fit_norm", ctypes.c_int32)]
+
+
+class SeedNet:
+    """Device-resident pressure-seed network (mc_mlp_*)."""
+
+    def __init__(self):
+        h = _VP()
+        check(lib().mc_mlp_create(ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, host_ptr: int) -> None:
+        check(lib().mc_mlp_set_params(self._h, _VP(host_ptr)))
+
+    def get_params(self, host_ptr: int) -> None:
+        check(lib().mc_mlp_get_params(self._h, _VP(host_ptr)))
+
+    def forward(self, n: int, features: int, out: int, stream: int = 0) -> None:
+        check(lib().mc_mlp_forward(self._h, int(n), _VP(features), _VP(out), _VP(stream)))
+
+    def grad(self, n: int, features: int, target: int, grads: int, loss: int, stream: int = 0):
+        check(lib().mc_mlp_grad(self._h, int(n), _VP(features), _VP(target), _VP(grads),
+                                _VP(loss), _VP(stream)))
+
+    def train(self, n: int, features: int, target: int, batch: int = 8192, epochs: int = 10,
+              lr: float = 2e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              seed: int = 1, fit_norm: bool = True, loss_out: int = 0, stream: int = 0) -> None:
+        cfg = TrainCfg(int(batch), int(epochs), lr, beta1, beta2, eps, int(seed), int(fit_norm))
+        check(lib().mc_mlp_train(self._h, int(n), _VP(features), _VP(target), ctypes.byref(cfg),
+                                 _VP(loss_out) if loss_out else None, _VP(stream)))
+
+
+def mlp_features(n: int, gamma: float, states, p_star: int, features: int, target: int,
+                 stream: int = 0) -> None:
+    """states: six device pointers (rho_l, u_l, p_l, rho_r, u_r, p_r)."""
+    check(lib().mc_mlp_features(int(n), float(gamma), *[_VP(s) for s in states],
+                                _VP(p_star) if p_star else None, _VP(features),
+                                _VP(target) if target else None, _VP(stream)))
+
+
+def riemann_exact(n: int, gamma: float, states, p_star: int, u_star: int, iters: int, flags: int,
+                  seed_mode: int = SEED_ADAPTIVE, net: "SeedNet | None" = None, tol: float = 1e-8,
+                  max_iter: int = 30, stats: int = 0, stream: int = 0) -> None:
+    """Exact Euler Riemann solves of n interfaces (device SoA pointers)."""
+    check(lib().mc_riemann_exact(int(n), float(gamma), *[_VP(s) for s in states], _VP(p_star),
+                                 _VP(u_star), _VP(iters) if iters else None,
+                                 _VP(flags) if flags else None, int(seed_mode),
+                                 net.handle if net is not None else None, float(tol),
+                                 int(max_iter), _VP(stats) if stats else None, _VP(stream)))

@@ -1,0 +1,415 @@
+// mc_exact.cu -- exact Euler Riemann solver with plain or learned pressure
+// seeds (mc_riemann_exact), and the seed network's device storage.
+//
+// Toro, ch. 4: p* is the root of f(p) = f_L(p) + f_R(p) + u_R - u_L with
+//   f_K(p) = (p - p_K) sqrt(A_K / (p + B_K)),      p > p_K (shock),
+//            A_K = 2 / ((gamma+1) rho_K), B_K = (gamma-1)/(gamma+1) p_K,
+//   f_K(p) = 2 c_K/(gamma-1) ((p/p_K)^z - 1),      p <= p_K (rarefaction),
+//            z = (gamma-1)/(2 gamma),
+// and u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2.  Newton runs in FP64;
+// seeds are Toro's PV, TR and TS guesses (ch. 9) or the network's proposal
+// p_TR exp(net(x)).  One thread per interface; a warp evaluates the network
+// for its 32 interfaces together on the tensor cores.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "mc_internal.h"
+#include "mc_seednet.cuh"
+
+namespace mc {
+
+constexpr double PFLOOR = 1e-12;
+
+struct ExactArgs {
+    long long n;
+    double gamma, tol;
+    int max_iter, seed_mode;
+    const float *rl, *ul, *pl, *rr, *ur, *pr;
+    float *ps, *us;
+    uint8_t *iters, *flags;
+    const MlpDev* net;
+    int64_t* stats;
+};
+
+struct Side {
+    double rho, u, p, c, A, B, kr, ik;
+};
+
+__device__ __forceinline__ Side make_side(double gamma, double rho, double u, double p)
+{
+    Side s;
+    s.rho = rho;
+    s.u = u;
+    s.p = p;
+    s.c = sqrt(gamma * p / rho);
+    s.A = 2.0 / ((gamma + 1.0) * rho);
+    s.B = (gamma - 1.0) / (gamma + 1.0) * p;
+    s.kr = 2.0 * s.c / (gamma - 1.0);
+    s.ik = 1.0 / (rho * s.c);
+    return s;
+}
+
+__device__ __forceinline__ void branch(const Side& s, double p, double z, double& f, double& fd)
+{
+    if (p > s.p) {
+        const double q = sqrt(s.A / (s.B + p));
+        f = (p - s.p) * q;
+        fd = q * (1.0 - 0.5 * (p - s.p) / (s.B + p));
+    } else {
+        const double r = p / s.p;
+        const double pz = pow(r, z);
+        f = s.kr * (pz - 1.0);
+        fd = s.ik * pz / r;   // (p/p_K)^(-(gamma+1)/(2 gamma)) = (p/p_K)^z / (p/p_K)
+    }
+}
+
+// Newton from p0; returns true on convergence, counts updates in it
+__device__ __forceinline__ bool newton(const Side& L, const Side& R, double z, double p0,
+                                       double tol, int max_iter, double& ps, int& it)
+{
+    double p = p0;
+    for (int k = 0; k < max_iter; k++) {
+        double fl, fdl, fr, fdr;
+        branch(L, p, z, fl, fdl);
+        branch(R, p, z, fr, fdr);
+        double pn = p - (fl + fr + (R.u - L.u)) / (fdl + fdr);
+        if (pn < PFLOOR) pn = PFLOOR;
+        it++;
+        if (!isfinite(pn)) {
+            ps = p;
+            return false;
+        }
+        if (fabs(pn - p) / pn < tol) {
+            ps = pn;
+            return true;
+        }
+        p = pn;
+    }
+    ps = p;
+    return false;
+}
+
+struct Seeds {
+    double pv_raw, pv, tr, ts, adaptive, pvtr;
+};
+
+__device__ __forceinline__ Seeds seeds(double gamma, const Side& L, const Side& R)
+{
+    Seeds s;
+    const double du = R.u - L.u;
+    const double z = 0.5 * (gamma - 1.0) / gamma;
+    s.pv_raw = 0.5 * (L.p + R.p) - 0.125 * du * (L.rho + R.rho) * (L.c + R.c);
+    s.pv = s.pv_raw < PFLOOR ? PFLOOR : s.pv_raw;
+    s.tr = pow((L.c + R.c - 0.5 * (gamma - 1.0) * du) / (L.c / pow(L.p, z) + R.c / pow(R.p, z)),
+               1.0 / z);
+    const double gl = sqrt(L.A / (L.B + s.pv)), gr = sqrt(R.A / (R.B + s.pv));
+    s.ts = (gl * L.p + gr * R.p - du) / (gl + gr);
+    if (s.ts < PFLOOR) s.ts = PFLOOR;
+    const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
+    const bool pv_ok = pmax / pmin < 2.0 && s.pv >= pmin && s.pv <= pmax;
+    s.adaptive = pv_ok ? s.pv : (s.pv < pmin ? s.tr : s.ts);
+    s.pvtr = pv_ok ? s.pv : s.tr;
+    return s;
+}
+
+// The network's ten raw inputs of one interface (FP32), from the FP64 states
+// and guesses: ln rho_L, ln rho_R, ln p_L, ln p_R, ln c_L, ln c_R, du,
+// du/(c_L + c_R), ln p_TR, ln max(p_PV, 1e-6).
+__device__ __forceinline__ void raw_features(const Side& L, const Side& R, const Seeds& sd,
+                                             float (&x)[10])
+{
+    const float du = float(R.u - L.u);
+    x[0] = logf(float(L.rho));
+    x[1] = logf(float(R.rho));
+    x[2] = logf(float(L.p));
+    x[3] = logf(float(R.p));
+    x[4] = logf(float(L.c));
+    x[5] = logf(float(R.c));
+    x[6] = du;
+    x[7] = du / float(L.c + R.c);
+    x[8] = logf(float(sd.tr));
+    x[9] = logf(float(fmax(sd.pv_raw, 1e-6)));
+}
+
+template <bool MLP>
+__global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    MlpShared* net = reinterpret_cast<MlpShared*>(smem);
+    __nv_bfloat16* xs = nullptr;
+    float* outs = nullptr;
+    if (MLP) {
+        mlp_load_shared(a.net, net);
+        xs = reinterpret_cast<__nv_bfloat16*>(smem + sizeof(MlpShared)) + warp * 32 * XP;
+        outs = reinterpret_cast<float*>(smem + sizeof(MlpShared) + 4 * 32 * XP * 2) + warp * 32;
+        __syncthreads();
+    }
+    const double gamma = a.gamma, z = 0.5 * (gamma - 1.0) / gamma;
+    long long c_n = 0, c_vac = 0, c_fb = 0, c_nc = 0, c_it = 0, c_max = 0;
+    const long long nchunks = (a.n + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * 4 + warp; ch < nchunks;
+         ch += (long long)gridDim.x * 4) {
+        const long long i = ch * 32 + lane;
+        const bool valid = i < a.n;
+        Side L, R;
+        if (valid) {
+            L = make_side(gamma, a.rl[i], a.ul[i], a.pl[i]);
+            R = make_side(gamma, a.rr[i], a.ur[i], a.pr[i]);
+        } else {
+            L = make_side(gamma, 1.0, 0.0, 1.0);
+            R = L;
+        }
+        const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
+        Seeds sd = seeds(gamma, L, R);
+        double p0;
+        switch (a.seed_mode) {
+        case MC_SEED_PV: p0 = sd.pv; break;
+        case MC_SEED_TR: p0 = sd.tr; break;
+        case MC_SEED_TS: p0 = sd.ts; break;
+        case MC_SEED_PVTR: p0 = sd.pvtr; break;
+        default: p0 = sd.adaptive; break;
+        }
+        int flag = 0, it = 0;
+        double ps = 0.0;
+        bool done = false;
+        if (MLP) {
+            float x[10];
+            if (!vacuum && valid) {
+                raw_features(L, R, sd, x);
+#pragma unroll
+                for (int k = 0; k < 10; k++) x[k] = (x[k] - net->mu[k]) / net->sig[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 10; k++) x[k] = 0.0f;
+            }
+            const float o = mlp_infer_warp(*net, x, xs, outs);
+            if (!vacuum && valid) {
+                const double prop = sd.tr * exp(double(o));
+                const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
+                if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
+                    newton(L, R, z, prop, a.tol, a.max_iter, ps, it)) {
+                    done = true;
+                } else {
+                    flag |= MC_RS_FALLBACK;
+                    p0 = sd.adaptive;
+                }
+            }
+        }
+        if (valid) {
+            if (vacuum) {
+                flag = MC_RS_VACUUM;
+                it = 0;
+                ps = 0.0;
+            } else if (!done) {
+                if (!newton(L, R, z, p0, a.tol, a.max_iter, ps, it)) flag |= MC_RS_NOCONV;
+            }
+            double us = __longlong_as_double(0x7ff8000000000000LL);   // NaN for vacuum
+            if (!vacuum) {
+                double fl, fdl, fr, fdr;
+                branch(L, ps, z, fl, fdl);
+                branch(R, ps, z, fr, fdr);
+                us = 0.5 * (L.u + R.u) + 0.5 * (fr - fl);
+            }
+            a.ps[i] = float(ps);
+            a.us[i] = float(us);
+            if (a.iters) a.iters[i] = uint8_t(it > 255 ? 255 : it);
+            if (a.flags) a.flags[i] = uint8_t(flag);
+            c_n++;
+            c_vac += vacuum;
+            c_fb += (flag & MC_RS_FALLBACK) != 0;
+            c_nc += (flag & MC_RS_NOCONV) != 0;
+            c_it += it;
+            c_max = c_max > it ? c_max : it;
+        }
+    }
+    if (a.stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c_n += __shfl_xor_sync(0xffffffffu, c_n, o);
+            c_vac += __shfl_xor_sync(0xffffffffu, c_vac, o);
+            c_fb += __shfl_xor_sync(0xffffffffu, c_fb, o);
+            c_nc += __shfl_xor_sync(0xffffffffu, c_nc, o);
+            c_it += __shfl_xor_sync(0xffffffffu, c_it, o);
+            long long m = __shfl_xor_sync(0xffffffffu, c_max, o);
+            c_max = c_max > m ? c_max : m;
+        }
+        if (lane == 0) {
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[0]), (unsigned long long)c_n);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[1]), (unsigned long long)c_vac);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[2]), (unsigned long long)c_fb);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)c_nc);
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[4]), (unsigned long long)c_it);
+            atomicMax(reinterpret_cast<unsigned long long*>(&a.stats[5]), (unsigned long long)c_max);
+        }
+    }
+}
+
+constexpr int EXACT_SMEM_MLP = (int)sizeof(MlpShared) + 4 * 32 * XP * 2 + 4 * 32 * 4;
+
+__global__ void features_kernel(long long n, double gamma, const float* rl, const float* ul,
+                                const float* pl, const float* rr, const float* ur,
+                                const float* pr, const float* ps, float* feat, float* target)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Side L = make_side(gamma, rl[i], ul[i], pl[i]);
+        const Side R = make_side(gamma, rr[i], ur[i], pr[i]);
+        const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
+        float x[10];
+        const Seeds sd = seeds(gamma, L, R);
+        raw_features(L, R, sd, x);
+        const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int k = 0; k < 10; k++) feat[i * 10 + k] = vacuum ? nan : x[k];
+        if (target) {
+            const float p = ps[i];
+            target[i] = (vacuum || !(p > 0.0f)) ? nan : float(log(double(p)) - log(sd.tr));
+        }
+    }
+}
+
+// BF16 copies of the weights in the fragment-friendly layouts
+__global__ void mlp_pack_kernel(MlpDev* d)
+{
+    for (int k = threadIdx.x + blockIdx.x * blockDim.x; k < NH * W2P;
+         k += blockDim.x * gridDim.x) {
+        const int r = k / W2P, c = k % W2P;
+        // W2 [in j][out k] -> w2t[out][in], w2[in][out]
+        d->w2t[k] = __float2bfloat16_rn(c < NH ? d->params[P_W2 + c * NH + r] : 0.0f);
+        d->w2[k] = __float2bfloat16_rn(c < NH ? d->params[P_W2 + r * NH + c] : 0.0f);
+        if (k < NH * W1P) {
+            const int r1 = k / W1P, c1 = k % W1P;
+            d->w1t[k] = __float2bfloat16_rn(c1 < 16 ? d->params[P_W1 + c1 * NH + r1] : 0.0f);
+        }
+        if (k < NH) d->w3r[k] = bf16_round(d->params[P_W3 + k]);
+    }
+}
+
+cudaError_t mlp_pack(MlpDev* d, cudaStream_t s)
+{
+    mlp_pack_kernel<<<(NH * W2P + 255) / 256, 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+extern "C" {
+
+mc_status mc_mlp_create(mc_mlp** out)
+{
+    if (!out) return set_error(MC_EINVAL, "output is NULL");
+    *out = nullptr;
+    mc_mlp* m = new (std::nothrow) mc_mlp();
+    if (!m) return set_error(MC_ENOMEM, "network handle allocation failed");
+    cudaError_t e = cudaMalloc(&m->dev, sizeof(MlpDev));
+    if (e == cudaSuccess) e = cudaMemset(m->dev, 0, sizeof(MlpDev));
+    if (e != cudaSuccess) {
+        cudaFree(m->dev);
+        delete m;
+        return cuda_error(e, "network allocation");
+    }
+    // unit feature scales until parameters are set
+    float ones[10] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+    e = cudaMemcpy(m->dev->params + P_SIG, ones, sizeof(ones), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev);
+        delete m;
+        return cuda_error(e, "network initialisation");
+    }
+    *out = m;
+    return MC_OK;
+}
+
+mc_status mc_mlp_destroy(mc_mlp* m)
+{
+    if (!m) return MC_OK;
+    cudaFree(m->dev);
+    delete m;
+    return MC_OK;
+}
+
+mc_status mc_mlp_set_params(mc_mlp* m, const float* host)
+{
+    if (!m || !host) return set_error(MC_EINVAL, "NULL argument");
+    for (int k = 0; k < 10; k++)
+        if (!(host[P_SIG + k] > 0.0f)) return set_error(MC_EINVAL, "feature scale %d must be > 0", k);
+    cudaError_t e = cudaMemcpy(m->dev->params, host, sizeof(float) * MC_MLP_NPARAM,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mlp_pack(m->dev, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "setting network parameters");
+}
+
+mc_status mc_mlp_get_params(const mc_mlp* m, float* host)
+{
+    if (!m || !host) return set_error(MC_EINVAL, "NULL argument");
+    cudaError_t e = cudaMemcpy(host, m->dev->params, sizeof(float) * MC_MLP_NPARAM,
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "reading network parameters");
+}
+
+mc_status mc_mlp_features(int64_t n, double gamma, const float* rho_l, const float* u_l,
+                          const float* p_l, const float* rho_r, const float* u_r,
+                          const float* p_r, const float* p_star, float* features, float* target,
+                          void* stream)
+{
+    if (n < 0) return set_error(MC_EINVAL, "n < 0");
+    if (n == 0) return MC_OK;
+    if (!rho_l || !u_l || !p_l || !rho_r || !u_r || !p_r || !features)
+        return set_error(MC_EINVAL, "NULL state or output pointer");
+    if (target && !p_star) return set_error(MC_EINVAL, "targets need p_star");
+    if (!(gamma > 1.0)) return set_error(MC_EINVAL, "gamma must be > 1");
+    long long blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    features_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, gamma, rho_l, u_l, p_l, rho_r, u_r, p_r, p_star, features, target);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "features launch");
+}
+
+mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const float* u_l,
+                           const float* p_l, const float* rho_r, const float* u_r,
+                           const float* p_r, float* p_star, float* u_star, uint8_t* iters,
+                           uint8_t* flags, int seed_mode, const mc_mlp* net, double tol,
+                           int max_iter, int64_t* stats, void* stream)
+{
+    if (n < 0) return set_error(MC_EINVAL, "n < 0");
+    if (n == 0) return MC_OK;
+    if (!rho_l || !u_l || !p_l || !rho_r || !u_r || !p_r || !p_star || !u_star)
+        return set_error(MC_EINVAL, "NULL state or output pointer");
+    if (!(gamma > 1.0)) return set_error(MC_EINVAL, "gamma must be > 1");
+    if (!(tol > 0.0) || max_iter < 1 || max_iter > 255)
+        return set_error(MC_EINVAL, "need tol > 0 and 1 <= max_iter <= 255");
+    if (seed_mode < MC_SEED_ADAPTIVE || seed_mode > MC_SEED_MLP)
+        return set_error(MC_EINVAL, "unknown seed mode %d", seed_mode);
+    if (seed_mode == MC_SEED_MLP && !net) return set_error(MC_EINVAL, "MLP seed needs a network");
+    ExactArgs a{n, gamma, tol, max_iter, seed_mode, rho_l, u_l, p_l, rho_r, u_r, p_r,
+                p_star, u_star, iters, flags, net ? net->dev : nullptr, stats};
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long nchunks = (n + 31) / 32;
+    long long blocks = (nchunks + 3) / 4;
+    const long long cap = (long long)sms * 16;
+    if (blocks > cap) blocks = cap;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (seed_mode == MC_SEED_MLP) {
+        cudaError_t e = cudaFuncSetAttribute(exact_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             EXACT_SMEM_MLP);
+        if (e != cudaSuccess) return cuda_error(e, "exact solver set-up");
+        exact_kernel<true><<<(unsigned)blocks, 128, EXACT_SMEM_MLP, s>>>(a);
+    } else {
+        exact_kernel<false><<<(unsigned)blocks, 128, 0, s>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "exact solver launch");
+}
+
+}  // extern "C"

@@ -20,6 +20,32 @@ __device__ __forceinline__ T tmin0(T a) { return a < T(0) ? a : T(0); }
 template <typename T>
 __device__ __forceinline__ T tmax0(T a) { return a > T(0) ? a : T(0); }
 
+// Reciprocal, square root and reciprocal square root.  FP32 uses the
+// hardware approximations (rcp/sqrt/rsqrt.approx: at most about 2 ulp, far
+// inside the FP32 parity tolerance); FP64 keeps correctly rounded division
+// and square root.
+__device__ __forceinline__ float rcp_(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rsqrt_(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+
 // ---------------------------------------------------------------- acoustics
 template <typename T>
 struct AcousticsRP {
@@ -115,12 +141,16 @@ struct SweRP {
             L.u = L.v = T(0); L.c = T(1); L.r2c = T(0.5);
             return;
         }
-        const T sl = sqrt(hl), sr = sqrt(hr);
-        const T w = T(1) / (sl + sr);
-        const T u = (ql[un] / sl + qr[un] / sr) * w;
-        const T v = (ql[ut] / sl + qr[ut] / sr) * w;
-        const T c = sqrt(g * T(0.5) * (hl + hr));
-        const T r2c = T(0.5) / c;
+        // Roe average: sqrt(h) u = hu / sqrt(h), so one reciprocal square
+        // root per state gives both weights
+        const T rsl = rsqrt_(hl), rsr = rsqrt_(hr);
+        const T w = rcp_(hl * rsl + hr * rsr);
+        const T u = (ql[un] * rsl + qr[un] * rsr) * w;
+        const T v = (ql[ut] * rsl + qr[ut] * rsr) * w;
+        const T gh = g * T(0.5) * (hl + hr);
+        const T rc = rsqrt_(gh);
+        const T c = gh * rc;
+        const T r2c = T(0.5) * rc;
         const T d0 = hr - hl, dn = qr[un] - ql[un], dt = qr[ut] - ql[ut];
         const T a1 = ((u + c) * d0 - dn) * r2c;
         const T a2 = dt - v * d0;
@@ -135,23 +165,27 @@ struct SweRP {
 
         T k0 = tmin0(s[0]), k2 = tmin0(s[2]);
         if (efix) {
-            // 1-wave: speeds of the left state and of ql + W1
-            T lam_l = ql[un] / hl - sqrt(g * hl);
-            T hm = hl + W[0][0];
-            if (hm > T(0)) {
-                T lam_r = (ql[un] + W[0][un]) / hm - sqrt(g * hm);
-                if (lam_l < T(0) && lam_r > T(0)) k0 = (lam_r - s[0]) / (lam_r - lam_l) * lam_l;
-            } else {
-                bad = true;
+            // Harten-Hyman: a nonlinear wave is transonic when the
+            // characteristic speed on its left is negative and on its right
+            // positive.  The signs of u -+ sqrt(g h) are decided without a
+            // square root or division (u < c  <=>  hu <= 0 or (hu)^2 < g h^3);
+            // only a transonic wave pays for the speeds themselves.  A
+            // non-positive intermediate depth leaves the wave unfixed.
+            const T hul = ql[un], hum = ql[un] + W[0][un], hm = hl + W[0][0];
+            const bool l_neg = hul <= T(0) || hul * hul < g * hl * hl * hl;
+            const bool r_pos = hm > T(0) && hum > T(0) && hum * hum > g * hm * hm * hm;
+            if (l_neg && r_pos) {
+                const T lam_l = hul * rcp_(hl) - sqrt_(g * hl);
+                const T lam_r = hum * rcp_(hm) - sqrt_(g * hm);
+                if (lam_l < T(0) && lam_r > T(0)) k0 = (lam_r - s[0]) * rcp_(lam_r - lam_l) * lam_l;
             }
-            // 3-wave: speeds of qr - W3 and of the right state
-            T hm3 = hr - W[2][0];
-            T lr = qr[un] / hr + sqrt(g * hr);
-            if (hm3 > T(0)) {
-                T ll = (qr[un] - W[2][un]) / hm3 + sqrt(g * hm3);
-                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) / (lr - ll) * ll;
-            } else {
-                bad = true;
+            const T hur = qr[un], hun = qr[un] - W[2][un], hn = hr - W[2][0];
+            const bool n_neg = hn > T(0) && hun < T(0) && hun * hun > g * hn * hn * hn;
+            const bool rr_pos = hur >= T(0) || hur * hur < g * hr * hr * hr;
+            if (n_neg && rr_pos) {
+                const T ll = hun * rcp_(hn) + sqrt_(g * hn);
+                const T lr = hur * rcp_(hr) + sqrt_(g * hr);
+                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) * rcp_(lr - ll) * ll;
             }
         }
         const T k1 = tmin0(s[1]);
@@ -192,7 +226,7 @@ struct EulerRP {
     static constexpr bool POSITIVE = true;    // density rho > 0
     T gamma, gm1;
     bool efix;
-    struct Lin { T u, v, H, c, gc2; };
+    struct Lin { T u, v, H, c, rc, gc2; };
 
     __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const
     {
@@ -217,12 +251,39 @@ struct EulerRP {
     {
         constexpr int un = 1 + DIR, ut = 2 - DIR;
         if (!(q[0] > T(0))) return false;
-        T r1 = T(1) / q[0];
+        T r1 = rcp_(q[0]);
         T u = q[un] * r1, v = q[ut] * r1;
         T p = gm1 * (q[3] - T(0.5) * q[0] * (u * u + v * v));
         if (!(p > T(0))) return false;
-        lam = u + sgn * sqrt(gamma * p * r1);
+        lam = u + sgn * sqrt_(gamma * p * r1);
         return true;
+    }
+
+    // gamma (gamma - 1) rho^2 e of a state, with rho e = E - (m^2+n^2)/(2 rho)
+    // (multiplied through by rho); positive iff the state is physical
+    __device__ __forceinline__ T g_rho2e(const T* q) const
+    {
+        return gamma * gm1 * (q[3] * q[0] - T(0.5) * (q[1] * q[1] + q[2] * q[2]));
+    }
+    // u_n < c_K (sgn = false: u - c < 0) or u_n < -c (sgn = true: u + c < 0),
+    // each also requiring a physical state
+    template <int DIR>
+    __device__ __forceinline__ bool slower_than_sound(const T* q, bool plus_side) const
+    {
+        constexpr int un = 1 + DIR;
+        const T e = g_rho2e(q), m = q[un];
+        if (!(q[0] > T(0) && e > T(0))) return false;
+        // plus_side: u + c > 0 <=> m >= 0 or m^2 < e;  else: u - c < 0 <=> m <= 0 or m^2 < e
+        return plus_side ? (m >= T(0) || m * m < e) : (m <= T(0) || m * m < e);
+    }
+    // u - c > 0 (plus_side = true) or u + c < 0 (plus_side = false)
+    template <int DIR>
+    __device__ __forceinline__ bool faster_than_sound(const T* q, bool plus_side) const
+    {
+        constexpr int un = 1 + DIR;
+        const T e = g_rho2e(q), m = q[un];
+        if (!(q[0] > T(0) && e > T(0))) return false;
+        return plus_side ? (m > T(0) && m * m > e) : (m < T(0) && m * m > e);
     }
 
     template <int DIR>
@@ -234,16 +295,17 @@ struct EulerRP {
         bool ok = rl > T(0) && rr > T(0);
         T u = T(0), v = T(0), H = T(0), c2 = T(0);
         if (ok) {
-            const T il = T(1) / rl, ir = T(1) / rr;
-            const T ul = ql[un] * il, vl = ql[ut] * il, ur = qr[un] * ir, vr = qr[ut] * ir;
-            const T pl = gm1 * (ql[3] - T(0.5) * rl * (ul * ul + vl * vl));
-            const T pr = gm1 * (qr[3] - T(0.5) * rr * (ur * ur + vr * vr));
-            const T Hl = (ql[3] + pl) * il, Hr = (qr[3] + pr) * ir;
-            const T sl = sqrt(rl), sr = sqrt(rr);
-            const T w = T(1) / (sl + sr);
-            u = (sl * ul + sr * ur) * w;
-            v = (sl * vl + sr * vr) * w;
-            H = (sl * Hl + sr * Hr) * w;
+            // sqrt(rho) weights from one reciprocal square root per state:
+            // sqrt(rho) u = m / sqrt(rho), sqrt(rho) H = (E + p) / sqrt(rho)
+            const T rsl = rsqrt_(rl), rsr = rsqrt_(rr);
+            const T il = rsl * rsl, ir = rsr * rsr;
+            const T kl = T(0.5) * (ql[un] * ql[un] + ql[ut] * ql[ut]) * il;
+            const T kr = T(0.5) * (qr[un] * qr[un] + qr[ut] * qr[ut]) * ir;
+            const T pl = gm1 * (ql[3] - kl), pr = gm1 * (qr[3] - kr);
+            const T w = rcp_(rl * rsl + rr * rsr);
+            u = (ql[un] * rsl + qr[un] * rsr) * w;
+            v = (ql[ut] * rsl + qr[ut] * rsr) * w;
+            H = ((ql[3] + pl) * rsl + (qr[3] + pr) * rsr) * w;
             c2 = gm1 * (H - T(0.5) * (u * u + v * v));
             ok = c2 > T(0);
         }
@@ -257,15 +319,16 @@ struct EulerRP {
             }
 #pragma unroll
             for (int m = 0; m < NEQ; m++) amdq[m] = apdq[m] = T(0);
-            L.u = L.v = L.H = T(0); L.c = T(1); L.gc2 = T(0);
+            L.u = L.v = L.H = T(0); L.c = T(1); L.rc = T(1); L.gc2 = T(0);
             return;
         }
-        const T c = sqrt(c2);
-        const T gc2 = gm1 / c2;
+        const T rc = rsqrt_(c2);
+        const T c = c2 * rc;
+        const T gc2 = gm1 * rc * rc;
         const T d0 = qr[0] - ql[0], dn = qr[un] - ql[un], dt = qr[ut] - ql[ut], dE = qr[3] - ql[3];
         const T a_sh = dt - v * d0;
         const T a_en = gc2 * ((H - u * u - v * v) * d0 + u * dn + v * dt - dE);
-        const T x = (dn - u * d0) / c;
+        const T x = (dn - u * d0) * rc;
         const T a4 = T(0.5) * (d0 - a_en + x);
         const T a1 = T(0.5) * (d0 - a_en - x);
         W[0][0] = a1; W[0][un] = a1 * (u - c); W[0][ut] = a1 * v; W[0][3] = a1 * (H - u * c);
@@ -275,25 +338,31 @@ struct EulerRP {
         s[0] = u - c;
         s[1] = u;
         s[2] = u + c;
-        L.u = u; L.v = v; L.H = H; L.c = c; L.gc2 = gc2;
+        L.u = u; L.v = v; L.H = H; L.c = c; L.rc = rc; L.gc2 = gc2;
 
         T k0 = tmin0(s[0]), k2 = tmin0(s[2]);
         if (efix) {
+            // Harten-Hyman, with the transonic test free of square roots and
+            // divisions: for a state (rho, m, n, E) with rho e = rho E - (m^2 +
+            // n^2)/2 > 0, u^2 < c^2 <=> m^2 < gamma (gamma-1) rho e.  The
+            // speeds themselves are computed only for a transonic wave; an
+            // intermediate state that is not physical leaves the wave unfixed.
             T qm[NEQ];
-            T ll, lr;
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = ql[m] + W[0][m];
-            if (cspeed<DIR>(ql, T(-1), ll) && cspeed<DIR>(qm, T(-1), lr)) {
-                if (ll < T(0) && lr > T(0)) k0 = (lr - s[0]) / (lr - ll) * ll;
-            } else {
-                bad = true;
+            if (slower_than_sound<DIR>(ql, false) && faster_than_sound<DIR>(qm, true)) {
+                T ll, lr;
+                if (cspeed<DIR>(ql, T(-1), ll) && cspeed<DIR>(qm, T(-1), lr) && ll < T(0) &&
+                    lr > T(0))
+                    k0 = (lr - s[0]) * rcp_(lr - ll) * ll;
             }
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = qr[m] - W[2][m];
-            if (cspeed<DIR>(qm, T(1), ll) && cspeed<DIR>(qr, T(1), lr)) {
-                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) / (lr - ll) * ll;
-            } else {
-                bad = true;
+            if (faster_than_sound<DIR>(qm, false) && slower_than_sound<DIR>(qr, true)) {
+                T ll, lr;
+                if (cspeed<DIR>(qm, T(1), ll) && cspeed<DIR>(qr, T(1), lr) && ll < T(0) &&
+                    lr > T(0))
+                    k2 = (lr - s[2]) * rcp_(lr - ll) * ll;
             }
         }
         const T k1 = tmin0(s[1]);
@@ -311,7 +380,7 @@ struct EulerRP {
         const T u = L.v, v = L.u, c = L.c, H = L.H;   // u: normal to the split direction
         const T b_sh = a[vt] - v * a[0];
         const T b_en = L.gc2 * ((H - u * u - v * v) * a[0] + u * a[vn] + v * a[vt] - a[3]);
-        const T x = (a[vn] - u * a[0]) / c;
+        const T x = (a[vn] - u * a[0]) * L.rc;
         const T b4 = T(0.5) * (a[0] - b_en + x);
         const T b1 = T(0.5) * (a[0] - b_en - x);
         const T l1 = u - c, l2 = u, l4 = u + c;

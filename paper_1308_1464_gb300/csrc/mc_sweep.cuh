@@ -68,7 +68,7 @@ template <typename T>
 __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
 {
     if (!(dr > T(0))) return T(0);
-    const T th = dl / dr;
+    const T th = dl * rcp_(dr);
     if (lim == 1) return fmax(T(0), fmin(T(1), th));
     if (lim == 4) return fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
     return T(1);

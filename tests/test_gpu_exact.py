@@ -1,0 +1,126 @@
+"""GPU parity of the exact Euler Riemann solver (mc_riemann_exact) against the
+oracle's solver, for every plain seed, the learned seed with an untrained
+network (exercising the fallback), and a sampled full-size batch of 2^24
+interfaces in the benchmark's launch configuration."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1308_1464_gb300 as mc
+from paper_1308_1464_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+GAMMA = 1.4
+ORACLE_SEED = {mc.SEED_ADAPTIVE: oracle.SEED_ADAPTIVE, mc.SEED_PV: oracle.SEED_PV,
+               mc.SEED_TR: oracle.SEED_TR, mc.SEED_TS: oracle.SEED_TS,
+               mc.SEED_PVTR: oracle.SEED_PVTR}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1308_1464_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def gpu_solve(states32, seed_mode=mc.SEED_ADAPTIVE, net=None, tol=1e-8, max_iter=30):
+    n = states32[0].size
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in states32]
+    ps = torch.empty(n, dtype=torch.float32, device="cuda")
+    us = torch.empty_like(ps)
+    it = torch.empty(n, dtype=torch.uint8, device="cuda")
+    fl = torch.empty_like(it)
+    stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+    mc.riemann_exact(n, GAMMA, [d.data_ptr() for d in dev], ps.data_ptr(), us.data_ptr(),
+                     it.data_ptr(), fl.data_ptr(), seed_mode, net, tol, max_iter, stats.data_ptr())
+    torch.cuda.synchronize()
+    return (ps.cpu().numpy(), us.cpu().numpy(), it.cpu().numpy().astype(np.int32),
+            fl.cpu().numpy().astype(np.int32), stats.cpu().numpy())
+
+
+def f32_states(n, seed, offset=0):
+    return [a.astype(np.float32) for a in workloads.riemann_states(n, seed=seed, offset=offset)]
+
+
+def compare(states32, ps, us, it, fl, ref):
+    ps_r, us_r, it_r, fl_r = ref
+    np.testing.assert_array_equal(fl & mc.RS_VACUUM, fl_r & oracle.RS_VACUUM)
+    ok = (fl_r & oracle.RS_VACUUM) == 0
+    assert ok.sum() > 0
+    # FP64 iterates on both sides; outputs are rounded to FP32
+    np.testing.assert_allclose(ps[ok], ps_r[ok].astype(np.float32), rtol=3e-7, atol=0)
+    scale = 1.0 + np.abs(us_r[ok])
+    assert np.all(np.abs(us[ok] - us_r[ok]) <= 1e-6 * scale)
+    assert np.all(ps[~ok] == 0.0) and np.all(np.isnan(us[~ok]))
+    d = np.abs(it[ok] - it_r[ok])
+    assert d.max() <= 1 and (d == 0).mean() >= 0.99, (d.max(), (d == 0).mean())
+
+
+@pytest.mark.parametrize("mode", [mc.SEED_ADAPTIVE, mc.SEED_PV, mc.SEED_TR, mc.SEED_TS,
+                                  mc.SEED_PVTR])
+def test_plain_seeds_match_oracle(mode):
+    st = f32_states(20011, seed=21)
+    ps, us, it, fl, stats = gpu_solve(st, mode)
+    ref = oracle.exact_batch(GAMMA, *[a.astype(np.float64) for a in st], seed_mode=ORACLE_SEED[mode])
+    compare(st, ps, us, it, fl, ref)
+    n = st[0].size
+    assert stats[0] == n
+    assert stats[1] == int(((fl & mc.RS_VACUUM) != 0).sum())
+    assert stats[3] == int(((fl & mc.RS_NOCONV) != 0).sum())
+    assert stats[4] == int(it.sum()) and stats[5] == int(it.max())
+
+
+def test_vacuum_criterion_and_edge_cases():
+    # vacuum by construction, tiny and ragged sizes
+    for n in (1, 31, 33, 100):
+        st = f32_states(n, seed=n)
+        ps, us, it, fl, _ = gpu_solve(st)
+        r = [a.astype(np.float64) for a in st]
+        cl, cr = np.sqrt(GAMMA * r[2] / r[0]), np.sqrt(GAMMA * r[5] / r[3])
+        vac = 2.0 / (GAMMA - 1.0) * (cl + cr) <= r[4] - r[1]
+        np.testing.assert_array_equal((fl & mc.RS_VACUUM) != 0, vac)
+        assert np.all(it[vac] == 0)
+
+
+def test_learned_seed_with_untrained_network_falls_back():
+    """Random weights: bad proposals fall back to the plain seed; p* agrees."""
+    rng = np.random.default_rng(3)
+    params = np.zeros(mc.MLP_NPARAM, dtype=np.float32)
+    params[: mc.MLP_NWEIGHT] = rng.normal(scale=0.5, size=mc.MLP_NWEIGHT)
+    params[:16 * 64].reshape(16, 64)[10:] = 0.0
+    params[mc.MLP_NWEIGHT + 10:] = 1.0    # sigma
+    net = mc.SeedNet()
+    net.set_params(params.ctypes.data)
+    st = f32_states(8000, seed=4)
+    ps_m, us_m, it_m, fl_m, stats = gpu_solve(st, mc.SEED_MLP, net)
+    ps_p, us_p, it_p, fl_p, _ = gpu_solve(st, mc.SEED_ADAPTIVE)
+    ok = (fl_p & mc.RS_VACUUM) == 0
+    np.testing.assert_array_equal(fl_m & mc.RS_VACUUM, fl_p & mc.RS_VACUUM)
+    # the same root to within the convergence tolerance: equal or one FP32 ulp
+    np.testing.assert_allclose(ps_m[ok], ps_p[ok], rtol=1.2e-7, atol=0)
+    assert stats[2] == int(((fl_m & mc.RS_FALLBACK) != 0).sum())
+    # fallback rows count the wasted updates too
+    fb = ok & ((fl_m & mc.RS_FALLBACK) != 0)
+    assert np.all(it_m[fb] >= it_p[fb])
+
+
+def test_full_size_sampled():
+    """2^24 interfaces (the benchmark's batch), adaptive seed; 20000 sampled
+    interfaces recomputed by the oracle, flags checked everywhere."""
+    n = 1 << 24
+    st = f32_states(n, seed=1308)
+    ps, us, it, fl, stats = gpu_solve(st)
+    r = [a.astype(np.float64) for a in st]
+    cl, cr = np.sqrt(GAMMA * r[2] / r[0]), np.sqrt(GAMMA * r[5] / r[3])
+    vac = 2.0 / (GAMMA - 1.0) * (cl + cr) <= r[4] - r[1]
+    np.testing.assert_array_equal((fl & mc.RS_VACUUM) != 0, vac)
+    idx = np.random.default_rng(0).choice(n, 20000, replace=False)
+    sub = [a[idx] for a in st]
+    ref = oracle.exact_batch(GAMMA, *[a.astype(np.float64) for a in sub])
+    compare(sub, ps[idx], us[idx], it[idx], fl[idx], ref)
+    assert stats[0] == n and stats[3] == 0
