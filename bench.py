@@ -256,6 +256,8 @@ def main():
     ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
+                    help="profiling aid: run K stand-alone fused steps (mc_step) and exit")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -286,6 +288,13 @@ def main():
     sh = stream.cuda_stream
     smax0 = ctx.max_cell_speed(a.ptr, sh)
     dt0 = wl["cfl"] / smax0
+    if args.kernel_only:
+        for _ in range(args.kernel_only):
+            ctx.step(a.ptr, b.ptr, dt0, want_smax=False, stream=sh)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": args.kernel_only, "workload": wl["desc"]}))
+        ctx.close()
+        return
 
     # warm-up (also builds the cached step graphs)
     t_sim, dt, inb, _ = ctx.advance(a.ptr, b.ptr, args.warmup, wl["cfl"], 1.0, 0.0, dt0, sh)

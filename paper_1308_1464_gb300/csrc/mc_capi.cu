@@ -186,8 +186,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 struct MapEntry {
     const void* ptr;
-    CUtensorMap map;
+    int slot;      // index in the context's device array of tensor maps
 };
+constexpr int MAP_SLOTS = 16;
 
 struct GraphEntry {
     const void* qa;
@@ -206,17 +207,28 @@ struct mc_ctx {
     mc_layout lay;
     int tile_rows;
     DevState* dev;                 // device scratch: time-step scalars and status
+    CUtensorMap* dmaps;            // device array of MAP_SLOTS tensor maps
     cudaStream_t capture;          // private stream used to capture graphs
     EncodeTiledFn encode;
     std::vector<MapEntry> maps;
     std::vector<GraphEntry> graphs;
+    int next_slot;
 };
 
+static void drop_graphs(mc_ctx* c)
+{
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+// Device pointer to the tensor map of state buffer q; a buffer seen for the
+// first time gets its map encoded on the host and copied (synchronously)
+// into a slot of the context's device array.
 static mc_status get_map(mc_ctx* c, const void* q, const CUtensorMap** out)
 {
     for (auto& e : c->maps)
         if (e.ptr == q) {
-            *out = &e.map;
+            *out = c->dmaps + e.slot;
             return MC_OK;
         }
     if (reinterpret_cast<uintptr_t>(q) % 16 != 0)
@@ -228,17 +240,27 @@ static mc_status get_map(mc_ctx* c, const void* q, const CUtensorMap** out)
     cuuint32_t box[3] = {(cuuint32_t)box_w(es), (cuuint32_t)stage_rows(es),
                          (cuuint32_t)c->lay.meqn};
     cuuint32_t estr[3] = {1, 1, 1};
-    MapEntry e;
-    e.ptr = q;
-    CUresult r = c->encode(&e.map,
+    CUtensorMap host_map;
+    CUresult r = c->encode(&host_map,
                            es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                            3, const_cast<void*>(q), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(MC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    if (c->maps.size() >= 16) c->maps.erase(c->maps.begin());
+    MapEntry e{q, 0};
+    if ((int)c->maps.size() >= MAP_SLOTS) {
+        // reuse the oldest slot; cached graphs may point at it
+        e.slot = c->maps.front().slot;
+        c->maps.erase(c->maps.begin());
+        drop_graphs(c);
+    } else {
+        e.slot = c->next_slot++;
+    }
+    cudaError_t ce = cudaMemcpy(c->dmaps + e.slot, &host_map, sizeof(CUtensorMap),
+                                cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_error(ce, "uploading a tensor map");
     c->maps.push_back(e);
-    *out = &c->maps.back().map;
+    *out = c->dmaps + e.slot;
     return MC_OK;
 }
 
@@ -293,10 +315,17 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
         delete c;
         return cuda_error(e, "cudaMalloc(device state)");
     }
+    e = cudaMalloc(&c->dmaps, sizeof(CUtensorMap) * MAP_SLOTS);
+    if (e != cudaSuccess) {
+        cudaFree(c->dev);
+        delete c;
+        return cuda_error(e, "cudaMalloc(tensor maps)");
+    }
     e = cudaMemset(c->dev, 0, sizeof(DevState));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = sweep_prepare(c->p);
     if (e != cudaSuccess) {
+        cudaFree(c->dmaps);
         cudaFree(c->dev);
         delete c;
         return cuda_error(e, "context set-up");
@@ -306,6 +335,7 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
     e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
         cudaStreamDestroy(c->capture);
+        cudaFree(c->dmaps);
         cudaFree(c->dev);
         delete c;
         return set_error(MC_ECUDA, "driver entry point cuTensorMapEncodeTiled unavailable");
@@ -318,8 +348,9 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
 mc_status mc_destroy(mc_ctx* c)
 {
     if (!c) return MC_OK;
-    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    drop_graphs(c);
     cudaStreamDestroy(c->capture);
+    cudaFree(c->dmaps);
     cudaFree(c->dev);
     delete c;
     return MC_OK;
@@ -330,10 +361,7 @@ mc_status mc_set_tile_rows(mc_ctx* c, int rows)
     if (!c) return set_error(MC_EINVAL, "context is NULL");
     if (rows == 0) rows = default_tile_rows(c->p);
     if (rows < 1 || rows > 4096) return set_error(MC_EINVAL, "tile rows %d out of range", rows);
-    if (rows != c->tile_rows) {
-        for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
-        c->graphs.clear();
-    }
+    if (rows != c->tile_rows) drop_graphs(c);
     c->tile_rows = rows;
     return MC_OK;
 }
@@ -383,6 +411,8 @@ static mc_status read_status(mc_ctx* c, DevState* h, cudaStream_t s)
     cudaError_t e = cudaMemcpyAsync(h, c->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_error(e, "reading device state");
+    if (h->status & ST_BADARG)
+        return set_error(MC_EINVAL, "the fused step found a misaligned tensor map or box");
     if (h->status & ST_TIMEOUT) return set_error(MC_ETIMEOUT, "a bounded device wait gave up");
     if (h->status & ST_NONPHYS)
         return set_error(MC_ENONPHYS, "non-physical state (depth/density <= 0 or NaN) met");

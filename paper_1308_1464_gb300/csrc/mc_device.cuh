@@ -10,7 +10,7 @@
 namespace mc {
 
 // bits of the device status word
-enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2, ST_CFL = 4 };
+enum : int { ST_NONPHYS = 1, ST_TIMEOUT = 2, ST_CFL = 4, ST_BADARG = 8 };
 
 // A bounded wait gives up after this many SM clock cycles (about 1 s at
 // the GB300 boost clock); nothing in a healthy run comes near it.
@@ -83,6 +83,16 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
         " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
+}
+
+// A tensor map written to global memory through the generic proxy (a host
+// copy) must be acquired by the tensormap proxy before a TMA instruction
+// reads it.
+__device__ __forceinline__ void acquire_tensormap(const CUtensorMap* map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(map))
+                 : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map)

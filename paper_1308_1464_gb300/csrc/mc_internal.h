@@ -15,7 +15,7 @@ struct DevState;
 struct SweepLaunch {
     mc_problem prob;
     mc_layout lay;
-    const CUtensorMap* map_a;
+    const CUtensorMap* map_a;  // device pointers to 64-byte aligned tensor maps
     const CUtensorMap* map_b;
     void* qa;
     void* qb;

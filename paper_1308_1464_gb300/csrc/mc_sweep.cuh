@@ -74,10 +74,12 @@ __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
     return T(1);
 }
 
+// The tensor maps of the two state buffers live in device global memory
+// (64-byte aligned, written by the host before the launch); the kernel takes
+// plain pointers to them.
 template <class RP>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32)
-    ctu_sweep_kernel(const __grid_constant__ CUtensorMap map_a,
-                     const __grid_constant__ CUtensorMap map_b, const SweepArgs<RP> a)
+    ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
 {
     using T = typename RP::real;
     constexpr int N = RP::NEQ, NW = RP::NW;
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     unsigned char* ring = smem + 128 + warp * NSTAGE * SB;
 
     const int cur = a.cur ? *a.cur : 0;
-    const CUtensorMap* map = cur ? &map_b : &map_a;
+    const CUtensorMap* map = cur ? map_b : map_a;
     const T* __restrict__ qin = cur ? a.qb : a.qa;
     T* __restrict__ qout = cur ? a.qa : a.qb;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     if (lane == 0) {
         for (int s = 0; s < NSTAGE; s++) mbar_init(&bars[s], 1);
         fence_mbar_init();
+        acquire_tensormap(map);
         prefetch_tensormap(map);
     }
     __syncwarp();
@@ -114,7 +117,13 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     bool bad = false;     // non-physical input seen by a valid lane
     T smx = T(0), smy = T(0);
 
-    for (int task = blockIdx.x * SWEEP_WARPS + warp; task < a.ntasks && !failed;
+    // TMA preconditions, checked instead of trusted: a 64-byte aligned map
+    // and (below) a 16-byte aligned box start; a violation is reported in the
+    // status word and the work is skipped
+    const bool map_ok = (reinterpret_cast<uintptr_t>(map) & 63) == 0;
+    if (!map_ok && lane == 0) atomicOr(a.status, ST_BADARG);
+
+    for (int task = blockIdx.x * SWEEP_WARPS + warp; task < a.ntasks && !failed && map_ok;
          task += gridDim.x * SWEEP_WARPS) {
         const int band = task % a.nbands;
         const int i0 = band * BAND_W;
@@ -129,6 +138,10 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
         const int sx = lane + 1 + int(gx - box_x);     // smem column of c; c-1 is sx-1
         const int rbase = j0 - 2;
         const int nfill = (jend + 1 - rbase + RS) / RS;
+        if ((box_x * ES) % 16 != 0 || box_x < 0) {
+            if (lane == 0) atomicOr(a.status, ST_BADARG);
+            break;
+        }
 
         // start the ring
         if (lane == 0) {

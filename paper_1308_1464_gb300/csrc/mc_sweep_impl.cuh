@@ -36,7 +36,7 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
     int blocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
-    ctu_sweep_kernel<RP><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(*L.map_a, *L.map_b, a);
+    ctu_sweep_kernel<RP><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
     return cudaGetLastError();
 }
 
