@@ -90,6 +90,7 @@ def lib():
         L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
         L.mc_step.argtypes = [_VP, _VP, _VP, ctypes.c_double, _DP, _VP]
         L.mc_sweep.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP]
+        L.mc_step_noalloc.argtypes = [P, _VP, _VP, ctypes.c_double, _DP, _VP]
         L.mc_max_cell_speed.argtypes = [_VP, _VP, _DP, _VP]
         L.mc_advance.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  _DP, _DP, _IP, _IP, _VP]
@@ -290,3 +291,12 @@ def riemann_exact(n: int, gamma: float, states, p_star: int, u_star: int, iters:
                                  _VP(flags) if flags else None, int(seed_mode),
                                  net.handle if net is not None else None, float(tol),
                                  int(max_iter), _VP(stats) if stats else None, _VP(stream)))
+
+
+def step_noalloc(problem: Problem, q_in: int, q_out: int, dt: float, want_smax: bool = True,
+                 stream: int = 0):
+    """mc_step_noalloc: one step without a context, allocating no device memory."""
+    smax = ctypes.c_double(0.0)
+    check(lib().mc_step_noalloc(ctypes.byref(problem), _VP(q_in), _VP(q_out), float(dt),
+                                ctypes.byref(smax) if want_smax else None, _VP(stream)))
+    return smax.value if want_smax else None
