@@ -186,6 +186,50 @@ mc_status mc_advance_host(mc_ctx* ctx, const void* host_q0, void* host_q, void* 
                           double* dt_inout, int* nrejected, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Batched uneven patches.
+ *
+ * The paper's execution model lets larger threads schedule pieces of work to
+ * finer-grained ones, and lets each refined grid manage its own time step
+ * ("local precision with minimal effects to global time stepping", §1.2,
+ * Table 1 "dynamic time stepping").  A batch is a set of independent patches
+ * of one problem kind (proto: solver, dtype, limiter, order, transverse, efix,
+ * param; all four boundaries must be MC_BC_WALL), each with its own size and
+ * spacing and two caller-owned device buffers in the layout mc_layout_of
+ * gives for that size.  Each patch advances with its own dt = cfl / smax,
+ * smax taken from the patch's previous step (from its initial cell speeds for
+ * the first step); there is no reject/retake in this form.
+ * ------------------------------------------------------------------------ */
+typedef struct mc_patch {
+    int32_t mx, my;      /* interior cells, each >= 4 */
+    double dx, dy;
+    void* qa;            /* device state holding the initial data (interior) */
+    void* qb;            /* device state, scratch of the ping-pong */
+} mc_patch;
+typedef struct mc_batch mc_batch;
+
+/* Validates the patches, builds their tensor maps and work tables (device
+ * memory owned by the batch).  Synchronous. */
+mc_status mc_batch_create(const mc_problem* proto, const mc_patch* patches, int32_t npatch,
+                          mc_batch** out);
+mc_status mc_batch_destroy(mc_batch* b);
+/* Rows per warp task for every patch (the per-patch work split); results do
+ * not depend on it.  The autotuner sets it. */
+mc_status mc_batch_set_tile_rows(mc_batch* b, const int32_t* rows);
+/* Advances every patch nsteps steps in ONE persistent launch captured in a
+ * CUDA graph (with the initial ghost fill and cell-speed pass before it): a
+ * global counter hands out (step, patch, task) items in step order; a task
+ * waits (bounded, MC_ETIMEOUT) for the previous step of its patch; tasks write
+ * the ghost cells of the next step themselves.  Result in qa if nsteps is even
+ * (*result_in_b = 0), else qb.  t_out (host, npatch, nullable) gets each
+ * patch's elapsed time.  Synchronous. */
+mc_status mc_batch_advance(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
+                           int* result_in_b, void* stream);
+/* The same computation as one launch per patch per step (dt, ghost fill and
+ * fused step per patch), for comparison; bitwise equal interiors. */
+mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
+                                 int* result_in_b, void* stream);
+
+/* ------------------------------------------------------------------------
  * Exact Euler Riemann solver with a learned pressure seed.
  *
  * The paper lists Euler among its Riemann kernels (§3, Tables 2-3) and keeps

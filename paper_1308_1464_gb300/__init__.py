@@ -105,6 +105,11 @@ def lib():
         L.mc_mlp_grad.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP]
         L.mc_mlp_train.argtypes = [_VP, ctypes.c_int64, _VP, _VP, ctypes.POINTER(TrainCfg),
                                    _VP, _VP]
+        L.mc_batch_create.argtypes = [P, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_VP)]
+        L.mc_batch_destroy.argtypes = [_VP]
+        L.mc_batch_set_tile_rows.argtypes = [_VP, ctypes.c_void_p]
+        for fn in (L.mc_batch_advance, L.mc_batch_advance_plain):
+            fn.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, _IP, _VP]
         L.mc_riemann_exact.argtypes = [ctypes.c_int64, ctypes.c_double] + [_VP] * 10 + [
             ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int, _VP, _VP]
         _lib = L
@@ -300,3 +305,53 @@ def step_noalloc(problem: Problem, q_in: int, q_out: int, dt: float, want_smax: 
     check(lib().mc_step_noalloc(ctypes.byref(problem), _VP(q_in), _VP(q_out), float(dt),
                                 ctypes.byref(smax) if want_smax else None, _VP(stream)))
     return smax.value if want_smax else None
+
+
+# ---------------------------------------------------------------- batched patches
+
+class PatchC(ctypes.Structure):
+    _fields_ = [("mx", ctypes.c_int32), ("my", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("qa", ctypes.c_void_p), ("qb", ctypes.c_void_p)]
+
+
+class Batch:
+    """Uneven wall-bounded patches advanced together (mc_batch_*).  patches:
+    sequence of (mx, my, dx, dy, qa_ptr, qb_ptr)."""
+
+    def __init__(self, proto: Problem, patches):
+        L = lib()
+        arr = (PatchC * len(patches))(*[PatchC(int(mx), int(my), float(dx), float(dy), int(qa),
+                                               int(qb)) for (mx, my, dx, dy, qa, qb) in patches])
+        h = _VP()
+        check(L.mc_batch_create(ctypes.byref(proto), arr, len(patches), ctypes.byref(h)))
+        self._h = h
+        self.npatch = len(patches)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile_rows(self, rows) -> None:
+        arr = (ctypes.c_int32 * self.npatch)(*[int(r) for r in rows])
+        check(lib().mc_batch_set_tile_rows(self._h, arr))
+
+    def _run(self, fn, nsteps, cfl, want_t, stream):
+        t = (ctypes.c_double * self.npatch)() if want_t else None
+        inb = ctypes.c_int(0)
+        check(fn(self._h, int(nsteps), float(cfl), t, ctypes.byref(inb), _VP(stream)))
+        return (list(t) if want_t else None), bool(inb.value)
+
+    def advance(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
+        """One persistent launch in a graph -> (t per patch or None, result_in_b)."""
+        return self._run(lib().mc_batch_advance, nsteps, cfl, want_t, stream)
+
+    def advance_plain(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
+        """One launch per patch per step -> (t per patch or None, result_in_b)."""
+        return self._run(lib().mc_batch_advance_plain, nsteps, cfl, want_t, stream)

@@ -1,0 +1,204 @@
+// mc_batch.cuh -- many uneven patches advanced together in one persistent
+// launch (batched form of the fused step).
+//
+// The paper motivates this with its execution model (§1.2): larger threads
+// schedule pieces of work to finer-grained ones, and each refined grid keeps
+// its own time step ("local precision with minimal effects to global time
+// stepping"; Table 1, dynamic time stepping).  Here every patch is an
+// independent grid with reflecting walls and its own dt = cfl / smax of its
+// previous step.  Work items are (step, patch, task) in step-major order,
+// handed out by one global counter; a task of step s waits (bounded) until all
+// tasks of step s-1 of its patch are done, which also makes the ping-pong
+// buffers safe to overwrite.  Because items are taken in increasing order,
+// every item a task waits for was taken earlier by a running warp, so the
+// scheme cannot deadlock whatever the grid size.  Ghost cells of the next
+// step are written by the tasks themselves (wall epilogue of sweep_task).
+#pragma once
+
+#include "mc_sweep.cuh"
+
+namespace mc {
+
+constexpr int BC_WALL_KIND = 2;   // reflecting wall in bc_map's numbering
+
+struct PatchDesc {
+    void* qa;
+    void* qb;
+    long long ld_x, ld_field;
+    double dx, dy;
+    int mx, my, nbands, tile_rows, ntasks, pad;
+};
+
+template <class RP>
+struct BatchArgs {
+    RP rp;
+    const PatchDesc* patches;
+    const CUtensorMap* maps;        // two per patch: [2p] of qa, [2p + 1] of qb
+    const long long* prefix;        // npatch + 1 cumulative task counts
+    int npatch, nsteps;
+    long long tasks_per_step;
+    long long x_offset;
+    double cfl;
+    int limiter, order, transverse;
+    unsigned long long* smax;       // npatch x (nsteps + 1): [p][0] initial cell speeds, [p][s+1] step s
+    double* dt_used;                // npatch x nsteps
+    unsigned int* done;             // npatch: tasks completed so far
+    unsigned long long* next_item;  // work counter
+    int* status;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Bounded wait until *counter >= target (acquire); false after WAIT_CYCLES.
+__device__ __forceinline__ bool wait_counter(const unsigned* counter, unsigned target)
+{
+    if (ld_acquire_u32(counter) >= target) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (ld_acquire_u32(counter) < target) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+    return true;
+}
+
+template <class RP>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const BatchArgs<RP> a)
+{
+    using T = typename RP::real;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    WarpRing W = warp_ring(smem, sizeof(T), RP::NEQ);
+    const bool second = a.order >= 2, trans = a.transverse != 0;
+    const long long total = (long long)a.nsteps * a.tasks_per_step;
+    const int stride = a.nsteps + 1;
+    bool failed = false, bad = false;
+
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(a.next_item, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int s = int(item / a.tasks_per_step);
+        const long long r = item - (long long)s * a.tasks_per_step;
+        int lo = 0, hi = a.npatch;   // prefix[lo] <= r < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (a.prefix[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        const int p = lo;
+        const int t = int(r - a.prefix[p]);
+        const PatchDesc d = a.patches[p];
+        if (s > 0) {
+            int ok = 1;
+            if (lane == 0) ok = wait_counter(&a.done[p], unsigned(s) * unsigned(d.ntasks));
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+        }
+        // the previous step's stores (generic proxy, acquired above) must be
+        // visible to this task's TMA reads (async proxy)
+        fence_proxy_async_global();
+        const double sprev = __longlong_as_double((long long)__ldcg(&a.smax[(long long)p * stride + s]));
+        const double dt = sprev > 0.0 ? a.cfl / sprev : 0.0;
+        const int cur = s & 1;
+        const CUtensorMap* map = a.maps + 2 * p + cur;
+        T* qout = static_cast<T*>(cur ? d.qa : d.qb);
+        if ((reinterpret_cast<uintptr_t>(map) & 63) != 0) {
+            if (lane == 0) atomicOr(a.status, ST_BADARG);
+            failed = true;
+            break;
+        }
+        if (lane == 0) acquire_tensormap(map);
+        __syncwarp();
+        const int i0 = (t % d.nbands) * BAND_W;
+        const int j0 = (t / d.nbands) * d.tile_rows;
+        const int jend = min(j0 + d.tile_rows, d.my);
+        T smx = T(0), smy = T(0);
+        if (!sweep_task<RP, true>(a.rp, map, qout, d.mx, d.my, d.ld_x, d.ld_field, a.x_offset, i0,
+                                  j0, jend, T(dt / d.dx), T(dt / d.dy), a.limiter, second, trans,
+                                  W, bad, smx, smy, a.status)) {
+            failed = true;
+            break;
+        }
+        double v = fmax(double(smx) / d.dx, double(smy) / d.dy);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) {
+            atomic_max_nonneg(&a.smax[(long long)p * stride + s + 1], v);
+            if (t == 0) a.dt_used[(long long)p * a.nsteps + s] = dt;
+            __threadfence();
+            atomicAdd(&a.done[p], 1u);
+        }
+        __syncwarp();
+    }
+    if (failed) {
+        drain_ring(W);
+        if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);
+}
+
+// Initial ghost fill (walls) and cell-speed maximum of every patch: one
+// block per patch.
+template <class RP>
+__global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long long x_offset,
+                                  int stride, unsigned long long* smax)
+{
+    using T = typename RP::real;
+    const PatchDesc d = patches[blockIdx.x];
+    T* q = static_cast<T*>(d.qa);
+    // ghosts: x of interior rows, then y over the full width (corners)
+    const long long W = d.mx + 4;
+    const long long nghost = 4 * W + 4LL * d.my;
+    for (long long g = threadIdx.x; g < nghost; g += blockDim.x) {
+        int i, j;
+        if (g < 4 * W) {
+            const int jr = int(g / W);
+            j = jr < 2 ? jr - 2 : d.my + jr - 2;
+            i = int(g % W) - 2;
+        } else {
+            const long long u = g - 4 * W;
+            j = int(u / 4);
+            const int ir = int(u % 4);
+            i = ir < 2 ? ir - 2 : d.mx + ir - 2;
+        }
+        bool fx = false, fy = false;
+        const int si = bc_map(i, d.mx, BC_WALL_KIND, BC_WALL_KIND, fx);
+        const int sj = bc_map(j, d.my, BC_WALL_KIND, BC_WALL_KIND, fy);
+        for (int m = 0; m < RP::NEQ; m++) {
+            T v = q[m * d.ld_field + (long long)(sj + 2) * d.ld_x + x_offset + si];
+            if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
+            q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i] = v;
+        }
+    }
+    double v = 0.0;
+    const long long n = (long long)d.mx * d.my;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+        const int i = int(k % d.mx), j = int(k / d.mx);
+        T qq[RP::NEQ];
+        for (int m = 0; m < RP::NEQ; m++) qq[m] = q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i];
+        T sx, sy;
+        rp.cell_speeds(qq, sx, sy);
+        v = fmax(v, fmax(double(sx) / d.dx, double(sy) / d.dy));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&smax[(long long)blockIdx.x * stride], v);
+}
+
+}  // namespace mc

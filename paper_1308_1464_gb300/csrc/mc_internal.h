@@ -54,3 +54,39 @@ mc_status set_error(mc_status st, const char* fmt, ...);
 mc_status cuda_error(cudaError_t e, const char* what);
 
 }  // namespace mc
+
+namespace mc {
+
+struct PatchDesc;
+
+// One launch of the batched persistent step (mc_batch.cu builds it).
+struct BatchLaunch {
+    mc_problem proto;
+    const PatchDesc* patches;
+    const CUtensorMap* maps;
+    const long long* prefix;
+    int npatch, nsteps;
+    long long tasks_per_step;
+    long long x_offset;
+    double cfl;
+    unsigned long long* smax;
+    double* dt_used;
+    unsigned int* done;
+    unsigned long long* next_item;
+    int* status;
+    int blocks;
+    cudaStream_t stream;
+};
+
+cudaError_t batch_launch_acoustics(const BatchLaunch& L);
+cudaError_t batch_launch_swe(const BatchLaunch& L);
+cudaError_t batch_launch_euler(const BatchLaunch& L);
+cudaError_t batch_init_acoustics(const BatchLaunch& L);
+cudaError_t batch_init_swe(const BatchLaunch& L);
+cudaError_t batch_init_euler(const BatchLaunch& L);
+// resident CTAs per SM of the batched kernel (also raises its smem limit)
+cudaError_t batch_occupancy_acoustics(int dtype, int* ctas);
+cudaError_t batch_occupancy_swe(int dtype, int* ctas);
+cudaError_t batch_occupancy_euler(int dtype, int* ctas);
+
+}  // namespace mc

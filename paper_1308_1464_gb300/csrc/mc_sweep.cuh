@@ -74,12 +74,28 @@ __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
     return T(1);
 }
 
-// The tensor maps of the two state buffers live in device global memory
-// (64-byte aligned, written by the host before the launch); the kernel takes
-// plain pointers to them.
-template <class RP>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32)
-    ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
+// Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage.
+struct WarpRing {
+    uint64_t* bars;
+    unsigned char* ring;
+    uint32_t phase;   // per-stage completion parity
+};
+
+// One warp task: the rows [j0, jend) of the band of columns starting at i0
+// of one grid, read from the state behind `map`, written to qout.  Returns
+// false if a bounded wait gave up.  With WALL_GHOSTS each written cell also
+// writes the ghost cells it is the mirror source of (reflecting walls on all
+// sides: x ghosts negate component 1, y ghosts component 2, corners both), so
+// the next step needs no separate ghost fill.
+template <class RP, bool WALL_GHOSTS>
+__device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
+                                           typename RP::real* __restrict__ qout, int mx, int my,
+                                           long long ld_x, long long ld_field, long long x_offset,
+                                           int i0, int j0, int jend, typename RP::real nux,
+                                           typename RP::real nuy, int limiter, bool second,
+                                           bool trans, WarpRing& W, bool& bad,
+                                           typename RP::real& smx, typename RP::real& smy,
+                                           int* status)
 {
     using T = typename RP::real;
     constexpr int N = RP::NEQ, NW = RP::NW;
@@ -89,257 +105,296 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     constexpr int RS = stage_rows(ES);
     constexpr int SB = stage_bytes(ES, N);
     constexpr int TB = box_bytes(ES, N);
+    const int lane = threadIdx.x & 31;
+    const T hnux = T(0.5) * nux, hnuy = T(0.5) * nuy;
 
+    const int c = i0 - 1 + lane;
+    const bool out_lane = lane >= 1 && lane <= BAND_W && c < mx;
+    const bool xe_lane = c >= 0 && c <= mx;      // x-edge c-1/2 is an interior edge
+    const bool ye_lane = c >= 0 && c < mx;       // y-edges of column c are interior
+    const long long gx = x_offset + i0 - 2;
+    const int box_x = int(gx - ((gx % AL) + AL) % AL);
+    const int sx = lane + 1 + int(gx - box_x);   // smem column of c; c-1 is sx-1
+    const int rbase = j0 - 2;
+    const int nfill = (jend + 1 - rbase + RS) / RS;
+    // TMA precondition, checked instead of trusted: a 16-byte aligned box start
+    if ((box_x * ES) % 16 != 0 || box_x < 0) {
+        if (lane == 0) atomicOr(status, ST_BADARG);
+        return true;
+    }
+
+    // start the ring
+    if (lane == 0) {
+        for (int f = 0; f < NSTAGE && f < nfill; f++) {
+            mbar_arrive_expect_tx(&W.bars[f], TB);
+            tma_load_3d(W.ring + f * SB, map, &W.bars[f], box_x, rbase + f * RS + 2, 0);
+        }
+    }
+
+    // fetch row r of columns c and c-1 into registers
+    auto fetch = [&](int r, T* qc, T* ql) -> bool {
+        const int rel = r - rbase, f = rel / RS, rr = rel - f * RS, st = f % NSTAGE;
+        if (rr == 0) {
+            const bool ok = mbar_wait_bounded(&W.bars[st], (W.phase >> st) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) return false;
+            W.phase ^= 1u << st;
+        }
+        const T* row = reinterpret_cast<const T*>(W.ring + st * SB) + rr * BW;
+#pragma unroll
+        for (int m = 0; m < N; m++) {
+            qc[m] = row[m * RS * BW + sx];
+            ql[m] = row[m * RS * BW + sx - 1];
+        }
+        if (rr == RS - 1) {
+            __syncwarp();
+            const int fn = f + NSTAGE;
+            if (lane == 0 && fn < nfill) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&W.bars[st], TB);
+                tma_load_3d(W.ring + st * SB, map, &W.bars[st], box_x, rbase + fn * RS + 2, 0);
+            }
+        }
+        return true;
+    };
+
+    // carried state (see the header comment for the schedule)
+    T qc0[N], qc1[N], ql1[N];
+    T Wy0[NW][N], Wy1[NW][N], sy0[NW], sy1[NW];
+    T Gprev[N], dqy[N], bp_pend[N], tyP_m[N], tyP_p[N];
+    T apdq0[N], amdq0[N], BpAp0[N], BpAm0[N], F0[N];
+#pragma unroll
+    for (int m = 0; m < N; m++) {
+        qc0[m] = Gprev[m] = dqy[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
+        apdq0[m] = amdq0[m] = BpAp0[m] = BpAm0[m] = F0[m] = T(0);
+    }
+#pragma unroll
+    for (int p = 0; p < NW; p++) {
+        sy0[p] = sy1[p] = T(0);
+#pragma unroll
+        for (int m = 0; m < N; m++) Wy0[p][m] = Wy1[p][m] = T(0);
+    }
+    if (!fetch(rbase, qc1, ql1)) return false;
+
+    for (int k = j0 - 3; k < jend; k++) {
+        T qc2[N], ql2[N];
+        if (!fetch(k + 2, qc2, ql2)) return false;
+
+        // ---- y-edge between rows k+1 and k+2 of column c
+        T Wy2[NW][N], sy2[NW], bm2[N], bp2[N];
+        typename RP::Lin Ly;
+        bool bady = false;
+        rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
+        T TAm[N], TAp[N];   // x-splits of the y-fluctuations entering row k+1
+        T nPm[N], nPp[N];   // ... entering row k+2
+        if (trans) {
+            T t1[N], t2[N];
+            rp.template transverse<1>(Ly, bm2, t1, t2);
+            rp.template transverse<1>(Ly, bp2, nPm, nPp);
+#pragma unroll
+            for (int m = 0; m < N; m++) {
+                TAm[m] = tyP_m[m] + t1[m];
+                TAp[m] = tyP_p[m] + t2[m];
+            }
+        }
+        T dqy_n[N];
+#pragma unroll
+        for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
+        if (ye_lane && k + 2 >= 0 && k + 2 <= my) {
+            bad |= bady;
+#pragma unroll
+            for (int p = 0; p < NW; p++) smy = fmax(smy, fabs(sy2[p]));
+        }
+
+        // ---- x-edge c-1/2 of row k+1
+        T Wx[NW][N], sxw[NW], amdq1[N], apdq1[N];
+        T BmAp1[N], BpAp1[N], BmAm1[N], BpAm1[N];
+        if (k >= j0 - 2) {
+            typename RP::Lin Lx;
+            bool badx = false;
+            rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+            if (trans) {
+                rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
+                rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
+            }
+            if (xe_lane && k + 1 >= 0 && k + 1 < my) {
+                bad |= badx;
+#pragma unroll
+                for (int p = 0; p < NW; p++) smx = fmax(smx, fabs(sxw[p]));
+            }
+        }
+
+        T Fn[N], Gn[N];
+        if (k >= j0 - 1) {
+            // ---- F at x-edge (c-1/2, k+1)
+#pragma unroll
+            for (int m = 0; m < N; m++) Fn[m] = T(0);
+            if (second) {
+#pragma unroll
+                for (int p = 0; p < NW; p++) {
+                    const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
+                    T dl = T(0), dr = T(0);
+#pragma unroll
+                    for (int m = 0; m < N; m++) {
+                        const T wu = shfl(Wx[p][m], src);
+                        dl += wu * Wx[p][m];
+                        dr += Wx[p][m] * Wx[p][m];
+                    }
+                    const T as = fabs(sxw[p]);
+                    const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(limiter, dl, dr);
+#pragma unroll
+                    for (int m = 0; m < N; m++) Fn[m] += cf * Wx[p][m];
+                }
+            }
+            if (trans) {
+#pragma unroll
+                for (int m = 0; m < N; m++) Fn[m] -= hnuy * (TAm[m] + shfl_up1(TAp[m]));
+            }
+            // ---- G at y-edge (c, k+1/2)
+#pragma unroll
+            for (int m = 0; m < N; m++) Gn[m] = T(0);
+            if (second) {
+#pragma unroll
+                for (int p = 0; p < NW; p++) {
+                    const bool upl = sy1[p] > T(0);
+                    T dl = T(0), dr = T(0);
+#pragma unroll
+                    for (int m = 0; m < N; m++) {
+                        const T wu = upl ? Wy0[p][m] : Wy2[p][m];
+                        dl += wu * Wy1[p][m];
+                        dr += Wy1[p][m] * Wy1[p][m];
+                    }
+                    const T as = fabs(sy1[p]);
+                    const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(limiter, dl, dr);
+#pragma unroll
+                    for (int m = 0; m < N; m++) Gn[m] += cf * Wy1[p][m];
+                }
+            }
+            if (trans) {
+#pragma unroll
+                for (int m = 0; m < N; m++)
+                    Gn[m] -= hnux * (BpAp0[m] + BmAp1[m] + shfl_down1(BpAm0[m] + BmAm1[m]));
+            }
+        }
+
+        // ---- cell (c, k)
+        if (k >= j0) {
+            T xr[N];
+#pragma unroll
+            for (int m = 0; m < N; m++) xr[m] = shfl_down1(amdq0[m] + F0[m]);
+            if (out_lane) {
+                T* o = qout + (long long)(k + 2) * ld_x + x_offset + c;
+                T qn[N];
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) -
+                            nuy * (dqy[m] + Gn[m] - Gprev[m]);
+                    o[m * ld_field] = qn[m];
+                }
+                if (RP::POSITIVE) bad |= !(qn[0] > T(0));
+                else bad |= qn[0] != qn[0];
+                if (WALL_GHOSTS) {
+                    const bool hx = c < 2 || c >= mx - 2, hy = k < 2 || k >= my - 2;
+                    const int gi = c < 2 ? -1 - c : 2 * mx - 1 - c;
+                    const int gj = k < 2 ? -1 - k : 2 * my - 1 - k;
+                    T* base = qout + x_offset;
+#pragma unroll
+                    for (int m = 0; m < N; m++) {
+                        if (hx) base[m * ld_field + (long long)(k + 2) * ld_x + gi] = m == 1 ? -qn[m] : qn[m];
+                        if (hy) base[m * ld_field + (long long)(gj + 2) * ld_x + c] = m == 2 ? -qn[m] : qn[m];
+                        if (hx && hy)
+                            base[m * ld_field + (long long)(gj + 2) * ld_x + gi] =
+                                (m == 1 || m == 2) ? -qn[m] : qn[m];
+                    }
+                }
+            }
+        }
+
+        // ---- rotate
+#pragma unroll
+        for (int m = 0; m < N; m++) {
+            qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
+            Gprev[m] = Gn[m];
+            dqy[m] = dqy_n[m];
+            bp_pend[m] = bp2[m];
+            if (trans) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
+            apdq0[m] = apdq1[m]; amdq0[m] = amdq1[m];
+            if (trans) { BpAp0[m] = BpAp1[m]; BpAm0[m] = BpAm1[m]; }
+            F0[m] = Fn[m];
+        }
+#pragma unroll
+        for (int p = 0; p < NW; p++) {
+            sy0[p] = sy1[p]; sy1[p] = sy2[p];
+#pragma unroll
+            for (int m = 0; m < N; m++) { Wy0[p][m] = Wy1[p][m]; Wy1[p][m] = Wy2[p][m]; }
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Bounded drain of the copies still in flight after a failed wait.
+__device__ __forceinline__ void drain_ring(WarpRing& W)
+{
+    for (int s = 0; s < NSTAGE; s++) (void)mbar_wait_bounded(&W.bars[s], (W.phase >> s) & 1u);
+}
+
+__device__ __forceinline__ WarpRing warp_ring(unsigned char* smem, int es, int neq)
+{
+    const int warp = threadIdx.x >> 5;
+    WarpRing W;
+    W.bars = reinterpret_cast<uint64_t*>(smem) + warp * NSTAGE;
+    W.ring = smem + 128 + warp * NSTAGE * stage_bytes(es, neq);
+    W.phase = 0;
+    if ((threadIdx.x & 31) == 0) {
+        for (int s = 0; s < NSTAGE; s++) mbar_init(&W.bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    return W;
+}
+
+// The fused step over one grid.  The tensor maps of the two state buffers
+// live in device global memory (64-byte aligned, written by the host before
+// the launch); the kernel takes plain pointers to them.
+template <class RP>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32)
+    ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
+{
+    using T = typename RP::real;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * NSTAGE;
-    unsigned char* ring = smem + 128 + warp * NSTAGE * SB;
+    WarpRing W = warp_ring(smem, sizeof(T), RP::NEQ);
 
     const int cur = a.cur ? *a.cur : 0;
     const CUtensorMap* map = cur ? map_b : map_a;
-    const T* __restrict__ qin = cur ? a.qb : a.qa;
     T* __restrict__ qout = cur ? a.qa : a.qb;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const T nux = T(dt / a.dx), nuy = T(dt / a.dy);
-    const T hnux = T(0.5) * nux, hnuy = T(0.5) * nuy;
     const bool second = a.order >= 2, trans = a.transverse != 0;
 
-    if (lane == 0) {
-        for (int s = 0; s < NSTAGE; s++) mbar_init(&bars[s], 1);
-        fence_mbar_init();
+    // TMA precondition, checked instead of trusted: a 64-byte aligned map
+    const bool map_ok = (reinterpret_cast<uintptr_t>(map) & 63) == 0;
+    if (!map_ok && lane == 0) atomicOr(a.status, ST_BADARG);
+    if (lane == 0 && map_ok) {
         acquire_tensormap(map);
         prefetch_tensormap(map);
     }
     __syncwarp();
 
-    uint32_t phase = 0;   // per-stage completion parity
-    bool failed = false;
-    bool bad = false;     // non-physical input seen by a valid lane
+    bool failed = false, bad = false;
     T smx = T(0), smy = T(0);
-
-    // TMA preconditions, checked instead of trusted: a 64-byte aligned map
-    // and (below) a 16-byte aligned box start; a violation is reported in the
-    // status word and the work is skipped
-    const bool map_ok = (reinterpret_cast<uintptr_t>(map) & 63) == 0;
-    if (!map_ok && lane == 0) atomicOr(a.status, ST_BADARG);
-
     for (int task = blockIdx.x * SWEEP_WARPS + warp; task < a.ntasks && !failed && map_ok;
          task += gridDim.x * SWEEP_WARPS) {
-        const int band = task % a.nbands;
-        const int i0 = band * BAND_W;
+        const int i0 = (task % a.nbands) * BAND_W;
         const int j0 = (task / a.nbands) * a.tile_rows;
         const int jend = min(j0 + a.tile_rows, a.my);
-        const int c = i0 - 1 + lane;
-        const bool out_lane = lane >= 1 && lane <= BAND_W && c < a.mx;
-        const bool xe_lane = c >= 0 && c <= a.mx;      // x-edge c-1/2 is an interior edge
-        const bool ye_lane = c >= 0 && c < a.mx;       // y-edges of column c are interior
-        const long long gx = a.x_offset + i0 - 2;
-        const int box_x = int(gx - ((gx % AL) + AL) % AL);
-        const int sx = lane + 1 + int(gx - box_x);     // smem column of c; c-1 is sx-1
-        const int rbase = j0 - 2;
-        const int nfill = (jend + 1 - rbase + RS) / RS;
-        if ((box_x * ES) % 16 != 0 || box_x < 0) {
-            if (lane == 0) atomicOr(a.status, ST_BADARG);
-            break;
-        }
-
-        // start the ring
-        if (lane == 0) {
-            for (int f = 0; f < NSTAGE && f < nfill; f++) {
-                mbar_arrive_expect_tx(&bars[f], TB);
-                tma_load_3d(ring + f * SB, map, &bars[f], box_x, rbase + f * RS + 2, 0);
-            }
-        }
-
-        // fetch row r of columns c and c-1 into registers
-        auto fetch = [&](int r, T* qc, T* ql) -> bool {
-            const int rel = r - rbase, f = rel / RS, rr = rel - f * RS, st = f % NSTAGE;
-            if (rr == 0) {
-                const bool ok = mbar_wait_bounded(&bars[st], (phase >> st) & 1u);
-                if (!__all_sync(0xffffffffu, ok)) return false;
-                phase ^= 1u << st;
-            }
-            const T* row = reinterpret_cast<const T*>(ring + st * SB) + rr * BW;
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                qc[m] = row[m * RS * BW + sx];
-                ql[m] = row[m * RS * BW + sx - 1];
-            }
-            if (rr == RS - 1) {
-                __syncwarp();
-                const int fn = f + NSTAGE;
-                if (lane == 0 && fn < nfill) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&bars[st], TB);
-                    tma_load_3d(ring + st * SB, map, &bars[st], box_x, rbase + fn * RS + 2, 0);
-                }
-            }
-            return true;
-        };
-
-        // carried state (see the header comment for the schedule)
-        T qc0[N], qc1[N], ql1[N];
-        T Wy0[NW][N], Wy1[NW][N], sy0[NW], sy1[NW];
-        T Gprev[N], dqy[N], bp_pend[N], tyP_m[N], tyP_p[N];
-        T apdq0[N], amdq0[N], BpAp0[N], BpAm0[N], F0[N];
-#pragma unroll
-        for (int m = 0; m < N; m++) {
-            qc0[m] = Gprev[m] = dqy[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
-            apdq0[m] = amdq0[m] = BpAp0[m] = BpAm0[m] = F0[m] = T(0);
-        }
-#pragma unroll
-        for (int p = 0; p < NW; p++) {
-            sy0[p] = sy1[p] = T(0);
-#pragma unroll
-            for (int m = 0; m < N; m++) Wy0[p][m] = Wy1[p][m] = T(0);
-        }
-        if (!fetch(rbase, qc1, ql1)) { failed = true; break; }
-
-        for (int k = j0 - 3; k < jend; k++) {
-            T qc2[N], ql2[N];
-            if (!fetch(k + 2, qc2, ql2)) { failed = true; break; }
-
-            // ---- y-edge between rows k+1 and k+2 of column c
-            T Wy2[NW][N], sy2[NW], bm2[N], bp2[N];
-            typename RP::Lin Ly;
-            bool bady = false;
-            a.rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
-            T TAm[N], TAp[N];   // x-splits of the y-fluctuations entering row k+1
-            T nPm[N], nPp[N];   // ... entering row k+2
-            if (trans) {
-                T t1[N], t2[N];
-                a.rp.template transverse<1>(Ly, bm2, t1, t2);
-                a.rp.template transverse<1>(Ly, bp2, nPm, nPp);
-#pragma unroll
-                for (int m = 0; m < N; m++) {
-                    TAm[m] = tyP_m[m] + t1[m];
-                    TAp[m] = tyP_p[m] + t2[m];
-                }
-            }
-            T dqy_n[N];
-#pragma unroll
-            for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
-            if (ye_lane && k + 2 >= 0 && k + 2 <= a.my) {
-                bad |= bady;
-#pragma unroll
-                for (int p = 0; p < NW; p++) smy = fmax(smy, fabs(sy2[p]));
-            }
-
-            // ---- x-edge c-1/2 of row k+1
-            T Wx[NW][N], sxw[NW], amdq1[N], apdq1[N];
-            T BmAp1[N], BpAp1[N], BmAm1[N], BpAm1[N];
-            if (k >= j0 - 2) {
-                typename RP::Lin Lx;
-                bool badx = false;
-                a.rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
-                if (trans) {
-                    a.rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
-                    a.rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
-                }
-                if (xe_lane && k + 1 >= 0 && k + 1 < a.my) {
-                    bad |= badx;
-#pragma unroll
-                    for (int p = 0; p < NW; p++) smx = fmax(smx, fabs(sxw[p]));
-                }
-            }
-
-            T Fn[N], Gn[N];
-            if (k >= j0 - 1) {
-                // ---- F at x-edge (c-1/2, k+1)
-#pragma unroll
-                for (int m = 0; m < N; m++) Fn[m] = T(0);
-                if (second) {
-#pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
-                        T dl = T(0), dr = T(0);
-#pragma unroll
-                        for (int m = 0; m < N; m++) {
-                            const T wu = shfl(Wx[p][m], src);
-                            dl += wu * Wx[p][m];
-                            dr += Wx[p][m] * Wx[p][m];
-                        }
-                        const T as = fabs(sxw[p]);
-                        const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(a.limiter, dl, dr);
-#pragma unroll
-                        for (int m = 0; m < N; m++) Fn[m] += cf * Wx[p][m];
-                    }
-                }
-                if (trans) {
-#pragma unroll
-                    for (int m = 0; m < N; m++) Fn[m] -= hnuy * (TAm[m] + shfl_up1(TAp[m]));
-                }
-                // ---- G at y-edge (c, k+1/2)
-#pragma unroll
-                for (int m = 0; m < N; m++) Gn[m] = T(0);
-                if (second) {
-#pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const bool upl = sy1[p] > T(0);
-                        T dl = T(0), dr = T(0);
-#pragma unroll
-                        for (int m = 0; m < N; m++) {
-                            const T wu = upl ? Wy0[p][m] : Wy2[p][m];
-                            dl += wu * Wy1[p][m];
-                            dr += Wy1[p][m] * Wy1[p][m];
-                        }
-                        const T as = fabs(sy1[p]);
-                        const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(a.limiter, dl, dr);
-#pragma unroll
-                        for (int m = 0; m < N; m++) Gn[m] += cf * Wy1[p][m];
-                    }
-                }
-                if (trans) {
-#pragma unroll
-                    for (int m = 0; m < N; m++)
-                        Gn[m] -= hnux * (BpAp0[m] + BmAp1[m] + shfl_down1(BpAm0[m] + BmAm1[m]));
-                }
-            }
-
-            // ---- cell (c, k)
-            if (k >= j0) {
-                T xr[N];
-#pragma unroll
-                for (int m = 0; m < N; m++) xr[m] = shfl_down1(amdq0[m] + F0[m]);
-                if (out_lane) {
-                    T* o = qout + (long long)(k + 2) * a.ld_x + a.x_offset + c;
-                    T qn[N];
-#pragma unroll
-                    for (int m = 0; m < N; m++) {
-                        qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) -
-                                nuy * (dqy[m] + Gn[m] - Gprev[m]);
-                        o[m * a.ld_field] = qn[m];
-                    }
-                    if (RP::POSITIVE) bad |= !(qn[0] > T(0));
-                    else bad |= qn[0] != qn[0];
-                }
-            }
-
-            // ---- rotate
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
-                Gprev[m] = Gn[m];
-                dqy[m] = dqy_n[m];
-                bp_pend[m] = bp2[m];
-                if (trans) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
-                apdq0[m] = apdq1[m]; amdq0[m] = amdq1[m];
-                if (trans) { BpAp0[m] = BpAp1[m]; BpAm0[m] = BpAm1[m]; }
-                F0[m] = Fn[m];
-            }
-#pragma unroll
-            for (int p = 0; p < NW; p++) {
-                sy0[p] = sy1[p]; sy1[p] = sy2[p];
-#pragma unroll
-                for (int m = 0; m < N; m++) { Wy0[p][m] = Wy1[p][m]; Wy1[p][m] = Wy2[p][m]; }
-            }
-        }
-        __syncwarp();
+        failed = !sweep_task<RP, false>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
+                                         a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
+                                         trans, W, bad, smx, smy, a.status);
     }
 
     if (failed) {
-        // give the copies still in flight a bounded chance to land
-        for (int s = 0; s < NSTAGE; s++) (void)mbar_wait_bounded(&bars[s], (phase >> s) & 1u);
+        drain_ring(W);
         if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);

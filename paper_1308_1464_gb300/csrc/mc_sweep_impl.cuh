@@ -2,6 +2,7 @@
 // included once per solver translation unit.
 #pragma once
 
+#include "mc_batch.cuh"
 #include "mc_internal.h"
 #include "mc_sweep.cuh"
 
@@ -68,6 +69,61 @@ cudaError_t maxspeed_launch_t(const mc_problem& p, const mc_layout& lay, const v
     return cudaGetLastError();
 }
 
+template <class RP>
+BatchArgs<RP> batch_args(const BatchLaunch& L)
+{
+    BatchArgs<RP> a;
+    a.rp.setup(L.proto.param, L.proto.efix);
+    a.patches = L.patches;
+    a.maps = L.maps;
+    a.prefix = L.prefix;
+    a.npatch = L.npatch;
+    a.nsteps = L.nsteps;
+    a.tasks_per_step = L.tasks_per_step;
+    a.x_offset = L.x_offset;
+    a.cfl = L.cfl;
+    a.limiter = L.proto.limiter;
+    a.order = L.proto.order;
+    a.transverse = L.proto.transverse;
+    a.smax = L.smax;
+    a.dt_used = L.dt_used;
+    a.done = L.done;
+    a.next_item = L.next_item;
+    a.status = L.status;
+    return a;
+}
+
+template <class RP>
+cudaError_t batch_launch_t(const BatchLaunch& L)
+{
+    using T = typename RP::real;
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    batch_sweep_kernel<RP><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+    return cudaGetLastError();
+}
+
+template <class RP>
+cudaError_t batch_init_t(const BatchLaunch& L)
+{
+    RP rp;
+    rp.setup(L.proto.param, L.proto.efix);
+    batch_init_kernel<RP><<<L.npatch, 256, 0, L.stream>>>(rp, L.patches, L.x_offset, L.nsteps + 1,
+                                                          L.smax);
+    return cudaGetLastError();
+}
+
+template <class RP>
+cudaError_t batch_occupancy_t(int* ctas)
+{
+    using T = typename RP::real;
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, batch_sweep_kernel<RP>,
+                                                         SWEEP_WARPS * 32, smem);
+}
+
 }  // namespace mc
 
 #define MC_DEFINE_SOLVER_LAUNCHERS(NAME, RPT)                                                  \
@@ -80,6 +136,21 @@ cudaError_t maxspeed_launch_t(const mc_problem& p, const mc_layout& lay, const v
     cudaError_t sweep_prepare_##NAME(int dtype)                                                \
     {                                                                                          \
         return dtype == MC_F64 ? sweep_prepare_t<RPT<double>>() : sweep_prepare_t<RPT<float>>(); \
+    }                                                                                          \
+    cudaError_t batch_launch_##NAME(const BatchLaunch& L)                                      \
+    {                                                                                          \
+        return L.proto.dtype == MC_F64 ? batch_launch_t<RPT<double>>(L)                        \
+                                       : batch_launch_t<RPT<float>>(L);                        \
+    }                                                                                          \
+    cudaError_t batch_init_##NAME(const BatchLaunch& L)                                        \
+    {                                                                                          \
+        return L.proto.dtype == MC_F64 ? batch_init_t<RPT<double>>(L)                          \
+                                       : batch_init_t<RPT<float>>(L);                          \
+    }                                                                                          \
+    cudaError_t batch_occupancy_##NAME(int dtype, int* ctas)                                   \
+    {                                                                                          \
+        return dtype == MC_F64 ? batch_occupancy_t<RPT<double>>(ctas)                          \
+                               : batch_occupancy_t<RPT<float>>(ctas);                          \
     }                                                                                          \
     cudaError_t maxspeed_launch_##NAME(const mc_problem& p, const mc_layout& lay,              \
                                        const void* q, unsigned long long* out, cudaStream_t s) \

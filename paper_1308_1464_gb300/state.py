@@ -58,3 +58,58 @@ class DeviceState:
         x0 = int(lay.x_offset) - 2
         torch.cuda.synchronize()
         return self.padded()[:, :, x0: x0 + p.mx + 4].cpu().numpy()
+
+
+class PatchSet:
+    """All patches of a batch in two device buffers (ping-pong), each patch in
+    the library layout at a 256-byte aligned offset.  Marshalling only."""
+
+    def __init__(self, proto, patches, device: str = "cuda"):
+        """patches: list of (mx, my, dx, dy, interior (meqn, my, mx) array)."""
+        from . import layout_of
+        import copy
+        self.proto = proto
+        self.specs = []
+        off = 0
+        for (mx, my, dx, dy, q) in patches:
+            p = copy.copy(proto)
+            p.mx, p.my, p.dx, p.dy = int(mx), int(my), float(dx), float(dy)
+            lay = layout_of(p)
+            self.specs.append((p, lay, off))
+            off += (int(lay.bytes) + 255) // 256 * 256
+        self.nbytes = off
+        es = int(self.specs[0][1].elem_bytes)
+        self.np_dtype = np.float64 if es == 8 else np.float32
+        host = np.zeros(off // es, dtype=self.np_dtype)
+        for (p, lay, o), (_, _, _, _, q) in zip(self.specs, patches):
+            v = self._view(host, p, lay, o)
+            v[:, 2:-2, int(lay.x_offset): int(lay.x_offset) + p.mx] = q
+        self._host0 = torch.from_numpy(host.view(np.uint8))
+        self.buf_a = self._host0.to(device)
+        self.buf_b = torch.zeros_like(self.buf_a)
+
+    def reset(self) -> None:
+        """Restore the initial state into buffer a."""
+        self.buf_a.copy_(self._host0)
+        torch.cuda.synchronize()
+
+    @staticmethod
+    def _view(flat, p, lay, off):
+        es = flat.itemsize
+        n = int(lay.meqn * lay.ld_field)
+        return flat[off // es: off // es + n].reshape(int(lay.meqn), p.my + 4, int(lay.ld_x))
+
+    def pointers(self):
+        """(mx, my, dx, dy, qa, qb) per patch, for Batch()."""
+        a, b = self.buf_a.data_ptr(), self.buf_b.data_ptr()
+        return [(p.mx, p.my, p.dx, p.dy, a + o, b + o) for (p, lay, o) in self.specs]
+
+    def interiors(self, in_b: bool):
+        """Host copies of every patch's interior from buffer b (or a)."""
+        torch.cuda.synchronize()
+        flat = (self.buf_b if in_b else self.buf_a).cpu().numpy().view(self.np_dtype)
+        out = []
+        for (p, lay, o) in self.specs:
+            v = self._view(flat, p, lay, o)
+            out.append(v[:, 2:-2, int(lay.x_offset): int(lay.x_offset) + p.mx].copy())
+        return out
