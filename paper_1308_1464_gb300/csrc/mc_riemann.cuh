@@ -57,6 +57,8 @@ struct AcousticsRP {
     struct Lin {};
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
+    // max over the edge's waves of |s| (the speeds are -c, +c)
+    __device__ __forceinline__ T max_speed(const Lin&) const { return c; }
 
     __host__ void setup(const double* param, int /*efix*/)
     {
@@ -108,6 +110,8 @@ struct SweRP {
     T g;
     bool efix;
     struct Lin { T u, v, c, r2c; };
+    // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
+    __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
     __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const
     {
@@ -128,19 +132,9 @@ struct SweRP {
     {
         constexpr int un = 1 + DIR, ut = 2 - DIR;
         const T hl = ql[0], hr = qr[0];
-        if (!(hl > T(0) && hr > T(0))) {
-            bad = true;
-#pragma unroll
-            for (int p = 0; p < NW; p++) {
-                s[p] = T(0);
-#pragma unroll
-                for (int m = 0; m < NEQ; m++) W[p][m] = T(0);
-            }
-#pragma unroll
-            for (int m = 0; m < NEQ; m++) amdq[m] = apdq[m] = T(0);
-            L.u = L.v = T(0); L.c = T(1); L.r2c = T(0.5);
-            return;
-        }
+        // a non-positive depth is flagged; the arithmetic then yields NaNs,
+        // which the caller's status word reports
+        bad = bad || !(hl > T(0) && hr > T(0));
         // Roe average: sqrt(h) u = hu / sqrt(h), so one reciprocal square
         // root per state gives both weights
         const T rsl = rsqrt_(hl), rsr = rsqrt_(hr);
@@ -227,6 +221,8 @@ struct EulerRP {
     T gamma, gm1;
     bool efix;
     struct Lin { T u, v, H, c, rc, gc2; };
+    // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
+    __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
     __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const
     {
@@ -292,36 +288,20 @@ struct EulerRP {
     {
         constexpr int un = 1 + DIR, ut = 2 - DIR;
         const T rl = ql[0], rr = qr[0];
-        bool ok = rl > T(0) && rr > T(0);
-        T u = T(0), v = T(0), H = T(0), c2 = T(0);
-        if (ok) {
-            // sqrt(rho) weights from one reciprocal square root per state:
-            // sqrt(rho) u = m / sqrt(rho), sqrt(rho) H = (E + p) / sqrt(rho)
-            const T rsl = rsqrt_(rl), rsr = rsqrt_(rr);
-            const T il = rsl * rsl, ir = rsr * rsr;
-            const T kl = T(0.5) * (ql[un] * ql[un] + ql[ut] * ql[ut]) * il;
-            const T kr = T(0.5) * (qr[un] * qr[un] + qr[ut] * qr[ut]) * ir;
-            const T pl = gm1 * (ql[3] - kl), pr = gm1 * (qr[3] - kr);
-            const T w = rcp_(rl * rsl + rr * rsr);
-            u = (ql[un] * rsl + qr[un] * rsr) * w;
-            v = (ql[ut] * rsl + qr[ut] * rsr) * w;
-            H = ((ql[3] + pl) * rsl + (qr[3] + pr) * rsr) * w;
-            c2 = gm1 * (H - T(0.5) * (u * u + v * v));
-            ok = c2 > T(0);
-        }
-        if (!ok) {
-            bad = true;
-#pragma unroll
-            for (int p = 0; p < NW; p++) {
-                s[p] = T(0);
-#pragma unroll
-                for (int m = 0; m < NEQ; m++) W[p][m] = T(0);
-            }
-#pragma unroll
-            for (int m = 0; m < NEQ; m++) amdq[m] = apdq[m] = T(0);
-            L.u = L.v = L.H = T(0); L.c = T(1); L.rc = T(1); L.gc2 = T(0);
-            return;
-        }
+        // sqrt(rho) weights from one reciprocal square root per state:
+        // sqrt(rho) u = m / sqrt(rho), sqrt(rho) H = (E + p) / sqrt(rho)
+        const T rsl = rsqrt_(rl), rsr = rsqrt_(rr);
+        const T il = rsl * rsl, ir = rsr * rsr;
+        const T kl = T(0.5) * (ql[un] * ql[un] + ql[ut] * ql[ut]) * il;
+        const T kr = T(0.5) * (qr[un] * qr[un] + qr[ut] * qr[ut]) * ir;
+        const T pl = gm1 * (ql[3] - kl), pr = gm1 * (qr[3] - kr);
+        const T w = rcp_(rl * rsl + rr * rsr);
+        const T u = (ql[un] * rsl + qr[un] * rsr) * w;
+        const T v = (ql[ut] * rsl + qr[ut] * rsr) * w;
+        const T H = ((ql[3] + pl) * rsl + (qr[3] + pr) * rsr) * w;
+        const T c2 = gm1 * (H - T(0.5) * (u * u + v * v));
+        // non-physical states are flagged; the arithmetic then yields NaNs
+        bad = bad || !(rl > T(0) && rr > T(0) && c2 > T(0));
         const T rc = rsqrt_(c2);
         const T c = c2 * rc;
         const T gc2 = gm1 * rc * rc;

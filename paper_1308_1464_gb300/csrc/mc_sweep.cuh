@@ -64,14 +64,17 @@ struct SweepArgs {
     int* status;
 };
 
+// phi(theta) with theta = dl / dr, branch-free: minmod (1), MC (4) or none
+// (0: phi = 1); a zero wave (dr = 0) gets no correction.  With a
+// compile-time limiter the selection folds away.
 template <typename T>
 __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
 {
-    if (!(dr > T(0))) return T(0);
     const T th = dl * rcp_(dr);
-    if (lim == 1) return fmax(T(0), fmin(T(1), th));
-    if (lim == 4) return fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
-    return T(1);
+    T phi = T(1);
+    if (lim == 4) phi = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
+    else if (lim == 1) phi = fmax(T(0), fmin(T(1), th));
+    return dr > T(0) ? phi : T(0);
 }
 
 // Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage.
@@ -87,16 +90,22 @@ struct WarpRing {
 // writes the ghost cells it is the mirror source of (reflecting walls on all
 // sides: x ghosts negate component 1, y ghosts component 2, corners both), so
 // the next step needs no separate ghost fill.
-template <class RP, bool WALL_GHOSTS>
+//
+// FAST compiles the common scheme (MC limiter, second order, transverse
+// splits) with those choices fixed; otherwise they are read at run time.
+template <class RP, bool WALL_GHOSTS, bool FAST>
 __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real* __restrict__ qout, int mx, int my,
                                            long long ld_x, long long ld_field, long long x_offset,
                                            int i0, int j0, int jend, typename RP::real nux,
-                                           typename RP::real nuy, int limiter, bool second,
-                                           bool trans, WarpRing& W, bool& bad,
+                                           typename RP::real nuy, int limiter_rt, bool second_rt,
+                                           bool trans_rt, WarpRing& W, bool& bad,
                                            typename RP::real& smx, typename RP::real& smy,
                                            int* status)
 {
+    const int limiter = FAST ? 4 : limiter_rt;
+    const bool second = FAST ? true : second_rt;
+    const bool trans = FAST ? true : trans_rt;
     using T = typename RP::real;
     constexpr int N = RP::NEQ, NW = RP::NW;
     constexpr int ES = sizeof(T);
@@ -199,10 +208,10 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         T dqy_n[N];
 #pragma unroll
         for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
-        if (ye_lane && k + 2 >= 0 && k + 2 <= my) {
-            bad |= bady;
-#pragma unroll
-            for (int p = 0; p < NW; p++) smy = fmax(smy, fabs(sy2[p]));
+        {
+            const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
+            bad |= in && bady;
+            smy = fmax(smy, in ? rp.max_speed(Ly) : T(0));
         }
 
         // ---- x-edge c-1/2 of row k+1
@@ -216,11 +225,9 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
                 rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
             }
-            if (xe_lane && k + 1 >= 0 && k + 1 < my) {
-                bad |= badx;
-#pragma unroll
-                for (int p = 0; p < NW; p++) smx = fmax(smx, fabs(sxw[p]));
-            }
+            const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
+            bad |= in && badx;
+            smx = fmax(smx, in ? rp.max_speed(Lx) : T(0));
         }
 
         T Fn[N], Gn[N];
@@ -281,17 +288,16 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             T xr[N];
 #pragma unroll
             for (int m = 0; m < N; m++) xr[m] = shfl_down1(amdq0[m] + F0[m]);
+            T qn[N];
+#pragma unroll
+            for (int m = 0; m < N; m++)
+                qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) - nuy * (dqy[m] + Gn[m] - Gprev[m]);
+            if (RP::POSITIVE) bad |= out_lane && !(qn[0] > T(0));
+            else bad |= out_lane && qn[0] != qn[0];
             if (out_lane) {
                 T* o = qout + (long long)(k + 2) * ld_x + x_offset + c;
-                T qn[N];
 #pragma unroll
-                for (int m = 0; m < N; m++) {
-                    qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) -
-                            nuy * (dqy[m] + Gn[m] - Gprev[m]);
-                    o[m * ld_field] = qn[m];
-                }
-                if (RP::POSITIVE) bad |= !(qn[0] > T(0));
-                else bad |= qn[0] != qn[0];
+                for (int m = 0; m < N; m++) o[m * ld_field] = qn[m];
                 if (WALL_GHOSTS) {
                     const bool hx = c < 2 || c >= mx - 2, hy = k < 2 || k >= my - 2;
                     const int gi = c < 2 ? -1 - c : 2 * mx - 1 - c;
@@ -356,7 +362,7 @@ __device__ __forceinline__ WarpRing warp_ring(unsigned char* smem, int es, int n
 // The fused step over one grid.  The tensor maps of the two state buffers
 // live in device global memory (64-byte aligned, written by the host before
 // the launch); the kernel takes plain pointers to them.
-template <class RP>
+template <class RP, bool FAST>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
 {
@@ -388,7 +394,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
         const int i0 = (task % a.nbands) * BAND_W;
         const int j0 = (task / a.nbands) * a.tile_rows;
         const int jend = min(j0 + a.tile_rows, a.my);
-        failed = !sweep_task<RP, false>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
+        failed = !sweep_task<RP, false, FAST>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
                                          a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
                                          trans, W, bad, smx, smy, a.status);
     }

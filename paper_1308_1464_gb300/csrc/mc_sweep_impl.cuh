@@ -8,6 +8,12 @@
 
 namespace mc {
 
+// the scheme the FAST kernels compile in: MC limiter, second order, transverse
+inline bool is_fast_scheme(const mc_problem& p)
+{
+    return p.limiter == MC_LIM_MC && p.order == 2 && p.transverse == 1;
+}
+
 template <class RP>
 cudaError_t sweep_launch_t(const SweepLaunch& L)
 {
@@ -37,7 +43,10 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
     int blocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
-    ctu_sweep_kernel<RP><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+    if (is_fast_scheme(L.prob))
+        ctu_sweep_kernel<RP, true><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+    else
+        ctu_sweep_kernel<RP, false><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
     return cudaGetLastError();
 }
 
@@ -48,8 +57,12 @@ cudaError_t sweep_prepare_t()
 {
     using T = typename RP::real;
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
-    return cudaFuncSetAttribute(ctu_sweep_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem);
+    cudaError_t e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
 template <class RP>
@@ -98,7 +111,10 @@ cudaError_t batch_launch_t(const BatchLaunch& L)
 {
     using T = typename RP::real;
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
-    batch_sweep_kernel<RP><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+    if (is_fast_scheme(L.proto))
+        batch_sweep_kernel<RP, true><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+    else
+        batch_sweep_kernel<RP, false><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
     return cudaGetLastError();
 }
 
@@ -117,10 +133,13 @@ cudaError_t batch_occupancy_t(int* ctas)
 {
     using T = typename RP::real;
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
-    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP>,
+    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_sweep_kernel<RP, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, batch_sweep_kernel<RP>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, batch_sweep_kernel<RP, true>,
                                                          SWEEP_WARPS * 32, smem);
 }
 
