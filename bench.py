@@ -52,6 +52,25 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(ms: float, world: int, device: str) -> float:
+    """The timed region's duration as the slowest rank saw it (all ranks
+    return the same value).  Each rank runs an independent replica of the
+    workload, so this is the only exchange between ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_throughput(ms: float, world: int, units_per_step: int, steps: int) -> float:
+    """Whole-job rate: the units every rank processed over the max-over-ranks time."""
+    return world * units_per_step * steps / (ms * 1e-3)
+
+
 def make_problem(mc, wl):
     from paper_1308_1464_gb300 import workloads
     n = wl["n"]
@@ -495,13 +514,9 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    ms = max_over_ranks(ms, world, "cuda")
     clocks = clk.summary()
-    value = world * n_cells * args.steps / (ms * 1e-3)
+    value = replica_throughput(ms, world, n_cells, args.steps)
     solves = world * ((p.mx + 1) * p.my + p.mx * (p.my + 1)) * args.steps / (ms * 1e-3)
 
     # kernel roofline: the fused step alone, CUDA events on its stream

@@ -228,6 +228,12 @@ mc_status mc_batch_advance(mc_batch* b, int32_t nsteps, double cfl, double* t_ou
  * fused step per patch), for comparison; bitwise equal interiors. */
 mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
                                  int* result_in_b, void* stream);
+/* Failure-detection hook for tests (no counterpart in the paper): during the
+ * next mc_batch_advance only, the tasks of `patch` wait for one more finished
+ * task of their previous step than will ever exist.  Their bounded waits give
+ * up after about a second, the kernel ends, the call returns MC_ETIMEOUT, and
+ * the batch stays usable (that patch's state is left part-advanced). */
+mc_status mc_batch_inject_stall(mc_batch* b, int32_t patch);
 
 /* ------------------------------------------------------------------------
  * Exact Euler Riemann solver with a learned pressure seed.

@@ -108,6 +108,7 @@ def lib():
         L.mc_batch_create.argtypes = [P, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(_VP)]
         L.mc_batch_destroy.argtypes = [_VP]
         L.mc_batch_set_tile_rows.argtypes = [_VP, ctypes.c_void_p]
+        L.mc_batch_inject_stall.argtypes = [_VP, ctypes.c_int32]
         for fn in (L.mc_batch_advance, L.mc_batch_advance_plain):
             fn.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, _IP, _VP]
         L.mc_riemann_exact.argtypes = [ctypes.c_int64, ctypes.c_double] + [_VP] * 10 + [
@@ -351,6 +352,10 @@ class Batch:
     def advance(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
         """One persistent launch in a graph -> (t per patch or None, result_in_b)."""
         return self._run(lib().mc_batch_advance, nsteps, cfl, want_t, stream)
+
+    def inject_stall(self, patch: int) -> None:
+        """Test hook: the next advance's waits for this patch run out (MC_ETIMEOUT)."""
+        check(lib().mc_batch_inject_stall(self._h, int(patch)))
 
     def advance_plain(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
         """One launch per patch per step -> (t per patch or None, result_in_b)."""

@@ -64,7 +64,18 @@ struct mc_batch {
     cudaGraphExec_t exec = nullptr;
     int exec_steps = -1;
     double exec_cfl = 0.0;
+    int stall_patch = -1;           // fault injection for the next advance
 };
+
+// Uploads the patch descriptors; with stall >= 0 that patch's descriptor
+// claims one task more than the work tables hand out, so its next-step tasks
+// wait for a completion that never comes.
+static cudaError_t upload_desc(mc_batch* b, int stall)
+{
+    std::vector<PatchDesc> d = b->desc;
+    if (stall >= 0) d[stall].ntasks += 1;
+    return cudaMemcpy(b->d_patches, d.data(), sizeof(PatchDesc) * b->npatch, cudaMemcpyHostToDevice);
+}
 
 static cudaError_t solver_batch_launch(const BatchLaunch& L)
 {
@@ -363,11 +374,27 @@ mc_status mc_batch_advance(mc_batch* b, int32_t nsteps, double cfl, double* t_ou
         b->exec_steps = nsteps;
         b->exec_cfl = cfl;
     }
-    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    const int stall = b->stall_patch;
+    b->stall_patch = -1;
+    cudaError_t e = cudaSuccess;
+    if (stall >= 0) e = upload_desc(b, stall);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
     if (e != cudaSuccess) return cuda_error(e, "batched graph launch");
     st = finish(b, nsteps, t_out, s);
+    if (stall >= 0) {
+        cudaError_t e2 = upload_desc(b, -1);
+        if (e2 != cudaSuccess && st == MC_OK) st = cuda_error(e2, "restoring patch descriptors");
+    }
     if (st == MC_OK && result_in_b) *result_in_b = nsteps & 1;
     return st;
+}
+
+mc_status mc_batch_inject_stall(mc_batch* b, int32_t patch)
+{
+    if (!b) return set_error(MC_EINVAL, "NULL batch");
+    if (patch < 0 || patch >= b->npatch) return set_error(MC_EINVAL, "patch %d out of range", patch);
+    b->stall_patch = patch;
+    return MC_OK;
 }
 
 mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double* t_out,

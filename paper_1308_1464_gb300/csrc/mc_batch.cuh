@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
     const bool second = a.order >= 2, trans = a.transverse != 0;
     const long long total = (long long)a.nsteps * a.tasks_per_step;
     const int stride = a.nsteps + 1;
-    bool failed = false, bad = false;
+    bool dep_failed = false, tma_failed = false, bad = false;
 
     for (;;) {
         long long item = 0;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
             if (lane == 0) ok = wait_counter(&a.done[p], unsigned(s) * unsigned(d.ntasks));
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
-                failed = true;
+                dep_failed = true;   // between tasks: no copies in flight
                 break;
             }
         }
@@ -120,7 +120,6 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         T* qout = static_cast<T*>(cur ? d.qa : d.qb);
         if ((reinterpret_cast<uintptr_t>(map) & 63) != 0) {
             if (lane == 0) atomicOr(a.status, ST_BADARG);
-            failed = true;
             break;
         }
         if (lane == 0) acquire_tensormap(map);
@@ -132,7 +131,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         if (!sweep_task<RP, true, FAST>(a.rp, map, qout, d.mx, d.my, d.ld_x, d.ld_field, a.x_offset, i0,
                                   j0, jend, T(dt / d.dx), T(dt / d.dy), a.limiter, second, trans,
                                   W, bad, smx, smy, a.status)) {
-            failed = true;
+            tma_failed = true;
             break;
         }
         double v = fmax(double(smx) / d.dx, double(smy) / d.dy);
@@ -146,10 +145,8 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         }
         __syncwarp();
     }
-    if (failed) {
-        drain_ring(W);
-        if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
-    }
+    if (tma_failed) drain_ring(W);
+    if ((tma_failed || dep_failed) && lane == 0) atomicOr(a.status, ST_TIMEOUT);
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);
 }
 

@@ -169,12 +169,16 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     // carried state (see the header comment for the schedule)
     T qc0[N], qc1[N], ql1[N];
     T Wy0[NW][N], Wy1[NW][N], sy0[NW], sy1[NW];
-    T Gprev[N], dqy[N], bp_pend[N], tyP_m[N], tyP_p[N];
-    T apdq0[N], amdq0[N], BpAp0[N], BpAm0[N], F0[N];
+    // XP = A+dQ(c-1/2) - F(c-1/2) and XM = A-dQ(c-1/2) + F(c-1/2) of row k (XM
+    // goes to lane l-1, whose right edge this is); Z = B+dQ(k-1/2) + B-dQ(k+1/2)
+    // - G(k-1/2) of row k: what the update of cell (c, k) needs from earlier
+    // iterations
+    T bp_pend[N], tyP_m[N], tyP_p[N];
+    T XP0[N], XM0[N], Z0[N], BpAp0[N], BpAm0[N];
 #pragma unroll
     for (int m = 0; m < N; m++) {
-        qc0[m] = Gprev[m] = dqy[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
-        apdq0[m] = amdq0[m] = BpAp0[m] = BpAm0[m] = F0[m] = T(0);
+        qc0[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
+        XP0[m] = XM0[m] = Z0[m] = BpAp0[m] = BpAm0[m] = T(0);
     }
 #pragma unroll
     for (int p = 0; p < NW; p++) {
@@ -287,11 +291,11 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         if (k >= j0) {
             T xr[N];
 #pragma unroll
-            for (int m = 0; m < N; m++) xr[m] = shfl_down1(amdq0[m] + F0[m]);
+            for (int m = 0; m < N; m++) xr[m] = shfl_down1(XM0[m]);
             T qn[N];
 #pragma unroll
             for (int m = 0; m < N; m++)
-                qn[m] = qc0[m] - nux * (apdq0[m] - F0[m] + xr[m]) - nuy * (dqy[m] + Gn[m] - Gprev[m]);
+                qn[m] = qc0[m] - nux * (XP0[m] + xr[m]) - nuy * (Z0[m] + Gn[m]);
             if (RP::POSITIVE) bad |= out_lane && !(qn[0] > T(0));
             else bad |= out_lane && qn[0] != qn[0];
             if (out_lane) {
@@ -319,13 +323,12 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 #pragma unroll
         for (int m = 0; m < N; m++) {
             qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
-            Gprev[m] = Gn[m];
-            dqy[m] = dqy_n[m];
+            Z0[m] = dqy_n[m] - Gn[m];
             bp_pend[m] = bp2[m];
             if (trans) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
-            apdq0[m] = apdq1[m]; amdq0[m] = amdq1[m];
+            XP0[m] = apdq1[m] - Fn[m];
+            XM0[m] = amdq1[m] + Fn[m];
             if (trans) { BpAp0[m] = BpAp1[m]; BpAm0[m] = BpAm1[m]; }
-            F0[m] = Fn[m];
         }
 #pragma unroll
         for (int p = 0; p < NW; p++) {

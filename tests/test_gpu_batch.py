@@ -119,3 +119,29 @@ def test_full_configuration_sampled():
     for k in range(len(pats)):
         m0 = pats[k][4][0].astype(np.float32).astype(np.float64).sum()
         assert abs(got[k][0].astype(np.float64).sum() - m0) <= 1e-5 * m0
+
+
+def test_bounded_wait_reports_timeout_and_batch_recovers():
+    """Fault injection on the host: one patch's tasks wait for a completion
+    that never comes.  The device waits are bounded (about a second), the call
+    returns MC_ETIMEOUT instead of hanging, and the next advance is correct."""
+    import time
+    pats = small_patches(4, seed=9)
+    ps = PatchSet(proto(mc.F32), pats)
+    b = mc.Batch(proto(mc.F32), ps.pointers())
+    b.inject_stall(2)
+    t0 = time.time()
+    with pytest.raises(mc.McError) as ei:
+        b.advance(4, 0.9)
+    assert ei.value.status == mc.MC_ETIMEOUT
+    assert time.time() - t0 < 60
+    # recovery: a clean run from the initial state equals the per-patch loop
+    ps.reset()
+    _, inb = b.advance(4, 0.9)
+    got = ps.interiors(inb)
+    ps.reset()
+    _, inb2 = b.advance_plain(4, 0.9)
+    ref = ps.interiors(inb2)
+    for a, c in zip(got, ref):
+        np.testing.assert_array_equal(a, c)
+    b.close()
