@@ -55,6 +55,11 @@ struct AcousticsRP {
     T c, Z, inv2Z;
     bool efix;  // unused: linear system
     struct Lin {};
+    // component m of wave p can be non-zero (the tangential velocity never is)
+    template <int DIR>
+    __host__ __device__ static constexpr bool wave_nz(int, int m) { return m != 2 - DIR; }
+    // the sweep keeps the y-edge waves of the row below (not their products)
+    static constexpr bool CARRY_DOT = false;
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
     // max over the edge's waves of |s| (the speeds are -c, +c)
@@ -82,11 +87,8 @@ struct AcousticsRP {
         W[1][0] = Z * a2;  W[1][un] = a2; W[1][ut] = T(0);
         s[0] = -c;
         s[1] = c;
-#pragma unroll
-        for (int m = 0; m < NEQ; m++) {
-            amdq[m] = -c * W[0][m];
-            apdq[m] = c * W[1][m];
-        }
+        amdq[0] = -c * W[0][0]; amdq[un] = -c * a1; amdq[ut] = T(0);
+        apdq[0] = c * W[1][0];  apdq[un] = c * a2;  apdq[ut] = T(0);
     }
 
     // split a fluctuation of a DIR-normal edge in direction 1 - DIR
@@ -110,6 +112,12 @@ struct SweRP {
     T g;
     bool efix;
     struct Lin { T u, v, c, r2c; };
+    // component m of wave p can be non-zero: the shear wave moves only the
+    // tangential momentum
+    template <int DIR>
+    __host__ __device__ static constexpr bool wave_nz(int p, int m) { return p != 1 || m == 2 - DIR; }
+    // the sweep keeps the y-edge waves of the row below (measured faster here)
+    static constexpr bool CARRY_DOT = false;
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
@@ -182,12 +190,17 @@ struct SweRP {
                 if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) * rcp_(lr - ll) * ll;
             }
         }
+        // A-dQ = sum_p k_p W^p, A+dQ = sum_p (s^p - k_p) W^p (k_p = min(s^p, 0)
+        // unless the entropy fix replaced it), over the non-zero components
         const T k1 = tmin0(s[1]);
-#pragma unroll
-        for (int m = 0; m < NEQ; m++) {
-            amdq[m] = k0 * W[0][m] + k1 * W[1][m] + k2 * W[2][m];
-            apdq[m] = s[0] * W[0][m] + s[1] * W[1][m] + s[2] * W[2][m] - amdq[m];
-        }
+        const T m1 = k0 * a1, m2 = k1 * a2, m3 = k2 * a3;
+        const T p1 = (s[0] - k0) * a1, p2 = (s[1] - k1) * a2, p3 = (s[2] - k2) * a3;
+        amdq[0] = m1 + m3;
+        amdq[un] = m1 * (u - c) + m3 * (u + c);
+        amdq[ut] = (m1 + m3) * v + m2;
+        apdq[0] = p1 + p3;
+        apdq[un] = p1 * (u - c) + p3 * (u + c);
+        apdq[ut] = (p1 + p3) * v + p2;
     }
 
     template <int DIR>
@@ -221,6 +234,12 @@ struct EulerRP {
     T gamma, gm1;
     bool efix;
     struct Lin { T u, v, H, c, rc, gc2; };
+    // every component of every wave can be non-zero
+    template <int DIR>
+    __host__ __device__ static constexpr bool wave_nz(int, int) { return true; }
+    // the sweep keeps the limiter's dot products of the row below instead of
+    // its 12 wave components (measured faster here)
+    static constexpr bool CARRY_DOT = true;
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 

@@ -140,7 +140,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         }
     }
 
-    // fetch row r of columns c and c-1 into registers
+    // fetch row r of columns c and c-1 into registers; a stage goes back to
+    // the TMA once its last row has been read
     auto fetch = [&](int r, T* qc, T* ql) -> bool {
         const int rel = r - rbase, f = rel / RS, rr = rel - f * RS, st = f % NSTAGE;
         if (rr == 0) {
@@ -166,9 +167,14 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         return true;
     };
 
-    // carried state (see the header comment for the schedule)
+    // carried state (see the header comment for the schedule).  The y-limiter
+    // of edge (c, k+1/2) needs, when s^p > 0, the dot product of its wave p
+    // with that of the edge below: a solver with CARRY_DOT keeps that product
+    // (dlo, formed one row earlier), otherwise the waves themselves (Wy0) are
+    // kept -- whichever the solver's register budget favours.
+    constexpr bool CD = RP::CARRY_DOT;
     T qc0[N], qc1[N], ql1[N];
-    T Wy0[NW][N], Wy1[NW][N], sy0[NW], sy1[NW];
+    T Wy0[CD ? 1 : NW][N], Wy1[NW][N], sy1[NW], dlo[NW];
     // XP = A+dQ(c-1/2) - F(c-1/2) and XM = A-dQ(c-1/2) + F(c-1/2) of row k (XM
     // goes to lane l-1, whose right edge this is); Z = B+dQ(k-1/2) + B-dQ(k+1/2)
     // - G(k-1/2) of row k: what the update of cell (c, k) needs from earlier
@@ -182,9 +188,12 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     }
 #pragma unroll
     for (int p = 0; p < NW; p++) {
-        sy0[p] = sy1[p] = T(0);
+        sy1[p] = dlo[p] = T(0);
 #pragma unroll
-        for (int m = 0; m < N; m++) Wy0[p][m] = Wy1[p][m] = T(0);
+        for (int m = 0; m < N; m++) {
+            Wy1[p][m] = T(0);
+            if constexpr (!CD) Wy0[p][m] = T(0);
+        }
     }
     if (!fetch(rbase, qc1, ql1)) return false;
 
@@ -212,6 +221,16 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         T dqy_n[N];
 #pragma unroll
         for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
+        // with CARRY_DOT: waves of y-edge (c, k+1/2) dotted with those of the
+        // edge above (the next row's dlo)
+        T dhi[NW];
+#pragma unroll
+        for (int p = 0; p < NW; p++) {
+            dhi[p] = T(0);
+#pragma unroll
+            for (int m = 0; m < N; m++)
+                if (CD && second && RP::template wave_nz<1>(p, m)) dhi[p] += Wy2[p][m] * Wy1[p][m];
+        }
         {
             const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
             bad |= in && bady;
@@ -246,6 +265,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     T dl = T(0), dr = T(0);
 #pragma unroll
                     for (int m = 0; m < N; m++) {
+                        if (!RP::template wave_nz<0>(p, m)) continue;
                         const T wu = shfl(Wx[p][m], src);
                         dl += wu * Wx[p][m];
                         dr += Wx[p][m] * Wx[p][m];
@@ -253,7 +273,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     const T as = fabs(sxw[p]);
                     const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(limiter, dl, dr);
 #pragma unroll
-                    for (int m = 0; m < N; m++) Fn[m] += cf * Wx[p][m];
+                    for (int m = 0; m < N; m++)
+                        if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
                 }
             }
             if (trans) {
@@ -270,14 +291,16 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     T dl = T(0), dr = T(0);
 #pragma unroll
                     for (int m = 0; m < N; m++) {
-                        const T wu = upl ? Wy0[p][m] : Wy2[p][m];
-                        dl += wu * Wy1[p][m];
+                        if (!RP::template wave_nz<1>(p, m)) continue;
+                        if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
                         dr += Wy1[p][m] * Wy1[p][m];
                     }
+                    if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
                     const T as = fabs(sy1[p]);
                     const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(limiter, dl, dr);
 #pragma unroll
-                    for (int m = 0; m < N; m++) Gn[m] += cf * Wy1[p][m];
+                    for (int m = 0; m < N; m++)
+                        if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
                 }
             }
             if (trans) {
@@ -332,9 +355,13 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         }
 #pragma unroll
         for (int p = 0; p < NW; p++) {
-            sy0[p] = sy1[p]; sy1[p] = sy2[p];
+            sy1[p] = sy2[p];
+            if constexpr (CD) dlo[p] = dhi[p];
 #pragma unroll
-            for (int m = 0; m < N; m++) { Wy0[p][m] = Wy1[p][m]; Wy1[p][m] = Wy2[p][m]; }
+            for (int m = 0; m < N; m++) {
+                if constexpr (!CD) Wy0[p][m] = Wy1[p][m];
+                Wy1[p][m] = Wy2[p][m];
+            }
         }
     }
     __syncwarp();
