@@ -46,6 +46,37 @@ __device__ __forceinline__ float sqrt_(float x)
 }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 
+// Packed FP32 pairs.  One iteration of the sweep solves an x-edge and a
+// y-edge with the same arithmetic; written in the edge-normal frame
+// (component 1 the normal momentum or velocity, 2 the tangential one) the two
+// solves are identical, so FP32 runs them side by side in the halves of a
+// float2 with the packed add/multiply/fma instructions of sm_100 and later:
+// one issue slot per pair instead of two.  Each half rounds like the scalar
+// instruction (round to nearest even), so a packed result equals the scalar
+// result of the same operation sequence.
+using f2 = float2;
+__device__ __forceinline__ f2 p_set(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 p_add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 p_mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 p_fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b as b (-1) + a: the product is exact, so one rounding like a - b
+__device__ __forceinline__ f2 p_sub(f2 a, f2 b) { return __ffma2_rn(b, p_set(-1.f), a); }
+__device__ __forceinline__ f2 p_neg(f2 a) { return p_mul(a, p_set(-1.f)); }
+__device__ __forceinline__ f2 p_rcp(f2 a) { return make_float2(rcp_(a.x), rcp_(a.y)); }
+__device__ __forceinline__ f2 p_rsqrt(f2 a) { return make_float2(rsqrt_(a.x), rsqrt_(a.y)); }
+__device__ __forceinline__ f2 p_sqrt(f2 a) { return make_float2(sqrt_(a.x), sqrt_(a.y)); }
+__device__ __forceinline__ f2 p_min0(f2 a) { return make_float2(tmin0(a.x), tmin0(a.y)); }
+__device__ __forceinline__ f2 p_max0(f2 a) { return make_float2(tmax0(a.x), tmax0(a.y)); }
+__device__ __forceinline__ float half(const f2& a, int h) { return h ? a.y : a.x; }
+__device__ __forceinline__ float& half(f2& a, int h) { return h ? a.y : a.x; }
+
+// Edge-normal frame: component m of the frame is component frame_comp(m, DIR)
+// of the physical state (the two momenta swap for a y-edge).
+__host__ __device__ constexpr int frame_comp(int m, int dir)
+{
+    return dir == 0 ? m : (m == 1 ? 2 : (m == 2 ? 1 : m));
+}
+
 // ---------------------------------------------------------------- acoustics
 template <typename T>
 struct AcousticsRP {
@@ -60,6 +91,7 @@ struct AcousticsRP {
     __host__ __device__ static constexpr bool wave_nz(int, int m) { return m != 2 - DIR; }
     // the sweep keeps the y-edge waves of the row below (not their products)
     static constexpr bool CARRY_DOT = false;
+    static constexpr bool PAIRED = false;   // scalar solves only
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
     // max over the edge's waves of |s| (the speeds are -c, +c)
@@ -203,6 +235,106 @@ struct SweRP {
         apdq[ut] = (p1 + p3) * v + p2;
     }
 
+    // ---- FP32 pairs: half .x an x-edge, .y a y-edge, both in the
+    // edge-normal frame (component 1 normal, 2 tangential momentum); the
+    // same arithmetic as normal<0> / transverse<0>, two edges per instruction
+    static constexpr bool PAIRED = sizeof(T) == 4;
+    struct LinP { f2 u, v, c, r2c; };
+    __device__ __forceinline__ float max_speed(const LinP& L, int h) const
+    {
+        return fabs(half(L.u, h)) + half(L.c, h);
+    }
+
+    __device__ __forceinline__ void normal_pair(const f2* ql, const f2* qr, f2 (&W)[NW][NEQ],
+                                                f2 (&s)[NW], f2* amdq, f2* apdq, LinP& L,
+                                                bool& badx, bool& bady) const
+    {
+        const f2 hl = ql[0], hr = qr[0];
+        badx = badx || !(hl.x > 0.f && hr.x > 0.f);
+        bady = bady || !(hl.y > 0.f && hr.y > 0.f);
+        const f2 rsl = p_rsqrt(hl), rsr = p_rsqrt(hr);
+        const f2 w = p_rcp(p_fma(hl, rsl, p_mul(hr, rsr)));
+        const f2 u = p_mul(p_fma(ql[1], rsl, p_mul(qr[1], rsr)), w);
+        const f2 v = p_mul(p_fma(ql[2], rsl, p_mul(qr[2], rsr)), w);
+        const f2 gh = p_mul(p_set(g * 0.5f), p_add(hl, hr));
+        const f2 rc = p_rsqrt(gh);
+        const f2 c = p_mul(gh, rc);
+        const f2 r2c = p_mul(p_set(0.5f), rc);
+        const f2 d0 = p_sub(hr, hl), ndn = p_sub(ql[1], qr[1]), dt = p_sub(qr[2], ql[2]);
+        const f2 sm = p_sub(u, c), sp = p_add(u, c);
+        // a1 = ((u + c) d0 - dn) / 2c, a2 = dt - v d0, a3 = (dn - (u - c) d0) / 2c
+        const f2 a1 = p_mul(p_fma(sp, d0, ndn), r2c);
+        const f2 a2 = p_fma(p_neg(v), d0, dt);
+        const f2 a3 = p_mul(p_fma(sm, d0, ndn), p_neg(r2c));
+        W[0][0] = a1; W[0][1] = p_mul(a1, sm); W[0][2] = p_mul(a1, v);
+        W[1][0] = p_set(0.f); W[1][1] = p_set(0.f); W[1][2] = a2;
+        W[2][0] = a3; W[2][1] = p_mul(a3, sp); W[2][2] = p_mul(a3, v);
+        s[0] = sm;
+        s[1] = u;
+        s[2] = sp;
+        L.u = u; L.v = v; L.c = c; L.r2c = r2c;
+
+        f2 k0 = p_min0(sm), k2 = p_min0(sp);
+        if (efix) {
+            // the transonic tests of normal(), both halves at once
+            const f2 gs = p_set(g);
+            const f2 hul = ql[1], hum = p_add(ql[1], W[0][1]), hm = p_add(hl, a1);
+            const f2 hur = qr[1], hun = p_sub(qr[1], W[2][1]), hn = p_sub(hr, a3);
+            const f2 hul2 = p_mul(hul, hul), gl3 = p_mul(p_mul(p_mul(gs, hl), hl), hl);
+            const f2 hum2 = p_mul(hum, hum), gm3 = p_mul(p_mul(p_mul(gs, hm), hm), hm);
+            const f2 hun2 = p_mul(hun, hun), gn3 = p_mul(p_mul(p_mul(gs, hn), hn), hn);
+            const f2 hur2 = p_mul(hur, hur), gr3 = p_mul(p_mul(p_mul(gs, hr), hr), hr);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const bool l_neg = half(hul, h) <= 0.f || half(hul2, h) < half(gl3, h);
+                const bool r_pos = half(hm, h) > 0.f && half(hum, h) > 0.f && half(hum2, h) > half(gm3, h);
+                if (l_neg && r_pos) {
+                    const float lam_l = half(hul, h) * rcp_(half(hl, h)) - sqrt_(g * half(hl, h));
+                    const float lam_r = half(hum, h) * rcp_(half(hm, h)) - sqrt_(g * half(hm, h));
+                    if (lam_l < 0.f && lam_r > 0.f)
+                        half(k0, h) = (lam_r - half(sm, h)) * rcp_(lam_r - lam_l) * lam_l;
+                }
+                const bool n_neg = half(hn, h) > 0.f && half(hun, h) < 0.f && half(hun2, h) > half(gn3, h);
+                const bool rr_pos = half(hur, h) >= 0.f || half(hur2, h) < half(gr3, h);
+                if (n_neg && rr_pos) {
+                    const float ll = half(hun, h) * rcp_(half(hn, h)) + sqrt_(g * half(hn, h));
+                    const float lr = half(hur, h) * rcp_(half(hr, h)) + sqrt_(g * half(hr, h));
+                    if (ll < 0.f && lr > 0.f)
+                        half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                }
+            }
+        }
+        const f2 k1 = p_min0(u);
+        const f2 m1 = p_mul(k0, a1), m2 = p_mul(k1, a2), m3 = p_mul(k2, a3);
+        const f2 q1 = p_mul(p_sub(sm, k0), a1), q2 = p_mul(p_max0(u), a2), q3 = p_mul(p_sub(sp, k2), a3);
+        amdq[0] = p_add(m1, m3);
+        amdq[1] = p_fma(m1, sm, p_mul(m3, sp));
+        amdq[2] = p_fma(amdq[0], v, m2);
+        apdq[0] = p_add(q1, q3);
+        apdq[1] = p_fma(q1, sm, p_mul(q3, sp));
+        apdq[2] = p_fma(apdq[0], v, q2);
+    }
+
+    __device__ __forceinline__ void transverse_pair(const LinP& L, const f2* a, f2* bm, f2* bp) const
+    {
+        // transverse<0> in the edge-normal frame: split direction normal
+        // component 2, tangential 1
+        const f2 u = L.v, v = L.u, c = L.c;
+        const f2 l1 = p_sub(u, c), l3 = p_add(u, c);
+        // b1 = ((u + c) a0 - a2) / 2c, b2 = a1 - v a0, b3 = (a2 - (u - c) a0) / 2c
+        const f2 b1 = p_mul(p_fma(p_neg(l3), a[0], a[2]), p_neg(L.r2c));
+        const f2 b2 = p_fma(p_neg(v), a[0], a[1]);
+        const f2 b3 = p_mul(p_fma(p_neg(l1), a[0], a[2]), L.r2c);
+        const f2 m1 = p_mul(p_min0(l1), b1), m2 = p_mul(p_min0(u), b2), m3 = p_mul(p_min0(l3), b3);
+        const f2 q1 = p_mul(p_max0(l1), b1), q2 = p_mul(p_max0(u), b2), q3 = p_mul(p_max0(l3), b3);
+        bm[0] = p_add(m1, m3);
+        bm[2] = p_fma(m1, l1, p_mul(m3, l3));
+        bm[1] = p_fma(bm[0], v, m2);
+        bp[0] = p_add(q1, q3);
+        bp[2] = p_fma(q1, l1, p_mul(q3, l3));
+        bp[1] = p_fma(bp[0], v, q2);
+    }
+
     template <int DIR>
     __device__ __forceinline__ void transverse(const Lin& L, const T* a, T* bm, T* bp) const
     {
@@ -240,6 +372,7 @@ struct EulerRP {
     // the sweep keeps the limiter's dot products of the row below instead of
     // its 12 wave components (measured faster here)
     static constexpr bool CARRY_DOT = true;
+    static constexpr bool PAIRED = sizeof(T) == 4;
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
@@ -394,6 +527,125 @@ struct EulerRP {
         bp[vn] = p1 * (u - c) + pe * u + p4 * (u + c);
         bp[vt] = (p1 + pe + p4) * v + ps;
         bp[3] = p1 * (H - u * c) + pe * ke + ps * v + p4 * (H + u * c);
+    }
+
+    // ---- FP32 pairs: half .x an x-edge, .y a y-edge, both in the
+    // edge-normal frame (component 1 normal, 2 tangential momentum); the
+    // arithmetic of normal<0> / transverse<0>, two edges per instruction
+    struct LinP { f2 u, v, H, c, rc, gc2; };
+    __device__ __forceinline__ float max_speed(const LinP& L, int h) const
+    {
+        return fabs(half(L.u, h)) + half(L.c, h);
+    }
+
+    __device__ __forceinline__ void normal_pair(const f2* ql, const f2* qr, f2 (&W)[NW][NEQ],
+                                                f2 (&s)[NW], f2* amdq, f2* apdq, LinP& L,
+                                                bool& badx, bool& bady) const
+    {
+        const f2 h2 = p_set(0.5f), g1 = p_set(gm1);
+        const f2 rl = ql[0], rr = qr[0];
+        const f2 rsl = p_rsqrt(rl), rsr = p_rsqrt(rr);
+        const f2 il = p_mul(rsl, rsl), ir = p_mul(rsr, rsr);
+        const f2 kl = p_mul(p_mul(h2, p_fma(ql[1], ql[1], p_mul(ql[2], ql[2]))), il);
+        const f2 kr = p_mul(p_mul(h2, p_fma(qr[1], qr[1], p_mul(qr[2], qr[2]))), ir);
+        const f2 pl = p_mul(g1, p_sub(ql[3], kl)), pr = p_mul(g1, p_sub(qr[3], kr));
+        const f2 w = p_rcp(p_fma(rl, rsl, p_mul(rr, rsr)));
+        const f2 u = p_mul(p_fma(ql[1], rsl, p_mul(qr[1], rsr)), w);
+        const f2 v = p_mul(p_fma(ql[2], rsl, p_mul(qr[2], rsr)), w);
+        const f2 H = p_mul(p_fma(p_add(ql[3], pl), rsl, p_mul(p_add(qr[3], pr), rsr)), w);
+        const f2 q2 = p_fma(u, u, p_mul(v, v));
+        const f2 c2 = p_mul(g1, p_fma(p_neg(h2), q2, H));
+        badx = badx || !(rl.x > 0.f && rr.x > 0.f && c2.x > 0.f);
+        bady = bady || !(rl.y > 0.f && rr.y > 0.f && c2.y > 0.f);
+        const f2 rc = p_rsqrt(c2);
+        const f2 c = p_mul(c2, rc);
+        const f2 gc2 = p_mul(p_mul(g1, rc), rc);
+        const f2 d0 = p_sub(qr[0], ql[0]), dn = p_sub(qr[1], ql[1]), dt = p_sub(qr[2], ql[2]);
+        const f2 ndE = p_sub(ql[3], qr[3]);
+        const f2 a_sh = p_fma(p_neg(v), d0, dt);
+        // a_en = gc2 ((H - u^2 - v^2) d0 + u dn + v dt - dE)
+        const f2 a_en = p_mul(gc2, p_fma(p_sub(H, q2), d0, p_fma(u, dn, p_fma(v, dt, ndE))));
+        const f2 x = p_mul(p_fma(p_neg(u), d0, dn), rc);
+        const f2 t = p_sub(d0, a_en);
+        const f2 a4 = p_mul(h2, p_add(t, x)), a1 = p_mul(h2, p_sub(t, x));
+        const f2 sm = p_sub(u, c), sp = p_add(u, c), uc = p_mul(u, c);
+        W[0][0] = a1; W[0][1] = p_mul(a1, sm); W[0][2] = p_mul(a1, v); W[0][3] = p_mul(a1, p_sub(H, uc));
+        W[1][0] = a_en; W[1][1] = p_mul(a_en, u); W[1][2] = p_fma(a_en, v, a_sh);
+        W[1][3] = p_fma(p_mul(a_en, h2), q2, p_mul(a_sh, v));
+        W[2][0] = a4; W[2][1] = p_mul(a4, sp); W[2][2] = p_mul(a4, v); W[2][3] = p_mul(a4, p_add(H, uc));
+        s[0] = sm;
+        s[1] = u;
+        s[2] = sp;
+        L.u = u; L.v = v; L.H = H; L.c = c; L.rc = rc; L.gc2 = gc2;
+
+        f2 k0 = p_min0(sm), k2 = p_min0(sp);
+        if (efix) {
+            // the tests of normal(), one half at a time (frame = x-edge frame)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                float qa[NEQ], qm[NEQ];
+#pragma unroll
+                for (int m = 0; m < NEQ; m++) {
+                    qa[m] = half(ql[m], h);
+                    qm[m] = qa[m] + half(W[0][m], h);
+                }
+                if (slower_than_sound<0>(qa, false) && faster_than_sound<0>(qm, true)) {
+                    float ll, lr;
+                    if (cspeed<0>(qa, -1.f, ll) && cspeed<0>(qm, -1.f, lr) && ll < 0.f && lr > 0.f)
+                        half(k0, h) = (lr - half(sm, h)) * rcp_(lr - ll) * ll;
+                }
+#pragma unroll
+                for (int m = 0; m < NEQ; m++) {
+                    qa[m] = half(qr[m], h);
+                    qm[m] = qa[m] - half(W[2][m], h);
+                }
+                if (faster_than_sound<0>(qm, false) && slower_than_sound<0>(qa, true)) {
+                    float ll, lr;
+                    if (cspeed<0>(qm, 1.f, ll) && cspeed<0>(qa, 1.f, lr) && ll < 0.f && lr > 0.f)
+                        half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                }
+            }
+        }
+        // A-dQ = sum_p k_p W^p, A+dQ = sum_p (s^p - k_p) W^p
+        const f2 k1 = p_min0(u), j0 = p_sub(sm, k0), j1 = p_max0(u), j2 = p_sub(sp, k2);
+#pragma unroll
+        for (int m = 0; m < NEQ; m++) {
+            amdq[m] = p_fma(k0, W[0][m], p_fma(k1, W[1][m], p_mul(k2, W[2][m])));
+            apdq[m] = p_fma(j0, W[0][m], p_fma(j1, W[1][m], p_mul(j2, W[2][m])));
+        }
+    }
+
+    __device__ __forceinline__ void transverse_pair(const LinP& L, const f2* a, f2* bm, f2* bp) const
+    {
+        // transverse<0> in the edge-normal frame: split direction normal
+        // component 2, tangential 1
+        const f2 h2 = p_set(0.5f);
+        const f2 u = L.v, v = L.u, c = L.c, H = L.H;
+        const f2 q2 = p_fma(u, u, p_mul(v, v));
+        const f2 b_sh = p_fma(p_neg(v), a[0], a[1]);
+        // b_en = gc2 ((H - u^2 - v^2) a0 + u a2 + v a1 - a3)
+        const f2 b_en = p_mul(L.gc2, p_fma(p_sub(H, q2), a[0], p_fma(u, a[2], p_fma(v, a[1], p_neg(a[3])))));
+        const f2 x = p_mul(p_fma(p_neg(u), a[0], a[2]), L.rc);
+        const f2 t = p_sub(a[0], b_en);
+        const f2 b4 = p_mul(h2, p_add(t, x)), b1 = p_mul(h2, p_sub(t, x));
+        const f2 l1 = p_sub(u, c), l4 = p_add(u, c), uc = p_mul(u, c);
+        const f2 ke = p_mul(h2, q2), e1 = p_sub(H, uc), e4 = p_add(H, uc);
+        {
+            const f2 n1 = p_min0(l1), n2 = p_min0(u), n4 = p_min0(l4);
+            const f2 m1 = p_mul(n1, b1), me = p_mul(n2, b_en), ms = p_mul(n2, b_sh), m4 = p_mul(n4, b4);
+            bm[0] = p_add(p_add(m1, me), m4);
+            bm[2] = p_fma(m1, l1, p_fma(me, u, p_mul(m4, l4)));
+            bm[1] = p_fma(bm[0], v, ms);
+            bm[3] = p_fma(m1, e1, p_fma(me, ke, p_fma(ms, v, p_mul(m4, e4))));
+        }
+        {
+            const f2 n1 = p_max0(l1), n2 = p_max0(u), n4 = p_max0(l4);
+            const f2 m1 = p_mul(n1, b1), me = p_mul(n2, b_en), ms = p_mul(n2, b_sh), m4 = p_mul(n4, b4);
+            bp[0] = p_add(p_add(m1, me), m4);
+            bp[2] = p_fma(m1, l1, p_fma(me, u, p_mul(m4, l4)));
+            bp[1] = p_fma(bp[0], v, ms);
+            bp[3] = p_fma(m1, e1, p_fma(me, ke, p_fma(ms, v, p_mul(m4, e4))));
+        }
     }
 };
 

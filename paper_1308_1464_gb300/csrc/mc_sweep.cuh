@@ -201,56 +201,116 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         T qc2[N], ql2[N];
         if (!fetch(k + 2, qc2, ql2)) return false;
 
-        // ---- y-edge between rows k+1 and k+2 of column c
+        // ---- y-edge between rows k+1 and k+2 of column c, x-edge c-1/2 of row k+1
         T Wy2[NW][N], sy2[NW], bm2[N], bp2[N];
-        typename RP::Lin Ly;
-        bool bady = false;
-        rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
-        T TAm[N], TAp[N];   // x-splits of the y-fluctuations entering row k+1
+        T t1[N], t2[N];     // x-splits of the y-fluctuations entering row k+1
         T nPm[N], nPp[N];   // ... entering row k+2
-        if (trans) {
-            T t1[N], t2[N];
-            rp.template transverse<1>(Ly, bm2, t1, t2);
-            rp.template transverse<1>(Ly, bp2, nPm, nPp);
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                TAm[m] = tyP_m[m] + t1[m];
-                TAp[m] = tyP_p[m] + t2[m];
-            }
-        }
-        T dqy_n[N];
-#pragma unroll
-        for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
-        // with CARRY_DOT: waves of y-edge (c, k+1/2) dotted with those of the
-        // edge above (the next row's dlo)
-        T dhi[NW];
-#pragma unroll
-        for (int p = 0; p < NW; p++) {
-            dhi[p] = T(0);
-#pragma unroll
-            for (int m = 0; m < N; m++)
-                if (CD && second && RP::template wave_nz<1>(p, m)) dhi[p] += Wy2[p][m] * Wy1[p][m];
-        }
-        {
-            const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
-            bad |= in && bady;
-            smy = fmax(smy, in ? rp.max_speed(Ly) : T(0));
-        }
-
-        // ---- x-edge c-1/2 of row k+1
         T Wx[NW][N], sxw[NW], amdq1[N], apdq1[N];
         T BmAp1[N], BpAp1[N], BmAm1[N], BpAm1[N];
-        if (k >= j0 - 2) {
-            typename RP::Lin Lx;
-            bool badx = false;
-            rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+        T TAm[N], TAp[N], dqy_n[N], dhi[NW];
+        // what the y-edge's results feed: the transverse sums entering row
+        // k+1, B+dQ(k+1/2) + B-dQ(k+3/2) waiting for row k+1's update, and,
+        // with CARRY_DOT, the dot products of the waves of y-edge (c, k+1/2)
+        // with those of the edge above (the next row's dlo)
+        auto y_tail = [&]() {
             if (trans) {
-                rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
-                rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    TAm[m] = tyP_m[m] + t1[m];
+                    TAp[m] = tyP_p[m] + t2[m];
+                }
             }
-            const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
-            bad |= in && badx;
-            smx = fmax(smx, in ? rp.max_speed(Lx) : T(0));
+#pragma unroll
+            for (int m = 0; m < N; m++) dqy_n[m] = bp_pend[m] + bm2[m];
+#pragma unroll
+            for (int p = 0; p < NW; p++) {
+                dhi[p] = T(0);
+#pragma unroll
+                for (int m = 0; m < N; m++)
+                    if (CD && second && RP::template wave_nz<1>(p, m)) dhi[p] += Wy2[p][m] * Wy1[p][m];
+            }
+        };
+        if constexpr (RP::PAIRED) {
+            // both edges at once in the edge-normal frame: half .x the
+            // x-edge (ql1 | qc1), half .y the y-edge (qc1 | qc2); the x-edge
+            // of the first march row is solved too (its row is resident) and
+            // left unused
+            f2 QL[N], QR[N];
+#pragma unroll
+            for (int m = 0; m < N; m++) {
+                QL[m] = make_float2(ql1[m], qc1[frame_comp(m, 1)]);
+                QR[m] = make_float2(qc1[m], qc2[frame_comp(m, 1)]);
+            }
+            f2 W2[NW][N], s2[NW], am2[N], ap2[N];
+            typename RP::LinP L2;
+            bool badx = false, bady = false;
+            rp.normal_pair(QL, QR, W2, s2, am2, ap2, L2, badx, bady);
+#pragma unroll
+            for (int p = 0; p < NW; p++) {
+                sxw[p] = s2[p].x;
+                sy2[p] = s2[p].y;
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    Wx[p][m] = W2[p][m].x;
+                    Wy2[p][frame_comp(m, 1)] = W2[p][m].y;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < N; m++) {
+                amdq1[m] = am2[m].x;
+                apdq1[m] = ap2[m].x;
+                bm2[frame_comp(m, 1)] = am2[m].y;
+                bp2[frame_comp(m, 1)] = ap2[m].y;
+            }
+            if (trans) {
+                f2 Tm[N], Tp[N], Um[N], Up[N];
+                rp.transverse_pair(L2, am2, Tm, Tp);
+                rp.transverse_pair(L2, ap2, Um, Up);
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    BmAm1[m] = Tm[m].x; BpAm1[m] = Tp[m].x;
+                    BmAp1[m] = Um[m].x; BpAp1[m] = Up[m].x;
+                    t1[frame_comp(m, 1)] = Tm[m].y; t2[frame_comp(m, 1)] = Tp[m].y;
+                    nPm[frame_comp(m, 1)] = Um[m].y; nPp[frame_comp(m, 1)] = Up[m].y;
+                }
+            }
+            {
+                const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
+                bad |= in && bady;
+                smy = fmax(smy, in ? rp.max_speed(L2, 1) : T(0));
+            }
+            {
+                const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
+                bad |= in && badx;
+                smx = fmax(smx, in ? rp.max_speed(L2, 0) : T(0));
+            }
+            y_tail();
+        } else {
+            typename RP::Lin Ly;
+            bool bady = false;
+            rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
+            if (trans) {
+                rp.template transverse<1>(Ly, bm2, t1, t2);
+                rp.template transverse<1>(Ly, bp2, nPm, nPp);
+            }
+            y_tail();
+            {
+                const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
+                bad |= in && bady;
+                smy = fmax(smy, in ? rp.max_speed(Ly) : T(0));
+            }
+            if (k >= j0 - 2) {
+                typename RP::Lin Lx;
+                bool badx = false;
+                rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+                if (trans) {
+                    rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
+                    rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
+                }
+                const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
+                bad |= in && badx;
+                smx = fmax(smx, in ? rp.max_speed(Lx) : T(0));
+            }
         }
 
         T Fn[N], Gn[N];

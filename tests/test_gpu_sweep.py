@@ -154,3 +154,51 @@ def test_full_size_windows(solver, dtype, mx, my, bc):
         m0, m1 = qin[0].astype(np.float64).sum(), out[0].sum()
         rel = abs(m1 - m0) / m0
         assert rel <= (1e-13 if dtype == mc.F64 else 1e-6), rel
+
+
+def _transonic_state(solver, mx, my, axis, seed):
+    """A Riemann problem across the middle of the grid along `axis` whose
+    left-going rarefaction is transonic (shallow water: h = 3, u_n = 1 against
+    h = 1, u_n = 4; Euler: Toro's first test, rho, u_n, p = 1, 0.75, 1 against
+    0.125, 0, 0.1), with 1% noise and a small tangential velocity."""
+    rng = np.random.default_rng(seed)
+    left = (np.arange(mx)[None, :] < mx // 2) if axis == 0 else (np.arange(my)[:, None] < my // 2)
+    left = np.broadcast_to(left, (my, mx))
+    noise = 1 + 0.01 * rng.uniform(-1, 1, (my, mx))
+    vt = 0.1 * rng.uniform(-1, 1, (my, mx))
+    if solver == "swe":
+        q = np.zeros((3, my, mx))
+        q[0] = np.where(left, 3.0, 1.0) * noise
+        q[1 + axis] = q[0] * np.where(left, 1.0, 4.0)
+        q[2 - axis] = q[0] * vt
+        return q
+    q = np.zeros((4, my, mx))
+    rho = np.where(left, 1.0, 0.125) * noise
+    un = np.where(left, 0.75, 0.0)
+    p = np.where(left, 1.0, 0.1)
+    q[0] = rho
+    q[1 + axis] = rho * un
+    q[2 - axis] = rho * vt
+    q[3] = p / (1.4 - 1) + 0.5 * rho * (un * un + vt * vt)
+    return q
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("solver,dtype", [("swe", mc.F32), ("swe", mc.F64),
+                                          ("euler", mc.F32), ("euler", mc.F64)])
+def test_entropy_fix_transonic(solver, dtype, axis):
+    """Harten-Hyman fix at a transonic rarefaction normal to x and to y (the
+    FP32 step solves an x-edge and a y-edge side by side, so both halves of
+    that path are exercised).  The fix must matter here: the oracle without it
+    differs by far more than the parity tolerance."""
+    mx, my = 40, 36
+    q = _transonic_state(solver, mx, my, axis, seed=11 + axis)
+    bc = (X, X, X, X)
+    p, op = problems(solver, mx, my, 0.01, 0.01, dtype, bc, efix=1)
+    got, want, smax, smax_ref, *_ = run_step(p, op, q)
+    assert scaled_error(solver, got, want) <= TOL[dtype]
+    _, op0 = problems(solver, mx, my, 0.01, 0.01, dtype, bc, efix=0)
+    qo = embed(op0, q.astype(np.float32 if dtype == mc.F32 else np.float64).astype(np.float64))
+    dt = 0.9 / oracle.max_cell_speed(op0, oracle.bc_fill(op0, qo))
+    unfixed, _, _ = oracle.step(op0, qo, dt)
+    assert scaled_error(solver, unfixed[:, 2:-2, 2:-2], want) > 50 * TOL[mc.F32]
