@@ -92,6 +92,7 @@ struct AcousticsRP {
     // the sweep keeps the y-edge waves of the row below (not their products)
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
+    static constexpr bool PAIR_LIMITER = false;
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
     // max over the edge's waves of |s| (the speeds are -c, +c)
@@ -239,6 +240,7 @@ struct SweRP {
     // edge-normal frame (component 1 normal, 2 tangential momentum); the
     // same arithmetic as normal<0> / transverse<0>, two edges per instruction
     static constexpr bool PAIRED = sizeof(T) == 4;
+    static constexpr bool PAIR_LIMITER = false;
     struct LinP { f2 u, v, c, r2c; };
     __device__ __forceinline__ float max_speed(const LinP& L, int h) const
     {
@@ -373,6 +375,7 @@ struct EulerRP {
     // its 12 wave components (measured faster here)
     static constexpr bool CARRY_DOT = true;
     static constexpr bool PAIRED = sizeof(T) == 4;
+    static constexpr bool PAIR_LIMITER = true;
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 

@@ -77,6 +77,22 @@ __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
     return dr > T(0) ? phi : T(0);
 }
 
+// limiter_phi of an x-edge and a y-edge wave at once (FP32 pairs)
+__device__ __forceinline__ f2 limiter_phi_pair(int lim, f2 dl, f2 dr)
+{
+    const f2 th = p_mul(dl, p_rcp(dr));
+    f2 phi = p_set(1.f);
+    if (lim == 4) {
+        const f2 a = p_fma(th, p_set(0.5f), p_set(0.5f)), b = p_add(th, th);
+        phi.x = fmaxf(0.f, fminf(fminf(a.x, 2.f), b.x));
+        phi.y = fmaxf(0.f, fminf(fminf(a.y, 2.f), b.y));
+    } else if (lim == 1) {
+        phi.x = fmaxf(0.f, fminf(1.f, th.x));
+        phi.y = fmaxf(0.f, fminf(1.f, th.y));
+    }
+    return make_float2(dr.x > 0.f ? phi.x : 0.f, dr.y > 0.f ? phi.y : 0.f);
+}
+
 // Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage.
 struct WarpRing {
     uint64_t* bars;
@@ -315,58 +331,94 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 
         T Fn[N], Gn[N];
         if (k >= j0 - 1) {
-            // ---- F at x-edge (c-1/2, k+1)
+            // ---- limited corrections: F at x-edge (c-1/2, k+1), G at y-edge (c, k+1/2)
 #pragma unroll
-            for (int m = 0; m < N; m++) Fn[m] = T(0);
+            for (int m = 0; m < N; m++) Fn[m] = Gn[m] = T(0);
             if (second) {
+                if constexpr (RP::PAIRED && RP::PAIR_LIMITER) {
+                    // both limiters as one pair, indexed in the edge-normal
+                    // frame: .x the x-edge, .y the y-edge (component m of the
+                    // frame is component frame_comp(m, 1) of the y-edge state)
+                    const f2 nnu = make_float2(-nux, -nuy);
+                    f2 FG[N];
 #pragma unroll
-                for (int p = 0; p < NW; p++) {
-                    const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
-                    T dl = T(0), dr = T(0);
+                    for (int m = 0; m < N; m++) FG[m] = p_set(0.f);
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
+                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
+                        const bool upl = sy1[p] > T(0);
+                        f2 dl = p_set(0.f), dr = p_set(0.f), LW[N];
+#pragma unroll
+                        for (int m = 0; m < N; m++) {
+                            if (!RP::template wave_nz<0>(p, m)) continue;
+                            const int my_ = frame_comp(m, 1);
+                            LW[m] = make_float2(Wx[p][m], Wy1[p][my_]);
+                            const float wux = shfl(Wx[p][m], src);
+                            if constexpr (CD) {
+                                dl.x += wux * Wx[p][m];
+                            } else {
+                                const float wuy = upl ? Wy0[p][my_] : Wy2[p][my_];
+                                dl = p_fma(make_float2(wux, wuy), LW[m], dl);
+                            }
+                            dr = p_fma(LW[m], LW[m], dr);
+                        }
+                        if constexpr (CD) dl.y = upl ? dlo[p] : dhi[p];
+                        const f2 as = make_float2(fabsf(sxw[p]), fabsf(sy1[p]));
+                        const f2 cf = p_mul(p_mul(p_mul(p_set(0.5f), as), p_fma(nnu, as, p_set(1.f))),
+                                            limiter_phi_pair(limiter, dl, dr));
+#pragma unroll
+                        for (int m = 0; m < N; m++)
+                            if (RP::template wave_nz<0>(p, m)) FG[m] = p_fma(cf, LW[m], FG[m]);
+                    }
 #pragma unroll
                     for (int m = 0; m < N; m++) {
-                        if (!RP::template wave_nz<0>(p, m)) continue;
-                        const T wu = shfl(Wx[p][m], src);
-                        dl += wu * Wx[p][m];
-                        dr += Wx[p][m] * Wx[p][m];
+                        Fn[m] = FG[m].x;
+                        Gn[frame_comp(m, 1)] = FG[m].y;
                     }
-                    const T as = fabs(sxw[p]);
-                    const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(limiter, dl, dr);
+                } else {
 #pragma unroll
-                    for (int m = 0; m < N; m++)
-                        if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
+                    for (int p = 0; p < NW; p++) {
+                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
+                        T dl = T(0), dr = T(0);
+#pragma unroll
+                        for (int m = 0; m < N; m++) {
+                            if (!RP::template wave_nz<0>(p, m)) continue;
+                            const T wu = shfl(Wx[p][m], src);
+                            dl += wu * Wx[p][m];
+                            dr += Wx[p][m] * Wx[p][m];
+                        }
+                        const T as = fabs(sxw[p]);
+                        const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(limiter, dl, dr);
+#pragma unroll
+                        for (int m = 0; m < N; m++)
+                            if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
+                    }
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
+                        const bool upl = sy1[p] > T(0);
+                        T dl = T(0), dr = T(0);
+#pragma unroll
+                        for (int m = 0; m < N; m++) {
+                            if (!RP::template wave_nz<1>(p, m)) continue;
+                            if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
+                            dr += Wy1[p][m] * Wy1[p][m];
+                        }
+                        if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
+                        const T as = fabs(sy1[p]);
+                        const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(limiter, dl, dr);
+#pragma unroll
+                        for (int m = 0; m < N; m++)
+                            if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
+                    }
                 }
             }
+            // ---- transverse parts of F and G
             if (trans) {
 #pragma unroll
-                for (int m = 0; m < N; m++) Fn[m] -= hnuy * (TAm[m] + shfl_up1(TAp[m]));
-            }
-            // ---- G at y-edge (c, k+1/2)
-#pragma unroll
-            for (int m = 0; m < N; m++) Gn[m] = T(0);
-            if (second) {
-#pragma unroll
-                for (int p = 0; p < NW; p++) {
-                    const bool upl = sy1[p] > T(0);
-                    T dl = T(0), dr = T(0);
-#pragma unroll
-                    for (int m = 0; m < N; m++) {
-                        if (!RP::template wave_nz<1>(p, m)) continue;
-                        if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
-                        dr += Wy1[p][m] * Wy1[p][m];
-                    }
-                    if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
-                    const T as = fabs(sy1[p]);
-                    const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(limiter, dl, dr);
-#pragma unroll
-                    for (int m = 0; m < N; m++)
-                        if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
-                }
-            }
-            if (trans) {
-#pragma unroll
-                for (int m = 0; m < N; m++)
+                for (int m = 0; m < N; m++) {
+                    Fn[m] -= hnuy * (TAm[m] + shfl_up1(TAp[m]));
                     Gn[m] -= hnux * (BpAp0[m] + BmAp1[m] + shfl_down1(BpAm0[m] + BmAm1[m]));
+                }
             }
         }
 
