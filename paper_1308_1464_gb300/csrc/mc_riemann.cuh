@@ -278,7 +278,8 @@ struct SweRP {
 
         f2 k0 = p_min0(sm), k2 = p_min0(sp);
         if (efix) {
-            // the transonic tests of normal(), both halves at once
+            // the transonic tests of normal(), both halves at once and free of
+            // branches; the rare transonic edge then takes one branch
             const f2 gs = p_set(g);
             const f2 hul = ql[1], hum = p_add(ql[1], W[0][1]), hm = p_add(hl, a1);
             const f2 hur = qr[1], hun = p_sub(qr[1], W[2][1]), hn = p_sub(hr, a3);
@@ -286,23 +287,31 @@ struct SweRP {
             const f2 hum2 = p_mul(hum, hum), gm3 = p_mul(p_mul(p_mul(gs, hm), hm), hm);
             const f2 hun2 = p_mul(hun, hun), gn3 = p_mul(p_mul(p_mul(gs, hn), hn), hn);
             const f2 hur2 = p_mul(hur, hur), gr3 = p_mul(p_mul(p_mul(gs, hr), hr), hr);
+            bool t0[2], t2[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const bool l_neg = half(hul, h) <= 0.f || half(hul2, h) < half(gl3, h);
-                const bool r_pos = half(hm, h) > 0.f && half(hum, h) > 0.f && half(hum2, h) > half(gm3, h);
-                if (l_neg && r_pos) {
-                    const float lam_l = half(hul, h) * rcp_(half(hl, h)) - sqrt_(g * half(hl, h));
-                    const float lam_r = half(hum, h) * rcp_(half(hm, h)) - sqrt_(g * half(hm, h));
-                    if (lam_l < 0.f && lam_r > 0.f)
-                        half(k0, h) = (lam_r - half(sm, h)) * rcp_(lam_r - lam_l) * lam_l;
-                }
-                const bool n_neg = half(hn, h) > 0.f && half(hun, h) < 0.f && half(hun2, h) > half(gn3, h);
-                const bool rr_pos = half(hur, h) >= 0.f || half(hur2, h) < half(gr3, h);
-                if (n_neg && rr_pos) {
-                    const float ll = half(hun, h) * rcp_(half(hn, h)) + sqrt_(g * half(hn, h));
-                    const float lr = half(hur, h) * rcp_(half(hr, h)) + sqrt_(g * half(hr, h));
-                    if (ll < 0.f && lr > 0.f)
-                        half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                const bool l_neg = (half(hul, h) <= 0.f) | (half(hul2, h) < half(gl3, h));
+                const bool r_pos = (half(hm, h) > 0.f) & (half(hum, h) > 0.f) & (half(hum2, h) > half(gm3, h));
+                const bool n_neg = (half(hn, h) > 0.f) & (half(hun, h) < 0.f) & (half(hun2, h) > half(gn3, h));
+                const bool rr_pos = (half(hur, h) >= 0.f) | (half(hur2, h) < half(gr3, h));
+                t0[h] = l_neg & r_pos;
+                t2[h] = n_neg & rr_pos;
+            }
+            if (t0[0] | t0[1] | t2[0] | t2[1]) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    if (t0[h]) {
+                        const float lam_l = half(hul, h) * rcp_(half(hl, h)) - sqrt_(g * half(hl, h));
+                        const float lam_r = half(hum, h) * rcp_(half(hm, h)) - sqrt_(g * half(hm, h));
+                        if (lam_l < 0.f && lam_r > 0.f)
+                            half(k0, h) = (lam_r - half(sm, h)) * rcp_(lam_r - lam_l) * lam_l;
+                    }
+                    if (t2[h]) {
+                        const float ll = half(hun, h) * rcp_(half(hn, h)) + sqrt_(g * half(hn, h));
+                        const float lr = half(hur, h) * rcp_(half(hr, h)) + sqrt_(g * half(hr, h));
+                        if (ll < 0.f && lr > 0.f)
+                            half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                    }
                 }
             }
         }
@@ -415,6 +424,11 @@ struct EulerRP {
     __device__ __forceinline__ T g_rho2e(const T* q) const
     {
         return gamma * gm1 * (q[3] * q[0] - T(0.5) * (q[1] * q[1] + q[2] * q[2]));
+    }
+    __device__ __forceinline__ f2 g_rho2e_pair(const f2* q) const
+    {
+        return p_mul(p_set(gamma * gm1),
+                     p_fma(q[3], q[0], p_mul(p_set(-0.5f), p_fma(q[1], q[1], p_mul(q[2], q[2])))));
     }
     // u_n < c_K (sgn = false: u - c < 0) or u_n < -c (sgn = true: u + c < 0),
     // each also requiring a physical state
@@ -583,29 +597,60 @@ struct EulerRP {
 
         f2 k0 = p_min0(sm), k2 = p_min0(sp);
         if (efix) {
-            // the tests of normal(), one half at a time (frame = x-edge frame)
+            // the tests of normal() for both halves, free of branches: for a
+            // state q, e = gamma (gamma-1) rho^2 e_int, m its normal momentum;
+            // u < c <=> m <= 0 or m^2 < e, u > c <=> m > 0 and m^2 > e, and the
+            // mirror tests for u + c (each also needs rho > 0 and e > 0)
+            f2 qm0[NEQ], qm2[NEQ];
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) {
+                qm0[m] = p_add(ql[m], W[0][m]);
+                qm2[m] = p_sub(qr[m], W[2][m]);
+            }
+            const f2 e_l = g_rho2e_pair(ql), e_m0 = g_rho2e_pair(qm0);
+            const f2 e_m2 = g_rho2e_pair(qm2), e_r = g_rho2e_pair(qr);
+            const f2 ml2 = p_mul(ql[1], ql[1]), mm02 = p_mul(qm0[1], qm0[1]);
+            const f2 mm22 = p_mul(qm2[1], qm2[1]), mr2 = p_mul(qr[1], qr[1]);
+            bool t0[2], t2[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                float qa[NEQ], qm[NEQ];
+                const bool ok_l = (half(ql[0], h) > 0.f) & (half(e_l, h) > 0.f);
+                const bool ok_m0 = (half(qm0[0], h) > 0.f) & (half(e_m0, h) > 0.f);
+                const bool ok_m2 = (half(qm2[0], h) > 0.f) & (half(e_m2, h) > 0.f);
+                const bool ok_r = (half(qr[0], h) > 0.f) & (half(e_r, h) > 0.f);
+                // wave 1: u - c < 0 on the left, u - c > 0 in the middle state
+                const bool l_slow = ok_l & ((half(ql[1], h) <= 0.f) | (half(ml2, h) < half(e_l, h)));
+                const bool m_fast = ok_m0 & (half(qm0[1], h) > 0.f) & (half(mm02, h) > half(e_m0, h));
+                // wave 3: u + c < 0 in the middle state, u + c > 0 on the right
+                const bool m_neg = ok_m2 & (half(qm2[1], h) < 0.f) & (half(mm22, h) > half(e_m2, h));
+                const bool r_pos = ok_r & ((half(qr[1], h) >= 0.f) | (half(mr2, h) < half(e_r, h)));
+                t0[h] = l_slow & m_fast;
+                t2[h] = m_neg & r_pos;
+            }
+            if (t0[0] | t0[1] | t2[0] | t2[1]) {
 #pragma unroll
-                for (int m = 0; m < NEQ; m++) {
-                    qa[m] = half(ql[m], h);
-                    qm[m] = qa[m] + half(W[0][m], h);
-                }
-                if (slower_than_sound<0>(qa, false) && faster_than_sound<0>(qm, true)) {
-                    float ll, lr;
-                    if (cspeed<0>(qa, -1.f, ll) && cspeed<0>(qm, -1.f, lr) && ll < 0.f && lr > 0.f)
-                        half(k0, h) = (lr - half(sm, h)) * rcp_(lr - ll) * ll;
-                }
+                for (int h = 0; h < 2; h++) {
+                    float qa[NEQ], qb[NEQ];
+                    if (t0[h]) {
 #pragma unroll
-                for (int m = 0; m < NEQ; m++) {
-                    qa[m] = half(qr[m], h);
-                    qm[m] = qa[m] - half(W[2][m], h);
-                }
-                if (faster_than_sound<0>(qm, false) && slower_than_sound<0>(qa, true)) {
-                    float ll, lr;
-                    if (cspeed<0>(qm, 1.f, ll) && cspeed<0>(qa, 1.f, lr) && ll < 0.f && lr > 0.f)
-                        half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                        for (int m = 0; m < NEQ; m++) {
+                            qa[m] = half(ql[m], h);
+                            qb[m] = half(qm0[m], h);
+                        }
+                        float ll, lr;
+                        if (cspeed<0>(qa, -1.f, ll) && cspeed<0>(qb, -1.f, lr) && ll < 0.f && lr > 0.f)
+                            half(k0, h) = (lr - half(sm, h)) * rcp_(lr - ll) * ll;
+                    }
+                    if (t2[h]) {
+#pragma unroll
+                        for (int m = 0; m < NEQ; m++) {
+                            qa[m] = half(qm2[m], h);
+                            qb[m] = half(qr[m], h);
+                        }
+                        float ll, lr;
+                        if (cspeed<0>(qa, 1.f, ll) && cspeed<0>(qb, 1.f, lr) && ll < 0.f && lr > 0.f)
+                            half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                    }
                 }
             }
         }

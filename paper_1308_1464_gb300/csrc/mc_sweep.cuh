@@ -65,8 +65,10 @@ struct SweepArgs {
 };
 
 // phi(theta) with theta = dl / dr, branch-free: minmod (1), MC (4) or none
-// (0: phi = 1); a zero wave (dr = 0) gets no correction.  With a
-// compile-time limiter the selection folds away.
+// (0: phi = 1).  With a compile-time limiter the selection folds away.  A
+// zero wave (dr = 0) needs no test: theta is then NaN or infinite, min/max
+// return their other operand, so phi stays in [0, 2] and multiplies a wave
+// whose components are all zero.
 template <typename T>
 __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
 {
@@ -74,7 +76,7 @@ __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
     T phi = T(1);
     if (lim == 4) phi = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
     else if (lim == 1) phi = fmax(T(0), fmin(T(1), th));
-    return dr > T(0) ? phi : T(0);
+    return phi;
 }
 
 // limiter_phi of an x-edge and a y-edge wave at once (FP32 pairs)
@@ -90,7 +92,7 @@ __device__ __forceinline__ f2 limiter_phi_pair(int lim, f2 dl, f2 dr)
         phi.x = fmaxf(0.f, fminf(1.f, th.x));
         phi.y = fmaxf(0.f, fminf(1.f, th.y));
     }
-    return make_float2(dr.x > 0.f ? phi.x : 0.f, dr.y > 0.f ? phi.y : 0.f);
+    return phi;
 }
 
 // Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage.
