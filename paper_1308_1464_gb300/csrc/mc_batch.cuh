@@ -160,18 +160,18 @@ __global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long lo
     const PatchDesc d = patches[blockIdx.x];
     T* q = static_cast<T*>(d.qa);
     // ghosts: x of interior rows, then y over the full width (corners)
-    const long long W = d.mx + 4;
-    const long long nghost = 4 * W + 4LL * d.my;
-    for (long long g = threadIdx.x; g < nghost; g += blockDim.x) {
+    const int W = d.mx + 4;
+    const int nghost = 4 * W + 4 * d.my;
+    for (int g = threadIdx.x; g < nghost; g += blockDim.x) {
         int i, j;
         if (g < 4 * W) {
-            const int jr = int(g / W);
+            const int jr = g / W;
             j = jr < 2 ? jr - 2 : d.my + jr - 2;
-            i = int(g % W) - 2;
+            i = g - jr * W - 2;
         } else {
-            const long long u = g - 4 * W;
-            j = int(u / 4);
-            const int ir = int(u % 4);
+            const int u = g - 4 * W;
+            j = u >> 2;
+            const int ir = u & 3;
             i = ir < 2 ? ir - 2 : d.mx + ir - 2;
         }
         bool fx = false, fy = false;
@@ -183,16 +183,21 @@ __global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long lo
             q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i] = v;
         }
     }
-    double v = 0.0;
-    const long long n = (long long)d.mx * d.my;
-    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
-        const int i = int(k % d.mx), j = int(k / d.mx);
-        T qq[RP::NEQ];
-        for (int m = 0; m < RP::NEQ; m++) qq[m] = q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i];
-        T sx, sy;
-        rp.cell_speeds(qq, sx, sy);
-        v = fmax(v, fmax(double(sx) / d.dx, double(sy) / d.dy));
+    // cell-speed maxima (see max_cell_speed_kernel): warps take rows
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T msx = T(0), msy = T(0);
+    for (int j = threadIdx.x >> 5; j < d.my; j += nw) {
+        const T* row = q + (long long)(j + 2) * d.ld_x + x_offset;
+        for (int i = lane; i < d.mx; i += 32) {
+            T qq[RP::NEQ];
+            for (int m = 0; m < RP::NEQ; m++) qq[m] = row[m * d.ld_field + i];
+            T sx, sy;
+            rp.cell_speeds(qq, sx, sy);
+            msx = fmax(msx, sx);
+            msy = fmax(msy, sy);
+        }
     }
+    double v = fmax(double(msx) / d.dx, double(msy) / d.dy);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&smax[(long long)blockIdx.x * stride], v);

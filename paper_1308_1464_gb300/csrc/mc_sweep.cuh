@@ -629,21 +629,28 @@ __global__ void max_cell_speed_kernel(const RP rp, const typename RP::real* q, i
                                       long long ld_x, long long ld_field, long long x_offset,
                                       double dx, double dy, unsigned long long* out)
 {
+    // warps take rows, lanes columns.  The maxima of the x and y speeds are
+    // kept in the state's precision and divided by dx, dy once: division by
+    // a positive number preserves order, so the result equals the maximum of
+    // the per-cell quotients.
     using T = typename RP::real;
-    double v = 0.0;
-    const long long n = (long long)mx * my;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = int(t % mx), j = int(t / mx);
-        T qq[RP::NEQ];
-        for (int m = 0; m < RP::NEQ; m++) qq[m] = q[m * ld_field + (j + 2) * ld_x + x_offset + i];
-        T sx, sy;
-        rp.cell_speeds(qq, sx, sy);
-        v = fmax(v, fmax(double(sx) / dx, double(sy) / dy));
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    T msx = T(0), msy = T(0);
+    for (int j = blockIdx.x * nw + (threadIdx.x >> 5); j < my; j += gridDim.x * nw) {
+        const T* row = q + (long long)(j + 2) * ld_x + x_offset;
+        for (int i = lane; i < mx; i += 32) {
+            T qq[RP::NEQ];
+            for (int m = 0; m < RP::NEQ; m++) qq[m] = row[m * ld_field + i];
+            T sx, sy;
+            rp.cell_speeds(qq, sx, sy);
+            msx = fmax(msx, sx);
+            msy = fmax(msy, sy);
+        }
     }
+    double v = fmax(double(msx) / dx, double(msy) / dy);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, v);
+    if (lane == 0) atomic_max_nonneg(out, v);
 }
 
 }  // namespace mc

@@ -72,8 +72,7 @@ cudaError_t maxspeed_launch_t(const mc_problem& p, const mc_layout& lay, const v
     using T = typename RP::real;
     RP rp;
     rp.setup(p.param, p.efix);
-    long long n = (long long)p.mx * p.my;
-    int blocks = int((n + 255) / 256);
+    int blocks = (p.my + 7) / 8;   // 8 warps of 256 threads, one row each
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     max_cell_speed_kernel<RP><<<blocks, 256, 0, s>>>(rp, static_cast<const T*>(q), p.mx, p.my,
