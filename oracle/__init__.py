@@ -27,8 +27,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["rp.c", "step.c", "exact.c", "mlp.c"]
 _LIBDIR = os.path.join(_HERE, "_lib")
 
-ACOUSTICS, SWE, EULER = 1, 2, 3
-LIM_NONE, LIM_MINMOD, LIM_MC = 0, 1, 4
+ACOUSTICS, SWE, EULER, ADVECTION = 1, 2, 3, 4
+LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_EXTRAP, BC_WALL, BC_GIVEN = 0, 1, 2, 3
 SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_GIVEN = range(6)
 RS_OK, RS_VACUUM, RS_NOCONV, RS_FALLBACK = 0, 1, 2, 4
@@ -83,11 +83,11 @@ class Problem:
 
     @property
     def meqn(self) -> int:
-        return 4 if self.solver == EULER else 3
+        return {EULER: 4, ADVECTION: 1}.get(self.solver, 3)
 
     @property
     def mwaves(self) -> int:
-        return 2 if self.solver == ACOUSTICS else 3
+        return {ACOUSTICS: 2, ADVECTION: 1}.get(self.solver, 3)
 
     @property
     def shape(self) -> tuple:

@@ -27,8 +27,12 @@
 extern "C" {
 #endif
 
-enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3 };
-enum { MCREF_LIM_NONE = 0, MCREF_LIM_MINMOD = 1, MCREF_LIM_MC = 4 };
+/* MCREF_ADVECTION: scalar q_t + u q_x + v q_y = 0 with constant (u, v) =
+ * (param[0], param[1]) (the paper's advection solver, §3) */
+enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3, MCREF_ADVECTION = 4 };
+/* Clawpack numbering: 1 minmod, 2 superbee, 3 van Leer, 4 monotonized central */
+enum { MCREF_LIM_NONE = 0, MCREF_LIM_MINMOD = 1, MCREF_LIM_SUPERBEE = 2, MCREF_LIM_VANLEER = 3,
+       MCREF_LIM_MC = 4 };
 /* MCREF_BC_GIVEN leaves that side's ghost layers as the caller set them: the
  * step of a window cut out of a larger grid then uses the true neighbours. */
 enum { MCREF_BC_PERIODIC = 0, MCREF_BC_EXTRAP = 1, MCREF_BC_WALL = 2, MCREF_BC_GIVEN = 3 };
@@ -40,16 +44,17 @@ enum { MCREF_F_NONPHYS = 1 };
 #define MCREF_MAXWAVE 3
 
 typedef struct {
-    int solver;      /* MCREF_ACOUSTICS | MCREF_SWE | MCREF_EULER */
+    int solver;      /* MCREF_ACOUSTICS | MCREF_SWE | MCREF_EULER | MCREF_ADVECTION */
     int mx, my;      /* interior cells */
     int mbc;         /* ghost layers, 2 */
     double dx, dy;
     int limiter;     /* MCREF_LIM_* */
     int order;       /* 1: no second-order corrections, 2: limited corrections */
-    int transverse;  /* 0: none, 1: transverse split of the fluctuations */
+    int transverse;  /* 0: none, 1: transverse split of the fluctuations,
+                      * 2: also of the limited corrections */
     int efix;        /* Harten-Hyman entropy fix on the nonlinear fields */
     int bc[4];       /* xlo, xhi, ylo, yhi */
-    double param[4]; /* acoustics: rho, K | swe: g | euler: gamma */
+    double param[4]; /* acoustics: rho, K | swe: g | euler: gamma | advection: u, v */
 } mcref_problem;
 
 int mcref_meqn(int solver);

@@ -21,7 +21,7 @@
 
 int mcref_meqn(int solver)
 {
-    return solver == MCREF_EULER ? 4 : 3;
+    return solver == MCREF_EULER ? 4 : (solver == MCREF_ADVECTION ? 1 : 3);
 }
 
 int mcref_mwaves(int solver)
@@ -30,6 +30,7 @@ int mcref_mwaves(int solver)
      * produces no fluctuation and no correction, so it is not carried.
      * Euler: entropy and shear waves travel at the same speed and are
      * carried as one wave. */
+    if (solver == MCREF_ADVECTION) return 1;
     return solver == MCREF_ACOUSTICS ? 2 : 3;
 }
 
@@ -161,6 +162,16 @@ int mcref_rpn2(const mcref_problem* p, int dir, const double* ql, const double* 
     double d[MCREF_MAXEQN], vec[4][MCREF_MAXEQN], lam[4];
     int flags = 0;
     for (int m = 0; m < meqn; m++) d[m] = qr[m] - ql[m];
+    if (p->solver == MCREF_ADVECTION) {
+        /* one wave, the jump, moving at the velocity normal to the edge
+         * (LeVeque 2002, §4.8 and §20.1) */
+        const double sn = p->param[dir];
+        wave[0] = d[0];
+        s[0] = sn;
+        amdq[0] = (sn < 0.0 ? sn : 0.0) * d[0];
+        apdq[0] = (sn > 0.0 ? sn : 0.0) * d[0];
+        return 0;
+    }
     roe_state st = roe_average(p, dir, ql, qr);
     if (!st.ok) {
         /* Non-physical input: report it and return zero waves. */
@@ -224,6 +235,13 @@ int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* 
 {
     const int meqn = mcref_meqn(p->solver);
     double vec[4][MCREF_MAXEQN], lam[4];
+    if (p->solver == MCREF_ADVECTION) {
+        /* the transverse velocity carries the whole fluctuation (§20.2) */
+        const double st = p->param[1 - dir];
+        bmasdq[0] = (st < 0.0 ? st : 0.0) * asdq[0];
+        bpasdq[0] = (st > 0.0 ? st : 0.0) * asdq[0];
+        return 0;
+    }
     roe_state st = roe_average(p, dir, ql, qr);
     for (int m = 0; m < meqn; m++) bmasdq[m] = bpasdq[m] = 0.0;
     if (!st.ok) return MCREF_F_NONPHYS;
@@ -247,6 +265,10 @@ int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* 
 void mcref_flux(const mcref_problem* p, int dir, const double* q, double* f)
 {
     const int mu = 1 + dir, mv = 2 - dir;
+    if (p->solver == MCREF_ADVECTION) {
+        f[0] = p->param[dir] * q[0];
+        return;
+    }
     if (p->solver == MCREF_ACOUSTICS) {
         double rho = p->param[0], K = p->param[1];
         f[0] = K * q[mu];
@@ -276,6 +298,18 @@ double mcref_philim(int limiter, double theta)
     case MCREF_LIM_MINMOD: {
         double a = theta < 1.0 ? theta : 1.0;
         return a > 0.0 ? a : 0.0;
+    }
+    case MCREF_LIM_SUPERBEE: {
+        /* max(0, min(1, 2 theta), min(2, theta)) */
+        double a = 2.0 * theta < 1.0 ? 2.0 * theta : 1.0;
+        double b = theta < 2.0 ? theta : 2.0;
+        double c = a > b ? a : b;
+        return c > 0.0 ? c : 0.0;
+    }
+    case MCREF_LIM_VANLEER: {
+        /* (theta + |theta|) / (1 + |theta|) */
+        double at = fabs(theta);
+        return (theta + at) / (1.0 + at);
     }
     case MCREF_LIM_MC: {
         double a = 0.5 * (1.0 + theta);

@@ -170,6 +170,33 @@ static void limited_correction(const mcref_problem* p, const edge_arrays* e, int
     }
 }
 
+/* The fluctuations an edge sends into its two cells, as the transverse split
+ * sees them.  Option 1 splits A+dQ (into the high cell) and A-dQ (into the
+ * low cell).  Option 2 splits the whole first- plus second-order
+ * contribution of the edge to each cell: the update takes
+ * -dt/dx (A+dQ - F) from the high cell and -dt/dx (A-dQ + F) from the low
+ * cell, F the limited correction of the edge (LeVeque 2002, ch. 21:
+ * transverse propagation of the correction waves; Clawpack's
+ * transverse_waves = 2). */
+static void effective_fluctuations(const mcref_problem* p, const edge_arrays* e, int dir, int i,
+                                   int j, double dtdx, double* ap, double* am)
+{
+    const int meqn = e->meqn;
+    const int64_t k = eidx(e, i, j);
+    for (int m = 0; m < meqn; m++) {
+        ap[m] = e->apdq[k * meqn + m];
+        am[m] = e->amdq[k * meqn + m];
+    }
+    if (p->transverse == 2 && p->order >= 2) {
+        double cq[MCREF_MAXEQN];
+        limited_correction(p, e, dir, i, j, dtdx, cq);
+        for (int m = 0; m < meqn; m++) {
+            ap[m] -= cq[m];
+            am[m] += cq[m];
+        }
+    }
+}
+
 int mcref_step(const mcref_problem* p, const double* qin, double* qout, double dt,
                double* smax_out, int nthreads)
 {
@@ -223,8 +250,11 @@ int mcref_step(const mcref_problem* p, const double* qin, double* qout, double d
                 get_cell(p, q, i - 1, j, ql);
                 get_cell(p, q, i, j, qr);
                 int64_t k = eidx(&ex, i, j);
-                mcref_rpt2(p, 0, ql, qr, ex.apdq + k * meqn, t, t + meqn);
-                mcref_rpt2(p, 0, ql, qr, ex.amdq + k * meqn, t + 2 * meqn, t + 3 * meqn);
+                double ap[MCREF_MAXEQN], am[MCREF_MAXEQN];
+                effective_fluctuations(p, &ex, 0, i, j, dtdx, ap, am);
+                mcref_rpt2(p, 0, ql, qr, ap, t, t + meqn);
+                mcref_rpt2(p, 0, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
+                (void)k;
             }
         }
         for (int j = -1; j <= my; j++) {
@@ -255,9 +285,10 @@ int mcref_step(const mcref_problem* p, const double* qin, double* qout, double d
                 double* t = ty + (((int64_t)j) * nyc + (i + 1)) * 4 * meqn;
                 get_cell(p, q, i, j - 1, ql);
                 get_cell(p, q, i, j, qr);
-                int64_t k = eidx(&ey, i, j);
-                mcref_rpt2(p, 1, ql, qr, ey.apdq + k * meqn, t, t + meqn);
-                mcref_rpt2(p, 1, ql, qr, ey.amdq + k * meqn, t + 2 * meqn, t + 3 * meqn);
+                double ap[MCREF_MAXEQN], am[MCREF_MAXEQN];
+                effective_fluctuations(p, &ey, 1, i, j, dtdy, ap, am);
+                mcref_rpt2(p, 1, ql, qr, ap, t, t + meqn);
+                mcref_rpt2(p, 1, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
             }
         }
         for (int j = 0; j <= my; j++) {
@@ -332,6 +363,9 @@ double mcref_max_cell_speed(const mcref_problem* p, const double* q)
             double u = 0, w = 0, c;
             if (p->solver == MCREF_ACOUSTICS) {
                 c = sqrt(p->param[1] / p->param[0]);
+            } else if (p->solver == MCREF_ADVECTION) {
+                u = p->param[0]; w = p->param[1];
+                c = 0.0;
             } else if (p->solver == MCREF_SWE) {
                 u = v[1] / v[0]; w = v[2] / v[0];
                 c = sqrt(p->param[0] * v[0]);

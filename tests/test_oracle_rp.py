@@ -278,15 +278,25 @@ def _golden_limiter():
 
 
 def test_limiter_table(oracle_mod):
-    for theta, phi_mm, phi_mc in _golden_limiter():
+    for theta, phi_mm, phi_mc, phi_sb, phi_vl in _golden_limiter():
         assert oracle_mod.philim(oracle_mod.LIM_MINMOD, theta) == pytest.approx(phi_mm, abs=1e-15)
         assert oracle_mod.philim(oracle_mod.LIM_MC, theta) == pytest.approx(phi_mc, abs=1e-15)
+        assert oracle_mod.philim(oracle_mod.LIM_SUPERBEE, theta) == pytest.approx(phi_sb, abs=1e-15)
+        assert oracle_mod.philim(oracle_mod.LIM_VANLEER, theta) == pytest.approx(phi_vl, abs=1e-15)
         assert oracle_mod.philim(oracle_mod.LIM_NONE, theta) == 1.0
 
 
 def test_limiter_tvd_region(oracle_mod):
-    """Sweby's TVD region: 0 <= phi <= min(2, 2 theta) for theta > 0, phi = 0 below, phi(1) = 1."""
-    for lim in (oracle_mod.LIM_MINMOD, oracle_mod.LIM_MC):
+    """Sweby's TVD region: 0 <= phi <= min(2, 2 theta) for theta > 0, phi = 0 below, phi(1) = 1;
+    minmod and superbee are its lower and upper boundaries, so every limiter lies between them."""
+    lims = (oracle_mod.LIM_MINMOD, oracle_mod.LIM_SUPERBEE, oracle_mod.LIM_VANLEER, oracle_mod.LIM_MC)
+    for theta in np.linspace(-5, 10, 301):
+        lo = oracle_mod.philim(oracle_mod.LIM_MINMOD, theta)
+        hi = oracle_mod.philim(oracle_mod.LIM_SUPERBEE, theta)
+        assert hi == pytest.approx(max(0.0, min(1.0, 2 * theta), min(2.0, theta)) if theta > 0 else 0.0)
+        for lim in lims:
+            assert lo - 1e-15 <= oracle_mod.philim(lim, theta) <= hi + 1e-15
+    for lim in lims:
         for theta in np.linspace(-5, 10, 301):
             phi = oracle_mod.philim(lim, theta)
             if theta <= 0:

@@ -44,9 +44,16 @@ def interior(prob, q):
     return q[:, m:-m, m:-m]
 
 
-def make(oracle, solver, mx, my, dx, dy, bc, limiter=None, efix=1, transverse=1, order=2):
-    sid = {"acoustics": oracle.ACOUSTICS, "swe": oracle.SWE, "euler": oracle.EULER}[solver]
-    param = {"acoustics": (1.0, 4.0, 0, 0), "swe": (G, 0, 0, 0), "euler": (GAMMA, 0, 0, 0)}[solver]
+ADV_UV = (1.0, 0.6)
+
+
+def make(oracle, solver, mx, my, dx, dy, bc, limiter=None, efix=1, transverse=1, order=2,
+         param=None):
+    sid = {"acoustics": oracle.ACOUSTICS, "swe": oracle.SWE, "euler": oracle.EULER,
+           "advection": oracle.ADVECTION}[solver]
+    if param is None:
+        param = {"acoustics": (1.0, 4.0, 0, 0), "swe": (G, 0, 0, 0), "euler": (GAMMA, 0, 0, 0),
+                 "advection": ADV_UV + (0, 0)}[solver]
     return oracle.Problem(sid, mx, my, dx, dy, limiter=oracle.LIM_MC if limiter is None else limiter,
                           order=order, transverse=transverse, efix=efix, bc=bc, param=param)
 
@@ -56,6 +63,8 @@ def smooth_state(solver, mx, my, rng):
     y = (np.arange(my) + 0.5) / my
     X, Y = np.meshgrid(x, y)
     bump = np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+    if solver == "advection":
+        return (np.exp(-30 * ((X - 0.4) ** 2 + (Y - 0.5) ** 2)) + 0.3 * bump)[None]
     if solver == "acoustics":
         return np.stack([bump, 0.3 * np.cos(2 * np.pi * X), 0.2 * np.sin(2 * np.pi * Y)])
     if solver == "swe":
@@ -67,10 +76,13 @@ def smooth_state(solver, mx, my, rng):
     return np.stack([rho, rho * u, rho * v, p / (GAMMA - 1) + 0.5 * rho * (u * u + v * v)])
 
 
-@pytest.mark.parametrize("solver", ["acoustics", "swe", "euler"])
-def test_conservation_periodic(oracle_mod, solver):
+@pytest.mark.parametrize("solver,transverse,limiter", [
+    ("acoustics", 1, None), ("swe", 1, None), ("euler", 1, None), ("advection", 1, None),
+    ("acoustics", 2, 3), ("swe", 2, 2), ("euler", 2, None), ("advection", 2, 2)])
+def test_conservation_periodic(oracle_mod, solver, transverse, limiter):
     mx, my = 24, 20
-    prob = make(oracle_mod, solver, mx, my, 1.0 / mx, 1.0 / my, (oracle_mod.BC_PERIODIC,) * 4)
+    prob = make(oracle_mod, solver, mx, my, 1.0 / mx, 1.0 / my, (oracle_mod.BC_PERIODIC,) * 4,
+                transverse=transverse, limiter=limiter)
     q = embed(prob, smooth_state(solver, mx, my, np.random.default_rng(1)))
     q = oracle_mod.bc_fill(prob, q)
     tot0 = interior(prob, q).sum(axis=(1, 2))
@@ -343,35 +355,50 @@ def naive_step(oracle_mod, prob, q, dt):
             out += 0.5 * abs(S[w]) * (1 - nu * abs(S[w])) * phi * W[w]
         return out
 
+    def lim_x(i, j):
+        return limited(xe(i, j), xe(i - 1, j), xe(i + 1, j), nux)
+
+    def lim_y(i, j):
+        return limited(ye(i, j), ye(i, j - 1), ye(i, j + 1), nuy)
+
+    # what an edge sends into its high / low cell, as the transverse split
+    # sees it: with transverse = 2 the edge's whole contribution to that
+    # cell's update, fluctuation and limited correction
+    t2 = prob.transverse == 2 and prob.order >= 2
+
+    def into_hi_y(i, j):
+        return ye(i, j)[3] - (lim_y(i, j) if t2 else 0.0)
+
+    def into_lo_y(i, j):
+        return ye(i, j)[2] + (lim_y(i, j) if t2 else 0.0)
+
+    def into_hi_x(i, j):
+        return xe(i, j)[3] - (lim_x(i, j) if t2 else 0.0)
+
+    def into_lo_x(i, j):
+        return xe(i, j)[2] + (lim_x(i, j) if t2 else 0.0)
+
     def Fx(i, j):   # correction flux at x-edge (i, j)
-        F = limited(xe(i, j), xe(i - 1, j), xe(i + 1, j), nux)
+        F = lim_x(i, j)
         if prob.transverse:
             # y-edge fluctuations entering cell (i, j) move left across this edge,
             # those entering (i-1, j) move right across it
             tr = np.zeros(prob.meqn)
-            bpdq = ye(i, j)[3]
-            tr += oracle_mod.rpt2(prob, 1, Q(i, j - 1), Q(i, j), bpdq)[0]
-            bmdq = ye(i, j + 1)[2]
-            tr += oracle_mod.rpt2(prob, 1, Q(i, j), Q(i, j + 1), bmdq)[0]
-            bpdq = ye(i - 1, j)[3]
-            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j - 1), Q(i - 1, j), bpdq)[1]
-            bmdq = ye(i - 1, j + 1)[2]
-            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j), Q(i - 1, j + 1), bmdq)[1]
+            tr += oracle_mod.rpt2(prob, 1, Q(i, j - 1), Q(i, j), into_hi_y(i, j))[0]
+            tr += oracle_mod.rpt2(prob, 1, Q(i, j), Q(i, j + 1), into_lo_y(i, j + 1))[0]
+            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j - 1), Q(i - 1, j), into_hi_y(i - 1, j))[1]
+            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j), Q(i - 1, j + 1), into_lo_y(i - 1, j + 1))[1]
             F -= 0.5 * nuy * tr
         return F
 
     def Gy(i, j):   # correction flux at y-edge (i, j)
-        Gv = limited(ye(i, j), ye(i, j - 1), ye(i, j + 1), nuy)
+        Gv = lim_y(i, j)
         if prob.transverse:
             tr = np.zeros(prob.meqn)
-            apdq = xe(i, j)[3]
-            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j), Q(i, j), apdq)[0]
-            amdq = xe(i + 1, j)[2]
-            tr += oracle_mod.rpt2(prob, 0, Q(i, j), Q(i + 1, j), amdq)[0]
-            apdq = xe(i, j - 1)[3]
-            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j - 1), Q(i, j - 1), apdq)[1]
-            amdq = xe(i + 1, j - 1)[2]
-            tr += oracle_mod.rpt2(prob, 0, Q(i, j - 1), Q(i + 1, j - 1), amdq)[1]
+            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j), Q(i, j), into_hi_x(i, j))[0]
+            tr += oracle_mod.rpt2(prob, 0, Q(i, j), Q(i + 1, j), into_lo_x(i + 1, j))[0]
+            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j - 1), Q(i, j - 1), into_hi_x(i, j - 1))[1]
+            tr += oracle_mod.rpt2(prob, 0, Q(i, j - 1), Q(i + 1, j - 1), into_lo_x(i + 1, j - 1))[1]
             Gv -= 0.5 * nux * tr
         return Gv
 
@@ -390,6 +417,11 @@ def naive_step(oracle_mod, prob, q, dt):
     ("swe", 5, 5, (0, 0, 2, 2), 1, 1),
     ("euler", 5, 4, (1, 1, 1, 1), 4, 1),
     ("euler", 4, 4, (2, 0, 0, 2), 1, 0),
+    ("acoustics", 4, 5, (0, 0, 2, 1), 3, 2),
+    ("swe", 5, 4, (2, 2, 0, 0), 2, 2),
+    ("euler", 4, 5, (1, 1, 0, 0), 4, 2),
+    ("advection", 5, 4, (0, 0, 0, 0), 3, 2),
+    ("advection", 4, 4, (1, 1, 2, 2), 2, 1),
 ])
 def test_brute_force_tiny_grids(oracle_mod, solver, mx, my, bc, lim, transverse):
     rng = np.random.default_rng(mx * 10 + my)
@@ -477,3 +509,85 @@ def test_given_ghosts_window_equals_full_grid(oracle_mod):
         qw = q[:, j0: j0 + h + 4, i0: i0 + w + 4].copy()
         out, _, _ = oracle_mod.step(win, qw, dt)
         np.testing.assert_array_equal(out[:, 2:-2, 2:-2], full[:, j0 + 2: j0 + h + 2, i0 + 2: i0 + w + 2])
+
+
+# ----------------------------------------------------------------- advection
+
+def test_advection_courant_one_exact_shift(oracle_mod):
+    """u = 1, v = 0, dt = dx: the profile moves exactly one cell to the right,
+    at any order and limiter (the correction factor 1 - dt/dx |s| vanishes)."""
+    mx, my = 20, 6
+    dx = 1.0 / mx
+    for lim in (0, 1, 2, 3, 4):
+        for tr in (0, 1, 2):
+            prob = make(oracle_mod, "advection", mx, my, dx, dx, (oracle_mod.BC_PERIODIC,) * 4,
+                        limiter=lim, transverse=tr, param=(1.0, 0.0, 0, 0))
+            q0 = smooth_state("advection", mx, my, None)
+            q1, smax, _ = oracle_mod.step(prob, embed(prob, q0), dx)
+            assert smax * dx == pytest.approx(1.0, abs=1e-15)
+            np.testing.assert_allclose(interior(prob, q1), np.roll(q0, 1, axis=2), atol=1e-14)
+
+
+def _advection_ctu_lw_stencil(Q, nu, mu, transverse):
+    """One step of the wave-propagation method for q_t + u q_x + v q_y = 0 with
+    u, v > 0, no limiter (phi = 1) and periodic boundaries, written out by hand
+    as a stencil (LeVeque 2002, ch. 20-21).  With Dx Q_ij = Q_ij - Q_i-1,j,
+    Dy likewise, nu = u dt/dx, mu = v dt/dy, the correction fluxes divided by
+    u (f, at x-edge i+1/2) and by v (g, at y-edge j+1/2) are
+
+      transverse 1: f = (1-nu)/2 Dx Q_i+1,j - mu/2 Dy Q_ij
+                    g = (1-mu)/2 Dy Q_i,j+1 - nu/2 Dx Q_ij
+      transverse 2: f = (1-nu)/2 Dx Q_i+1,j - mu/4 [(1+mu) Dy Q_ij + (1-mu) Dy Q_i,j+1]
+                    g = (1-mu)/2 Dy Q_i,j+1 - nu/4 [(1+nu) Dx Q_ij + (1-nu) Dx Q_i+1,j]
+
+    (option 2 splits u Dx Q - F = u(1+nu)/2 Dx Q into the cell on the right of
+    an x-edge and F = u(1-nu)/2 Dx Q into the cell on its left; only the
+    upward part, v times either, exists), and
+      Q' = Q - nu Dx Q - mu Dy Q - nu (f_i+1/2 - f_i-1/2) - mu (g_j+1/2 - g_j-1/2).
+    Arrays are indexed [j, i]."""
+    sx = lambda A, k: np.roll(A, k, axis=1)    # sx(A, 1)[j, i] = A[j, i-1]
+    sy = lambda A, k: np.roll(A, k, axis=0)
+    Dx = Q - sx(Q, 1)
+    Dy = Q - sy(Q, 1)
+    Dx_r, Dy_u = sx(Dx, -1), sy(Dy, -1)        # Dx Q_i+1,j and Dy Q_i,j+1
+    if transverse == 1:
+        f = 0.5 * (1 - nu) * Dx_r - 0.5 * mu * Dy
+        g = 0.5 * (1 - mu) * Dy_u - 0.5 * nu * Dx
+    else:
+        f = 0.5 * (1 - nu) * Dx_r - 0.25 * mu * ((1 + mu) * Dy + (1 - mu) * Dy_u)
+        g = 0.5 * (1 - mu) * Dy_u - 0.25 * nu * ((1 + nu) * Dx + (1 - nu) * Dx_r)
+    return Q - nu * Dx - mu * Dy - nu * (f - sx(f, 1)) - mu * (g - sy(g, 1))
+
+
+@pytest.mark.parametrize("transverse", [1, 2])
+def test_advection_matches_hand_derived_stencil(oracle_mod, transverse):
+    mx, my = 18, 14
+    dx, dy = 1.0 / mx, 1.0 / my
+    u, v = 1.0, 0.6
+    prob = make(oracle_mod, "advection", mx, my, dx, dy, (oracle_mod.BC_PERIODIC,) * 4,
+                limiter=oracle_mod.LIM_NONE, transverse=transverse, param=(u, v, 0, 0))
+    rng = np.random.default_rng(5)
+    Q = smooth_state("advection", mx, my, None)[0] + 0.1 * rng.uniform(-1, 1, (my, mx))
+    dt = 0.7 * min(dx / u, dy / v)
+    got, _, _ = oracle_mod.step(prob, embed(prob, Q[None]), dt)
+    want = _advection_ctu_lw_stencil(Q, u * dt / dx, v * dt / dy, transverse)
+    np.testing.assert_allclose(interior(prob, got)[0], want, atol=1e-14)
+    # the two options differ here, so the comparison tells them apart
+    other = _advection_ctu_lw_stencil(Q, u * dt / dx, v * dt / dy, 3 - transverse)
+    assert np.abs(other - want).max() > 1e-4
+
+
+@pytest.mark.parametrize("solver", ["acoustics", "swe", "euler", "advection"])
+def test_transverse_two_is_one_at_first_order(oracle_mod, solver):
+    """Without limited corrections there is nothing extra to split."""
+    mx, my = 9, 7
+    rng = np.random.default_rng(2)
+    base = smooth_state(solver, mx, my, rng)
+    outs = []
+    for tr in (1, 2):
+        prob = make(oracle_mod, solver, mx, my, 0.1, 0.1, (oracle_mod.BC_PERIODIC,) * 4,
+                    transverse=tr, order=1)
+        q = embed(prob, base)
+        dt = 0.6 / oracle_mod.max_cell_speed(prob, oracle_mod.bc_fill(prob, q))
+        outs.append(oracle_mod.step(prob, q, dt)[0])
+    np.testing.assert_array_equal(outs[0], outs[1])
