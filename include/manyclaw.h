@@ -59,26 +59,34 @@ typedef enum {
     MC_ENOTSUP = -7     /* combination not supported */
 } mc_status;
 
-enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3 };
-/* limiter numbering as in Clawpack: 0 none (Lax-Wendroff), 1 minmod, 4 MC */
-enum { MC_LIM_NONE = 0, MC_LIM_MINMOD = 1, MC_LIM_MC = 4 };
+/* MC_ADVECTION: scalar q_t + u q_x + v q_y = 0 with constant (u, v) =
+ * (param[0], param[1]), the paper's advection solver (§3) */
+enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3, MC_ADVECTION = 4 };
+/* limiter numbering as in Clawpack: 0 none (Lax-Wendroff), 1 minmod,
+ * 2 superbee, 3 van Leer, 4 MC (LeVeque 2002, eq. 6.39) */
+enum { MC_LIM_NONE = 0, MC_LIM_MINMOD = 1, MC_LIM_SUPERBEE = 2, MC_LIM_VANLEER = 3, MC_LIM_MC = 4 };
 enum { MC_BC_PERIODIC = 0, MC_BC_EXTRAP = 1, MC_BC_WALL = 2 };
 enum { MC_F32 = 0, MC_F64 = 1 };
 
 /* A 2D problem.  meqn follows from the solver (acoustics (p, u, v): 3;
- * shallow water (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4). */
+ * shallow water (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4;
+ * advection (q): 1). */
 typedef struct mc_problem {
-    int32_t solver;      /* MC_ACOUSTICS | MC_SWE_ROE | MC_EULER_ROE */
+    int32_t solver;      /* MC_ACOUSTICS | MC_SWE_ROE | MC_EULER_ROE | MC_ADVECTION */
     int32_t dtype;       /* MC_F32 | MC_F64: storage and arithmetic precision */
     int32_t mx, my;      /* interior cells, each >= 1 */
     int32_t mbc;         /* ghost layers; must be 2 */
     int32_t limiter;     /* MC_LIM_* */
     int32_t order;       /* 1: first order, 2: limited second-order corrections */
-    int32_t transverse;  /* 0: none, 1: transverse split of the fluctuations */
+    int32_t transverse;  /* 0: none, 1: transverse split of the fluctuations,
+                          * 2: also of the limited corrections (LeVeque 2002,
+                          * ch. 21; each edge's whole contribution to a cell,
+                          * A+dQ - F or A-dQ + F, is split) */
     int32_t efix;        /* 1: Harten-Hyman entropy fix (shallow water, Euler) */
     int32_t bc[4];       /* boundary kinds at xlo, xhi, ylo, yhi (MC_BC_*) */
     double dx, dy;       /* cell sizes, > 0 */
-    double param[4];     /* acoustics: rho, K | shallow water: g | Euler: gamma */
+    double param[4];     /* acoustics: rho, K | shallow water: g | Euler: gamma |
+                          * advection: u, v */
 } mc_problem;
 
 typedef struct mc_layout {

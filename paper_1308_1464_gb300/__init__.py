@@ -21,8 +21,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "manyclaw.h")
 
 MC_OK, MC_EINVAL, MC_ECUDA, MC_ENOMEM, MC_ECFL, MC_ENONPHYS, MC_ETIMEOUT, MC_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6, -7)
-ACOUSTICS, SWE_ROE, EULER_ROE = 1, 2, 3
-LIM_NONE, LIM_MINMOD, LIM_MC = 0, 1, 4
+ACOUSTICS, SWE_ROE, EULER_ROE, ADVECTION = 1, 2, 3, 4
+LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_EXTRAP, BC_WALL = 0, 1, 2
 F32, F64 = 0, 1
 
@@ -54,7 +54,7 @@ class Problem(ctypes.Structure):
 
     @property
     def meqn(self) -> int:
-        return 4 if self.solver == EULER_ROE else 3
+        return {EULER_ROE: 4, ADVECTION: 1}.get(self.solver, 3)
 
 
 class Layout(ctypes.Structure):

@@ -82,6 +82,7 @@ static cudaError_t solver_batch_launch(const BatchLaunch& L)
     switch (L.proto.solver) {
     case MC_ACOUSTICS: return batch_launch_acoustics(L);
     case MC_SWE_ROE: return batch_launch_swe(L);
+    case MC_ADVECTION: return batch_launch_advection(L);
     default: return batch_launch_euler(L);
     }
 }
@@ -91,6 +92,7 @@ static cudaError_t solver_batch_init(const BatchLaunch& L)
     switch (L.proto.solver) {
     case MC_ACOUSTICS: return batch_init_acoustics(L);
     case MC_SWE_ROE: return batch_init_swe(L);
+    case MC_ADVECTION: return batch_init_advection(L);
     default: return batch_init_euler(L);
     }
 }
@@ -100,6 +102,7 @@ static cudaError_t solver_batch_occupancy(const mc_problem& p, int* ctas)
     switch (p.solver) {
     case MC_ACOUSTICS: return batch_occupancy_acoustics(p.dtype, ctas);
     case MC_SWE_ROE: return batch_occupancy_swe(p.dtype, ctas);
+    case MC_ADVECTION: return batch_occupancy_advection(p.dtype, ctas);
     default: return batch_occupancy_euler(p.dtype, ctas);
     }
 }
@@ -275,7 +278,7 @@ mc_status mc_batch_create(const mc_problem* proto, const mc_patch* patches, int3
     }
     EncodeFn encode = reinterpret_cast<EncodeFn>(fn);
     const int es = proto->dtype == MC_F64 ? 8 : 4;
-    const int meqn = proto->solver == MC_EULER_ROE ? 4 : 3;
+    const int meqn = solver_meqn(proto->solver);
     std::vector<CUtensorMap> maps(2 * (size_t)npatch);
     for (int p = 0; p < npatch; p++) {
         const PatchDesc& d = b->desc[p];
@@ -434,6 +437,7 @@ mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double
             switch (q.solver) {
             case MC_ACOUSTICS: e = sweep_launch_acoustics(S); break;
             case MC_SWE_ROE: e = sweep_launch_swe(S); break;
+            case MC_ADVECTION: e = sweep_launch_advection(S); break;
             default: e = sweep_launch_euler(S); break;
             }
         }

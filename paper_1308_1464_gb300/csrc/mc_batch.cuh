@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     WarpRing W = warp_ring(smem, sizeof(T), RP::NEQ);
-    const bool second = a.order >= 2, trans = a.transverse != 0;
+    const bool second = a.order >= 2;
     const long long total = (long long)a.nsteps * a.tasks_per_step;
     const int stride = a.nsteps + 1;
     bool dep_failed = false, tma_failed = false, bad = false;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         const int jend = min(j0 + d.tile_rows, d.my);
         T smx = T(0), smy = T(0);
         if (!sweep_task<RP, true, FAST>(a.rp, map, qout, d.mx, d.my, d.ld_x, d.ld_field, a.x_offset, i0,
-                                  j0, jend, T(dt / d.dx), T(dt / d.dy), a.limiter, second, trans,
+                                  j0, jend, T(dt / d.dx), T(dt / d.dy), a.limiter, second, a.transverse,
                                   W, bad, smx, smy, a.status)) {
             tma_failed = true;
             break;

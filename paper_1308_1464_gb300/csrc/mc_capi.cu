@@ -44,12 +44,12 @@ int ntasks_for(const mc_problem& p, int tile_rows, int* nbands)
     return nb * nr;
 }
 
-static int meqn_of(int solver) { return solver == MC_EULER_ROE ? 4 : 3; }
+static int meqn_of(int solver) { return solver_meqn(solver); }
 
 static mc_status validate(const mc_problem* p)
 {
     if (!p) return set_error(MC_EINVAL, "problem is NULL");
-    if (p->solver < MC_ACOUSTICS || p->solver > MC_EULER_ROE)
+    if (p->solver < MC_ACOUSTICS || p->solver > MC_ADVECTION)
         return set_error(MC_EINVAL, "unknown solver %d", p->solver);
     if (p->dtype != MC_F32 && p->dtype != MC_F64)
         return set_error(MC_EINVAL, "unknown dtype %d", p->dtype);
@@ -58,11 +58,11 @@ static mc_status validate(const mc_problem* p)
     if ((long long)p->mx * p->my > (1LL << 40))
         return set_error(MC_EINVAL, "grid %d x %d too large", p->mx, p->my);
     if (p->mbc != 2) return set_error(MC_EINVAL, "mbc must be 2 (got %d)", p->mbc);
-    if (p->limiter != MC_LIM_NONE && p->limiter != MC_LIM_MINMOD && p->limiter != MC_LIM_MC)
+    if (p->limiter < MC_LIM_NONE || p->limiter > MC_LIM_MC)
         return set_error(MC_EINVAL, "unknown limiter %d", p->limiter);
     if (p->order != 1 && p->order != 2) return set_error(MC_EINVAL, "order must be 1 or 2");
-    if (p->transverse != 0 && p->transverse != 1)
-        return set_error(MC_EINVAL, "transverse must be 0 or 1");
+    if (p->transverse < 0 || p->transverse > 2)
+        return set_error(MC_EINVAL, "transverse must be 0, 1 or 2");
     if (p->efix != 0 && p->efix != 1) return set_error(MC_EINVAL, "efix must be 0 or 1");
     for (int k = 0; k < 4; k++)
         if (p->bc[k] < MC_BC_PERIODIC || p->bc[k] > MC_BC_WALL)
@@ -78,6 +78,8 @@ static mc_status validate(const mc_problem* p)
         return set_error(MC_EINVAL, "shallow water needs g > 0");
     if (p->solver == MC_EULER_ROE && !(p->param[0] > 1.0))
         return set_error(MC_EINVAL, "Euler needs gamma > 1");
+    if (p->solver == MC_ADVECTION && !(isfinite(p->param[0]) && isfinite(p->param[1])))
+        return set_error(MC_EINVAL, "advection needs finite velocities");
     return MC_OK;
 }
 
@@ -99,6 +101,7 @@ static cudaError_t sweep_launch(const SweepLaunch& L)
     switch (L.prob.solver) {
     case MC_ACOUSTICS: return sweep_launch_acoustics(L);
     case MC_SWE_ROE: return sweep_launch_swe(L);
+    case MC_ADVECTION: return sweep_launch_advection(L);
     default: return sweep_launch_euler(L);
     }
 }
@@ -108,6 +111,7 @@ static cudaError_t sweep_prepare(const mc_problem& p)
     switch (p.solver) {
     case MC_ACOUSTICS: return sweep_prepare_acoustics(p.dtype);
     case MC_SWE_ROE: return sweep_prepare_swe(p.dtype);
+    case MC_ADVECTION: return sweep_prepare_advection(p.dtype);
     default: return sweep_prepare_euler(p.dtype);
     }
 }
@@ -118,6 +122,7 @@ static cudaError_t maxspeed_launch(const mc_problem& p, const mc_layout& lay, co
     switch (p.solver) {
     case MC_ACOUSTICS: return maxspeed_launch_acoustics(p, lay, q, out, s);
     case MC_SWE_ROE: return maxspeed_launch_swe(p, lay, q, out, s);
+    case MC_ADVECTION: return maxspeed_launch_advection(p, lay, q, out, s);
     default: return maxspeed_launch_euler(p, lay, q, out, s);
     }
 }

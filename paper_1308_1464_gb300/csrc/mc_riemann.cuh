@@ -136,6 +136,56 @@ struct AcousticsRP {
     }
 };
 
+// ---------------------------------------------------------------- advection
+// q_t + u q_x + v q_y = 0 with constant velocity (u, v) = (param[0],
+// param[1]): one wave, the jump, moving at the edge-normal velocity
+// (LeVeque 2002, §4.8, §20.1); the transverse velocity carries a fluctuation
+// across the other edges (§20.2).
+template <typename T>
+struct AdvectionRP {
+    using real = T;
+    static constexpr int NEQ = 1, NW = 1;
+    static constexpr bool POSITIVE = false;
+    template <int DIR>
+    __host__ __device__ static constexpr bool wave_nz(int, int) { return true; }
+    static constexpr bool CARRY_DOT = false;
+    static constexpr bool PAIRED = false;   // scalar solves only
+    static constexpr bool PAIR_LIMITER = false;
+    T u, v;
+    bool efix;  // unused: linear
+    struct Lin { T s; };
+    __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.s); }
+    __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const
+    {
+        sx = fabs(u);
+        sy = fabs(v);
+    }
+    __host__ void setup(const double* param, int)
+    {
+        u = T(param[0]);
+        v = T(param[1]);
+        efix = false;
+    }
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin& L, bool&) const
+    {
+        const T sn = DIR == 0 ? u : v;
+        W[0][0] = qr[0] - ql[0];
+        s[0] = sn;
+        amdq[0] = tmin0(sn) * W[0][0];
+        apdq[0] = tmax0(sn) * W[0][0];
+        L.s = sn;
+    }
+    template <int DIR>
+    __device__ __forceinline__ void transverse(const Lin&, const T* a, T* bm, T* bp) const
+    {
+        const T st = DIR == 0 ? v : u;
+        bm[0] = tmin0(st) * a[0];
+        bp[0] = tmax0(st) * a[0];
+    }
+};
+
 // ---------------------------------------------------------------- shallow water
 template <typename T>
 struct SweRP {
@@ -242,6 +292,11 @@ struct SweRP {
     static constexpr bool PAIRED = sizeof(T) == 4;
     static constexpr bool PAIR_LIMITER = false;
     struct LinP { f2 u, v, c, r2c; };
+    // the scalar linearised state of half h (x-edge 0, y-edge 1)
+    __device__ __forceinline__ Lin lin_half(const LinP& P, int h) const
+    {
+        return Lin{half(P.u, h), half(P.v, h), half(P.c, h), half(P.r2c, h)};
+    }
     __device__ __forceinline__ float max_speed(const LinP& L, int h) const
     {
         return fabs(half(L.u, h)) + half(L.c, h);
@@ -550,6 +605,11 @@ struct EulerRP {
     // edge-normal frame (component 1 normal, 2 tangential momentum); the
     // arithmetic of normal<0> / transverse<0>, two edges per instruction
     struct LinP { f2 u, v, H, c, rc, gc2; };
+    // the scalar linearised state of half h (x-edge 0, y-edge 1)
+    __device__ __forceinline__ Lin lin_half(const LinP& P, int h) const
+    {
+        return Lin{half(P.u, h), half(P.v, h), half(P.H, h), half(P.c, h), half(P.rc, h), half(P.gc2, h)};
+    }
     __device__ __forceinline__ float max_speed(const LinP& L, int h) const
     {
         return fabs(half(L.u, h)) + half(L.c, h);

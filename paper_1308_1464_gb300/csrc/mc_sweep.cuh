@@ -64,18 +64,28 @@ struct SweepArgs {
     int* status;
 };
 
-// phi(theta) with theta = dl / dr, branch-free: minmod (1), MC (4) or none
-// (0: phi = 1).  With a compile-time limiter the selection folds away.  A
-// zero wave (dr = 0) needs no test: theta is then NaN or infinite, min/max
-// return their other operand, so phi stays in [0, 2] and multiplies a wave
-// whose components are all zero.
+// phi(theta) with theta = dl / dr, branch-free (LeVeque 2002, eq. 6.39):
+// minmod (1), superbee (2), van Leer (3), MC (4) or none (0: phi = 1).  With a
+// compile-time limiter the selection folds away.  A zero wave (dr = 0) needs
+// no test: theta is then NaN or infinite, min/max return their other
+// operand, so phi stays in [0, 2] and multiplies a wave whose components are
+// all zero.  Van Leer's (theta + |theta|)/(1 + |theta|) is written as
+// 2 - 2/(1 + t) with t = max(theta, 0), which keeps that property.
 template <typename T>
 __device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
 {
     const T th = dl * rcp_(dr);
     T phi = T(1);
-    if (lim == 4) phi = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
-    else if (lim == 1) phi = fmax(T(0), fmin(T(1), th));
+    if (lim == 4) {
+        phi = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
+    } else if (lim == 1) {
+        phi = fmax(T(0), fmin(T(1), th));
+    } else if (lim == 2) {
+        phi = fmax(T(0), fmax(fmin(T(1), T(2) * th), fmin(T(2), th)));
+    } else if (lim == 3) {
+        const T t = fmax(th, T(0));
+        phi = T(2) - T(2) * rcp_(T(1) + t);
+    }
     return phi;
 }
 
@@ -88,9 +98,9 @@ __device__ __forceinline__ f2 limiter_phi_pair(int lim, f2 dl, f2 dr)
         const f2 a = p_fma(th, p_set(0.5f), p_set(0.5f)), b = p_add(th, th);
         phi.x = fmaxf(0.f, fminf(fminf(a.x, 2.f), b.x));
         phi.y = fmaxf(0.f, fminf(fminf(a.y, 2.f), b.y));
-    } else if (lim == 1) {
-        phi.x = fmaxf(0.f, fminf(1.f, th.x));
-        phi.y = fmaxf(0.f, fminf(1.f, th.y));
+    } else if (lim == 1 || lim == 2 || lim == 3) {
+        phi.x = limiter_phi(lim, dl.x, dr.x);
+        phi.y = limiter_phi(lim, dl.y, dr.y);
     }
     return phi;
 }
@@ -110,20 +120,31 @@ struct WarpRing {
 // the next step needs no separate ghost fill.
 //
 // FAST compiles the common scheme (MC limiter, second order, transverse
-// splits) with those choices fixed; otherwise they are read at run time.
+// splits of the fluctuations) with those choices fixed; otherwise they are
+// read at run time.
+//
+// Transverse option 2 splits each edge's whole contribution to a cell
+// (A+dQ - F into the high cell, A-dQ + F into the low one, F the limited
+// correction).  An x-edge's F is known in the iteration that solves it, so
+// its splits only move behind the limiter.  A y-edge's limiter needs the edge
+// above it, so the y splits of edge (c, k+1/2) run one iteration late, at k:
+// the part entering row k+1 joins F of row k+1 as before, and the part
+// entering row k is added to row k's carried x-edge terms just before row k
+// is updated.
 template <class RP, bool WALL_GHOSTS, bool FAST>
 __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real* __restrict__ qout, int mx, int my,
                                            long long ld_x, long long ld_field, long long x_offset,
                                            int i0, int j0, int jend, typename RP::real nux,
                                            typename RP::real nuy, int limiter_rt, bool second_rt,
-                                           bool trans_rt, WarpRing& W, bool& bad,
+                                           int transverse_rt, WarpRing& W, bool& bad,
                                            typename RP::real& smx, typename RP::real& smy,
                                            int* status)
 {
     const int limiter = FAST ? 4 : limiter_rt;
     const bool second = FAST ? true : second_rt;
-    const bool trans = FAST ? true : trans_rt;
+    const bool trans = FAST ? true : transverse_rt != 0;
+    const bool trans2 = FAST ? false : (transverse_rt == 2 && second_rt);
     using T = typename RP::real;
     constexpr int N = RP::NEQ, NW = RP::NW;
     constexpr int ES = sizeof(T);
@@ -199,9 +220,13 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     // iterations
     T bp_pend[N], tyP_m[N], tyP_p[N];
     T XP0[N], XM0[N], Z0[N], BpAp0[N], BpAm0[N];
+    // transverse option 2: B-dQ of y-edge (c, k+1/2) and that edge's
+    // linearised state, split one iteration late
+    T bm_prev[N];
+    typename RP::Lin Lx_cur{}, Ly_cur{}, Ly_prev{};
 #pragma unroll
     for (int m = 0; m < N; m++) {
-        qc0[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = T(0);
+        qc0[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = bm_prev[m] = T(0);
         XP0[m] = XM0[m] = Z0[m] = BpAp0[m] = BpAm0[m] = T(0);
     }
 #pragma unroll
@@ -231,7 +256,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         // with CARRY_DOT, the dot products of the waves of y-edge (c, k+1/2)
         // with those of the edge above (the next row's dlo)
         auto y_tail = [&]() {
-            if (trans) {
+            if (trans && !trans2) {
 #pragma unroll
                 for (int m = 0; m < N; m++) {
                     TAm[m] = tyP_m[m] + t1[m];
@@ -280,7 +305,10 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 bm2[frame_comp(m, 1)] = am2[m].y;
                 bp2[frame_comp(m, 1)] = ap2[m].y;
             }
-            if (trans) {
+            if (trans2) {
+                Lx_cur = rp.lin_half(L2, 0);
+                Ly_cur = rp.lin_half(L2, 1);
+            } else if (trans) {
                 f2 Tm[N], Tp[N], Um[N], Up[N];
                 rp.transverse_pair(L2, am2, Tm, Tp);
                 rp.transverse_pair(L2, ap2, Um, Up);
@@ -307,7 +335,9 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             typename RP::Lin Ly;
             bool bady = false;
             rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
-            if (trans) {
+            if (trans2) {
+                Ly_cur = Ly;
+            } else if (trans) {
                 rp.template transverse<1>(Ly, bm2, t1, t2);
                 rp.template transverse<1>(Ly, bp2, nPm, nPp);
             }
@@ -321,7 +351,9 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 typename RP::Lin Lx;
                 bool badx = false;
                 rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
-                if (trans) {
+                if (trans2) {
+                    Lx_cur = Lx;
+                } else if (trans) {
                     rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
                     rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
                 }
@@ -332,7 +364,10 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         }
 
         T Fn[N], Gn[N];
-        if (k >= j0 - 1) {
+        // with option 2 the x-edge splits live in this block, and those of
+        // row j0-1 feed G at y-edge (c, j0-1/2): start one row earlier (the
+        // extra row's other results are not used)
+        if (k >= j0 - (trans2 ? 2 : 1)) {
             // ---- limited corrections: F at x-edge (c-1/2, k+1), G at y-edge (c, k+1/2)
 #pragma unroll
             for (int m = 0; m < N; m++) Fn[m] = Gn[m] = T(0);
@@ -414,6 +449,36 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     }
                 }
             }
+            if (trans2) {
+                // option 2: split the x-edge fluctuations of row k+1 together
+                // with its limited correction (Fn holds only that so far) ...
+                T apx[N], amx[N];
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    apx[m] = apdq1[m] - Fn[m];
+                    amx[m] = amdq1[m] + Fn[m];
+                }
+                rp.template transverse<0>(Lx_cur, apx, BmAp1, BpAp1);
+                rp.template transverse<0>(Lx_cur, amx, BmAm1, BpAm1);
+                // ... and those of y-edge (c, k+1/2), now that its limited
+                // correction (Gn so far) is known: the part entering row k+1
+                // feeds F of row k+1 below, the part entering row k completes
+                // row k's x-edge terms
+                T bmL[N], bpL[N], sm_[N], sp_[N];
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    bmL[m] = bm_prev[m] + Gn[m];
+                    bpL[m] = bp_pend[m] - Gn[m];
+                }
+                rp.template transverse<1>(Ly_prev, bmL, sm_, sp_);
+                rp.template transverse<1>(Ly_prev, bpL, TAm, TAp);
+#pragma unroll
+                for (int m = 0; m < N; m++) {
+                    const T dF = -hnuy * (sm_[m] + shfl_up1(sp_[m]));
+                    XP0[m] -= dF;
+                    XM0[m] += dF;
+                }
+            }
             // ---- transverse parts of F and G
             if (trans) {
 #pragma unroll
@@ -462,11 +527,13 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
             Z0[m] = dqy_n[m] - Gn[m];
             bp_pend[m] = bp2[m];
-            if (trans) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
+            if (trans && !trans2) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
+            if (trans2) bm_prev[m] = bm2[m];
             XP0[m] = apdq1[m] - Fn[m];
             XM0[m] = amdq1[m] + Fn[m];
             if (trans) { BpAp0[m] = BpAp1[m]; BpAm0[m] = BpAm1[m]; }
         }
+        if (trans2) Ly_prev = Ly_cur;
 #pragma unroll
         for (int p = 0; p < NW; p++) {
             sy1[p] = sy2[p];
@@ -520,7 +587,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     T* __restrict__ qout = cur ? a.qa : a.qb;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const T nux = T(dt / a.dx), nuy = T(dt / a.dy);
-    const bool second = a.order >= 2, trans = a.transverse != 0;
+    const bool second = a.order >= 2;
 
     // TMA precondition, checked instead of trusted: a 64-byte aligned map
     const bool map_ok = (reinterpret_cast<uintptr_t>(map) & 63) == 0;
@@ -540,7 +607,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
         const int jend = min(j0 + a.tile_rows, a.my);
         failed = !sweep_task<RP, false, FAST>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
                                          a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
-                                         trans, W, bad, smx, smy, a.status);
+                                         a.transverse, W, bad, smx, smy, a.status);
     }
 
     if (failed) {

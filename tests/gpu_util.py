@@ -10,7 +10,8 @@ G = 9.81
 GAMMA = 1.4
 SOLVER_IDS = {"acoustics": (mc.ACOUSTICS, oracle.ACOUSTICS, (1.0, 4.0, 0, 0)),
               "swe": (mc.SWE_ROE, oracle.SWE, (G, 0, 0, 0)),
-              "euler": (mc.EULER_ROE, oracle.EULER, (GAMMA, 0, 0, 0))}
+              "euler": (mc.EULER_ROE, oracle.EULER, (GAMMA, 0, 0, 0)),
+              "advection": (mc.ADVECTION, oracle.ADVECTION, (1.0, -0.6, 0, 0))}
 TOL = {mc.F64: 1e-12, mc.F32: 2e-5}
 
 
@@ -25,7 +26,7 @@ def problems(solver, mx, my, dx, dy, dtype, bc, limiter=4, order=2, transverse=1
 
 def field_scales(solver, q):
     """Per-field scales S_m of the parity norm max|gpu - oracle| / S_m."""
-    if solver == "acoustics":
+    if solver in ("acoustics", "advection"):
         return np.ones(q.shape[0])
     if solver == "swe":
         h = np.abs(q[0]).max()
@@ -53,6 +54,11 @@ def embed(op, interior):
 def initial_state(solver, mx, my, seed=0):
     """Seeded test data with every term of the step active."""
     rng = np.random.default_rng(seed)
+    if solver == "advection":
+        g = workloads.acoustics_pulse(mx, my)
+        q = g.q[:1].copy() + 0.3 * np.sin(2 * np.pi * np.arange(mx) / mx)[None, None, :]
+        q += 0.01 * rng.uniform(-1, 1, size=q.shape)
+        return q, g.dx, g.dy
     if solver == "acoustics":
         g = workloads.acoustics_pulse(mx, my)
         q = g.q.copy()

@@ -43,10 +43,14 @@ def test_layout(L):
     assert lay.bytes == 3 * lay.ld_field * 4
     lay = mc.layout_of(base_problem(dtype=mc.F64, solver=mc.EULER_ROE, param=(1.4, 0, 0, 0)))
     assert lay.elem_bytes == 8 and lay.meqn == 4 and lay.x_offset * 8 % 16 == 0
+    lay = mc.layout_of(base_problem(solver=mc.ADVECTION, param=(1.0, -0.5, 0, 0), limiter=mc.LIM_VANLEER,
+                                    transverse=2))
+    assert lay.meqn == 1 and lay.bytes == lay.ld_field * 4
 
 
 @pytest.mark.parametrize("kw", [
-    dict(solver=7), dict(dtype=3), dict(mx=0), dict(my=-1), dict(limiter=2), dict(order=3),
+    dict(solver=7), dict(solver=0), dict(dtype=3), dict(mx=0), dict(my=-1), dict(limiter=5),
+    dict(limiter=-1), dict(order=3), dict(transverse=3),
     dict(bc=(mc.BC_PERIODIC, mc.BC_WALL, 0, 0)), dict(dx=0.0), dict(param=(0.0, 0, 0, 0)),
     dict(solver=mc.EULER_ROE, param=(1.0, 0, 0, 0)),
 ])

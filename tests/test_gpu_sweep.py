@@ -62,6 +62,19 @@ CASES = [
     ("euler", mc.F64, (X, X, X, X), 4, 1),
     ("euler", mc.F32, (W, W, P, P), 1, 1),
     ("euler", mc.F64, (P, P, W, X), 4, 0),
+    # advection, the superbee and van Leer limiters, transverse option 2
+    ("advection", mc.F32, (P, P, P, P), 4, 1),
+    ("advection", mc.F64, (W, X, P, P), 2, 2),
+    ("advection", mc.F32, (X, X, W, W), 3, 2),
+    ("advection", mc.F64, (P, P, X, X), 0, 0),
+    ("acoustics", mc.F64, (P, P, W, W), 3, 2),
+    ("acoustics", mc.F32, (W, W, P, P), 2, 2),
+    ("swe", mc.F32, (W, W, W, W), 2, 2),
+    ("swe", mc.F64, (X, W, P, P), 3, 2),
+    ("swe", mc.F32, (W, X, X, W), 4, 2),
+    ("euler", mc.F32, (X, X, X, X), 3, 2),
+    ("euler", mc.F64, (W, W, X, X), 4, 2),
+    ("euler", mc.F32, (P, P, W, W), 2, 1),
 ]
 
 
@@ -89,24 +102,27 @@ def test_first_order_and_no_limiter():
 
 @pytest.mark.parametrize("mx,my", [(1, 1), (1, 7), (7, 1), (2, 3), (29, 2), (30, 31), (59, 5),
                                    (58, 9), (87, 3)])
-@pytest.mark.parametrize("solver,dtype,bc", [("swe", mc.F64, (W, W, W, W)),
-                                             ("euler", mc.F32, (X, X, P, P)),
-                                             ("acoustics", mc.F64, (P, P, W, W))])
-def test_tiny_and_odd_grids(mx, my, solver, dtype, bc):
+@pytest.mark.parametrize("solver,dtype,bc,trans", [("swe", mc.F64, (W, W, W, W), 1),
+                                                   ("euler", mc.F32, (X, X, P, P), 1),
+                                                   ("acoustics", mc.F64, (P, P, W, W), 1),
+                                                   ("swe", mc.F32, (W, X, X, W), 2),
+                                                   ("advection", mc.F64, (P, P, X, W), 2)])
+def test_tiny_and_odd_grids(mx, my, solver, dtype, bc, trans):
     q, _, _ = initial_state(solver, max(mx, 4), max(my, 4), seed=mx * 100 + my)
     q = np.ascontiguousarray(q[:, :my, :mx])
-    p, op = problems(solver, mx, my, 0.01, 0.013, dtype, bc)
+    p, op = problems(solver, mx, my, 0.01, 0.013, dtype, bc, transverse=trans)
     got, want, smax, smax_ref, ghosts, ghosts_ref = run_step(p, op, q, cfl=0.5)
     assert scaled_error(solver, got, want) <= TOL[dtype]
     assert smax == pytest.approx(smax_ref, rel=1e-12 if dtype == mc.F64 else 2e-6)
 
 
-@pytest.mark.parametrize("solver,dtype", [("swe", mc.F32), ("euler", mc.F64)])
-def test_tile_shape_invariance(solver, dtype):
+@pytest.mark.parametrize("solver,dtype,trans", [("swe", mc.F32, 1), ("euler", mc.F64, 1),
+                                                ("swe", mc.F32, 2), ("euler", mc.F32, 2)])
+def test_tile_shape_invariance(solver, dtype, trans):
     """Results do not depend on the tile height: bitwise equal outputs."""
     mx, my = 100, 130
     q, dx, dy = initial_state(solver, mx, my, seed=9)
-    p, op = problems(solver, mx, my, dx, dy, dtype, (W, X, X, W))
+    p, op = problems(solver, mx, my, dx, dy, dtype, (W, X, X, W), transverse=trans)
     outs = [run_step(p, op, q, tile_rows=t)[0] for t in (8, 17, 64, 256)]
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
