@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["rp.c", "step.c", "exact.c", "mlp.c"]
 _LIBDIR = os.path.join(_HERE, "_lib")
 
-ACOUSTICS, SWE, EULER, ADVECTION = 1, 2, 3, 4
+ACOUSTICS, SWE, EULER, ADVECTION, ACOUSTICS_VAR = 1, 2, 3, 4, 5
 LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_EXTRAP, BC_WALL, BC_GIVEN = 0, 1, 2, 3
 SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_GIVEN = range(6)
@@ -86,12 +86,18 @@ class Problem:
         return {EULER: 4, ADVECTION: 1}.get(self.solver, 3)
 
     @property
+    def nplane(self) -> int:
+        """Planes of a state array: the conserved fields, then (variable-
+        coefficient acoustics) the density and sound speed of each cell."""
+        return self.meqn + (2 if self.solver == ACOUSTICS_VAR else 0)
+
+    @property
     def mwaves(self) -> int:
-        return {ACOUSTICS: 2, ADVECTION: 1}.get(self.solver, 3)
+        return {ACOUSTICS: 2, ACOUSTICS_VAR: 2, ADVECTION: 1}.get(self.solver, 3)
 
     @property
     def shape(self) -> tuple:
-        return (self.meqn, self.my + 2 * self.mbc, self.mx + 2 * self.mbc)
+        return (self.nplane, self.my + 2 * self.mbc, self.mx + 2 * self.mbc)
 
     def c(self) -> _Problem:
         s = _Problem()
@@ -116,6 +122,7 @@ def lib():
         P = ctypes.POINTER(_Problem)
         L.mcref_rpn2.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.mcref_rpt2.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D]
+        L.mcref_rpt2_var.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.mcref_flux.argtypes = [P, ctypes.c_int, _D, _D]
         L.mcref_flux.restype = None
         L.mcref_philim.argtypes = [ctypes.c_int, ctypes.c_double]
@@ -180,6 +187,17 @@ def rpt2(prob: Problem, direction: int, ql, qr, asdq):
     bm = np.zeros(prob.meqn)
     bp = np.zeros(prob.meqn)
     lib().mcref_rpt2(ctypes.byref(prob.c()), direction, _p(ql), _p(qr), _p(asdq), _p(bm), _p(bp))
+    return bm, bp
+
+
+def rpt2_var(prob: Problem, direction: int, qlo, qc, qhi, asdq):
+    """Variable-coefficient acoustics: split asdq entering cell qc between its
+    neighbours qlo and qhi across the other direction -> (bm, bp)."""
+    qlo, qc, qhi, asdq = _f64(qlo), _f64(qc), _f64(qhi), _f64(asdq)
+    bm = np.zeros(prob.meqn)
+    bp = np.zeros(prob.meqn)
+    lib().mcref_rpt2_var(ctypes.byref(prob.c()), direction, _p(qlo), _p(qc), _p(qhi), _p(asdq),
+                         _p(bm), _p(bp))
     return bm, bp
 
 

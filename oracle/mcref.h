@@ -29,7 +29,12 @@ extern "C" {
 
 /* MCREF_ADVECTION: scalar q_t + u q_x + v q_y = 0 with constant (u, v) =
  * (param[0], param[1]) (the paper's advection solver, §3) */
-enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3, MCREF_ADVECTION = 4 };
+/* MCREF_ACOUSTICS_VAR: acoustics with a density rho and sound speed c per
+ * cell (the paper's variable-coefficient acoustics, §3, Table 2); the state
+ * carries them as two extra planes after (p, u, v), which the step copies
+ * unchanged. */
+enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3, MCREF_ADVECTION = 4,
+       MCREF_ACOUSTICS_VAR = 5 };
 /* Clawpack numbering: 1 minmod, 2 superbee, 3 van Leer, 4 monotonized central */
 enum { MCREF_LIM_NONE = 0, MCREF_LIM_MINMOD = 1, MCREF_LIM_SUPERBEE = 2, MCREF_LIM_VANLEER = 3,
        MCREF_LIM_MC = 4 };
@@ -40,7 +45,7 @@ enum { MCREF_BC_PERIODIC = 0, MCREF_BC_EXTRAP = 1, MCREF_BC_WALL = 2, MCREF_BC_G
 /* Flags raised by the oracle (bitmask). */
 enum { MCREF_F_NONPHYS = 1 };
 
-#define MCREF_MAXEQN 4
+#define MCREF_MAXEQN 5   /* planes of a cell vector: conserved fields + material */
 #define MCREF_MAXWAVE 3
 
 typedef struct {
@@ -58,6 +63,8 @@ typedef struct {
 } mcref_problem;
 
 int mcref_meqn(int solver);
+/* planes of a state array: mcref_meqn conserved fields, then material planes */
+int mcref_nplane(int solver);
 int mcref_mwaves(int solver);
 
 /* Pointwise normal Riemann solve across an edge whose normal is direction
@@ -72,6 +79,14 @@ int mcref_rpn2(const mcref_problem* p, int dir, const double* ql, const double* 
  * the same linearised state as the normal solve of (ql, qr). */
 int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* qr,
                const double* asdq, double* bmasdq, double* bpasdq);
+
+/* Transverse split for variable-coefficient acoustics: asdq enters the cell
+ * qc (an edge of normal dir), and qlo / qhi are that cell's neighbours on
+ * either side in the other direction; the down- (left-) going part moves
+ * into qlo's medium, the up- (right-) going part into qhi's.  Cell vectors
+ * carry (p, u, v, rho, c). */
+int mcref_rpt2_var(const mcref_problem* p, int dir, const double* qlo, const double* qc,
+                   const double* qhi, const double* asdq, double* bmasdq, double* bpasdq);
 
 /* Physical flux in direction dir (used by the pins). */
 void mcref_flux(const mcref_problem* p, int dir, const double* q, double* f);

@@ -24,6 +24,11 @@ int mcref_meqn(int solver)
     return solver == MCREF_EULER ? 4 : (solver == MCREF_ADVECTION ? 1 : 3);
 }
 
+int mcref_nplane(int solver)
+{
+    return mcref_meqn(solver) + (solver == MCREF_ACOUSTICS_VAR ? 2 : 0);
+}
+
 int mcref_mwaves(int solver)
 {
     /* acoustics: the zero-speed wave carrying the tangential velocity jump
@@ -31,7 +36,7 @@ int mcref_mwaves(int solver)
      * Euler: entropy and shear waves travel at the same speed and are
      * carried as one wave. */
     if (solver == MCREF_ADVECTION) return 1;
-    return solver == MCREF_ACOUSTICS ? 2 : 3;
+    return (solver == MCREF_ACOUSTICS || solver == MCREF_ACOUSTICS_VAR) ? 2 : 3;
 }
 
 /* ------------------------------------------------------------------ */
@@ -172,6 +177,27 @@ int mcref_rpn2(const mcref_problem* p, int dir, const double* ql, const double* 
         apdq[0] = (sn > 0.0 ? sn : 0.0) * d[0];
         return 0;
     }
+    if (p->solver == MCREF_ACOUSTICS_VAR) {
+        /* LeVeque (2002) §9.6: the left-going wave lies along the left
+         * medium's eigenvector (-Z_l, 1, 0) at speed -c_l, the right-going one
+         * along the right medium's (Z_r, 1, 0) at speed +c_r; the two
+         * strengths follow from the jump in p and the normal velocity. */
+        const int un = 1 + dir, ut = 2 - dir;
+        const double zl = ql[3] * ql[4], zr = qr[3] * qr[4];
+        const double a1 = (-d[0] + zr * d[un]) / (zl + zr);
+        const double a2 = (d[0] + zl * d[un]) / (zl + zr);
+        double* w1 = wave;
+        double* w2 = wave + meqn;
+        w1[0] = -zl * a1; w1[un] = a1; w1[ut] = 0.0;
+        w2[0] = zr * a2;  w2[un] = a2; w2[ut] = 0.0;
+        s[0] = -ql[4];
+        s[1] = qr[4];
+        for (int m = 0; m < meqn; m++) {
+            amdq[m] = s[0] * w1[m];
+            apdq[m] = s[1] * w2[m];
+        }
+        return 0;
+    }
     roe_state st = roe_average(p, dir, ql, qr);
     if (!st.ok) {
         /* Non-physical input: report it and return zero waves. */
@@ -235,6 +261,11 @@ int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* 
 {
     const int meqn = mcref_meqn(p->solver);
     double vec[4][MCREF_MAXEQN], lam[4];
+    if (p->solver == MCREF_ACOUSTICS_VAR) {
+        /* needs the receiving cell and its neighbours: mcref_rpt2_var */
+        for (int m = 0; m < meqn; m++) bmasdq[m] = bpasdq[m] = 0.0;
+        return MCREF_F_NONPHYS;
+    }
     if (p->solver == MCREF_ADVECTION) {
         /* the transverse velocity carries the whole fluctuation (§20.2) */
         const double st = p->param[1 - dir];
@@ -262,9 +293,42 @@ int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* 
     return 0;
 }
 
+int mcref_rpt2_var(const mcref_problem* p, int dir, const double* qlo, const double* qc,
+                   const double* qhi, const double* asdq, double* bmasdq, double* bpasdq)
+{
+    /* LeVeque (2002) §21.x for heterogeneous acoustics: the part of asdq
+     * that moves toward qlo is its component along qlo's medium eigenvector
+     * (-Z_lo, 1) (velocity along the split direction) in the decomposition
+     * at the interface between qlo and qc, times -c_lo; the part moving
+     * toward qhi is its component along (Z_hi, 1) at the interface between
+     * qc and qhi, times +c_hi.  Reflections at the two interfaces are why
+     * the parts do not add up to B asdq. */
+    (void)p;
+    const int vn = 2 - dir, vt = 1 + dir;   /* velocity along / across the split direction */
+    const double zlo = qlo[3] * qlo[4], z = qc[3] * qc[4], zhi = qhi[3] * qhi[4];
+    const double bdown = (-asdq[0] + z * asdq[vn]) / (zlo + z);
+    const double bup = (asdq[0] + z * asdq[vn]) / (z + zhi);
+    bmasdq[0] = qlo[4] * zlo * bdown;
+    bmasdq[vn] = -qlo[4] * bdown;
+    bmasdq[vt] = 0.0;
+    bpasdq[0] = qhi[4] * zhi * bup;
+    bpasdq[vn] = qhi[4] * bup;
+    bpasdq[vt] = 0.0;
+    return 0;
+}
+
 void mcref_flux(const mcref_problem* p, int dir, const double* q, double* f)
 {
     const int mu = 1 + dir, mv = 2 - dir;
+    if (p->solver == MCREF_ACOUSTICS_VAR) {
+        /* p_t + K div u = 0, u_t + grad p / rho = 0 with the cell's own
+         * material, K = rho c^2 */
+        const double rho = q[3], K = q[3] * q[4] * q[4];
+        f[0] = K * q[mu];
+        f[mu] = q[0] / rho;
+        f[mv] = 0.0;
+        return;
+    }
     if (p->solver == MCREF_ADVECTION) {
         f[0] = p->param[dir] * q[0];
         return;

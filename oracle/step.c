@@ -38,7 +38,7 @@ static inline int64_t qidx(const mcref_problem* p, int m, int i, int j)
 
 static void get_cell(const mcref_problem* p, const double* q, int i, int j, double* v)
 {
-    int meqn = mcref_meqn(p->solver);
+    int meqn = mcref_nplane(p->solver);
     for (int m = 0; m < meqn; m++) v[m] = q[qidx(p, m, i, j)];
 }
 
@@ -47,7 +47,7 @@ static void get_cell(const mcref_problem* p, const double* q, int i, int j, doub
 static void bc_copy(const mcref_problem* p, double* q, int i_dst, int j_dst, int i_src, int j_src,
                     int negate_comp)
 {
-    int meqn = mcref_meqn(p->solver);
+    int meqn = mcref_nplane(p->solver);
     for (int m = 0; m < meqn; m++) {
         double v = q[qidx(p, m, i_src, j_src)];
         q[qidx(p, m, i_dst, j_dst)] = (m == negate_comp) ? -v : v;
@@ -203,7 +203,8 @@ int mcref_step(const mcref_problem* p, const double* qin, double* qout, double d
     const int mx = p->mx, my = p->my;
     const int meqn = mcref_meqn(p->solver), mw = mcref_mwaves(p->solver);
     const double dtdx = dt / p->dx, dtdy = dt / p->dy;
-    const int64_t nq = (int64_t)meqn * NXG(p) * NYG(p);
+    const int64_t nq = (int64_t)mcref_nplane(p->solver) * NXG(p) * NYG(p);
+    const int var = p->solver == MCREF_ACOUSTICS_VAR;
     int flags = 0;
     if (nthreads < 1) nthreads = 1;
 
@@ -252,8 +253,20 @@ int mcref_step(const mcref_problem* p, const double* qin, double* qout, double d
                 int64_t k = eidx(&ex, i, j);
                 double ap[MCREF_MAXEQN], am[MCREF_MAXEQN];
                 effective_fluctuations(p, &ex, 0, i, j, dtdx, ap, am);
-                mcref_rpt2(p, 0, ql, qr, ap, t, t + meqn);
-                mcref_rpt2(p, 0, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
+                if (var) {
+                    /* A+dQ enters cell (i, j), A-dQ cell (i-1, j); each is
+                     * split between that cell's neighbours below and above */
+                    double lo[MCREF_MAXEQN], hi[MCREF_MAXEQN];
+                    get_cell(p, q, i, j - 1, lo);
+                    get_cell(p, q, i, j + 1, hi);
+                    mcref_rpt2_var(p, 0, lo, qr, hi, ap, t, t + meqn);
+                    get_cell(p, q, i - 1, j - 1, lo);
+                    get_cell(p, q, i - 1, j + 1, hi);
+                    mcref_rpt2_var(p, 0, lo, ql, hi, am, t + 2 * meqn, t + 3 * meqn);
+                } else {
+                    mcref_rpt2(p, 0, ql, qr, ap, t, t + meqn);
+                    mcref_rpt2(p, 0, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
+                }
                 (void)k;
             }
         }
@@ -287,8 +300,20 @@ int mcref_step(const mcref_problem* p, const double* qin, double* qout, double d
                 get_cell(p, q, i, j, qr);
                 double ap[MCREF_MAXEQN], am[MCREF_MAXEQN];
                 effective_fluctuations(p, &ey, 1, i, j, dtdy, ap, am);
-                mcref_rpt2(p, 1, ql, qr, ap, t, t + meqn);
-                mcref_rpt2(p, 1, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
+                if (var) {
+                    /* B+dQ enters cell (i, j), B-dQ cell (i, j-1); each is
+                     * split between that cell's neighbours left and right */
+                    double lo[MCREF_MAXEQN], hi[MCREF_MAXEQN];
+                    get_cell(p, q, i - 1, j, lo);
+                    get_cell(p, q, i + 1, j, hi);
+                    mcref_rpt2_var(p, 1, lo, qr, hi, ap, t, t + meqn);
+                    get_cell(p, q, i - 1, j - 1, lo);
+                    get_cell(p, q, i + 1, j - 1, hi);
+                    mcref_rpt2_var(p, 1, lo, ql, hi, am, t + 2 * meqn, t + 3 * meqn);
+                } else {
+                    mcref_rpt2(p, 1, ql, qr, ap, t, t + meqn);
+                    mcref_rpt2(p, 1, ql, qr, am, t + 2 * meqn, t + 3 * meqn);
+                }
             }
         }
         for (int j = 0; j <= my; j++) {
@@ -366,6 +391,8 @@ double mcref_max_cell_speed(const mcref_problem* p, const double* q)
             } else if (p->solver == MCREF_ADVECTION) {
                 u = p->param[0]; w = p->param[1];
                 c = 0.0;
+            } else if (p->solver == MCREF_ACOUSTICS_VAR) {
+                c = v[4];
             } else if (p->solver == MCREF_SWE) {
                 u = v[1] / v[0]; w = v[2] / v[0];
                 c = sqrt(p->param[0] * v[0]);

@@ -50,10 +50,10 @@ ADV_UV = (1.0, 0.6)
 def make(oracle, solver, mx, my, dx, dy, bc, limiter=None, efix=1, transverse=1, order=2,
          param=None):
     sid = {"acoustics": oracle.ACOUSTICS, "swe": oracle.SWE, "euler": oracle.EULER,
-           "advection": oracle.ADVECTION}[solver]
+           "advection": oracle.ADVECTION, "acoustics_var": oracle.ACOUSTICS_VAR}[solver]
     if param is None:
         param = {"acoustics": (1.0, 4.0, 0, 0), "swe": (G, 0, 0, 0), "euler": (GAMMA, 0, 0, 0),
-                 "advection": ADV_UV + (0, 0)}[solver]
+                 "advection": ADV_UV + (0, 0), "acoustics_var": (0, 0, 0, 0)}[solver]
     return oracle.Problem(sid, mx, my, dx, dy, limiter=oracle.LIM_MC if limiter is None else limiter,
                           order=order, transverse=transverse, efix=efix, bc=bc, param=param)
 
@@ -65,6 +65,12 @@ def smooth_state(solver, mx, my, rng):
     bump = np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
     if solver == "advection":
         return (np.exp(-30 * ((X - 0.4) ** 2 + (Y - 0.5) ** 2)) + 0.3 * bump)[None]
+    if solver == "acoustics_var":
+        # a smooth wave over a layered medium with a density jump and a
+        # sound-speed gradient
+        rho = np.where(Y < 0.5, 1.0, 2.5) * (1 + 0.1 * X)
+        c = 1.0 + 0.5 * X * Y
+        return np.stack([bump, 0.3 * np.cos(2 * np.pi * X), 0.2 * np.sin(2 * np.pi * Y), rho, c])
     if solver == "acoustics":
         return np.stack([bump, 0.3 * np.cos(2 * np.pi * X), 0.2 * np.sin(2 * np.pi * Y)])
     if solver == "swe":
@@ -378,16 +384,33 @@ def naive_step(oracle_mod, prob, q, dt):
     def into_lo_x(i, j):
         return xe(i, j)[2] + (lim_x(i, j) if t2 else 0.0)
 
+    var = prob.solver == oracle_mod.ACOUSTICS_VAR
+
+    def split_y(i, je, a, into_hi):
+        """x-split of what y-edge (i, je) sends into cell (i, je) (into_hi) or
+        (i, je - 1): at the edge's linearised state, or, with variable
+        material, across the receiving cell and its left and right neighbours."""
+        if var:
+            jc = je if into_hi else je - 1
+            return oracle_mod.rpt2_var(prob, 1, Q(i - 1, jc), Q(i, jc), Q(i + 1, jc), a)
+        return oracle_mod.rpt2(prob, 1, Q(i, je - 1), Q(i, je), a)
+
+    def split_x(ie, j, a, into_hi):
+        if var:
+            ic = ie if into_hi else ie - 1
+            return oracle_mod.rpt2_var(prob, 0, Q(ic, j - 1), Q(ic, j), Q(ic, j + 1), a)
+        return oracle_mod.rpt2(prob, 0, Q(ie - 1, j), Q(ie, j), a)
+
     def Fx(i, j):   # correction flux at x-edge (i, j)
         F = lim_x(i, j)
         if prob.transverse:
             # y-edge fluctuations entering cell (i, j) move left across this edge,
             # those entering (i-1, j) move right across it
             tr = np.zeros(prob.meqn)
-            tr += oracle_mod.rpt2(prob, 1, Q(i, j - 1), Q(i, j), into_hi_y(i, j))[0]
-            tr += oracle_mod.rpt2(prob, 1, Q(i, j), Q(i, j + 1), into_lo_y(i, j + 1))[0]
-            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j - 1), Q(i - 1, j), into_hi_y(i - 1, j))[1]
-            tr += oracle_mod.rpt2(prob, 1, Q(i - 1, j), Q(i - 1, j + 1), into_lo_y(i - 1, j + 1))[1]
+            tr += split_y(i, j, into_hi_y(i, j), True)[0]
+            tr += split_y(i, j + 1, into_lo_y(i, j + 1), False)[0]
+            tr += split_y(i - 1, j, into_hi_y(i - 1, j), True)[1]
+            tr += split_y(i - 1, j + 1, into_lo_y(i - 1, j + 1), False)[1]
             F -= 0.5 * nuy * tr
         return F
 
@@ -395,19 +418,20 @@ def naive_step(oracle_mod, prob, q, dt):
         Gv = lim_y(i, j)
         if prob.transverse:
             tr = np.zeros(prob.meqn)
-            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j), Q(i, j), into_hi_x(i, j))[0]
-            tr += oracle_mod.rpt2(prob, 0, Q(i, j), Q(i + 1, j), into_lo_x(i + 1, j))[0]
-            tr += oracle_mod.rpt2(prob, 0, Q(i - 1, j - 1), Q(i, j - 1), into_hi_x(i, j - 1))[1]
-            tr += oracle_mod.rpt2(prob, 0, Q(i, j - 1), Q(i + 1, j - 1), into_lo_x(i + 1, j - 1))[1]
+            tr += split_x(i, j, into_hi_x(i, j), True)[0]
+            tr += split_x(i + 1, j, into_lo_x(i + 1, j), False)[0]
+            tr += split_x(i, j - 1, into_hi_x(i, j - 1), True)[1]
+            tr += split_x(i + 1, j - 1, into_lo_x(i + 1, j - 1), False)[1]
             Gv -= 0.5 * nux * tr
         return Gv
 
     out = q.copy()
+    ne = prob.meqn
     for j in range(prob.my):
         for i in range(prob.mx):
             d = -nux * (xe(i, j)[3] + xe(i + 1, j)[2]) - nuy * (ye(i, j)[3] + ye(i, j + 1)[2])
             d -= nux * (Fx(i + 1, j) - Fx(i, j)) + nuy * (Gy(i, j + 1) - Gy(i, j))
-            out[:, j + m, i + m] = Q(i, j) + d
+            out[:ne, j + m, i + m] = Q(i, j)[:ne] + d
     return out
 
 
@@ -422,6 +446,8 @@ def naive_step(oracle_mod, prob, q, dt):
     ("euler", 4, 5, (1, 1, 0, 0), 4, 2),
     ("advection", 5, 4, (0, 0, 0, 0), 3, 2),
     ("advection", 4, 4, (1, 1, 2, 2), 2, 1),
+    ("acoustics_var", 5, 4, (0, 0, 1, 2), 4, 1),
+    ("acoustics_var", 4, 5, (2, 1, 0, 0), 3, 2),
 ])
 def test_brute_force_tiny_grids(oracle_mod, solver, mx, my, bc, lim, transverse):
     rng = np.random.default_rng(mx * 10 + my)
