@@ -60,19 +60,26 @@ typedef enum {
 } mc_status;
 
 /* MC_ADVECTION: scalar q_t + u q_x + v q_y = 0 with constant (u, v) =
- * (param[0], param[1]), the paper's advection solver (§3) */
-enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3, MC_ADVECTION = 4 };
+ * (param[0], param[1]), the paper's advection solver (§3).
+ * MC_ACOUSTICS_VAR: acoustics with a density rho and sound speed c per cell,
+ * the paper's variable-coefficient acoustics (§3, Table 2); the state array
+ * holds (p, u, v, rho, c): the two material planes follow the three fields
+ * and every step copies them unchanged into its output, ghost layers filled
+ * like the fields (never negated).  Not available for batched patches. */
+enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3, MC_ADVECTION = 4, MC_ACOUSTICS_VAR = 5 };
 /* limiter numbering as in Clawpack: 0 none (Lax-Wendroff), 1 minmod,
  * 2 superbee, 3 van Leer, 4 MC (LeVeque 2002, eq. 6.39) */
 enum { MC_LIM_NONE = 0, MC_LIM_MINMOD = 1, MC_LIM_SUPERBEE = 2, MC_LIM_VANLEER = 3, MC_LIM_MC = 4 };
 enum { MC_BC_PERIODIC = 0, MC_BC_EXTRAP = 1, MC_BC_WALL = 2 };
 enum { MC_F32 = 0, MC_F64 = 1 };
 
-/* A 2D problem.  meqn follows from the solver (acoustics (p, u, v): 3;
- * shallow water (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4;
- * advection (q): 1). */
+/* A 2D problem.  The planes of a state array follow from the solver
+ * (acoustics (p, u, v): 3; shallow water (h, hu, hv): 3; Euler (rho, rho u,
+ * rho v, E): 4; advection (q): 1; variable-coefficient acoustics
+ * (p, u, v, rho, c): 5). */
 typedef struct mc_problem {
-    int32_t solver;      /* MC_ACOUSTICS | MC_SWE_ROE | MC_EULER_ROE | MC_ADVECTION */
+    int32_t solver;      /* MC_ACOUSTICS | MC_SWE_ROE | MC_EULER_ROE | MC_ADVECTION |
+                          * MC_ACOUSTICS_VAR */
     int32_t dtype;       /* MC_F32 | MC_F64: storage and arithmetic precision */
     int32_t mx, my;      /* interior cells, each >= 1 */
     int32_t mbc;         /* ghost layers; must be 2 */
@@ -94,7 +101,7 @@ typedef struct mc_layout {
     int64_t ld_x;        /* row pitch, elements */
     int64_t ld_field;    /* field-plane pitch, elements */
     int64_t elem_bytes;  /* 4 or 8 */
-    int64_t meqn;        /* fields */
+    int64_t meqn;        /* planes of a state array (fields, then material planes) */
     int64_t bytes;       /* bytes of one state array */
 } mc_layout;
 

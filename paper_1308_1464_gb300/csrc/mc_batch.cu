@@ -83,6 +83,7 @@ static cudaError_t solver_batch_launch(const BatchLaunch& L)
     case MC_ACOUSTICS: return batch_launch_acoustics(L);
     case MC_SWE_ROE: return batch_launch_swe(L);
     case MC_ADVECTION: return batch_launch_advection(L);
+    case MC_ACOUSTICS_VAR: return batch_launch_acoustics_var(L);
     default: return batch_launch_euler(L);
     }
 }
@@ -93,6 +94,7 @@ static cudaError_t solver_batch_init(const BatchLaunch& L)
     case MC_ACOUSTICS: return batch_init_acoustics(L);
     case MC_SWE_ROE: return batch_init_swe(L);
     case MC_ADVECTION: return batch_init_advection(L);
+    case MC_ACOUSTICS_VAR: return batch_init_acoustics_var(L);
     default: return batch_init_euler(L);
     }
 }
@@ -103,6 +105,7 @@ static cudaError_t solver_batch_occupancy(const mc_problem& p, int* ctas)
     case MC_ACOUSTICS: return batch_occupancy_acoustics(p.dtype, ctas);
     case MC_SWE_ROE: return batch_occupancy_swe(p.dtype, ctas);
     case MC_ADVECTION: return batch_occupancy_advection(p.dtype, ctas);
+    case MC_ACOUSTICS_VAR: return batch_occupancy_acoustics_var(p.dtype, ctas);
     default: return batch_occupancy_euler(p.dtype, ctas);
     }
 }
@@ -214,6 +217,8 @@ mc_status mc_batch_create(const mc_problem* proto, const mc_patch* patches, int3
     for (int k = 0; k < 4; k++)
         if (proto->bc[k] != MC_BC_WALL)
             return set_error(MC_ENOTSUP, "batched patches support reflecting walls only");
+    if (proto->solver == MC_ACOUSTICS_VAR)
+        return set_error(MC_ENOTSUP, "batched patches do not carry material planes");
     mc_batch* b = new (std::nothrow) mc_batch();
     if (!b) return set_error(MC_ENOMEM, "batch allocation failed");
     b->proto = *proto;
@@ -438,6 +443,7 @@ mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double
             case MC_ACOUSTICS: e = sweep_launch_acoustics(S); break;
             case MC_SWE_ROE: e = sweep_launch_swe(S); break;
             case MC_ADVECTION: e = sweep_launch_advection(S); break;
+            case MC_ACOUSTICS_VAR: e = sweep_launch_acoustics_var(S); break;
             default: e = sweep_launch_euler(S); break;
             }
         }

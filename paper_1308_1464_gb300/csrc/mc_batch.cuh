@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
     using T = typename RP::real;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
-    WarpRing W = warp_ring(smem, sizeof(T), RP::NEQ);
+    WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
     const bool second = a.order >= 2;
     const long long total = (long long)a.nsteps * a.tasks_per_step;
     const int stride = a.nsteps + 1;
@@ -177,7 +177,7 @@ __global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long lo
         bool fx = false, fy = false;
         const int si = bc_map(i, d.mx, BC_WALL_KIND, BC_WALL_KIND, fx);
         const int sj = bc_map(j, d.my, BC_WALL_KIND, BC_WALL_KIND, fy);
-        for (int m = 0; m < RP::NEQ; m++) {
+        for (int m = 0; m < RP::NPLANE; m++) {
             T v = q[m * d.ld_field + (long long)(sj + 2) * d.ld_x + x_offset + si];
             if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
             q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i] = v;
@@ -189,8 +189,8 @@ __global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long lo
     for (int j = threadIdx.x >> 5; j < d.my; j += nw) {
         const T* row = q + (long long)(j + 2) * d.ld_x + x_offset;
         for (int i = lane; i < d.mx; i += 32) {
-            T qq[RP::NEQ];
-            for (int m = 0; m < RP::NEQ; m++) qq[m] = row[m * d.ld_field + i];
+            T qq[RP::NPLANE];
+            for (int m = 0; m < RP::NPLANE; m++) qq[m] = row[m * d.ld_field + i];
             T sx, sy;
             rp.cell_speeds(qq, sx, sy);
             msx = fmax(msx, sx);

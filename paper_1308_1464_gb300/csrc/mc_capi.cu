@@ -49,7 +49,7 @@ static int meqn_of(int solver) { return solver_meqn(solver); }
 static mc_status validate(const mc_problem* p)
 {
     if (!p) return set_error(MC_EINVAL, "problem is NULL");
-    if (p->solver < MC_ACOUSTICS || p->solver > MC_ADVECTION)
+    if (p->solver < MC_ACOUSTICS || p->solver > MC_ACOUSTICS_VAR)
         return set_error(MC_EINVAL, "unknown solver %d", p->solver);
     if (p->dtype != MC_F32 && p->dtype != MC_F64)
         return set_error(MC_EINVAL, "unknown dtype %d", p->dtype);
@@ -102,6 +102,7 @@ static cudaError_t sweep_launch(const SweepLaunch& L)
     case MC_ACOUSTICS: return sweep_launch_acoustics(L);
     case MC_SWE_ROE: return sweep_launch_swe(L);
     case MC_ADVECTION: return sweep_launch_advection(L);
+    case MC_ACOUSTICS_VAR: return sweep_launch_acoustics_var(L);
     default: return sweep_launch_euler(L);
     }
 }
@@ -112,6 +113,7 @@ static cudaError_t sweep_prepare(const mc_problem& p)
     case MC_ACOUSTICS: return sweep_prepare_acoustics(p.dtype);
     case MC_SWE_ROE: return sweep_prepare_swe(p.dtype);
     case MC_ADVECTION: return sweep_prepare_advection(p.dtype);
+    case MC_ACOUSTICS_VAR: return sweep_prepare_acoustics_var(p.dtype);
     default: return sweep_prepare_euler(p.dtype);
     }
 }
@@ -123,6 +125,7 @@ static cudaError_t maxspeed_launch(const mc_problem& p, const mc_layout& lay, co
     case MC_ACOUSTICS: return maxspeed_launch_acoustics(p, lay, q, out, s);
     case MC_SWE_ROE: return maxspeed_launch_swe(p, lay, q, out, s);
     case MC_ADVECTION: return maxspeed_launch_advection(p, lay, q, out, s);
+    case MC_ACOUSTICS_VAR: return maxspeed_launch_acoustics_var(p, lay, q, out, s);
     default: return maxspeed_launch_euler(p, lay, q, out, s);
     }
 }

@@ -9,11 +9,17 @@
 
 namespace mc {
 
-// fields of a solver's state (acoustics (p, u, v) and shallow water
-// (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4; advection (q): 1)
+// planes of a solver's state array (acoustics (p, u, v) and shallow water
+// (h, hu, hv): 3; Euler (rho, rho u, rho v, E): 4; advection (q): 1;
+// variable-coefficient acoustics (p, u, v, rho, c): 5)
 inline int solver_meqn(int solver)
 {
-    return solver == MC_EULER_ROE ? 4 : (solver == MC_ADVECTION ? 1 : 3);
+    switch (solver) {
+    case MC_EULER_ROE: return 4;
+    case MC_ADVECTION: return 1;
+    case MC_ACOUSTICS_VAR: return 5;
+    default: return 3;
+    }
 }
 
 struct DevState;
@@ -41,10 +47,12 @@ cudaError_t sweep_launch_acoustics(const SweepLaunch& L);
 cudaError_t sweep_launch_swe(const SweepLaunch& L);
 cudaError_t sweep_launch_euler(const SweepLaunch& L);
 cudaError_t sweep_launch_advection(const SweepLaunch& L);
+cudaError_t sweep_launch_acoustics_var(const SweepLaunch& L);
 cudaError_t sweep_prepare_acoustics(int dtype);
 cudaError_t sweep_prepare_swe(int dtype);
 cudaError_t sweep_prepare_euler(int dtype);
 cudaError_t sweep_prepare_advection(int dtype);
+cudaError_t sweep_prepare_acoustics_var(int dtype);
 cudaError_t maxspeed_launch_acoustics(const mc_problem& p, const mc_layout& lay, const void* q,
                                       unsigned long long* out, cudaStream_t s);
 cudaError_t maxspeed_launch_swe(const mc_problem& p, const mc_layout& lay, const void* q,
@@ -53,6 +61,8 @@ cudaError_t maxspeed_launch_euler(const mc_problem& p, const mc_layout& lay, con
                                   unsigned long long* out, cudaStream_t s);
 cudaError_t maxspeed_launch_advection(const mc_problem& p, const mc_layout& lay, const void* q,
                                       unsigned long long* out, cudaStream_t s);
+cudaError_t maxspeed_launch_acoustics_var(const mc_problem& p, const mc_layout& lay, const void* q,
+                                          unsigned long long* out, cudaStream_t s);
 
 // ghost fill (mc_capi.cu)
 cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
@@ -93,14 +103,17 @@ cudaError_t batch_launch_acoustics(const BatchLaunch& L);
 cudaError_t batch_launch_swe(const BatchLaunch& L);
 cudaError_t batch_launch_euler(const BatchLaunch& L);
 cudaError_t batch_launch_advection(const BatchLaunch& L);
+cudaError_t batch_launch_acoustics_var(const BatchLaunch& L);
 cudaError_t batch_init_acoustics(const BatchLaunch& L);
 cudaError_t batch_init_swe(const BatchLaunch& L);
 cudaError_t batch_init_euler(const BatchLaunch& L);
 cudaError_t batch_init_advection(const BatchLaunch& L);
+cudaError_t batch_init_acoustics_var(const BatchLaunch& L);
 // resident CTAs per SM of the batched kernel (also raises its smem limit)
 cudaError_t batch_occupancy_acoustics(int dtype, int* ctas);
 cudaError_t batch_occupancy_swe(int dtype, int* ctas);
 cudaError_t batch_occupancy_euler(int dtype, int* ctas);
 cudaError_t batch_occupancy_advection(int dtype, int* ctas);
+cudaError_t batch_occupancy_acoustics_var(int dtype, int* ctas);
 
 }  // namespace mc

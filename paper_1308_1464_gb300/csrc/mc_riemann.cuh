@@ -82,6 +82,7 @@ template <typename T>
 struct AcousticsRP {
     using real = T;
     static constexpr int NEQ = 3, NW = 2;
+    static constexpr int NAUX = 0, NPLANE = NEQ;   // state planes: the conserved fields
     static constexpr bool POSITIVE = false;   // no positivity constraint on (p, u, v)
     T c, Z, inv2Z;
     bool efix;  // unused: linear system
@@ -136,6 +137,68 @@ struct AcousticsRP {
     }
 };
 
+// ---------------------------------------------------------------- acoustics, variable coefficients
+// Density rho and sound speed c per cell, carried as state planes 3 and 4
+// after (p, u, v) and copied unchanged by the step (the paper's
+// variable-coefficient acoustics, §3 Table 2).  The normal solve puts the
+// left-going wave on the left medium's eigenvector (-Z_l, 1, 0) at speed -c_l
+// and the right-going one on the right medium's (Z_r, 1, 0) at +c_r
+// (LeVeque 2002, §9.6).  The transverse split of a fluctuation entering a
+// cell takes, toward each neighbour across the split direction, the
+// component along that neighbour's outgoing eigenvector at the interface
+// between the two cells; reflections there are why the parts do not add up.
+template <typename T>
+struct AcousticsVarRP {
+    using real = T;
+    static constexpr int NEQ = 3, NW = 2;
+    static constexpr int NAUX = 2, NPLANE = NEQ + NAUX;
+    static constexpr bool POSITIVE = false;
+    template <int DIR>
+    __host__ __device__ static constexpr bool wave_nz(int, int m) { return m != 2 - DIR; }
+    static constexpr bool CARRY_DOT = false;
+    static constexpr bool PAIRED = false;   // scalar solves only
+    static constexpr bool PAIR_LIMITER = false;
+    bool efix;  // unused: linear
+    struct Lin { T cl, cr; };
+    __device__ __forceinline__ T max_speed(const Lin& L) const { return fmax(L.cl, L.cr); }
+    __device__ __forceinline__ void cell_speeds(const T* q, T& sx, T& sy) const { sx = sy = q[4]; }
+    __host__ void setup(const double*, int) { efix = false; }
+
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin& L, bool&) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        const T zl = ql[3] * ql[4], zr = qr[3] * qr[4];
+        const T dp = qr[0] - ql[0], du = qr[un] - ql[un];
+        const T rz = rcp_(zl + zr);
+        const T a1 = (zr * du - dp) * rz, a2 = (zl * du + dp) * rz;
+        W[0][0] = -zl * a1; W[0][un] = a1; W[0][ut] = T(0);
+        W[1][0] = zr * a2;  W[1][un] = a2; W[1][ut] = T(0);
+        s[0] = -ql[4];
+        s[1] = qr[4];
+        amdq[0] = s[0] * W[0][0]; amdq[un] = s[0] * a1; amdq[ut] = T(0);
+        apdq[0] = s[1] * W[1][0]; apdq[un] = s[1] * a2; apdq[ut] = T(0);
+        L.cl = ql[4];
+        L.cr = qr[4];
+    }
+
+    // a enters the cell with material (rho, c) = mid; lo and hi are its
+    // neighbours across the split direction (below/above for an x-edge's
+    // fluctuation, DIR = 0; left/right for a y-edge's, DIR = 1)
+    template <int DIR>
+    __device__ __forceinline__ void transverse_cells(const T* lo, const T* mid, const T* hi, const T* a,
+                                                     T* bm, T* bp) const
+    {
+        constexpr int vn = 2 - DIR, vt = 1 + DIR;
+        const T zlo = lo[0] * lo[1], z = mid[0] * mid[1], zhi = hi[0] * hi[1];
+        const T dn = (z * a[vn] - a[0]) * rcp_(zlo + z);
+        const T up = (z * a[vn] + a[0]) * rcp_(z + zhi);
+        bm[0] = lo[1] * zlo * dn; bm[vn] = -lo[1] * dn; bm[vt] = T(0);
+        bp[0] = hi[1] * zhi * up; bp[vn] = hi[1] * up;  bp[vt] = T(0);
+    }
+};
+
 // ---------------------------------------------------------------- advection
 // q_t + u q_x + v q_y = 0 with constant velocity (u, v) = (param[0],
 // param[1]): one wave, the jump, moving at the edge-normal velocity
@@ -145,6 +208,7 @@ template <typename T>
 struct AdvectionRP {
     using real = T;
     static constexpr int NEQ = 1, NW = 1;
+    static constexpr int NAUX = 0, NPLANE = NEQ;
     static constexpr bool POSITIVE = false;
     template <int DIR>
     __host__ __device__ static constexpr bool wave_nz(int, int) { return true; }
@@ -191,6 +255,7 @@ template <typename T>
 struct SweRP {
     using real = T;
     static constexpr int NEQ = 3, NW = 3;
+    static constexpr int NAUX = 0, NPLANE = NEQ;
     static constexpr bool POSITIVE = true;    // depth h > 0
     T g;
     bool efix;
@@ -428,6 +493,7 @@ template <typename T>
 struct EulerRP {
     using real = T;
     static constexpr int NEQ = 4, NW = 3;
+    static constexpr int NAUX = 0, NPLANE = NEQ;
     static constexpr bool POSITIVE = true;    // density rho > 0
     T gamma, gm1;
     bool efix;

@@ -146,13 +146,14 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     const bool trans = FAST ? true : transverse_rt != 0;
     const bool trans2 = FAST ? false : (transverse_rt == 2 && second_rt);
     using T = typename RP::real;
-    constexpr int N = RP::NEQ, NW = RP::NW;
+    // N conserved fields; NP state planes (with material planes after them)
+    constexpr int N = RP::NEQ, NW = RP::NW, NP = RP::NPLANE;
     constexpr int ES = sizeof(T);
     constexpr int AL = align_elems(ES);
     constexpr int BW = box_w(ES);
     constexpr int RS = stage_rows(ES);
-    constexpr int SB = stage_bytes(ES, N);
-    constexpr int TB = box_bytes(ES, N);
+    constexpr int SB = stage_bytes(ES, NP);
+    constexpr int TB = box_bytes(ES, NP);
     const int lane = threadIdx.x & 31;
     const T hnux = T(0.5) * nux, hnuy = T(0.5) * nuy;
 
@@ -190,7 +191,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         }
         const T* row = reinterpret_cast<const T*>(W.ring + st * SB) + rr * BW;
 #pragma unroll
-        for (int m = 0; m < N; m++) {
+        for (int m = 0; m < NP; m++) {
             qc[m] = row[m * RS * BW + sx];
             ql[m] = row[m * RS * BW + sx - 1];
         }
@@ -212,7 +213,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     // (dlo, formed one row earlier), otherwise the waves themselves (Wy0) are
     // kept -- whichever the solver's register budget favours.
     constexpr bool CD = RP::CARRY_DOT;
-    T qc0[N], qc1[N], ql1[N];
+    T qc0[NP], qc1[NP], ql1[NP];
     T Wy0[CD ? 1 : NW][N], Wy1[NW][N], sy1[NW], dlo[NW];
     // XP = A+dQ(c-1/2) - F(c-1/2) and XM = A-dQ(c-1/2) + F(c-1/2) of row k (XM
     // goes to lane l-1, whose right edge this is); Z = B+dQ(k-1/2) + B-dQ(k+1/2)
@@ -225,8 +226,10 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     T bm_prev[N];
     typename RP::Lin Lx_cur{}, Ly_cur{}, Ly_prev{};
 #pragma unroll
+    for (int m = 0; m < NP; m++) qc0[m] = T(0);
+#pragma unroll
     for (int m = 0; m < N; m++) {
-        qc0[m] = bp_pend[m] = tyP_m[m] = tyP_p[m] = bm_prev[m] = T(0);
+        bp_pend[m] = tyP_m[m] = tyP_p[m] = bm_prev[m] = T(0);
         XP0[m] = XM0[m] = Z0[m] = BpAp0[m] = BpAm0[m] = T(0);
     }
 #pragma unroll
@@ -240,8 +243,39 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     }
     if (!fetch(rbase, qc1, ql1)) return false;
 
+    // transverse splits.  A y-edge fluctuation entering the cell of column c
+    // whose plane vector is `cell`; with material planes the split needs that
+    // cell's left and right neighbours, held by lanes l-1 and l+1.
+    auto tsplit_y = [&](const typename RP::Lin& L, const T* cell, const T* a, T* bm, T* bp) {
+        if constexpr (RP::NAUX > 0) {
+            T lo[RP::NAUX > 0 ? RP::NAUX : 1], hi[RP::NAUX > 0 ? RP::NAUX : 1];
+#pragma unroll
+            for (int q = 0; q < RP::NAUX; q++) {
+                lo[q] = shfl_up1(cell[N + q]);
+                hi[q] = shfl_down1(cell[N + q]);
+            }
+            rp.template transverse_cells<1>(lo, cell + N, hi, a, bm, bp);
+        } else {
+            rp.template transverse<1>(L, a, bm, bp);
+        }
+    };
+    // An x-edge fluctuation entering a cell whose neighbours below and above
+    // have plane vectors lo and hi.
+    auto tsplit_x = [&](const typename RP::Lin& L, const T* lo, const T* mid, const T* hi, const T* a,
+                        T* bm, T* bp) {
+        if constexpr (RP::NAUX > 0) rp.template transverse_cells<0>(lo + N, mid + N, hi + N, a, bm, bp);
+        else rp.template transverse<0>(L, a, bm, bp);
+    };
+
     for (int k = j0 - 3; k < jend; k++) {
-        T qc2[N], ql2[N];
+        T qc2[NP], ql2[NP];
+        // material of cell (c-1, k), the neighbour below where A-dQ of x-edge
+        // (c-1/2, k+1) enters
+        T ql0[NP];
+        if constexpr (RP::NAUX > 0) {
+#pragma unroll
+            for (int q = 0; q < RP::NAUX; q++) ql0[N + q] = shfl_up1(qc0[N + q]);
+        }
         if (!fetch(k + 2, qc2, ql2)) return false;
 
         // ---- y-edge between rows k+1 and k+2 of column c, x-edge c-1/2 of row k+1
@@ -338,8 +372,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             if (trans2) {
                 Ly_cur = Ly;
             } else if (trans) {
-                rp.template transverse<1>(Ly, bm2, t1, t2);
-                rp.template transverse<1>(Ly, bp2, nPm, nPp);
+                tsplit_y(Ly, qc1, bm2, t1, t2);
+                tsplit_y(Ly, qc2, bp2, nPm, nPp);
             }
             y_tail();
             {
@@ -354,8 +388,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 if (trans2) {
                     Lx_cur = Lx;
                 } else if (trans) {
-                    rp.template transverse<0>(Lx, apdq1, BmAp1, BpAp1);
-                    rp.template transverse<0>(Lx, amdq1, BmAm1, BpAm1);
+                    tsplit_x(Lx, qc0, qc1, qc2, apdq1, BmAp1, BpAp1);
+                    tsplit_x(Lx, ql0, ql1, ql2, amdq1, BmAm1, BpAm1);
                 }
                 const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
                 bad |= in && badx;
@@ -458,8 +492,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     apx[m] = apdq1[m] - Fn[m];
                     amx[m] = amdq1[m] + Fn[m];
                 }
-                rp.template transverse<0>(Lx_cur, apx, BmAp1, BpAp1);
-                rp.template transverse<0>(Lx_cur, amx, BmAm1, BpAm1);
+                tsplit_x(Lx_cur, qc0, qc1, qc2, apx, BmAp1, BpAp1);
+                tsplit_x(Lx_cur, ql0, ql1, ql2, amx, BmAm1, BpAm1);
                 // ... and those of y-edge (c, k+1/2), now that its limited
                 // correction (Gn so far) is known: the part entering row k+1
                 // feeds F of row k+1 below, the part entering row k completes
@@ -470,8 +504,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     bmL[m] = bm_prev[m] + Gn[m];
                     bpL[m] = bp_pend[m] - Gn[m];
                 }
-                rp.template transverse<1>(Ly_prev, bmL, sm_, sp_);
-                rp.template transverse<1>(Ly_prev, bpL, TAm, TAp);
+                tsplit_y(Ly_prev, qc0, bmL, sm_, sp_);
+                tsplit_y(Ly_prev, qc1, bpL, TAm, TAp);
 #pragma unroll
                 for (int m = 0; m < N; m++) {
                     const T dF = -hnuy * (sm_[m] + shfl_up1(sp_[m]));
@@ -504,6 +538,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 T* o = qout + (long long)(k + 2) * ld_x + x_offset + c;
 #pragma unroll
                 for (int m = 0; m < N; m++) o[m * ld_field] = qn[m];
+#pragma unroll
+                for (int m = N; m < NP; m++) o[m * ld_field] = qc0[m];   // material, unchanged
                 if (WALL_GHOSTS) {
                     const bool hx = c < 2 || c >= mx - 2, hy = k < 2 || k >= my - 2;
                     const int gi = c < 2 ? -1 - c : 2 * mx - 1 - c;
@@ -523,8 +559,11 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 
         // ---- rotate
 #pragma unroll
-        for (int m = 0; m < N; m++) {
+        for (int m = 0; m < NP; m++) {
             qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
+        }
+#pragma unroll
+        for (int m = 0; m < N; m++) {
             Z0[m] = dqy_n[m] - Gn[m];
             bp_pend[m] = bp2[m];
             if (trans && !trans2) { tyP_m[m] = nPm[m]; tyP_p[m] = nPp[m]; }
@@ -580,7 +619,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     using T = typename RP::real;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpRing W = warp_ring(smem, sizeof(T), RP::NEQ);
+    WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
 
     const int cur = a.cur ? *a.cur : 0;
     const CUtensorMap* map = cur ? map_b : map_a;
@@ -706,8 +745,8 @@ __global__ void max_cell_speed_kernel(const RP rp, const typename RP::real* q, i
     for (int j = blockIdx.x * nw + (threadIdx.x >> 5); j < my; j += gridDim.x * nw) {
         const T* row = q + (long long)(j + 2) * ld_x + x_offset;
         for (int i = lane; i < mx; i += 32) {
-            T qq[RP::NEQ];
-            for (int m = 0; m < RP::NEQ; m++) qq[m] = row[m * ld_field + i];
+            T qq[RP::NPLANE];
+            for (int m = 0; m < RP::NPLANE; m++) qq[m] = row[m * ld_field + i];
             T sx, sy;
             rp.cell_speeds(qq, sx, sy);
             msx = fmax(msx, sx);

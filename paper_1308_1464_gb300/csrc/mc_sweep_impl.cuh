@@ -40,7 +40,7 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.smax_bits = L.smax_bits;
     a.status = L.status;
 
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
     int blocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
     if (is_fast_scheme(L.prob))
@@ -56,7 +56,7 @@ template <class RP>
 cudaError_t sweep_prepare_t()
 {
     using T = typename RP::real;
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
     cudaError_t e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
@@ -109,7 +109,7 @@ template <class RP>
 cudaError_t batch_launch_t(const BatchLaunch& L)
 {
     using T = typename RP::real;
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
     if (is_fast_scheme(L.proto))
         batch_sweep_kernel<RP, true><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
     else
@@ -131,7 +131,7 @@ template <class RP>
 cudaError_t batch_occupancy_t(int* ctas)
 {
     using T = typename RP::real;
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NEQ);
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
     cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)

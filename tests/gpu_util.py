@@ -11,7 +11,8 @@ GAMMA = 1.4
 SOLVER_IDS = {"acoustics": (mc.ACOUSTICS, oracle.ACOUSTICS, (1.0, 4.0, 0, 0)),
               "swe": (mc.SWE_ROE, oracle.SWE, (G, 0, 0, 0)),
               "euler": (mc.EULER_ROE, oracle.EULER, (GAMMA, 0, 0, 0)),
-              "advection": (mc.ADVECTION, oracle.ADVECTION, (1.0, -0.6, 0, 0))}
+              "advection": (mc.ADVECTION, oracle.ADVECTION, (1.0, -0.6, 0, 0)),
+              "acoustics_var": (mc.ACOUSTICS_VAR, oracle.ACOUSTICS_VAR, (0, 0, 0, 0))}
 TOL = {mc.F64: 1e-12, mc.F32: 2e-5}
 
 
@@ -26,7 +27,7 @@ def problems(solver, mx, my, dx, dy, dtype, bc, limiter=4, order=2, transverse=1
 
 def field_scales(solver, q):
     """Per-field scales S_m of the parity norm max|gpu - oracle| / S_m."""
-    if solver in ("acoustics", "advection"):
+    if solver in ("acoustics", "advection", "acoustics_var"):
         return np.ones(q.shape[0])
     if solver == "swe":
         h = np.abs(q[0]).max()
@@ -54,6 +55,17 @@ def embed(op, interior):
 def initial_state(solver, mx, my, seed=0):
     """Seeded test data with every term of the step active."""
     rng = np.random.default_rng(seed)
+    if solver == "acoustics_var":
+        # a pulse over a layered medium: density jump at mid-height, sound
+        # speed growing along x, small noise in the material too
+        g = workloads.acoustics_pulse(mx, my)
+        x = (np.arange(mx) + 0.5) / mx
+        y = (np.arange(my) + 0.5) / my
+        X, Y = np.meshgrid(x, y)
+        rho = np.where(Y < 0.5, 1.0, 3.0) * (1 + 0.05 * rng.uniform(-1, 1, size=X.shape))
+        c = (1.0 + X) * (1 + 0.05 * rng.uniform(-1, 1, size=X.shape))
+        p0 = g.q[0]
+        return np.stack([p0, 0.3 * np.roll(p0, 3, axis=1), -0.2 * np.roll(p0, 2, axis=0), rho, c]), g.dx, g.dy
     if solver == "advection":
         g = workloads.acoustics_pulse(mx, my)
         q = g.q[:1].copy() + 0.3 * np.sin(2 * np.pi * np.arange(mx) / mx)[None, None, :]

@@ -75,6 +75,11 @@ CASES = [
     ("euler", mc.F32, (X, X, X, X), 3, 2),
     ("euler", mc.F64, (W, W, X, X), 4, 2),
     ("euler", mc.F32, (P, P, W, W), 2, 1),
+    # variable-coefficient acoustics (material planes carried with the state)
+    ("acoustics_var", mc.F64, (P, P, P, P), 4, 1),
+    ("acoustics_var", mc.F32, (W, X, P, P), 3, 2),
+    ("acoustics_var", mc.F64, (X, X, W, W), 1, 0),
+    ("acoustics_var", mc.F32, (W, W, W, W), 2, 1),
 ]
 
 
@@ -106,7 +111,8 @@ def test_first_order_and_no_limiter():
                                                    ("euler", mc.F32, (X, X, P, P), 1),
                                                    ("acoustics", mc.F64, (P, P, W, W), 1),
                                                    ("swe", mc.F32, (W, X, X, W), 2),
-                                                   ("advection", mc.F64, (P, P, X, W), 2)])
+                                                   ("advection", mc.F64, (P, P, X, W), 2),
+                                                   ("acoustics_var", mc.F32, (X, W, P, P), 2)])
 def test_tiny_and_odd_grids(mx, my, solver, dtype, bc, trans):
     q, _, _ = initial_state(solver, max(mx, 4), max(my, 4), seed=mx * 100 + my)
     q = np.ascontiguousarray(q[:, :my, :mx])
