@@ -43,6 +43,15 @@ WORKLOADS = {
                     desc="Euler Roe+HH four-quadrant 4096x4096 fp32, extrapolation, MC, CFL 0.8"),
     "acoustics": dict(solver="acoustics", dtype="f64", n=128, cfl=0.9, bc="periodic",
                       desc="acoustics Gaussian pulse 128x128 fp64, periodic, MC, CFL 0.9"),
+    # further solvers and options of the step, measured on the same grid size
+    "adv32": dict(solver="advection", dtype="f32", n=4096, cfl=0.9, bc="periodic",
+                  desc="advection (u, v) = (1, 0.6) Gaussian 4096x4096 fp32, periodic, MC, CFL 0.9"),
+    "acvar32": dict(solver="acoustics_var", dtype="f32", n=4096, cfl=0.9, bc="extrap",
+                    desc="variable-coefficient acoustics, layered medium 4096x4096 fp32, "
+                         "extrapolation, MC, CFL 0.9"),
+    "swe32t2": dict(solver="swe", dtype="f32", n=4096, cfl=0.9, bc="wall", limiter=3, transverse=2,
+                    desc="shallow-water Roe+HH dam break 4096x4096 fp32, walls, van Leer, "
+                         "transverse option 2, CFL 0.9"),
 }
 G, GAMMA = 9.81, 1.4
 
@@ -80,11 +89,18 @@ def make_problem(mc, wl):
     elif wl["solver"] == "euler":
         g = workloads.euler_quadrants(n, n)
         sid, param, bc = mc.EULER_ROE, (GAMMA, 0, 0, 0), mc.BC_EXTRAP
+    elif wl["solver"] == "advection":
+        g = workloads.advection_pulse(n, n)
+        sid, param, bc = mc.ADVECTION, (1.0, 0.6, 0, 0), mc.BC_PERIODIC
+    elif wl["solver"] == "acoustics_var":
+        g = workloads.acoustics_layered(n, n)
+        sid, param, bc = mc.ACOUSTICS_VAR, (0, 0, 0, 0), mc.BC_EXTRAP
     else:
         g = workloads.acoustics_pulse(n, n)
         sid, param, bc = mc.ACOUSTICS, (1.0, 4.0, 0, 0), mc.BC_PERIODIC
     dtype = mc.F64 if wl["dtype"] == "f64" else mc.F32
-    p = mc.Problem.make(sid, n, n, g.dx, g.dy, dtype=dtype, bc=(bc,) * 4, param=param)
+    p = mc.Problem.make(sid, n, n, g.dx, g.dy, dtype=dtype, bc=(bc,) * 4, param=param,
+                        limiter=wl.get("limiter", mc.LIM_MC), transverse=wl.get("transverse", 1))
     return p, g
 
 
@@ -181,24 +197,39 @@ def ncu_traffic(workload: str):
     return None
 
 
+def oracle_problem(wl, n):
+    """The oracle's problem and seeded input for workload wl on an n x n grid."""
+    import oracle
+    from paper_1308_1464_gb300 import workloads
+    opts = dict(limiter=wl.get("limiter", oracle.LIM_MC), transverse=wl.get("transverse", 1))
+    if wl["solver"] == "swe":
+        g = workloads.swe_dambreak(n, n)
+        op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
+                            param=(G, 0, 0, 0), **opts)
+    elif wl["solver"] == "euler":
+        g = workloads.euler_quadrants(n, n)
+        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
+                            param=(GAMMA, 0, 0, 0), **opts)
+    elif wl["solver"] == "advection":
+        g = workloads.advection_pulse(n, n)
+        op = oracle.Problem(oracle.ADVECTION, n, n, g.dx, g.dy, param=(1.0, 0.6, 0, 0), **opts)
+    elif wl["solver"] == "acoustics_var":
+        g = workloads.acoustics_layered(n, n)
+        op = oracle.Problem(oracle.ACOUSTICS_VAR, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
+                            param=(0, 0, 0, 0), **opts)
+    else:
+        g = workloads.acoustics_pulse(n, n)
+        op = oracle.Problem(oracle.ACOUSTICS, n, n, g.dx, g.dy, param=(1.0, 4.0, 0, 0), **opts)
+    return op, g
+
+
 def cpu_baseline(wl, budget_s=12.0):
     """The FP64 oracle, as it stands, timed on this machine's cores on a bounded
     sample of the workload: steps of the same problem on an n x n grid."""
     import oracle
-    from paper_1308_1464_gb300 import workloads
     cores = len(os.sched_getaffinity(0))
     n = 1024 if wl["solver"] != "acoustics" else 128
-    if wl["solver"] == "swe":
-        g = workloads.swe_dambreak(n, n)
-        op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
-                            param=(G, 0, 0, 0))
-    elif wl["solver"] == "euler":
-        g = workloads.euler_quadrants(n, n)
-        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
-                            param=(GAMMA, 0, 0, 0))
-    else:
-        g = workloads.acoustics_pulse(n, n)
-        op = oracle.Problem(oracle.ACOUSTICS, n, n, g.dx, g.dy, param=(1.0, 4.0, 0, 0))
+    op, g = oracle_problem(wl, n)
     q = np.zeros(op.shape)
     q[:, 2:-2, 2:-2] = g.q
     dt = wl["cfl"] / oracle.max_cell_speed(op, oracle.bc_fill(op, q))
@@ -228,18 +259,7 @@ def run_reference(args, wl):
     probe = cpu_baseline(wl, budget_s=1.0)
     rate = probe["value"]
     n = int(max(16, min(wl["n"], (rate * per_step_budget) ** 0.5)))
-    from paper_1308_1464_gb300 import workloads
-    if wl["solver"] == "swe":
-        g = workloads.swe_dambreak(n, n)
-        op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
-                            param=(G, 0, 0, 0))
-    elif wl["solver"] == "euler":
-        g = workloads.euler_quadrants(n, n)
-        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
-                            param=(GAMMA, 0, 0, 0))
-    else:
-        g = workloads.acoustics_pulse(n, n)
-        op = oracle.Problem(oracle.ACOUSTICS, n, n, g.dx, g.dy, param=(1.0, 4.0, 0, 0))
+    op, g = oracle_problem(wl, n)
     q = np.zeros(op.shape)
     q[:, 2:-2, 2:-2] = g.q
     dt = wl["cfl"] / oracle.max_cell_speed(op, oracle.bc_fill(op, q))

@@ -77,6 +77,32 @@ def acoustics_pulse(mx: int = 128, my: int = 128) -> Grid:
     return Grid(q, dx, dy, 0.0, 0.0)
 
 
+def advection_pulse(mx: int = 4096, my: int = 4096) -> Grid:
+    """Scalar Gaussian q = exp(-80 r^2) at (0.5, 0.5) on [0,1]^2 plus a unit
+    background, for constant-velocity advection on a periodic domain."""
+    x, dx = _centres(mx, 0.0, 1.0)
+    y, dy = _centres(my, 0.0, 1.0)
+    X, Y = np.meshgrid(x, y)
+    q = (1.0 + np.exp(-80.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2)))[None]
+    return Grid(q, dx, dy, 0.0, 0.0)
+
+
+def acoustics_layered(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED) -> Grid:
+    """Pressure pulse in a layered medium on [0,1]^2 for variable-coefficient
+    acoustics: planes (p, u, v, rho, c).  p = exp(-80 r^2) at (0.5, 0.3),
+    u = v = 0; density 1 below y = 0.5 and 3 above, times 1 + U(-0.05, 0.05)
+    per cell; sound speed 1 + x, times 1 + U(-0.05, 0.05) per cell."""
+    x, dx = _centres(mx, 0.0, 1.0)
+    y, dy = _centres(my, 0.0, 1.0)
+    X, Y = np.meshgrid(x, y)
+    idx = np.arange(mx * my, dtype=np.uint64).reshape(my, mx)
+    q = np.zeros((5, my, mx))
+    q[0] = np.exp(-80.0 * ((X - 0.5) ** 2 + (Y - 0.3) ** 2))
+    q[3] = np.where(Y < 0.5, 1.0, 3.0) * (1.0 + 0.05 * (2.0 * uniform(seed, 21, idx) - 1.0))
+    q[4] = (1.0 + X) * (1.0 + 0.05 * (2.0 * uniform(seed, 22, idx) - 1.0))
+    return Grid(q, dx, dy, 0.0, 0.0)
+
+
 def swe_dambreak(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED,
                  noise: float = 1e-3) -> Grid:
     """Radial dam break on [-1,1]^2: h = 2 for r < 0.5 else 1, plus U(-noise, noise)."""

@@ -135,22 +135,32 @@ def test_tile_shape_invariance(solver, dtype, trans):
 
 
 FULL = [
-    ("swe", mc.F32, 4096, 4096, (W, W, W, W)),     # shallow-water dam break, bench configuration
-    ("swe", mc.F64, 4096, 4096, (W, W, W, W)),
-    ("euler", mc.F32, 4096, 4096, (X, X, X, X)),   # four-quadrant Euler
+    ("swe", mc.F32, 4096, 4096, (W, W, W, W), {}),     # shallow-water dam break, bench configuration
+    ("swe", mc.F64, 4096, 4096, (W, W, W, W), {}),
+    ("euler", mc.F32, 4096, 4096, (X, X, X, X), {}),   # four-quadrant Euler
+    ("advection", mc.F32, 4096, 4096, (P, P, P, P), {}),
+    ("acoustics_var", mc.F32, 4096, 4096, (X, X, X, X), {}),
+    ("swe", mc.F32, 4096, 4096, (W, W, W, W), dict(limiter=3, transverse=2)),
 ]
 
 
-@pytest.mark.parametrize("solver,dtype,mx,my,bc", FULL)
-def test_full_size_windows(solver, dtype, mx, my, bc):
+@pytest.mark.parametrize("solver,dtype,mx,my,bc,opts", FULL)
+def test_full_size_windows(solver, dtype, mx, my, bc, opts):
     """Full-size grid, default launch configuration: 40 windows of 8 x 8 cells
     (corners, edges, random interior) recomputed by the oracle from the GPU
     step's filled input, plus conservation of mass across the walls/extrapolation."""
     if solver == "swe":
         g = workloads.swe_dambreak(mx, my)
+    elif solver == "advection":
+        g = workloads.advection_pulse(mx, my)
+    elif solver == "acoustics_var":
+        g = workloads.acoustics_layered(mx, my)
     else:
         g = workloads.euler_quadrants(mx, my)
-    p, op = problems(solver, mx, my, g.dx, g.dy, dtype, bc)
+    p, op = problems(solver, mx, my, g.dx, g.dy, dtype, bc, **opts)
+    if solver == "advection":
+        p.param[0], p.param[1] = 1.0, 0.6
+        op.param = (1.0, 0.6, 0, 0)
     npdt = np.float64 if dtype == mc.F64 else np.float32
     qin = g.q.astype(npdt)
     # dt from the oracle's cell-speed rule on the same rounded input
