@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SOURCES = ["rp.c", "step.c", "exact.c", "mlp.c"]
 _LIBDIR = os.path.join(_HERE, "_lib")
 
-ACOUSTICS, SWE, EULER, ADVECTION, ACOUSTICS_VAR = 1, 2, 3, 4, 5
+ACOUSTICS, SWE, EULER, ADVECTION, ACOUSTICS_VAR, EULER_GODUNOV = 1, 2, 3, 4, 5, 6
 LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_EXTRAP, BC_WALL, BC_GIVEN = 0, 1, 2, 3
 SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_GIVEN = range(6)
@@ -83,7 +83,7 @@ class Problem:
 
     @property
     def meqn(self) -> int:
-        return {EULER: 4, ADVECTION: 1}.get(self.solver, 3)
+        return {EULER: 4, EULER_GODUNOV: 4, ADVECTION: 1}.get(self.solver, 3)
 
     @property
     def nplane(self) -> int:
@@ -123,6 +123,8 @@ def lib():
         L.mcref_rpn2.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D, _D]
         L.mcref_rpt2.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D]
         L.mcref_rpt2_var.argtypes = [P, ctypes.c_int, _D, _D, _D, _D, _D, _D]
+        L.mcref_exact_sample.argtypes = [ctypes.c_double] * 9 + [_D, _D, _D]
+        L.mcref_exact_sample.restype = None
         L.mcref_flux.argtypes = [P, ctypes.c_int, _D, _D]
         L.mcref_flux.restype = None
         L.mcref_philim.argtypes = [ctypes.c_int, ctypes.c_double]
@@ -199,6 +201,14 @@ def rpt2_var(prob: Problem, direction: int, qlo, qc, qhi, asdq):
     lib().mcref_rpt2_var(ctypes.byref(prob.c()), direction, _p(qlo), _p(qc), _p(qhi), _p(asdq),
                          _p(bm), _p(bp))
     return bm, bp
+
+
+def exact_sample(gamma, rl, ul, pl, rr, ur, pr, pstar, ustar):
+    """(rho, u, p) of the exact 1D Riemann solution at x/t = 0."""
+    out = [ctypes.c_double() for _ in range(3)]
+    lib().mcref_exact_sample(*(float(v) for v in (gamma, rl, ul, pl, rr, ur, pr, pstar, ustar)),
+                             *(ctypes.byref(o) for o in out))
+    return tuple(o.value for o in out)
 
 
 def flux(prob: Problem, direction: int, q):

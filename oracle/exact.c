@@ -195,3 +195,121 @@ void mcref_exact_batch(int64_t n, double gamma, const double* rl, const double* 
         iters[k] = it;
     }
 }
+
+
+/* ------------------------------------------------------------------ */
+/* Godunov normal solve with the exact solution (Toro ch. 4)           */
+/* ------------------------------------------------------------------ */
+
+/* Star-region density behind the wave facing side K: Rankine-Hugoniot for a
+ * shock (p* > p_K, Toro eq. 4.50), isentropic for a rarefaction (eq. 4.53). */
+static double star_density(double gamma, double rK, double pK, double ps)
+{
+    const double r = ps / pK;
+    if (ps > pK) {
+        const double g6 = (gamma - 1.0) / (gamma + 1.0);
+        return rK * (r + g6) / (g6 * r + 1.0);
+    }
+    return rK * pow(r, 1.0 / gamma);
+}
+
+/* Speed of the shock facing side K (sgn = -1 left, +1 right; Toro eq. 4.52). */
+static double shock_speed(double gamma, double uK, double pK, double cK, double ps, double sgn)
+{
+    return uK + sgn * cK * sqrt((gamma + 1.0) / (2.0 * gamma) * ps / pK + (gamma - 1.0) / (2.0 * gamma));
+}
+
+void mcref_exact_sample(double gamma, double rl, double ul, double pl, double rr, double ur,
+                        double pr, double pstar, double ustar, double* rho0, double* u0, double* p0)
+{
+    /* Toro §4.5 at x/t = 0.  The side of the contact that contains the
+     * interface is the left one if u* >= 0; the mirror image handles the
+     * right side (sgn = +1 flips velocities of the left-side formulas). */
+    const int left = ustar >= 0.0;
+    const double rK = left ? rl : rr, pK = left ? pl : pr;
+    const double sgn = left ? -1.0 : 1.0;          /* wave facing side K travels in direction sgn */
+    const double uK = left ? ul : ur;
+    const double cK = sound(gamma, rK, pK);
+    if (pstar > pK) {
+        const double S = shock_speed(gamma, uK, pK, cK, pstar, sgn);
+        if ((left && S >= 0.0) || (!left && S <= 0.0)) {
+            *rho0 = rK; *u0 = uK; *p0 = pK;
+        } else {
+            *rho0 = star_density(gamma, rK, pK, pstar); *u0 = ustar; *p0 = pstar;
+        }
+        return;
+    }
+    const double head = uK + sgn * cK;
+    const double cs = cK * pow(pstar / pK, 0.5 * (gamma - 1.0) / gamma);
+    const double tail = ustar + sgn * cs;
+    if ((left && head >= 0.0) || (!left && head <= 0.0)) {
+        *rho0 = rK; *u0 = uK; *p0 = pK;
+    } else if ((left && tail <= 0.0) || (!left && tail >= 0.0)) {
+        *rho0 = star_density(gamma, rK, pK, pstar); *u0 = ustar; *p0 = pstar;
+    } else {
+        /* inside the fan, at x/t = 0 (Toro eq. 4.56 / 4.63 with S = 0) */
+        const double c = 2.0 / (gamma + 1.0) * (cK - sgn * 0.5 * (gamma - 1.0) * uK);
+        *u0 = -sgn * c;
+        *rho0 = rK * pow(c / cK, 2.0 / (gamma - 1.0));
+        *p0 = pK * pow(c / cK, 2.0 * gamma / (gamma - 1.0));
+    }
+}
+
+/* conserved vector of (rho, u_n, u_t, p) on the edge of normal dir */
+static void conserved(double gamma, int dir, double rho, double un, double ut, double pr, double* q)
+{
+    const int mu = 1 + dir, mv = 2 - dir;
+    q[0] = rho;
+    q[mu] = rho * un;
+    q[mv] = rho * ut;
+    q[3] = pr / (gamma - 1.0) + 0.5 * rho * (un * un + ut * ut);
+}
+
+int mcref_godunov_rpn2(const mcref_problem* p, int dir, const double* ql, const double* qr,
+                       double* wave, double* s, double* amdq, double* apdq)
+{
+    const int mu = 1 + dir, mv = 2 - dir;
+    const double gamma = p->param[0];
+    for (int k = 0; k < 12; k++) wave[k] = 0.0;
+    for (int k = 0; k < 3; k++) s[k] = 0.0;
+    for (int m = 0; m < 4; m++) amdq[m] = apdq[m] = 0.0;
+    if (!(ql[0] > 0.0 && qr[0] > 0.0)) return MCREF_F_NONPHYS;
+    const double rl = ql[0], ul = ql[mu] / rl, vl = ql[mv] / rl;
+    const double rr = qr[0], ur = qr[mu] / rr, vr = qr[mv] / rr;
+    const double pl = (gamma - 1.0) * (ql[3] - 0.5 * rl * (ul * ul + vl * vl));
+    const double pr = (gamma - 1.0) * (qr[3] - 0.5 * rr * (ur * ur + vr * vr));
+    if (!(pl > 0.0 && pr > 0.0)) return MCREF_F_NONPHYS;
+    double ps, us;
+    int it;
+    int fl = mcref_exact_riemann(gamma, rl, ul, pl, rr, ur, pr, MCREF_SEED_ADAPTIVE, 0.0, 1e-14, 100,
+                                 &ps, &us, &it);
+    if (fl & MCREF_RS_VACUUM) return MCREF_F_NONPHYS;
+    if (fl & MCREF_RS_NOCONV) mcref_exact_bisect(gamma, rl, ul, pl, rr, ur, pr, &ps, &us);
+    const double cl = sound(gamma, rl, pl), cr = sound(gamma, rr, pr);
+    /* states on either side of the contact, and the jumps across the waves */
+    double qsl[4], qsr[4];
+    conserved(gamma, dir, star_density(gamma, rl, pl, ps), us, vl, ps, qsl);
+    conserved(gamma, dir, star_density(gamma, rr, pr, ps), us, vr, ps, qsr);
+    for (int m = 0; m < 4; m++) {
+        wave[m] = qsl[m] - ql[m];
+        wave[4 + m] = qsr[m] - qsl[m];
+        wave[8 + m] = qr[m] - qsr[m];
+    }
+    /* wave speeds: the shock speed, or a rarefaction's head (its fastest
+     * signal), the contact at u* */
+    s[0] = ps > pl ? shock_speed(gamma, ul, pl, cl, ps, -1.0) : ul - cl;
+    s[1] = us;
+    s[2] = ps > pr ? shock_speed(gamma, ur, pr, cr, ps, 1.0) : ur + cr;
+    /* fluctuations: flux differences to the interface state */
+    double r0, u0, p0, q0[4], f0[4], fl_[4], fr_[4];
+    mcref_exact_sample(gamma, rl, ul, pl, rr, ur, pr, ps, us, &r0, &u0, &p0);
+    conserved(gamma, dir, r0, u0, us >= 0.0 ? vl : vr, p0, q0);
+    mcref_flux(p, dir, q0, f0);
+    mcref_flux(p, dir, ql, fl_);
+    mcref_flux(p, dir, qr, fr_);
+    for (int m = 0; m < 4; m++) {
+        amdq[m] = f0[m] - fl_[m];
+        apdq[m] = fr_[m] - f0[m];
+    }
+    return 0;
+}

@@ -33,8 +33,13 @@ extern "C" {
  * cell (the paper's variable-coefficient acoustics, §3, Table 2); the state
  * carries them as two extra planes after (p, u, v), which the step copies
  * unchanged. */
+/* MCREF_EULER_GODUNOV: the Euler equations with the exact Riemann solution
+ * (Toro ch. 4) in the normal solve instead of Roe's linearisation: the
+ * fluctuations are flux differences to the state sampled at x/t = 0, the
+ * waves are the jumps across the two nonlinear waves and the contact; the
+ * transverse split stays Roe's. */
 enum { MCREF_ACOUSTICS = 1, MCREF_SWE = 2, MCREF_EULER = 3, MCREF_ADVECTION = 4,
-       MCREF_ACOUSTICS_VAR = 5 };
+       MCREF_ACOUSTICS_VAR = 5, MCREF_EULER_GODUNOV = 6 };
 /* Clawpack numbering: 1 minmod, 2 superbee, 3 van Leer, 4 monotonized central */
 enum { MCREF_LIM_NONE = 0, MCREF_LIM_MINMOD = 1, MCREF_LIM_SUPERBEE = 2, MCREF_LIM_VANLEER = 3,
        MCREF_LIM_MC = 4 };
@@ -87,6 +92,15 @@ int mcref_rpt2(const mcref_problem* p, int dir, const double* ql, const double* 
  * carry (p, u, v, rho, c). */
 int mcref_rpt2_var(const mcref_problem* p, int dir, const double* qlo, const double* qc,
                    const double* qhi, const double* asdq, double* bmasdq, double* bpasdq);
+
+/* Godunov normal solve of MCREF_EULER_GODUNOV (called by mcref_rpn2). */
+int mcref_godunov_rpn2(const mcref_problem* p, int dir, const double* ql, const double* qr,
+                       double* wave, double* s, double* amdq, double* apdq);
+
+/* The state of the exact 1D Euler Riemann solution at x/t = 0 (primitive
+ * rho, u, p of the normal problem; Toro §4.5), for the pins. */
+void mcref_exact_sample(double gamma, double rl, double ul, double pl, double rr, double ur,
+                        double pr, double pstar, double ustar, double* rho0, double* u0, double* p0);
 
 /* Physical flux in direction dir (used by the pins). */
 void mcref_flux(const mcref_problem* p, int dir, const double* q, double* f);

@@ -21,7 +21,8 @@
 
 int mcref_meqn(int solver)
 {
-    return solver == MCREF_EULER ? 4 : (solver == MCREF_ADVECTION ? 1 : 3);
+    if (solver == MCREF_EULER || solver == MCREF_EULER_GODUNOV) return 4;
+    return solver == MCREF_ADVECTION ? 1 : 3;
 }
 
 int mcref_nplane(int solver)
@@ -166,6 +167,7 @@ int mcref_rpn2(const mcref_problem* p, int dir, const double* ql, const double* 
     const int meqn = mcref_meqn(p->solver), mw = mcref_mwaves(p->solver);
     double d[MCREF_MAXEQN], vec[4][MCREF_MAXEQN], lam[4];
     int flags = 0;
+    if (p->solver == MCREF_EULER_GODUNOV) return mcref_godunov_rpn2(p, dir, ql, qr, wave, s, amdq, apdq);
     for (int m = 0; m < meqn; m++) d[m] = qr[m] - ql[m];
     if (p->solver == MCREF_ADVECTION) {
         /* one wave, the jump, moving at the velocity normal to the edge
