@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "manyclaw.h")
 
 MC_OK, MC_EINVAL, MC_ECUDA, MC_ENOMEM, MC_ECFL, MC_ENONPHYS, MC_ETIMEOUT, MC_ENOTSUP = (
     0, -1, -2, -3, -4, -5, -6, -7)
-ACOUSTICS, SWE_ROE, EULER_ROE, ADVECTION, ACOUSTICS_VAR = 1, 2, 3, 4, 5
+ACOUSTICS, SWE_ROE, EULER_ROE, ADVECTION, ACOUSTICS_VAR, EULER_GODUNOV = 1, 2, 3, 4, 5, 6
 LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_EXTRAP, BC_WALL = 0, 1, 2
 F32, F64 = 0, 1
@@ -55,7 +55,7 @@ class Problem(ctypes.Structure):
     @property
     def meqn(self) -> int:
         """Planes of a state array (conserved fields, then material planes)."""
-        return {EULER_ROE: 4, ADVECTION: 1, ACOUSTICS_VAR: 5}.get(self.solver, 3)
+        return {EULER_ROE: 4, EULER_GODUNOV: 4, ADVECTION: 1, ACOUSTICS_VAR: 5}.get(self.solver, 3)
 
 
 class Layout(ctypes.Structure):

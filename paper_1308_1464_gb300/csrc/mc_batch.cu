@@ -84,6 +84,7 @@ static cudaError_t solver_batch_launch(const BatchLaunch& L)
     case MC_SWE_ROE: return batch_launch_swe(L);
     case MC_ADVECTION: return batch_launch_advection(L);
     case MC_ACOUSTICS_VAR: return batch_launch_acoustics_var(L);
+    case MC_EULER_GODUNOV: return batch_launch_euler_godunov(L);
     default: return batch_launch_euler(L);
     }
 }
@@ -95,6 +96,7 @@ static cudaError_t solver_batch_init(const BatchLaunch& L)
     case MC_SWE_ROE: return batch_init_swe(L);
     case MC_ADVECTION: return batch_init_advection(L);
     case MC_ACOUSTICS_VAR: return batch_init_acoustics_var(L);
+    case MC_EULER_GODUNOV: return batch_init_euler_godunov(L);
     default: return batch_init_euler(L);
     }
 }
@@ -106,6 +108,7 @@ static cudaError_t solver_batch_occupancy(const mc_problem& p, int* ctas)
     case MC_SWE_ROE: return batch_occupancy_swe(p.dtype, ctas);
     case MC_ADVECTION: return batch_occupancy_advection(p.dtype, ctas);
     case MC_ACOUSTICS_VAR: return batch_occupancy_acoustics_var(p.dtype, ctas);
+    case MC_EULER_GODUNOV: return batch_occupancy_euler_godunov(p.dtype, ctas);
     default: return batch_occupancy_euler(p.dtype, ctas);
     }
 }
@@ -444,6 +447,7 @@ mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double
             case MC_SWE_ROE: e = sweep_launch_swe(S); break;
             case MC_ADVECTION: e = sweep_launch_advection(S); break;
             case MC_ACOUSTICS_VAR: e = sweep_launch_acoustics_var(S); break;
+            case MC_EULER_GODUNOV: e = sweep_launch_euler_godunov(S); break;
             default: e = sweep_launch_euler(S); break;
             }
         }

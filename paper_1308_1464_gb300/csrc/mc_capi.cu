@@ -49,7 +49,7 @@ static int meqn_of(int solver) { return solver_meqn(solver); }
 static mc_status validate(const mc_problem* p)
 {
     if (!p) return set_error(MC_EINVAL, "problem is NULL");
-    if (p->solver < MC_ACOUSTICS || p->solver > MC_ACOUSTICS_VAR)
+    if (p->solver < MC_ACOUSTICS || p->solver > MC_EULER_GODUNOV)
         return set_error(MC_EINVAL, "unknown solver %d", p->solver);
     if (p->dtype != MC_F32 && p->dtype != MC_F64)
         return set_error(MC_EINVAL, "unknown dtype %d", p->dtype);
@@ -76,7 +76,7 @@ static mc_status validate(const mc_problem* p)
         return set_error(MC_EINVAL, "acoustics needs rho > 0 and K > 0");
     if (p->solver == MC_SWE_ROE && !(p->param[0] > 0.0))
         return set_error(MC_EINVAL, "shallow water needs g > 0");
-    if (p->solver == MC_EULER_ROE && !(p->param[0] > 1.0))
+    if ((p->solver == MC_EULER_ROE || p->solver == MC_EULER_GODUNOV) && !(p->param[0] > 1.0))
         return set_error(MC_EINVAL, "Euler needs gamma > 1");
     if (p->solver == MC_ADVECTION && !(isfinite(p->param[0]) && isfinite(p->param[1])))
         return set_error(MC_EINVAL, "advection needs finite velocities");
@@ -103,6 +103,7 @@ static cudaError_t sweep_launch(const SweepLaunch& L)
     case MC_SWE_ROE: return sweep_launch_swe(L);
     case MC_ADVECTION: return sweep_launch_advection(L);
     case MC_ACOUSTICS_VAR: return sweep_launch_acoustics_var(L);
+    case MC_EULER_GODUNOV: return sweep_launch_euler_godunov(L);
     default: return sweep_launch_euler(L);
     }
 }
@@ -114,6 +115,7 @@ static cudaError_t sweep_prepare(const mc_problem& p)
     case MC_SWE_ROE: return sweep_prepare_swe(p.dtype);
     case MC_ADVECTION: return sweep_prepare_advection(p.dtype);
     case MC_ACOUSTICS_VAR: return sweep_prepare_acoustics_var(p.dtype);
+    case MC_EULER_GODUNOV: return sweep_prepare_euler_godunov(p.dtype);
     default: return sweep_prepare_euler(p.dtype);
     }
 }
@@ -126,6 +128,7 @@ static cudaError_t maxspeed_launch(const mc_problem& p, const mc_layout& lay, co
     case MC_SWE_ROE: return maxspeed_launch_swe(p, lay, q, out, s);
     case MC_ADVECTION: return maxspeed_launch_advection(p, lay, q, out, s);
     case MC_ACOUSTICS_VAR: return maxspeed_launch_acoustics_var(p, lay, q, out, s);
+    case MC_EULER_GODUNOV: return maxspeed_launch_euler_godunov(p, lay, q, out, s);
     default: return maxspeed_launch_euler(p, lay, q, out, s);
     }
 }

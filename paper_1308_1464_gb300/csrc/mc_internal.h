@@ -15,7 +15,8 @@ namespace mc {
 inline int solver_meqn(int solver)
 {
     switch (solver) {
-    case MC_EULER_ROE: return 4;
+    case MC_EULER_ROE:
+    case MC_EULER_GODUNOV: return 4;
     case MC_ADVECTION: return 1;
     case MC_ACOUSTICS_VAR: return 5;
     default: return 3;
@@ -48,11 +49,13 @@ cudaError_t sweep_launch_swe(const SweepLaunch& L);
 cudaError_t sweep_launch_euler(const SweepLaunch& L);
 cudaError_t sweep_launch_advection(const SweepLaunch& L);
 cudaError_t sweep_launch_acoustics_var(const SweepLaunch& L);
+cudaError_t sweep_launch_euler_godunov(const SweepLaunch& L);
 cudaError_t sweep_prepare_acoustics(int dtype);
 cudaError_t sweep_prepare_swe(int dtype);
 cudaError_t sweep_prepare_euler(int dtype);
 cudaError_t sweep_prepare_advection(int dtype);
 cudaError_t sweep_prepare_acoustics_var(int dtype);
+cudaError_t sweep_prepare_euler_godunov(int dtype);
 cudaError_t maxspeed_launch_acoustics(const mc_problem& p, const mc_layout& lay, const void* q,
                                       unsigned long long* out, cudaStream_t s);
 cudaError_t maxspeed_launch_swe(const mc_problem& p, const mc_layout& lay, const void* q,
@@ -62,6 +65,8 @@ cudaError_t maxspeed_launch_euler(const mc_problem& p, const mc_layout& lay, con
 cudaError_t maxspeed_launch_advection(const mc_problem& p, const mc_layout& lay, const void* q,
                                       unsigned long long* out, cudaStream_t s);
 cudaError_t maxspeed_launch_acoustics_var(const mc_problem& p, const mc_layout& lay, const void* q,
+                                          unsigned long long* out, cudaStream_t s);
+cudaError_t maxspeed_launch_euler_godunov(const mc_problem& p, const mc_layout& lay, const void* q,
                                           unsigned long long* out, cudaStream_t s);
 
 // ghost fill (mc_capi.cu)
@@ -104,16 +109,19 @@ cudaError_t batch_launch_swe(const BatchLaunch& L);
 cudaError_t batch_launch_euler(const BatchLaunch& L);
 cudaError_t batch_launch_advection(const BatchLaunch& L);
 cudaError_t batch_launch_acoustics_var(const BatchLaunch& L);
+cudaError_t batch_launch_euler_godunov(const BatchLaunch& L);
 cudaError_t batch_init_acoustics(const BatchLaunch& L);
 cudaError_t batch_init_swe(const BatchLaunch& L);
 cudaError_t batch_init_euler(const BatchLaunch& L);
 cudaError_t batch_init_advection(const BatchLaunch& L);
 cudaError_t batch_init_acoustics_var(const BatchLaunch& L);
+cudaError_t batch_init_euler_godunov(const BatchLaunch& L);
 // resident CTAs per SM of the batched kernel (also raises its smem limit)
 cudaError_t batch_occupancy_acoustics(int dtype, int* ctas);
 cudaError_t batch_occupancy_swe(int dtype, int* ctas);
 cudaError_t batch_occupancy_euler(int dtype, int* ctas);
 cudaError_t batch_occupancy_advection(int dtype, int* ctas);
 cudaError_t batch_occupancy_acoustics_var(int dtype, int* ctas);
+cudaError_t batch_occupancy_euler_godunov(int dtype, int* ctas);
 
 }  // namespace mc

@@ -148,6 +148,7 @@ extern "C" mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_ou
     case MC_SWE_ROE: e = sweep_launch_swe(L); break;
     case MC_ADVECTION: e = sweep_launch_advection(L); break;
     case MC_ACOUSTICS_VAR: e = sweep_launch_acoustics_var(L); break;
+    case MC_EULER_GODUNOV: e = sweep_launch_euler_godunov(L); break;
     default: e = sweep_launch_euler(L); break;
     }
     if (e != cudaSuccess) return cuda_error(e, "sweep launch");

@@ -45,6 +45,16 @@ __device__ __forceinline__ float sqrt_(float x)
     return r;
 }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+// x^y for x > 0: FP32 as 2^(y log2 x) with the hardware base-2 approximations
+// (relative error a few ulp for the moderate exponents used here), FP64 pow
+__device__ __forceinline__ float pow_(float x, float y)
+{
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y * l));
+    return r;
+}
+__device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
 
 // Packed FP32 pairs.  One iteration of the sweep solves an x-edge and a
 // y-edge with the same arithmetic; written in the edge-normal frame
@@ -819,6 +829,192 @@ struct EulerRP {
             bp[2] = p_fma(m1, l1, p_fma(me, u, p_mul(m4, l4)));
             bp[1] = p_fma(bp[0], v, ms);
             bp[3] = p_fma(m1, e1, p_fma(me, ke, p_fma(ms, v, p_mul(m4, e4))));
+        }
+    }
+};
+
+// ---------------------------------------------------------------- Euler, exact solution
+// Godunov normal solve: the exact Riemann solution of the normal problem
+// (Toro ch. 4; p* by Newton from Toro's adaptive PV/TR/TS guess) gives the
+// fluctuations as flux differences to the state at x/t = 0 (Toro §4.5), and
+// the waves as the jumps across the two nonlinear waves and the contact (the
+// tangential velocity jumps with the contact), at the shock speeds or the
+// rarefaction heads and u*.  The transverse split is Roe's at the edge's Roe
+// average (EulerRP::transverse).  No entropy fix is needed.
+template <typename T>
+struct EulerGodunovRP : EulerRP<T> {
+    using Base = EulerRP<T>;
+    using real = T;
+    using Base::NEQ;
+    using Base::NW;
+    using Base::gamma;
+    using Base::gm1;
+    static constexpr bool PAIRED = false;   // scalar solves only
+    static constexpr bool PAIR_LIMITER = false;
+    static constexpr bool CARRY_DOT = true;
+    struct Lin : Base::Lin { T smax; };
+    __device__ __forceinline__ T max_speed(const Lin& L) const { return L.smax; }
+
+    // one side's branch of the pressure function f_K(p) and f_K'(p)
+    __device__ __forceinline__ void fK(T p, T rK, T pK, T cK, T& f, T& fd) const
+    {
+        if (p > pK) {
+            const T A = T(2) / ((gamma + T(1)) * rK), B = gm1 / (gamma + T(1)) * pK;
+            const T q = sqrt_(A * rcp_(B + p));
+            f = (p - pK) * q;
+            fd = q * (T(1) - T(0.5) * (p - pK) * rcp_(B + p));
+        } else {
+            const T r = p * rcp_(pK);
+            const T pz = pow_(r, T(0.5) * gm1 / gamma);
+            f = T(2) * cK / gm1 * (pz - T(1));
+            fd = pz * rcp_(r * rK * cK);   // (p/p_K)^(-(gamma+1)/(2 gamma)) / (rho_K c_K)
+        }
+    }
+    __device__ __forceinline__ T star_density(T rK, T pK, T ps) const
+    {
+        const T r = ps * rcp_(pK);
+        if (ps > pK) {
+            const T g6 = gm1 / (gamma + T(1));
+            return rK * (r + g6) * rcp_(g6 * r + T(1));
+        }
+        return rK * pow_(r, T(1) / gamma);
+    }
+    __device__ __forceinline__ T shock_speed(T uK, T pK, T cK, T ps, T sgn) const
+    {
+        return uK + sgn * cK * sqrt_((gamma + T(1)) / (T(2) * gamma) * ps * rcp_(pK) + gm1 / (T(2) * gamma));
+    }
+    // normal flux of (rho, u_n, u_t, p) in the edge frame (0: mass, 1: normal
+    // momentum, 2: tangential momentum, 3: energy)
+    __device__ __forceinline__ void nflux(T rho, T un, T ut, T p, T* f) const
+    {
+        const T E = p / gm1 + T(0.5) * rho * (un * un + ut * ut);
+        f[0] = rho * un;
+        f[1] = rho * un * un + p;
+        f[2] = rho * un * ut;
+        f[3] = un * (E + p);
+    }
+    __device__ __forceinline__ void cons(T rho, T un, T ut, T p, T* q) const
+    {
+        q[0] = rho;
+        q[1] = rho * un;
+        q[2] = rho * ut;
+        q[3] = p / gm1 + T(0.5) * rho * (un * un + ut * ut);
+    }
+
+    template <int DIR>
+    __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
+                                           T* amdq, T* apdq, Lin& L, bool& bad) const
+    {
+        constexpr int un_ = 1 + DIR, ut_ = 2 - DIR;
+        // Roe average of the edge, for the transverse split and as a guard
+        const T rl = ql[0], rr = qr[0];
+        const T rsl = rsqrt_(rl), rsr = rsqrt_(rr);
+        const T il = rsl * rsl, ir = rsr * rsr;
+        const T ul = ql[un_] * il, vl = ql[ut_] * il, ur = qr[un_] * ir, vr = qr[ut_] * ir;
+        const T pl = gm1 * (ql[3] - T(0.5) * rl * (ul * ul + vl * vl));
+        const T pr = gm1 * (qr[3] - T(0.5) * rr * (ur * ur + vr * vr));
+        const T w = rcp_(rl * rsl + rr * rsr);
+        L.u = (ql[un_] * rsl + qr[un_] * rsr) * w;
+        L.v = (ql[ut_] * rsl + qr[ut_] * rsr) * w;
+        L.H = ((ql[3] + pl) * rsl + (qr[3] + pr) * rsr) * w;
+        const T c2 = gm1 * (L.H - T(0.5) * (L.u * L.u + L.v * L.v));
+        L.rc = rsqrt_(c2);
+        L.c = c2 * L.rc;
+        L.gc2 = gm1 * L.rc * L.rc;
+        const T cl = sqrt_(gamma * pl * il), cr = sqrt_(gamma * pr * ir);
+        const bool phys = rl > T(0) && rr > T(0) && pl > T(0) && pr > T(0) && c2 > T(0);
+        // vacuum is generated when 2 (c_L + c_R)/(gamma - 1) <= u_R - u_L
+        const bool vac = T(2) * (cl + cr) <= gm1 * (ur - ul);
+        bad = bad || !phys || vac;
+
+        // star pressure: Newton on f_L + f_R + u_R - u_L from the adaptive guess
+        const T du = ur - ul;
+        const T z = T(0.5) * gm1 / gamma;
+        const T pmin = fmin(pl, pr), pmax = fmax(pl, pr);
+        T ppv = T(0.5) * (pl + pr) - T(0.125) * du * (rl + rr) * (cl + cr);
+        ppv = fmax(ppv, pmin * T(1e-6));
+        T p0;
+        if (pmax < T(2) * pmin && ppv >= pmin && ppv <= pmax) {
+            p0 = ppv;
+        } else if (ppv < pmin) {
+            p0 = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), T(1) / z);
+        } else {
+            const T gl = sqrt_(T(2) / ((gamma + T(1)) * rl) * rcp_(gm1 / (gamma + T(1)) * pl + ppv));
+            const T gr = sqrt_(T(2) / ((gamma + T(1)) * rr) * rcp_(gm1 / (gamma + T(1)) * pr + ppv));
+            p0 = (gl * pl + gr * pr - du) * rcp_(gl + gr);
+        }
+        T ps = fmax(p0, pmin * T(1e-6));
+        const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
+        for (int it = 0; it < 40; it++) {
+            T fl, fdl, fr, fdr;
+            fK(ps, rl, pl, cl, fl, fdl);
+            fK(ps, rr, pr, cr, fr, fdr);
+            T pn = ps - (fl + fr + du) * rcp_(fdl + fdr);
+            pn = fmax(pn, pmin * T(1e-8));
+            const bool done = fabs(pn - ps) <= tol * pn;
+            ps = pn;
+            if (done || !(ps == ps)) break;
+        }
+        T fl, fdl, fr, fdr;
+        fK(ps, rl, pl, cl, fl, fdl);
+        fK(ps, rr, pr, cr, fr, fdr);
+        const T us = T(0.5) * (ul + ur) + T(0.5) * (fr - fl);
+
+        // waves and speeds, in the edge frame, then to the physical frame
+        T qL[4], qSL[4], qSR[4], qR[4];
+        cons(rl, ul, vl, pl, qL);
+        cons(star_density(rl, pl, ps), us, vl, ps, qSL);
+        cons(star_density(rr, pr, ps), us, vr, ps, qSR);
+        cons(rr, ur, vr, pr, qR);
+        const int fc[4] = {0, un_, ut_, 3};
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            W[0][fc[m]] = qSL[m] - qL[m];
+            W[1][fc[m]] = qSR[m] - qSL[m];
+            W[2][fc[m]] = qR[m] - qSR[m];
+        }
+        s[0] = ps > pl ? shock_speed(ul, pl, cl, ps, T(-1)) : ul - cl;
+        s[1] = us;
+        s[2] = ps > pr ? shock_speed(ur, pr, cr, ps, T(1)) : ur + cr;
+        L.smax = fmax(fmax(fabs(s[0]), fabs(s[2])), fabs(s[1]));
+
+        // the state at x/t = 0 (Toro §4.5): on the side of the contact that
+        // holds the interface, behind or ahead of that side's wave, or inside
+        // its fan at the sonic point
+        const bool left = us >= T(0);
+        const T rK = left ? rl : rr, pK = left ? pl : pr, uK = left ? ul : ur, cK = left ? cl : cr;
+        const T vK = left ? vl : vr, sgn = left ? T(-1) : T(1);
+        T r0, u0, p0s;
+        if (ps > pK) {
+            const T S = shock_speed(uK, pK, cK, ps, sgn);
+            const bool ahead = left ? S >= T(0) : S <= T(0);
+            r0 = ahead ? rK : star_density(rK, pK, ps);
+            u0 = ahead ? uK : us;
+            p0s = ahead ? pK : ps;
+        } else {
+            const T head = uK + sgn * cK;
+            const T cs = cK * pow_(ps * rcp_(pK), z);
+            const T tail = us + sgn * cs;
+            if (left ? head >= T(0) : head <= T(0)) {
+                r0 = rK; u0 = uK; p0s = pK;
+            } else if (left ? tail <= T(0) : tail >= T(0)) {
+                r0 = star_density(rK, pK, ps); u0 = us; p0s = ps;
+            } else {
+                const T c = T(2) / (gamma + T(1)) * (cK - sgn * T(0.5) * gm1 * uK);
+                const T rc_ = c * rcp_(cK);
+                u0 = -sgn * c;
+                r0 = rK * pow_(rc_, T(2) / gm1);
+                p0s = pK * pow_(rc_, T(2) * gamma / gm1);
+            }
+        }
+        T f0[4], fL[4], fR[4];
+        nflux(r0, u0, vK, p0s, f0);
+        nflux(rl, ul, vl, pl, fL);
+        nflux(rr, ur, vr, pr, fR);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            amdq[fc[m]] = f0[m] - fL[m];
+            apdq[fc[m]] = fR[m] - f0[m];
         }
     }
 };

@@ -12,7 +12,8 @@ SOLVER_IDS = {"acoustics": (mc.ACOUSTICS, oracle.ACOUSTICS, (1.0, 4.0, 0, 0)),
               "swe": (mc.SWE_ROE, oracle.SWE, (G, 0, 0, 0)),
               "euler": (mc.EULER_ROE, oracle.EULER, (GAMMA, 0, 0, 0)),
               "advection": (mc.ADVECTION, oracle.ADVECTION, (1.0, -0.6, 0, 0)),
-              "acoustics_var": (mc.ACOUSTICS_VAR, oracle.ACOUSTICS_VAR, (0, 0, 0, 0))}
+              "acoustics_var": (mc.ACOUSTICS_VAR, oracle.ACOUSTICS_VAR, (0, 0, 0, 0)),
+              "euler_godunov": (mc.EULER_GODUNOV, oracle.EULER_GODUNOV, (GAMMA, 0, 0, 0))}
 TOL = {mc.F64: 1e-12, mc.F32: 2e-5}
 
 

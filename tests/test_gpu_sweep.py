@@ -80,6 +80,11 @@ CASES = [
     ("acoustics_var", mc.F32, (W, X, P, P), 3, 2),
     ("acoustics_var", mc.F64, (X, X, W, W), 1, 0),
     ("acoustics_var", mc.F32, (W, W, W, W), 2, 1),
+    # Euler with the exact-solution normal solve
+    ("euler_godunov", mc.F32, (X, X, X, X), 4, 1),
+    ("euler_godunov", mc.F64, (W, W, P, P), 3, 2),
+    ("euler_godunov", mc.F32, (P, P, X, X), 1, 0),
+    ("euler_godunov", mc.F64, (X, X, X, X), 4, 1),
 ]
 
 
@@ -112,7 +117,8 @@ def test_first_order_and_no_limiter():
                                                    ("acoustics", mc.F64, (P, P, W, W), 1),
                                                    ("swe", mc.F32, (W, X, X, W), 2),
                                                    ("advection", mc.F64, (P, P, X, W), 2),
-                                                   ("acoustics_var", mc.F32, (X, W, P, P), 2)])
+                                                   ("acoustics_var", mc.F32, (X, W, P, P), 2),
+                                                   ("euler_godunov", mc.F32, (W, X, X, W), 1)])
 def test_tiny_and_odd_grids(mx, my, solver, dtype, bc, trans):
     q, _, _ = initial_state(solver, max(mx, 4), max(my, 4), seed=mx * 100 + my)
     q = np.ascontiguousarray(q[:, :my, :mx])
@@ -141,6 +147,7 @@ FULL = [
     ("advection", mc.F32, 4096, 4096, (P, P, P, P), {}),
     ("acoustics_var", mc.F32, 4096, 4096, (X, X, X, X), {}),
     ("swe", mc.F32, 4096, 4096, (W, W, W, W), dict(limiter=3, transverse=2)),
+    ("euler_godunov", mc.F32, 4096, 4096, (X, X, X, X), {}),
 ]
 
 
@@ -155,7 +162,7 @@ def test_full_size_windows(solver, dtype, mx, my, bc, opts):
         g = workloads.advection_pulse(mx, my)
     elif solver == "acoustics_var":
         g = workloads.acoustics_layered(mx, my)
-    else:
+    else:   # Euler, either normal solve
         g = workloads.euler_quadrants(mx, my)
     p, op = problems(solver, mx, my, g.dx, g.dy, dtype, bc, **opts)
     if solver == "advection":
@@ -234,3 +241,16 @@ def test_entropy_fix_transonic(solver, dtype, axis):
     dt = 0.9 / oracle.max_cell_speed(op0, oracle.bc_fill(op0, qo))
     unfixed, _, _ = oracle.step(op0, qo, dt)
     assert scaled_error(solver, unfixed[:, 2:-2, 2:-2], want) > 50 * TOL[mc.F32]
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("dtype", [mc.F32, mc.F64])
+def test_godunov_transonic(dtype, axis):
+    """The exact-solution normal solve at a transonic rarefaction (no entropy
+    fix involved), along x and along y."""
+    mx, my = 40, 36
+    q = _transonic_state("euler", mx, my, axis, seed=21 + axis)
+    p, op = problems("euler_godunov", mx, my, 0.01, 0.01, dtype, (X, X, X, X))
+    got, want, smax, smax_ref, *_ = run_step(p, op, q)
+    assert scaled_error("euler_godunov", got, want) <= TOL[dtype]
+    assert smax == pytest.approx(smax_ref, rel=1e-12 if dtype == mc.F64 else 1e-5)
