@@ -49,6 +49,9 @@ WORKLOADS = {
     "acvar32": dict(solver="acoustics_var", dtype="f32", n=4096, cfl=0.9, bc="extrap",
                     desc="variable-coefficient acoustics, layered medium 4096x4096 fp32, "
                          "extrapolation, MC, CFL 0.9"),
+    "eulg32": dict(solver="euler_godunov", dtype="f32", n=4096, cfl=0.8, bc="extrap",
+                   desc="Euler with the exact-solution (Godunov) normal solve, four-quadrant "
+                        "4096x4096 fp32, extrapolation, MC, CFL 0.8"),
     "swe32t2": dict(solver="swe", dtype="f32", n=4096, cfl=0.9, bc="wall", limiter=3, transverse=2,
                     desc="shallow-water Roe+HH dam break 4096x4096 fp32, walls, van Leer, "
                          "transverse option 2, CFL 0.9"),
@@ -86,9 +89,10 @@ def make_problem(mc, wl):
     if wl["solver"] == "swe":
         g = workloads.swe_dambreak(n, n)
         sid, param, bc = mc.SWE_ROE, (G, 0, 0, 0), mc.BC_WALL
-    elif wl["solver"] == "euler":
+    elif wl["solver"] in ("euler", "euler_godunov"):
         g = workloads.euler_quadrants(n, n)
-        sid, param, bc = mc.EULER_ROE, (GAMMA, 0, 0, 0), mc.BC_EXTRAP
+        sid = mc.EULER_ROE if wl["solver"] == "euler" else mc.EULER_GODUNOV
+        param, bc = (GAMMA, 0, 0, 0), mc.BC_EXTRAP
     elif wl["solver"] == "advection":
         g = workloads.advection_pulse(n, n)
         sid, param, bc = mc.ADVECTION, (1.0, 0.6, 0, 0), mc.BC_PERIODIC
@@ -206,9 +210,10 @@ def oracle_problem(wl, n):
         g = workloads.swe_dambreak(n, n)
         op = oracle.Problem(oracle.SWE, n, n, g.dx, g.dy, bc=(oracle.BC_WALL,) * 4,
                             param=(G, 0, 0, 0), **opts)
-    elif wl["solver"] == "euler":
+    elif wl["solver"] in ("euler", "euler_godunov"):
         g = workloads.euler_quadrants(n, n)
-        op = oracle.Problem(oracle.EULER, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
+        sid = oracle.EULER if wl["solver"] == "euler" else oracle.EULER_GODUNOV
+        op = oracle.Problem(sid, n, n, g.dx, g.dy, bc=(oracle.BC_EXTRAP,) * 4,
                             param=(GAMMA, 0, 0, 0), **opts)
     elif wl["solver"] == "advection":
         g = workloads.advection_pulse(n, n)
@@ -379,28 +384,9 @@ def bench_exact(args, rank, world):
                          it.data_ptr(), fl.data_ptr(), mode, net, tol, 30, stats.data_ptr())
         return ps, it, fl, stats
 
-    ntrain = 1 << 22
-    train = dev_states(ntrain, offset=1 << 26)
-    p_star, _, _, _ = solve(train, mc.SEED_ADAPTIVE, None, tol=1e-12)
-    feat = torch.empty((ntrain, 10), dtype=torch.float32, device="cuda")
-    tgt = torch.empty(ntrain, dtype=torch.float32, device="cuda")
-    mc.mlp_features(ntrain, GAM, [s.data_ptr() for s in train], p_star.data_ptr(),
-                    feat.data_ptr(), tgt.data_ptr())
-    net = mc.SeedNet()
-    rng = np.random.default_rng(0)
-    params = np.zeros(mc.MLP_NPARAM, dtype=np.float32)
-    params[0:1024] = (rng.normal(size=(16, 64)) * 0.2 * (np.arange(16) < 10)[:, None]).ravel()
-    params[1088:5184] = rng.normal(size=4096) * 0.1
-    params[5248:5312] = rng.normal(size=64) * 0.1
-    params[mc.MLP_NWEIGHT + 10:] = 1.0
-    net.set_params(params.ctypes.data)
-    epochs = 12
-    losses = np.zeros(epochs, dtype=np.float32)
-    t0 = time.perf_counter()
-    net.train(ntrain, feat.data_ptr(), tgt.data_ptr(), batch=16384, epochs=epochs, lr=2e-3,
-              seed=3, loss_out=losses.ctypes.data)
-    train_s = time.perf_counter() - t0
-    del feat, tgt, train, p_star
+    from paper_1308_1464_gb300.seednet import train_seed_net
+    ntrain, epochs = 1 << 22, 12
+    net, losses, train_s = train_seed_net(ntrain=ntrain, epochs=epochs, gamma=GAM)
 
     n = 1 << 24
     test = dev_states(n, offset=0)
@@ -584,6 +570,31 @@ def main():
                "steps_per_call": nsteps_e2e,
                "note": "mc_advance_host: dense host state in, 100 steps, dense host state out"}
 
+    # the exact-solution solver: the same timed steps with the learned
+    # pressure seed, and Newton updates per normal solve with either seed
+    seeds = None
+    if wl["solver"] == "euler_godunov":
+        from paper_1308_1464_gb300.seednet import train_seed_net
+        net, losses, train_s = train_seed_net(ntrain=1 << 22, epochs=12, gamma=GAMMA)
+        seeds = {"train_rows": 1 << 22, "train_epochs": 12, "train_s": round(train_s, 2)}
+        for name, nn in (("plain", None), ("learned", net)):
+            ctx.set_seed_net(nn)
+            a.upload(q0)
+            t1, d1, i1, _ = ctx.advance(a.ptr, b.ptr, args.warmup, wl["cfl"], 1.0, 0.0, dt0, sh)
+            x, y = (b, a) if i1 else (a, b)
+            ctx.newton_stats(reset=True, stream=sh)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.advance(x.ptr, y.ptr, args.steps, wl["cfl"], 1.0, t1, d1, sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sms = e0.elapsed_time(e1)
+            upd, nsolve = ctx.newton_stats(reset=True, stream=sh)
+            seeds[name] = {"value": n_cells * args.steps / (sms * 1e-3), "ms_per_step": sms / args.steps,
+                           "newton_updates_per_solve": upd / max(nsolve, 1)}
+        ctx.set_seed_net(None)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
@@ -602,6 +613,8 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * (args.steps + nrej), "clocks": clocks,
         }
+        if seeds is not None:
+            line["pressure_seed"] = seeds
         print(json.dumps(line))
     ctx.close()
     if world > 1:

@@ -136,6 +136,23 @@ mc_status mc_destroy(mc_ctx* ctx);
  * default.  Used by the autotuner; results do not depend on it. */
 mc_status mc_set_tile_rows(mc_ctx* ctx, int rows);
 
+/* Pressure seeds for the exact-solution Euler solver (MC_EULER_GODUNOV): with
+ * a trained seed network attached (see mc_mlp_* below), a normal solve of the
+ * fused step whose jump is too strong for Toro's PV guess (the adaptive rule
+ * would leave PV) starts Newton from the network's proposal p_TR exp(net(x)),
+ * evaluated per warp on the tensor cores when any lane of the warp needs it;
+ * it restarts from Toro's adaptive guess when the proposal is implausible or
+ * does not converge (the Riemann kernel stays pointwise, as the paper keeps
+ * it, §2; only its starting guess changes).  net = NULL detaches.  The network is
+ * borrowed: it must outlive every step that uses it.  Changing it drops the
+ * context's captured step graphs.  MC_ENOTSUP for other solvers. */
+typedef struct mc_mlp mc_mlp;
+mc_status mc_set_seed_net(mc_ctx* ctx, const mc_mlp* net);
+/* Newton updates and normal solves the exact-solution solver counted in this
+ * context's fused steps since the last reset (synchronises the stream;
+ * reset != 0 zeroes the counters afterwards). */
+mc_status mc_newton_stats(mc_ctx* ctx, int64_t* updates, int64_t* solves, int32_t reset, void* stream);
+
 /* Host <-> device copies between a dense interior array (meqn x my x mx,
  * x fastest, the problem's dtype) and a device state in the library layout.
  * Asynchronous on stream. */
@@ -290,7 +307,7 @@ enum { MC_RS_OK = 0, MC_RS_VACUUM = 1, MC_RS_NOCONV = 2, MC_RS_FALLBACK = 4 };
  * ln p_TR, ln max(p_PV, 1e-6); the output is ln p* - ln p_TR. */
 #define MC_MLP_NWEIGHT (16 * 64 + 64 + 64 * 64 + 64 + 64 + 1)
 #define MC_MLP_NPARAM (MC_MLP_NWEIGHT + 20)
-typedef struct mc_mlp mc_mlp;
+/* (mc_mlp is declared above, with mc_set_seed_net) */
 
 /* Allocates the network's device storage (zero weights) on the current device. */
 mc_status mc_mlp_create(mc_mlp** out);

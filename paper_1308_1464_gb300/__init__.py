@@ -86,6 +86,9 @@ def lib():
         L.mc_create.argtypes = [P, ctypes.POINTER(_VP)]
         L.mc_destroy.argtypes = [_VP]
         L.mc_set_tile_rows.argtypes = [_VP, ctypes.c_int]
+        L.mc_set_seed_net.argtypes = [_VP, _VP]
+        L.mc_newton_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.c_int32, _VP]
         L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_download.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
@@ -168,6 +171,17 @@ class Context:
 
     def set_tile_rows(self, rows: int) -> None:
         check(lib().mc_set_tile_rows(self._h, int(rows)))
+
+    def set_seed_net(self, net) -> None:
+        """Attach a SeedNet (or None) to the exact-solution Euler solver."""
+        self._seed_net = net   # keep it alive while attached
+        check(lib().mc_set_seed_net(self._h, net.handle if net is not None else None))
+
+    def newton_stats(self, reset: bool = True, stream: int = 0):
+        """(Newton updates, normal solves) counted since the last reset."""
+        u, n = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().mc_newton_stats(self._h, ctypes.byref(u), ctypes.byref(n), int(reset), _VP(stream)))
+        return u.value, n.value
 
     def upload(self, host_dense_ptr: int, q_dev: int, stream: int = 0) -> None:
         check(lib().mc_upload(self._h, _VP(host_dense_ptr), _VP(q_dev), _VP(stream)))

@@ -224,7 +224,15 @@ struct mc_ctx {
     std::vector<MapEntry> maps;
     std::vector<GraphEntry> graphs;
     int next_slot;
+    const mc_mlp* seed_net = nullptr;   // pressure seeds of the exact-solution solver, or none
 };
+
+// the context's extras for every fused-step launch
+static void launch_extras(const mc_ctx* c, SweepLaunch& L)
+{
+    L.seed_net = c->seed_net ? c->seed_net->dev : nullptr;
+    L.newton = c->dev->newton;
+}
 
 static void drop_graphs(mc_ctx* c)
 {
@@ -377,6 +385,30 @@ mc_status mc_set_tile_rows(mc_ctx* c, int rows)
     return MC_OK;
 }
 
+mc_status mc_set_seed_net(mc_ctx* c, const mc_mlp* net)
+{
+    if (!c) return set_error(MC_EINVAL, "context is NULL");
+    if (net && c->p.solver != MC_EULER_GODUNOV)
+        return set_error(MC_ENOTSUP, "pressure seeds apply to the exact-solution Euler solver only");
+    if (net != c->seed_net) drop_graphs(c);   // captured launches hold the old pointer
+    c->seed_net = net;
+    return MC_OK;
+}
+
+mc_status mc_newton_stats(mc_ctx* c, int64_t* updates, int64_t* solves, int32_t reset, void* stream)
+{
+    if (!c || !updates || !solves) return set_error(MC_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, c->dev->newton, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(c->dev->newton, 0, sizeof(h), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "Newton counters");
+    *updates = (int64_t)h[0];
+    *solves = (int64_t)h[1];
+    return MC_OK;
+}
+
 static mc_status copy_dense(mc_ctx* c, const void* src, void* dst, bool upload, cudaStream_t s)
 {
     const long long es = c->lay.elem_bytes;
@@ -446,6 +478,7 @@ mc_status mc_step(mc_ctx* c, void* q_in, void* q_out, double dt, double* smax_ou
     if (e != cudaSuccess) return cuda_error(e, "step set-up");
     SweepLaunch L{c->p, c->lay, map, map, q_in, q_out, nullptr, nullptr, dt,
                   &c->dev->smax_bits, &c->dev->status, c->tile_rows, 0, s};
+    launch_extras(c, L);
     e = sweep_launch(L);
     if (e != cudaSuccess) return cuda_error(e, "sweep launch");
     if (smax_out) {
@@ -473,6 +506,7 @@ mc_status mc_sweep(mc_ctx* c, const void* q_in, void* q_out, double dt, void* st
     SweepLaunch L{c->p, c->lay, map, map, const_cast<void*>(q_in), q_out, nullptr, nullptr, dt,
                   &c->dev->smax_bits, &c->dev->status, c->tile_rows, 0,
                   static_cast<cudaStream_t>(stream)};
+    launch_extras(c, L);
     cudaError_t e = sweep_launch(L);
     return e == cudaSuccess ? MC_OK : cuda_error(e, "sweep launch");
 }
@@ -500,6 +534,7 @@ static cudaError_t enqueue_attempts(mc_ctx* c, const CUtensorMap* ma, const CUte
 {
     SweepLaunch L{c->p, c->lay, ma, mb, qa, qb, &c->dev->cur, &c->dev->dt, 0.0,
                   &c->dev->smax_bits, &c->dev->status, c->tile_rows, 0, s};
+    launch_extras(c, L);
     for (int k = 0; k < attempts; k++) {
         cudaError_t e = bc_launch(c->p, c->lay, qa, qb, &c->dev->cur, s);
         if (e == cudaSuccess) e = sweep_launch(L);

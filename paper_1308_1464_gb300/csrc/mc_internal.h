@@ -41,6 +41,8 @@ struct SweepLaunch {
     int tile_rows;
     int max_blocks;            // 0: one warp per task
     cudaStream_t stream;
+    const void* seed_net = nullptr;            // MlpDev of a pressure-seed network (SEEDED solvers)
+    unsigned long long* newton = nullptr;      // Newton update / solve counters, or null
 };
 
 // per-solver launchers (mc_sweep_<solver>.cu), dispatching on dtype

@@ -104,6 +104,7 @@ struct AcousticsRP {
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
     static constexpr bool PAIR_LIMITER = false;
+    static constexpr bool SEEDED = false;   // no external pressure seed
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
     // max over the edge's waves of |s| (the speeds are -c, +c)
@@ -168,6 +169,7 @@ struct AcousticsVarRP {
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
     static constexpr bool PAIR_LIMITER = false;
+    static constexpr bool SEEDED = false;   // no external pressure seed
     bool efix;  // unused: linear
     struct Lin { T cl, cr; };
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fmax(L.cl, L.cr); }
@@ -225,6 +227,7 @@ struct AdvectionRP {
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
     static constexpr bool PAIR_LIMITER = false;
+    static constexpr bool SEEDED = false;   // no external pressure seed
     T u, v;
     bool efix;  // unused: linear
     struct Lin { T s; };
@@ -366,6 +369,7 @@ struct SweRP {
     // same arithmetic as normal<0> / transverse<0>, two edges per instruction
     static constexpr bool PAIRED = sizeof(T) == 4;
     static constexpr bool PAIR_LIMITER = false;
+    static constexpr bool SEEDED = false;   // no external pressure seed
     struct LinP { f2 u, v, c, r2c; };
     // the scalar linearised state of half h (x-edge 0, y-edge 1)
     __device__ __forceinline__ Lin lin_half(const LinP& P, int h) const
@@ -516,6 +520,7 @@ struct EulerRP {
     static constexpr bool CARRY_DOT = true;
     static constexpr bool PAIRED = sizeof(T) == 4;
     static constexpr bool PAIR_LIMITER = true;
+    static constexpr bool SEEDED = false;   // no external pressure seed
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
@@ -851,8 +856,52 @@ struct EulerGodunovRP : EulerRP<T> {
     using Base::gm1;
     static constexpr bool PAIRED = false;   // scalar solves only
     static constexpr bool PAIR_LIMITER = false;
+    // accepts a pressure seed for Newton (normal_seeded), e.g. the learned one
+    static constexpr bool SEEDED = true;
     static constexpr bool CARRY_DOT = true;
     struct Lin : Base::Lin { T smax; };
+
+    // primitive (rho, u_n, u_t, p) and sound speed of a state on an edge of
+    // normal DIR
+    template <int DIR>
+    __device__ __forceinline__ void prim(const T* q, T& r, T& un, T& ut, T& p, T& c) const
+    {
+        r = q[0];
+        const T ir = rcp_(r);
+        un = q[1 + DIR] * ir;
+        ut = q[2 - DIR] * ir;
+        p = gm1 * (q[3] - T(0.5) * r * (un * un + ut * ut));
+        c = sqrt_(gamma * p * ir);
+    }
+    // the seed network's ten raw inputs of the edge's normal problem (ln rho,
+    // ln p, ln c of both sides, du, du/(c_L + c_R), ln p_TR, ln max(p_PV,
+    // 1e-6)) and the two-rarefaction guess p_TR its output multiplies
+    // pv_ok: Toro's adaptive rule would keep the PV guess (p_max < 2 p_min and
+    // p_PV within [p_min, p_max]), i.e. the edge's jump is mild
+    template <int DIR>
+    __device__ __forceinline__ void seed_features(const T* ql, const T* qr, float (&x)[10], float& ptr,
+                                                  bool& pv_ok) const
+    {
+        T rl, ul, vl, pl, cl, rr, ur, vr, pr, cr;
+        prim<DIR>(ql, rl, ul, vl, pl, cl);
+        prim<DIR>(qr, rr, ur, vr, pr, cr);
+        const T du = ur - ul, z = T(0.5) * gm1 / gamma;
+        const T pv = T(0.5) * (pl + pr) - T(0.125) * du * (rl + rr) * (cl + cr);
+        const T pmin = fmin(pl, pr), pmax = fmax(pl, pr);
+        pv_ok = pmax < T(2) * pmin && pv >= pmin && pv <= pmax;
+        const T tr = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), T(1) / z);
+        x[0] = __logf(float(rl));
+        x[1] = __logf(float(rr));
+        x[2] = __logf(float(pl));
+        x[3] = __logf(float(pr));
+        x[4] = __logf(float(cl));
+        x[5] = __logf(float(cr));
+        x[6] = float(du);
+        x[7] = float(du / (cl + cr));
+        x[8] = __logf(float(tr));
+        x[9] = __logf(fmaxf(float(pv), 1e-6f));
+        ptr = float(tr);
+    }
     __device__ __forceinline__ T max_speed(const Lin& L) const { return L.smax; }
 
     // one side's branch of the pressure function f_K(p) and f_K'(p)
@@ -905,6 +954,17 @@ struct EulerGodunovRP : EulerRP<T> {
     __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
                                            T* amdq, T* apdq, Lin& L, bool& bad) const
     {
+        (void)normal_seeded<DIR>(ql, qr, T(0), W, s, amdq, apdq, L, bad);
+    }
+
+    // The normal solve with Newton started from pseed when it is a plausible
+    // pressure (finite, within [1e-6 p_min, 1e6 p_max]), else from Toro's
+    // adaptive guess; a seeded run that does not converge restarts from that
+    // guess.  Returns the number of Newton updates.
+    template <int DIR>
+    __device__ __forceinline__ int normal_seeded(const T* ql, const T* qr, T pseed, T (&W)[NW][NEQ],
+                                                 T (&s)[NW], T* amdq, T* apdq, Lin& L, bool& bad) const
+    {
         constexpr int un_ = 1 + DIR, ut_ = 2 - DIR;
         // Roe average of the edge, for the transverse split and as a guard
         const T rl = ql[0], rr = qr[0];
@@ -943,17 +1003,25 @@ struct EulerGodunovRP : EulerRP<T> {
             const T gr = sqrt_(T(2) / ((gamma + T(1)) * rr) * rcp_(gm1 / (gamma + T(1)) * pr + ppv));
             p0 = (gl * pl + gr * pr - du) * rcp_(gl + gr);
         }
-        T ps = fmax(p0, pmin * T(1e-6));
         const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
-        for (int it = 0; it < 40; it++) {
-            T fl, fdl, fr, fdr;
-            fK(ps, rl, pl, cl, fl, fdl);
-            fK(ps, rr, pr, cr, fr, fdr);
-            T pn = ps - (fl + fr + du) * rcp_(fdl + fdr);
-            pn = fmax(pn, pmin * T(1e-8));
-            const bool done = fabs(pn - ps) <= tol * pn;
-            ps = pn;
-            if (done || !(ps == ps)) break;
+        const bool seeded = pseed >= T(1e-6) * pmin && pseed <= T(1e6) * pmax;   // false for NaN
+        T ps = seeded ? pseed : fmax(p0, pmin * T(1e-6));
+        int updates = 0;
+        for (int pass = seeded ? 0 : 1; pass < 2; pass++) {
+            bool conv = false;
+            for (int it = 0; it < 40; it++) {
+                T fl, fdl, fr, fdr;
+                fK(ps, rl, pl, cl, fl, fdl);
+                fK(ps, rr, pr, cr, fr, fdr);
+                T pn = ps - (fl + fr + du) * rcp_(fdl + fdr);
+                pn = fmax(pn, pmin * T(1e-8));
+                updates++;
+                conv = fabs(pn - ps) <= tol * pn;
+                ps = pn;
+                if (conv || !(ps == ps)) break;
+            }
+            if (conv) break;
+            if (pass == 0) ps = fmax(p0, pmin * T(1e-6));   // the seeded run failed: restart from the guess
         }
         T fl, fdl, fr, fdr;
         fK(ps, rl, pl, cl, fl, fdl);
@@ -1016,6 +1084,7 @@ struct EulerGodunovRP : EulerRP<T> {
             amdq[fc[m]] = f0[m] - fL[m];
             apdq[fc[m]] = fR[m] - f0[m];
         }
+        return updates;
     }
 };
 

@@ -42,6 +42,7 @@
 
 #include "mc_device.cuh"
 #include "mc_riemann.cuh"
+#include "mc_seednet.cuh"
 #include "mc_tile.h"
 
 namespace mc {
@@ -62,6 +63,8 @@ struct SweepArgs {
     int nbands, ntasks, tile_rows;
     unsigned long long* smax_bits;
     int* status;
+    const MlpDev* net;                    // pressure-seed network, or null (solvers with SEEDED)
+    unsigned long long* newton_updates;   // [0] Newton updates, [1] normal solves, or null
 };
 
 // phi(theta) with theta = dl / dr, branch-free (LeVeque 2002, eq. 6.39):
@@ -105,11 +108,17 @@ __device__ __forceinline__ f2 limiter_phi_pair(int lim, f2 dl, f2 dr)
     return phi;
 }
 
-// Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage.
+// Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage;
+// with a seed network also the CTA's shared copy of it and the warp's scratch
+// tiles for its inference, and the Newton counters.
 struct WarpRing {
     uint64_t* bars;
     unsigned char* ring;
     uint32_t phase;   // per-stage completion parity
+    const MlpShared* net = nullptr;
+    __nv_bfloat16* xs = nullptr;
+    float* outs = nullptr;
+    unsigned long long* newton = nullptr;
 };
 
 // One warp task: the rows [j0, jend) of the band of columns starting at i0
@@ -267,6 +276,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         else rp.template transverse<0>(L, a, bm, bp);
     };
 
+    int newton_n = 0, newton_s = 0;   // Newton updates and solves of this lane (SEEDED solvers)
     for (int k = j0 - 3; k < jend; k++) {
         T qc2[NP], ql2[NP];
         // material of cell (c-1, k), the neighbour below where A-dQ of x-edge
@@ -368,7 +378,34 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         } else {
             typename RP::Lin Ly;
             bool bady = false;
-            rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
+            // pressure seeds of the two normal problems from the network, for
+            // edges whose jump is too strong for the PV guess (Toro's rule);
+            // the whole warp evaluates it (x-edges, then y-edges), and only
+            // when one of its lanes has such an edge
+            T seed_x = T(0), seed_y = T(0);
+            if constexpr (RP::SEEDED) {
+                if (W.net) {
+                    float fx[10], fy[10], trx, try_;
+                    bool okx, oky;
+                    rp.template seed_features<0>(ql1, qc1, fx, trx, okx);
+                    rp.template seed_features<1>(qc1, qc2, fy, try_, oky);
+                    if (__any_sync(0xffffffffu, !(okx && oky))) {
+#pragma unroll
+                        for (int m = 0; m < 10; m++) {
+                            fx[m] = (fx[m] - W.net->mu[m]) / W.net->sig[m];
+                            fy[m] = (fy[m] - W.net->mu[m]) / W.net->sig[m];
+                        }
+                        const float ox = mlp_infer_warp(*W.net, fx, W.xs, W.outs);
+                        const float oy = mlp_infer_warp(*W.net, fy, W.xs, W.outs);
+                        if (!okx) seed_x = T(trx * __expf(ox));
+                        if (!oky) seed_y = T(try_ * __expf(oy));
+                    }
+                }
+                newton_n += rp.template normal_seeded<1>(qc1, qc2, seed_y, Wy2, sy2, bm2, bp2, Ly, bady);
+                newton_s += 1;
+            } else {
+                rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
+            }
             if (trans2) {
                 Ly_cur = Ly;
             } else if (trans) {
@@ -384,7 +421,12 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             if (k >= j0 - 2) {
                 typename RP::Lin Lx;
                 bool badx = false;
-                rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+                if constexpr (RP::SEEDED) {
+                    newton_n += rp.template normal_seeded<0>(ql1, qc1, seed_x, Wx, sxw, amdq1, apdq1, Lx, badx);
+                    newton_s += 1;
+                } else {
+                    rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
+                }
                 if (trans2) {
                     Lx_cur = Lx;
                 } else if (trans) {
@@ -584,6 +626,19 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             }
         }
     }
+    if constexpr (RP::SEEDED) {
+        if (W.newton) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                newton_n += __shfl_xor_sync(0xffffffffu, newton_n, o);
+                newton_s += __shfl_xor_sync(0xffffffffu, newton_s, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&W.newton[0], (unsigned long long)newton_n);
+                atomicAdd(&W.newton[1], (unsigned long long)newton_s);
+            }
+        }
+    }
     __syncwarp();
     return true;
 }
@@ -620,6 +675,19 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
+    if constexpr (RP::SEEDED) {
+        // the seed network after the rings: weights, then per-warp scratch
+        W.newton = a.newton_updates;
+        if (a.net) {
+            unsigned char* base = smem + sweep_smem_bytes(sizeof(T), RP::NPLANE);
+            MlpShared* ns = reinterpret_cast<MlpShared*>(base);
+            mlp_load_shared(a.net, ns);
+            W.net = ns;
+            W.xs = reinterpret_cast<__nv_bfloat16*>(base + sizeof(MlpShared)) + warp * 32 * XP;
+            W.outs = reinterpret_cast<float*>(base + sizeof(MlpShared) + SWEEP_WARPS * 32 * XP * 2) + warp * 32;
+            __syncthreads();
+        }
+    }
 
     const int cur = a.cur ? *a.cur : 0;
     const CUtensorMap* map = cur ? map_b : map_a;
@@ -726,6 +794,7 @@ struct DevState {
     unsigned long long smax_bits;
     double dt, t, cfl_last, cfl_maxseen;
     int cur, nacc, nrej, status;
+    unsigned long long newton[2];   // Newton updates and normal solves (exact-solution solver)
 };
 
 // ------------------------------------------------------------------ cell speeds

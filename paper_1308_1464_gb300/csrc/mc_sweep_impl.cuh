@@ -8,6 +8,13 @@
 
 namespace mc {
 
+// dynamic shared memory the seed network adds to the fused step: its shared
+// copy, then per warp the [32][XP] BF16 input tile and 32 output floats
+inline int seednet_smem_bytes()
+{
+    return int(sizeof(MlpShared)) + SWEEP_WARPS * 32 * XP * 2 + SWEEP_WARPS * 32 * 4;
+}
+
 // the scheme the FAST kernels compile in: MC limiter, second order, transverse
 inline bool is_fast_scheme(const mc_problem& p)
 {
@@ -39,8 +46,10 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.ntasks = ntasks_for(L.prob, L.tile_rows, &a.nbands);
     a.smax_bits = L.smax_bits;
     a.status = L.status;
+    a.net = RP::SEEDED ? static_cast<const MlpDev*>(L.seed_net) : nullptr;
+    a.newton_updates = RP::SEEDED ? L.newton : nullptr;
 
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
+    const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (a.net ? seednet_smem_bytes() : 0);
     int blocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
     if (is_fast_scheme(L.prob))
@@ -56,7 +65,7 @@ template <class RP>
 cudaError_t sweep_prepare_t()
 {
     using T = typename RP::real;
-    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
+    const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (RP::SEEDED ? seednet_smem_bytes() : 0);
     cudaError_t e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
