@@ -860,6 +860,23 @@ struct EulerGodunovRP : EulerRP<T> {
     static constexpr bool SEEDED = true;
     static constexpr bool CARRY_DOT = true;
     struct Lin : Base::Lin { T smax; };
+    // gamma's constants, set once on the host (no divisions in the solve):
+    // z = (g-1)/(2g), g6 = (g-1)/(g+1), a2 = 2/(g+1), sk = (g+1)/(2g),
+    // ig = 1/g, igm1 = 1/(g-1), tgm1 = 2/(g-1), rz = 1/z
+    T z, g6, a2, sk, ig, igm1, tgm1, rz;
+    __host__ void setup(const double* param, int ef)
+    {
+        Base::setup(param, ef);
+        const double g = param[0];
+        z = T(0.5 * (g - 1.0) / g);
+        g6 = T((g - 1.0) / (g + 1.0));
+        a2 = T(2.0 / (g + 1.0));
+        sk = T((g + 1.0) / (2.0 * g));
+        ig = T(1.0 / g);
+        igm1 = T(1.0 / (g - 1.0));
+        tgm1 = T(2.0 / (g - 1.0));
+        rz = T(2.0 * g / (g - 1.0));
+    }
 
     // primitive (rho, u_n, u_t, p) and sound speed of a state on an edge of
     // normal DIR
@@ -885,11 +902,11 @@ struct EulerGodunovRP : EulerRP<T> {
         T rl, ul, vl, pl, cl, rr, ur, vr, pr, cr;
         prim<DIR>(ql, rl, ul, vl, pl, cl);
         prim<DIR>(qr, rr, ur, vr, pr, cr);
-        const T du = ur - ul, z = T(0.5) * gm1 / gamma;
+        const T du = ur - ul;
         const T pv = T(0.5) * (pl + pr) - T(0.125) * du * (rl + rr) * (cl + cr);
         const T pmin = fmin(pl, pr), pmax = fmax(pl, pr);
         pv_ok = pmax < T(2) * pmin && pv >= pmin && pv <= pmax;
-        const T tr = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), T(1) / z);
+        const T tr = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), rz);
         x[0] = __logf(float(rl));
         x[1] = __logf(float(rr));
         x[2] = __logf(float(pl));
@@ -897,7 +914,7 @@ struct EulerGodunovRP : EulerRP<T> {
         x[4] = __logf(float(cl));
         x[5] = __logf(float(cr));
         x[6] = float(du);
-        x[7] = float(du / (cl + cr));
+        x[7] = float(du * rcp_(cl + cr));
         x[8] = __logf(float(tr));
         x[9] = __logf(fmaxf(float(pv), 1e-6f));
         ptr = float(tr);
@@ -908,14 +925,14 @@ struct EulerGodunovRP : EulerRP<T> {
     __device__ __forceinline__ void fK(T p, T rK, T pK, T cK, T& f, T& fd) const
     {
         if (p > pK) {
-            const T A = T(2) / ((gamma + T(1)) * rK), B = gm1 / (gamma + T(1)) * pK;
+            const T A = a2 * rcp_(rK), B = g6 * pK;
             const T q = sqrt_(A * rcp_(B + p));
             f = (p - pK) * q;
             fd = q * (T(1) - T(0.5) * (p - pK) * rcp_(B + p));
         } else {
             const T r = p * rcp_(pK);
-            const T pz = pow_(r, T(0.5) * gm1 / gamma);
-            f = T(2) * cK / gm1 * (pz - T(1));
+            const T pz = pow_(r, z);
+            f = tgm1 * cK * (pz - T(1));
             fd = pz * rcp_(r * rK * cK);   // (p/p_K)^(-(gamma+1)/(2 gamma)) / (rho_K c_K)
         }
     }
@@ -923,20 +940,19 @@ struct EulerGodunovRP : EulerRP<T> {
     {
         const T r = ps * rcp_(pK);
         if (ps > pK) {
-            const T g6 = gm1 / (gamma + T(1));
             return rK * (r + g6) * rcp_(g6 * r + T(1));
         }
-        return rK * pow_(r, T(1) / gamma);
+        return rK * pow_(r, ig);
     }
     __device__ __forceinline__ T shock_speed(T uK, T pK, T cK, T ps, T sgn) const
     {
-        return uK + sgn * cK * sqrt_((gamma + T(1)) / (T(2) * gamma) * ps * rcp_(pK) + gm1 / (T(2) * gamma));
+        return uK + sgn * cK * sqrt_(sk * ps * rcp_(pK) + z);
     }
     // normal flux of (rho, u_n, u_t, p) in the edge frame (0: mass, 1: normal
     // momentum, 2: tangential momentum, 3: energy)
     __device__ __forceinline__ void nflux(T rho, T un, T ut, T p, T* f) const
     {
-        const T E = p / gm1 + T(0.5) * rho * (un * un + ut * ut);
+        const T E = p * igm1 + T(0.5) * rho * (un * un + ut * ut);
         f[0] = rho * un;
         f[1] = rho * un * un + p;
         f[2] = rho * un * ut;
@@ -947,7 +963,7 @@ struct EulerGodunovRP : EulerRP<T> {
         q[0] = rho;
         q[1] = rho * un;
         q[2] = rho * ut;
-        q[3] = p / gm1 + T(0.5) * rho * (un * un + ut * ut);
+        q[3] = p * igm1 + T(0.5) * rho * (un * un + ut * ut);
     }
 
     template <int DIR>
@@ -989,7 +1005,6 @@ struct EulerGodunovRP : EulerRP<T> {
 
         // star pressure: Newton on f_L + f_R + u_R - u_L from the adaptive guess
         const T du = ur - ul;
-        const T z = T(0.5) * gm1 / gamma;
         const T pmin = fmin(pl, pr), pmax = fmax(pl, pr);
         T ppv = T(0.5) * (pl + pr) - T(0.125) * du * (rl + rr) * (cl + cr);
         ppv = fmax(ppv, pmin * T(1e-6));
@@ -997,10 +1012,10 @@ struct EulerGodunovRP : EulerRP<T> {
         if (pmax < T(2) * pmin && ppv >= pmin && ppv <= pmax) {
             p0 = ppv;
         } else if (ppv < pmin) {
-            p0 = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), T(1) / z);
+            p0 = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), rz);
         } else {
-            const T gl = sqrt_(T(2) / ((gamma + T(1)) * rl) * rcp_(gm1 / (gamma + T(1)) * pl + ppv));
-            const T gr = sqrt_(T(2) / ((gamma + T(1)) * rr) * rcp_(gm1 / (gamma + T(1)) * pr + ppv));
+            const T gl = sqrt_(a2 * rcp_(rl * (g6 * pl + ppv)));
+            const T gr = sqrt_(a2 * rcp_(rr * (g6 * pr + ppv)));
             p0 = (gl * pl + gr * pr - du) * rcp_(gl + gr);
         }
         const T tol = sizeof(T) == 4 ? T(1e-6) : T(1e-14);
@@ -1068,11 +1083,11 @@ struct EulerGodunovRP : EulerRP<T> {
             } else if (left ? tail <= T(0) : tail >= T(0)) {
                 r0 = star_density(rK, pK, ps); u0 = us; p0s = ps;
             } else {
-                const T c = T(2) / (gamma + T(1)) * (cK - sgn * T(0.5) * gm1 * uK);
+                const T c = a2 * (cK - sgn * T(0.5) * gm1 * uK);
                 const T rc_ = c * rcp_(cK);
                 u0 = -sgn * c;
-                r0 = rK * pow_(rc_, T(2) / gm1);
-                p0s = pK * pow_(rc_, T(2) * gamma / gm1);
+                r0 = rK * pow_(rc_, tgm1);
+                p0s = pK * pow_(rc_, gamma * tgm1);
             }
         }
         T f0[4], fL[4], fR[4];
