@@ -24,7 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["rp.c", "step.c", "exact.c", "mlp.c"]
+_SOURCES = ["rp.c", "step.c", "exact.c", "mlp.c", "amr.c"]
 _LIBDIR = os.path.join(_HERE, "_lib")
 
 ACOUSTICS, SWE, EULER, ADVECTION, ACOUSTICS_VAR, EULER_GODUNOV = 1, 2, 3, 4, 5, 6
@@ -201,6 +201,72 @@ def rpt2_var(prob: Problem, direction: int, qlo, qc, qhi, asdq):
     lib().mcref_rpt2_var(ctypes.byref(prob.c()), direction, _p(qlo), _p(qc), _p(qhi), _p(asdq),
                          _p(bm), _p(bp))
     return bm, bp
+
+
+class _AmrPatch(ctypes.Structure):
+    _fields_ = [("ci0", ctypes.c_int), ("cj0", ctypes.c_int), ("cw", ctypes.c_int), ("ch", ctypes.c_int)]
+
+
+def _amr_lib():
+    L = lib()
+    if not getattr(L, "_amr_ready", False):
+        P = ctypes.POINTER(_Problem)
+        AP = ctypes.POINTER(_AmrPatch)
+        DPP = ctypes.POINTER(_D)
+        L.mcref_fine_problem.argtypes = [P, ctypes.c_int, AP, P]
+        L.mcref_fine_problem.restype = None
+        L.mcref_amr_fill_ghosts.argtypes = [P, ctypes.c_int, _D, _D, ctypes.c_double, AP, ctypes.c_int, DPP]
+        L.mcref_amr_fill_ghosts.restype = None
+        L.mcref_amr_average_down.argtypes = [P, ctypes.c_int, AP, ctypes.c_int, DPP, _D]
+        L.mcref_amr_average_down.restype = None
+        L.mcref_amr_step.argtypes = [P, ctypes.c_int, AP, ctypes.c_int, _D, _D, DPP, ctypes.c_double,
+                                     ctypes.c_int]
+        L._amr_ready = True
+    return L
+
+
+def fine_problem(coarse: Problem, ratio: int, patch) -> Problem:
+    """The fine patch's problem: coarse sizes / ratio, ghosts given."""
+    ci0, cj0, cw, ch = patch
+    return Problem(coarse.solver, ratio * cw, ratio * ch, coarse.dx / ratio, coarse.dy / ratio,
+                   limiter=coarse.limiter, order=coarse.order, transverse=coarse.transverse,
+                   efix=coarse.efix, bc=(BC_GIVEN,) * 4, param=coarse.param, mbc=coarse.mbc)
+
+
+def _patch_array(patches):
+    arr = (_AmrPatch * max(1, len(patches)))()
+    for k, (ci0, cj0, cw, ch) in enumerate(patches):
+        arr[k] = _AmrPatch(ci0, cj0, cw, ch)
+    return arr
+
+
+def amr_fill_ghosts(coarse: Problem, ratio, qc0, qc1, alpha, patches, qf):
+    """Fill the ghost layers of the patch arrays qf (list, modified in place)."""
+    qc0, qc1 = _f64(qc0), _f64(qc1)
+    ptrs = (_D * max(1, len(qf)))(*[_p(a) for a in qf])
+    _amr_lib().mcref_amr_fill_ghosts(ctypes.byref(coarse.c()), int(ratio), _p(qc0), _p(qc1),
+                                     float(alpha), _patch_array(patches), len(patches), ptrs)
+
+
+def amr_average_down(coarse: Problem, ratio, patches, qf, qc):
+    qc = _f64(qc).copy()
+    ptrs = (_D * max(1, len(qf)))(*[_p(a) for a in qf])
+    _amr_lib().mcref_amr_average_down(ctypes.byref(coarse.c()), int(ratio), _patch_array(patches),
+                                      len(patches), ptrs, _p(qc))
+    return qc
+
+
+def amr_step(coarse: Problem, ratio, patches, qc, qf, dt, nthreads=1):
+    """One coarse step with ratio fine steps per patch -> (qc_new, flags); the
+    patch arrays in the list qf are advanced in place."""
+    qc = _f64(qc)
+    out = np.zeros_like(qc)
+    for a in qf:
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    ptrs = (_D * max(1, len(qf)))(*[_p(a) for a in qf])
+    flags = _amr_lib().mcref_amr_step(ctypes.byref(coarse.c()), int(ratio), _patch_array(patches),
+                                      len(patches), _p(qc), _p(out), ptrs, float(dt), int(nthreads))
+    return out, flags
 
 
 def exact_sample(gamma, rl, ul, pl, rr, ur, pr, pstar, ustar):

@@ -175,6 +175,33 @@ double mcref_mlp_backward(int64_t B, const double* X, const double* y,
                           double* gW3, double* gb3);
 double mcref_round_bf16(double x);
 
+/* ------------------------------------------------------------------ */
+/* Refined patches on a coarse grid (amr.c)                            */
+/* ------------------------------------------------------------------ */
+
+/* A fine patch over the coarse cells [ci0, ci0+cw) x [cj0, cj0+ch): its grid
+ * has ratio*cw x ratio*ch cells of size dx/ratio, dy/ratio. */
+typedef struct {
+    int ci0, cj0, cw, ch;
+} mcref_amr_patch;
+
+/* the fine patch's problem: coarse one with the fine sizes and given ghosts */
+void mcref_fine_problem(const mcref_problem* coarse, int ratio, const mcref_amr_patch* pt,
+                        mcref_problem* fine);
+/* Ghost layers of every patch: copy from another patch covering the fine
+ * cell, else conservative MC-limited linear interpolation of the coarse state
+ * (1 - alpha) qc0 + alpha qc1 (both with filled ghosts).  qf[p] are the
+ * patches' state arrays. */
+void mcref_amr_fill_ghosts(const mcref_problem* pc, int ratio, const double* qc0, const double* qc1,
+                           double alpha, const mcref_amr_patch* pts, int npatch, double** qf);
+/* Covered coarse cells take the mean of their ratio x ratio fine cells. */
+void mcref_amr_average_down(const mcref_problem* pc, int ratio, const mcref_amr_patch* pts,
+                            int npatch, double* const* qf, double* qc);
+/* One coarse step of dt with ratio fine steps of dt/ratio on every patch
+ * (Berger-Oliger); qf[p] are updated in place, qc_out gets filled ghosts. */
+int mcref_amr_step(const mcref_problem* pc, int ratio, const mcref_amr_patch* pts, int npatch,
+                   const double* qc_in, double* qc_out, double** qf, double dt, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
