@@ -136,6 +136,42 @@ mc_status mc_destroy(mc_ctx* ctx);
  * default.  Used by the autotuner; results do not depend on it. */
 mc_status mc_set_tile_rows(mc_ctx* ctx, int rows);
 
+/* Refined patches with their own time steps (the paper's "dynamic time
+ * stepping" kernel, §1.2 Table 1: each refined grid manages its own time step
+ * and takes the values at its boundary from the adjacent grid by spatial and
+ * temporal interpolation).  Two levels, Berger-Oliger: one coarse step of dt
+ * on the whole coarse grid, then `ratio` steps of dt/ratio on every patch;
+ * before each, the patches' two ghost layers are filled cell by cell from the
+ * other patch covering the cell, or else from the coarse state interpolated
+ * linearly in time and by a conservative MC-limited linear reconstruction in
+ * space; afterwards every covered coarse cell takes the mean of its fine
+ * cells.  There is no flux correction at coarse-fine boundaries (refluxing).
+ *
+ * A patch covers the coarse cells [ci0, ci0+cw) x [cj0, cj0+ch) inside the
+ * coarse interior; patches do not overlap.  Its grid has ratio*cw x ratio*ch
+ * cells of size dx/ratio x dy/ratio (mc_amr_fine_problem gives the problem,
+ * and mc_layout_of of it the layout of its two buffers qa, qb, caller-owned).
+ * The initial fine state goes into qa (interior).  Not for variable-
+ * coefficient acoustics (MC_ENOTSUP). */
+typedef struct mc_amr_patch {
+    int32_t ci0, cj0, cw, ch;
+    void* qa;
+    void* qb;
+} mc_amr_patch;
+typedef struct mc_amr mc_amr;
+mc_status mc_amr_fine_problem(const mc_problem* coarse, int32_t ratio, const mc_amr_patch* patch,
+                              mc_problem* out);
+mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_patch* patches,
+                        int32_t npatch, mc_amr** out);
+mc_status mc_amr_destroy(mc_amr* amr);
+/* nsteps coarse steps of dt.  The coarse state alternates between qc_a and
+ * qc_b (coarse_in_b: which holds the result); every patch's state is in its
+ * qb after the call when *fine_in_b is 1, else in its qa (the same for all
+ * patches, and carried over to the next call).  Asynchronous on stream except
+ * for the final status check (MC_ENONPHYS, MC_ETIMEOUT from any grid). */
+mc_status mc_amr_advance(mc_amr* amr, void* qc_a, void* qc_b, int32_t nsteps, double dt,
+                         int32_t* coarse_in_b, int32_t* fine_in_b, void* stream);
+
 /* Pressure seeds for the exact-solution Euler solver (MC_EULER_GODUNOV): with
  * a trained seed network attached (see mc_mlp_* below), a normal solve of the
  * fused step whose jump is too strong for Toro's PV guess (the adaptive rule

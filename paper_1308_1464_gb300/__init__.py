@@ -58,6 +58,11 @@ class Problem(ctypes.Structure):
         return {EULER_ROE: 4, EULER_GODUNOV: 4, ADVECTION: 1, ACOUSTICS_VAR: 5}.get(self.solver, 3)
 
 
+class AmrPatch(ctypes.Structure):
+    _fields_ = [("ci0", ctypes.c_int32), ("cj0", ctypes.c_int32), ("cw", ctypes.c_int32),
+                ("ch", ctypes.c_int32), ("qa", ctypes.c_void_p), ("qb", ctypes.c_void_p)]
+
+
 class Layout(ctypes.Structure):
     _fields_ = [("x_offset", ctypes.c_int64), ("ld_x", ctypes.c_int64),
                 ("ld_field", ctypes.c_int64), ("elem_bytes", ctypes.c_int64),
@@ -87,6 +92,12 @@ def lib():
         L.mc_destroy.argtypes = [_VP]
         L.mc_set_tile_rows.argtypes = [_VP, ctypes.c_int]
         L.mc_set_seed_net.argtypes = [_VP, _VP]
+        L.mc_amr_fine_problem.argtypes = [P, ctypes.c_int32, ctypes.POINTER(AmrPatch), P]
+        L.mc_amr_create.argtypes = [P, ctypes.c_int32, ctypes.POINTER(AmrPatch), ctypes.c_int32,
+                                    ctypes.POINTER(_VP)]
+        L.mc_amr_destroy.argtypes = [_VP]
+        L.mc_amr_advance.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _VP]
         L.mc_newton_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.c_int32, _VP]
         L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
@@ -375,3 +386,41 @@ class Batch:
     def advance_plain(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
         """One launch per patch per step -> (t per patch or None, result_in_b)."""
         return self._run(lib().mc_batch_advance_plain, nsteps, cfl, want_t, stream)
+
+
+def amr_fine_problem(coarse: Problem, ratio: int, ci0: int, cj0: int, cw: int, ch: int) -> Problem:
+    """The problem of a fine patch over coarse cells [ci0, ci0+cw) x [cj0, cj0+ch)."""
+    out = Problem()
+    patch = AmrPatch(ci0, cj0, cw, ch, None, None)
+    check(lib().mc_amr_fine_problem(ctypes.byref(coarse), int(ratio), ctypes.byref(patch),
+                                    ctypes.byref(out)))
+    return out
+
+
+class Amr:
+    """Refined patches on a coarse grid (mc_amr_*).  patches: list of
+    (ci0, cj0, cw, ch, qa_ptr, qb_ptr)."""
+
+    def __init__(self, coarse: Problem, ratio: int, patches):
+        arr = (AmrPatch * max(1, len(patches)))(*[AmrPatch(*pt) for pt in patches])
+        h = _VP()
+        check(lib().mc_amr_create(ctypes.byref(coarse), int(ratio), arr, len(patches), ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mc_amr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def advance(self, qc_a: int, qc_b: int, nsteps: int, dt: float, stream: int = 0):
+        """-> (coarse result in b, fine result in b)."""
+        cb, fb = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().mc_amr_advance(self._h, _VP(qc_a), _VP(qc_b), int(nsteps), float(dt),
+                                   ctypes.byref(cb), ctypes.byref(fb), _VP(stream)))
+        return bool(cb.value), bool(fb.value)

@@ -462,6 +462,21 @@ static mc_status read_status(mc_ctx* c, DevState* h, cudaStream_t s)
     return MC_OK;
 }
 
+}  // extern "C"
+
+namespace mc {
+mc_status ctx_check_status(mc_ctx* c, void* stream)
+{
+    DevState h;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    mc_status st = read_status(c, &h, s);
+    if (h.status) cudaMemsetAsync(&c->dev->status, 0, sizeof(int), s);
+    return st;
+}
+}  // namespace mc
+
+extern "C" {
+
 mc_status mc_step(mc_ctx* c, void* q_in, void* q_out, double dt, double* smax_out, void* stream)
 {
     if (!c || !q_in || !q_out) return set_error(MC_EINVAL, "NULL argument");

@@ -45,6 +45,9 @@ struct SweepLaunch {
     unsigned long long* newton = nullptr;      // Newton update / solve counters, or null
 };
 
+// the status word of a context's fused steps (synchronises; cleared after)
+mc_status ctx_check_status(mc_ctx* c, void* stream);
+
 // per-solver launchers (mc_sweep_<solver>.cu), dispatching on dtype
 cudaError_t sweep_launch_acoustics(const SweepLaunch& L);
 cudaError_t sweep_launch_swe(const SweepLaunch& L);
