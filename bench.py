@@ -358,6 +358,100 @@ def bench_batch(args, rank, world):
     }
 
 
+def bench_amr(args, rank, world):
+    """Shallow-water dam break on a 2048^2 coarse grid (FP32, walls) with
+    ratio-2 patches of 128^2 coarse cells over the ring 0.3 <= r <= 0.7 that
+    the waves cross: K coarse steps of mc_amr_advance (two fine steps per
+    patch each), against a uniformly fine 4096^2 grid advanced over the same
+    simulated time with the fused step alone."""
+    import torch
+    import paper_1308_1464_gb300 as mc
+    from paper_1308_1464_gb300 import workloads
+    from paper_1308_1464_gb300.state import DeviceState
+    nc, r, blk = 2048, 2, 128
+    g = workloads.swe_dambreak(nc, nc)
+    p = mc.Problem.make(mc.SWE_ROE, nc, nc, g.dx, g.dy, dtype=mc.F32, bc=(mc.BC_WALL,) * 4,
+                        param=(G, 0, 0, 0))
+    ctx = mc.Context(p)
+    qa, qb = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+    q0 = np.ascontiguousarray(g.q.astype(np.float32))
+    qa.upload(q0)
+    patches, fine = [], []
+    for bj in range(nc // blk):
+        for bi in range(nc // blk):
+            xc = g.x_lo + (bi + 0.5) * blk * g.dx
+            yc = g.y_lo + (bj + 0.5) * blk * g.dy
+            if 0.3 <= (xc * xc + yc * yc) ** 0.5 <= 0.7:
+                fp = mc.amr_fine_problem(p, r, bi * blk, bj * blk, blk, blk)
+                lay = mc.layout_of(fp)
+                a = torch.zeros(int(lay.bytes), dtype=torch.uint8, device="cuda")
+                b = torch.zeros_like(a)
+                # fine initial data: each coarse value on its r x r fine cells
+                sub = q0[:, bj * blk:(bj + 1) * blk, bi * blk:(bi + 1) * blk]
+                v = a.view(torch.float32)[: lay.meqn * lay.ld_field].view(int(lay.meqn), fp.my + 4, int(lay.ld_x))
+                x0 = int(lay.x_offset)
+                v[:, 2:-2, x0: x0 + fp.mx] = torch.from_numpy(np.repeat(np.repeat(sub, r, 1), r, 2)).cuda()
+                patches.append((bi * blk, bj * blk, blk, blk, a.data_ptr(), b.data_ptr()))
+                fine.append((a, b))
+    amr = mc.Amr(p, r, patches)
+    smax = ctx.max_cell_speed(qa.ptr)
+    dt = 0.8 / smax
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    for _ in range(args.warmup):
+        amr.advance(qa.ptr, qb.ptr, 2, dt, sh)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        amr.advance(qa.ptr, qb.ptr, K, dt, sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fine_cells = len(patches) * (r * blk) ** 2
+    updates = K * (nc * nc + r * fine_cells)
+    # the same simulated time on a uniformly fine grid: r K fused steps of dt / r
+    gf = workloads.swe_dambreak(r * nc, r * nc)
+    pf = mc.Problem.make(mc.SWE_ROE, r * nc, r * nc, gf.dx, gf.dy, dtype=mc.F32, bc=(mc.BC_WALL,) * 4,
+                         param=(G, 0, 0, 0))
+    cf = mc.Context(pf)
+    fa, fb = DeviceState(cf).zero_(), DeviceState(cf).zero_()
+    fa.upload(np.ascontiguousarray(gf.q.astype(np.float32)))
+    cf.bc_fill(fa.ptr, sh)
+    for _ in range(3):
+        cf.sweep(fa.ptr, fb.ptr, dt / r, sh)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for k in range(r * K):
+        src, dst = (fa, fb) if k % 2 == 0 else (fb, fa)
+        cf.step(src.ptr, dst.ptr, dt / r, want_smax=False, stream=sh)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fms = f0.elapsed_time(f1)
+    amr.close()
+    return {
+        "metric": "cell-updates/s", "value": world * updates / (ms * 1e-3), "unit": "cell-updates/s",
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "shallow-water dam break, 2048^2 coarse fp32 walls, ratio-2 patches "
+                               "of 128^2 coarse cells over the ring 0.3 <= r <= 0.7, CFL 0.8",
+                   "patches": len(patches), "fine_cells": fine_cells,
+                   "l2": "inputs larger than L2 (%d MB coarse state, %d MB of patch states)"
+                         % (int(ctx.layout.bytes) // 10**6,
+                            sum(int(a.numel()) for a, _ in fine) // 10**6)},
+        "uniform_fine": {"grid": f"{r * nc}x{r * nc}", "ms_for_same_time": fms,
+                         "amr_ms": ms, "amr_speedup": fms / ms},
+        # per coarse step: ghost fill + fused step (coarse), ghost fill of the
+        # new coarse state, ratio x (patch ghosts + one multi-patch fused step),
+        # average down
+        "gpu_launches": K * (2 + 1 + 2 * r + 1),
+        "clocks": clk.summary(),
+    }
+
+
 def bench_exact(args, rank, world):
     """2^24 exact Euler Riemann problems (rho in [0.01, 10], p in [0.01, 100]
     log-uniform, |u| <= 5), FP64 Newton to |dp|/p < 1e-8: the plain adaptive
@@ -441,13 +535,13 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS) + ["batch", "exact"])
+    ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS) + ["batch", "exact", "amr"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
                     help="profiling aid: run K stand-alone fused steps (mc_step) and exit")
     args = ap.parse_args()
-    if args.workload in ("batch", "exact"):
+    if args.workload in ("batch", "exact", "amr"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is timed "
                               "for the grid workloads only"}))
@@ -457,7 +551,7 @@ def main():
         rank, world, local = dist_info()
         torch.cuda.set_device(local)
         _build.build()
-        line = (bench_batch if args.workload == "batch" else bench_exact)(args, rank, world)
+        line = {"batch": bench_batch, "exact": bench_exact, "amr": bench_amr}[args.workload](args, rank, world)
         if rank == 0:
             print(json.dumps(line))
         return

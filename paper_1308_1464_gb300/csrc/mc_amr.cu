@@ -10,9 +10,11 @@
 // coarse state interpolated linearly in time (weight s/ratio between the
 // coarse states before and after its step) and in space by the coarse
 // cell's value plus MC-limited slopes, a conservative reconstruction.
-// Afterwards one kernel replaces every covered coarse cell by the mean of
-// its fine cells.  There is no refluxing.  Everything is enqueued on the
-// caller's stream; the only synchronisation is the status check at the end.
+// The patches' steps are one launch of the fused step over all of them
+// (mc_multi.cuh).  Afterwards one kernel replaces every covered coarse cell by
+// the mean of its fine cells.  There is no refluxing.  Everything is enqueued
+// on the caller's stream; the only synchronisation is the status check at
+// the end.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,6 +23,7 @@
 #include <vector>
 
 #include "mc_internal.h"
+#include "mc_multi.cuh"
 
 namespace mc {
 
@@ -151,26 +154,42 @@ __global__ void amr_average_kernel(const AmrArgs a)
 using namespace mc;
 
 struct mc_amr {
-    mc_problem coarse;
+    mc_problem coarse, fine;      // fine: the patches' scheme (sizes per patch)
     mc_layout clay;
     int ratio;
     mc_ctx* cctx;
     std::vector<mc_amr_patch> patches;
-    std::vector<mc_ctx*> fctx;
     std::vector<AmrPatchDev> host_desc;
-    AmrPatchDev* desc;
-    long long nghost, ncell;
-    int fine_in_b;   // which buffer of every patch holds its current state
+    AmrPatchDev* desc = nullptr;
+    MultiGrid* grids = nullptr;   // the patches for the multi-grid fused step
+    CUtensorMap* maps = nullptr;  // two per patch (64-byte aligned device array)
+    long long* prefix = nullptr;
+    int* status = nullptr;
+    long long nghost = 0, ncell = 0, ntask = 0;
+    int fine_in_b = 0;   // which buffer of every patch holds its current state
 };
 
 static void amr_free(mc_amr* a)
 {
     if (!a) return;
-    for (mc_ctx* c : a->fctx)
-        if (c) mc_destroy(c);
     if (a->cctx) mc_destroy(a->cctx);
-    if (a->desc) cudaFree(a->desc);
+    cudaFree(a->desc);
+    cudaFree(a->grids);
+    cudaFree(a->maps);
+    cudaFree(a->prefix);
+    cudaFree(a->status);
     delete a;
+}
+
+static cudaError_t multi_launch(const MultiLaunch& L)
+{
+    switch (L.prob.solver) {
+    case MC_ACOUSTICS: return multi_launch_acoustics(L);
+    case MC_SWE_ROE: return multi_launch_swe(L);
+    case MC_ADVECTION: return multi_launch_advection(L);
+    case MC_EULER_GODUNOV: return multi_launch_euler_godunov(L);
+    default: return multi_launch_euler(L);
+    }
 }
 
 extern "C" {
@@ -224,19 +243,40 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
         amr_free(A);
         return st;
     }
-    long long g = 0, c = 0;
+    long long g = 0, c = 0, tk = 0;
+    std::vector<MultiGrid> grids;
+    std::vector<CUtensorMap> maps(2 * (size_t)(npatch > 0 ? npatch : 1));
+    std::vector<long long> prefix(1, 0);
     for (int p = 0; p < npatch; p++) {
         mc_problem fp;
         st = mc_amr_fine_problem(coarse, ratio, &patches[p], &fp);
-        mc_ctx* fc = nullptr;
-        if (st == MC_OK) st = mc_create(&fp, &fc);
-        A->fctx.push_back(fc);
         if (st != MC_OK) {
             amr_free(A);
             return st;
         }
+        A->fine = fp;
         mc_layout fl;
         mc_layout_of(&fp, &fl);
+        MultiGrid mg;
+        mg.mx = fp.mx;
+        mg.my = fp.my;
+        mg.nbands = (fp.mx + BAND_W - 1) / BAND_W;
+        mg.tile_rows = fp.my < DEFAULT_TILE_ROWS ? fp.my : DEFAULT_TILE_ROWS;
+        mg.ld_x = fl.ld_x;
+        mg.ld_field = fl.ld_field;
+        mg.q[0] = patches[p].qa;
+        mg.q[1] = patches[p].qb;
+        grids.push_back(mg);
+        tk += (long long)mg.nbands * ((fp.my + mg.tile_rows - 1) / mg.tile_rows);
+        prefix.push_back(tk);
+        for (int k = 0; k < 2; k++) {
+            cudaError_t e = encode_state_map(&maps[2 * p + k], mg.q[k], (int)fl.elem_bytes, (int)fl.meqn,
+                                             fl.ld_x, fp.my, fl.ld_field);
+            if (e != cudaSuccess) {
+                amr_free(A);
+                return set_error(MC_EINVAL, "tensor map of patch %d buffer %d (16-byte aligned?)", p, k);
+            }
+        }
         AmrPatchDev d;
         d.ci0 = patches[p].ci0;
         d.cj0 = patches[p].cj0;
@@ -256,10 +296,26 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
     }
     A->nghost = g;
     A->ncell = c;
+    A->ntask = tk;
+    cudaError_t e0 = cudaMalloc(&A->status, sizeof(int));
+    if (e0 == cudaSuccess) e0 = cudaMemset(A->status, 0, sizeof(int));
+    if (e0 != cudaSuccess) {
+        amr_free(A);
+        return cuda_error(e0, "status word");
+    }
     if (npatch > 0) {
         cudaError_t e = cudaMalloc(&A->desc, sizeof(AmrPatchDev) * npatch);
         if (e == cudaSuccess)
             e = cudaMemcpy(A->desc, A->host_desc.data(), sizeof(AmrPatchDev) * npatch, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&A->grids, sizeof(MultiGrid) * npatch);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(A->grids, grids.data(), sizeof(MultiGrid) * npatch, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&A->maps, sizeof(CUtensorMap) * 2 * npatch);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(A->maps, maps.data(), sizeof(CUtensorMap) * 2 * npatch, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&A->prefix, sizeof(long long) * (npatch + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(A->prefix, prefix.data(), sizeof(long long) * (npatch + 1), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             amr_free(A);
             return cuda_error(e, "patch descriptors");
@@ -283,7 +339,9 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int np = (int)A->patches.size();
     const int es = (int)A->clay.elem_bytes;
-    int cb = 0, fb = 0;
+    int cb = 0, fb = A->fine_in_b;
+    MultiLaunch M{A->fine, A->grids, A->maps, A->prefix, np, 0, A->ntask, A->clay.x_offset,
+                  dt / A->ratio / A->fine.dx, dt / A->ratio / A->fine.dy, A->status, s};
     AmrArgs a;
     a.P = A->desc;
     a.npatch = np;
@@ -311,11 +369,9 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
             else amr_ghost_kernel<float><<<gblocks > 0 ? gblocks : 1, 256, 0, s>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_error(e, "patch ghost fill");
-            for (int p = 0; p < np; p++) {
-                const AmrPatchDev& d = A->host_desc[p];
-                st = mc_sweep(A->fctx[p], d.q[fb], d.q[fb ^ 1], dt / A->ratio, stream);
-                if (st != MC_OK) return st;
-            }
+            M.cur = fb;
+            e = multi_launch(M);
+            if (e != cudaSuccess) return cuda_error(e, "patch steps");
             fb ^= 1;
         }
         if (np > 0) {
@@ -327,16 +383,16 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
         }
         cb ^= 1;
     }
-    // fold the fine buffers back so that patch buffer a holds the state again
-    if (fb) {
-        for (int p = 0; p < np; p++) std::swap(A->host_desc[p].q[0], A->host_desc[p].q[1]);
-        cudaError_t e = cudaMemcpyAsync(A->desc, A->host_desc.data(), sizeof(AmrPatchDev) * np,
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_error(e, "patch descriptors");
-        A->fine_in_b ^= 1;
-    }
+    A->fine_in_b = fb;
     mc_status st = ctx_check_status(A->cctx, stream);
-    for (int p = 0; p < np && st == MC_OK; p++) st = ctx_check_status(A->fctx[p], stream);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, A->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(A->status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "patch status");
+    if (st == MC_OK && (h & ST_BADARG)) st = set_error(MC_EINVAL, "a patch's tensor map or box is misaligned");
+    if (st == MC_OK && (h & ST_TIMEOUT)) st = set_error(MC_ETIMEOUT, "a bounded device wait gave up");
+    if (st == MC_OK && (h & ST_NONPHYS)) st = set_error(MC_ENONPHYS, "non-physical state met on a patch");
     if (coarse_in_b) *coarse_in_b = cb;
     if (fine_in_b) *fine_in_b = A->fine_in_b;
     return st;

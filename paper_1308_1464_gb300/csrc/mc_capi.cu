@@ -465,6 +465,30 @@ static mc_status read_status(mc_ctx* c, DevState* h, cudaStream_t s)
 }  // extern "C"
 
 namespace mc {
+cudaError_t encode_state_map(CUtensorMap* out, const void* q, int es, int nplane, long long ld_x, int my,
+                             long long ld_field)
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &qr);
+        if (e != cudaSuccess) return e;
+        if (qr != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)ld_x, (cuuint64_t)(my + 4), (cuuint64_t)nplane};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld_x * es), (cuuint64_t)(ld_field * es)};
+    cuuint32_t box[3] = {(cuuint32_t)box_w(es), (cuuint32_t)stage_rows(es), (cuuint32_t)nplane};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(out, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        const_cast<void*>(q), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 mc_status ctx_check_status(mc_ctx* c, void* stream)
 {
     DevState h;

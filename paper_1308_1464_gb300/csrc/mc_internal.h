@@ -45,6 +45,29 @@ struct SweepLaunch {
     unsigned long long* newton = nullptr;      // Newton update / solve counters, or null
 };
 
+// One launch of the fused step over many grids (mc_multi.cuh); grids and
+// prefix are device arrays (MultiGrid, ngrid + 1 task offsets).
+struct MultiLaunch {
+    mc_problem prob;             // scheme and parameters (sizes come from the grids)
+    const void* grids;
+    const CUtensorMap* maps;     // two per grid
+    const long long* prefix;
+    int ngrid, cur;
+    long long total, x_offset;
+    double nux, nuy;
+    int* status;
+    cudaStream_t stream;
+};
+cudaError_t multi_launch_acoustics(const MultiLaunch& L);
+cudaError_t multi_launch_swe(const MultiLaunch& L);
+cudaError_t multi_launch_euler(const MultiLaunch& L);
+cudaError_t multi_launch_advection(const MultiLaunch& L);
+cudaError_t multi_launch_acoustics_var(const MultiLaunch& L);
+cudaError_t multi_launch_euler_godunov(const MultiLaunch& L);
+// a tensor map of a state array in the library layout (the box of the fused step)
+cudaError_t encode_state_map(CUtensorMap* out, const void* q, int elem_bytes, int nplane,
+                             long long ld_x, int my, long long ld_field);
+
 // the status word of a context's fused steps (synchronises; cleared after)
 mc_status ctx_check_status(mc_ctx* c, void* stream);
 

@@ -4,6 +4,7 @@
 
 #include "mc_batch.cuh"
 #include "mc_internal.h"
+#include "mc_multi.cuh"
 #include "mc_sweep.cuh"
 
 namespace mc {
@@ -151,10 +152,50 @@ cudaError_t batch_occupancy_t(int* ctas)
                                                          SWEEP_WARPS * 32, smem);
 }
 
+template <class RP>
+cudaError_t multi_launch_t(const MultiLaunch& L)
+{
+    using T = typename RP::real;
+    MultiArgs<RP> a;
+    a.rp.setup(L.prob.param, L.prob.efix);
+    a.grids = static_cast<const MultiGrid*>(L.grids);
+    a.maps = L.maps;
+    a.prefix = L.prefix;
+    a.ngrid = L.ngrid;
+    a.cur = L.cur;
+    a.total = L.total;
+    a.x_offset = L.x_offset;
+    a.nux = L.nux;
+    a.nuy = L.nuy;
+    a.limiter = L.prob.limiter;
+    a.order = L.prob.order;
+    a.transverse = L.prob.transverse;
+    a.status = L.status;
+    constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
+    long long blocks = (L.total + SWEEP_WARPS - 1) / SWEEP_WARPS;
+    if (blocks < 1) blocks = 1;
+    cudaError_t e;
+    if (is_fast_scheme(L.prob)) {
+        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            multi_sweep_kernel<RP, true><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            multi_sweep_kernel<RP, false><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
 }  // namespace mc
 
 #define MC_DEFINE_SOLVER_LAUNCHERS(NAME, RPT)                                                  \
     namespace mc {                                                                             \
+    cudaError_t multi_launch_##NAME(const MultiLaunch& L)                                      \
+    {                                                                                          \
+        return L.prob.dtype == MC_F64 ? multi_launch_t<RPT<double>>(L)                         \
+                                      : multi_launch_t<RPT<float>>(L);                         \
+    }                                                                                          \
     cudaError_t sweep_launch_##NAME(const SweepLaunch& L)                                      \
     {                                                                                          \
         return L.prob.dtype == MC_F64 ? sweep_launch_t<RPT<double>>(L)                         \
