@@ -78,7 +78,12 @@ enum { MC_ACOUSTICS = 1, MC_SWE_ROE = 2, MC_EULER_ROE = 3, MC_ADVECTION = 4, MC_
 /* limiter numbering as in Clawpack: 0 none (Lax-Wendroff), 1 minmod,
  * 2 superbee, 3 van Leer, 4 MC (LeVeque 2002, eq. 6.39) */
 enum { MC_LIM_NONE = 0, MC_LIM_MINMOD = 1, MC_LIM_SUPERBEE = 2, MC_LIM_VANLEER = 3, MC_LIM_MC = 4 };
-enum { MC_BC_PERIODIC = 0, MC_BC_EXTRAP = 1, MC_BC_WALL = 2 };
+/* boundary kinds; MC_BC_GIVEN: the caller writes that side's two ghost
+ * layers before every step (a neighbouring block's halo, mc_halo_unpack) and
+ * the ghost fills leave them as they are.  A grid with a GIVEN side needs at
+ * least 2 x 2 cells; mc_advance, mc_advance_host, the batch and the refined
+ * patches reject it. */
+enum { MC_BC_PERIODIC = 0, MC_BC_EXTRAP = 1, MC_BC_WALL = 2, MC_BC_GIVEN = 3 };
 enum { MC_F32 = 0, MC_F64 = 1 };
 
 /* A 2D problem.  The planes of a state array follow from the solver
@@ -199,8 +204,39 @@ mc_status mc_download(mc_ctx* ctx, const void* q_dev, void* host_dense, void* st
  * wrap, zero-order extrapolation, or a reflecting wall (mirror with the
  * wall-normal momentum negated), per side (LeVeque 2002, ch. 7 and §21.8).
  * Corners take the values of filling x ghosts of the interior rows first and
- * then y ghosts over the full width. */
+ * then y ghosts over the full width.  Sides of kind MC_BC_GIVEN are left as
+ * they are. */
 mc_status mc_bc_fill(mc_ctx* ctx, void* q, void* stream);
+
+/* ---- Blocks of a decomposed grid ------------------------------------------
+ * A grid split into blocks (one per device or rank) steps each block alone;
+ * a cell's update reads cells up to two away, diagonal ones included through
+ * the transverse terms (LeVeque 2002, §21.8), so before every step the two
+ * ghost layers on a side shared with another block must hold that block's
+ * two interior layers next to the side, while sides on the global boundary
+ * keep their kind.  Corners come out as in mc_bc_fill when the fill runs in
+ * two phases: (x) exchange the x strips and mc_bc_fill_dir(.., 0, ..), then
+ * (y) exchange the y strips, which span the ghost columns, and
+ * mc_bc_fill_dir(.., 1, ..).  Sides: 0 xlo, 1 xhi, 2 ylo, 3 yhi.
+ *
+ * Strip layout (dense, the state's element type): x sides [meqn][my][2],
+ * the two interior columns next to the side (pack) or its two ghost columns
+ * (unpack), in increasing i, interior rows only; y sides [meqn][2][mx + 4],
+ * the two interior rows next to the side or its two ghost rows, in
+ * increasing j, columns -2 .. mx + 1.  The strip packed at side s of one
+ * block is unpacked at side s ^ 1 of its neighbour.  Buffers are device
+ * memory owned by the caller; the calls are asynchronous on `stream`. */
+
+/* Elements of the strip of `side` for problem p (grids of at least 2 x 2). */
+mc_status mc_halo_elems(const mc_problem* p, int32_t side, int64_t* elems);
+/* Copies the two interior layers of q next to `side` into buf. */
+mc_status mc_halo_pack(mc_ctx* ctx, const void* q, int32_t side, void* buf, void* stream);
+/* Copies a strip from buf into the two ghost layers of q on `side`. */
+mc_status mc_halo_unpack(mc_ctx* ctx, const void* buf, int32_t side, void* q, void* stream);
+/* One phase of mc_bc_fill: dir 0 fills the x ghost columns of the interior
+ * rows, dir 1 the y ghost rows across the full padded width, each on the
+ * sides whose kind is not MC_BC_GIVEN.  dir 0 then dir 1 equals mc_bc_fill. */
+mc_status mc_bc_fill_dir(mc_ctx* ctx, void* q, int32_t dir, void* stream);
 
 /* One unsplit step with explicit dt: fills q_in's ghosts, then writes the
  * updated interior of q_out (q_out's ghosts are left untouched; q_in and

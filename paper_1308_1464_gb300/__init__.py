@@ -23,7 +23,7 @@ MC_OK, MC_EINVAL, MC_ECUDA, MC_ENOMEM, MC_ECFL, MC_ENONPHYS, MC_ETIMEOUT, MC_ENO
     0, -1, -2, -3, -4, -5, -6, -7)
 ACOUSTICS, SWE_ROE, EULER_ROE, ADVECTION, ACOUSTICS_VAR, EULER_GODUNOV = 1, 2, 3, 4, 5, 6
 LIM_NONE, LIM_MINMOD, LIM_SUPERBEE, LIM_VANLEER, LIM_MC = 0, 1, 2, 3, 4
-BC_PERIODIC, BC_EXTRAP, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_EXTRAP, BC_WALL, BC_GIVEN = 0, 1, 2, 3
 F32, F64 = 0, 1
 
 
@@ -103,6 +103,10 @@ def lib():
         L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_download.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
+        L.mc_bc_fill_dir.argtypes = [_VP, _VP, ctypes.c_int32, _VP]
+        L.mc_halo_elems.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+        L.mc_halo_pack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
+        L.mc_halo_unpack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
         L.mc_step.argtypes = [_VP, _VP, _VP, ctypes.c_double, _DP, _VP]
         L.mc_sweep.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP]
         L.mc_step_noalloc.argtypes = [P, _VP, _VP, ctypes.c_double, _DP, _VP]
@@ -202,6 +206,20 @@ class Context:
 
     def bc_fill(self, q_dev: int, stream: int = 0) -> None:
         check(lib().mc_bc_fill(self._h, _VP(q_dev), _VP(stream)))
+
+    def bc_fill_dir(self, q_dev: int, direction: int, stream: int = 0) -> None:
+        check(lib().mc_bc_fill_dir(self._h, _VP(q_dev), int(direction), _VP(stream)))
+
+    def halo_elems(self, side: int) -> int:
+        n = ctypes.c_int64(0)
+        check(lib().mc_halo_elems(ctypes.byref(self.problem), int(side), ctypes.byref(n)))
+        return n.value
+
+    def halo_pack(self, q_dev: int, side: int, buf_dev: int, stream: int = 0) -> None:
+        check(lib().mc_halo_pack(self._h, _VP(q_dev), int(side), _VP(buf_dev), _VP(stream)))
+
+    def halo_unpack(self, buf_dev: int, side: int, q_dev: int, stream: int = 0) -> None:
+        check(lib().mc_halo_unpack(self._h, _VP(buf_dev), int(side), _VP(q_dev), _VP(stream)))
 
     def step(self, q_in: int, q_out: int, dt: float, want_smax: bool = True, stream: int = 0):
         smax = ctypes.c_double(0.0)

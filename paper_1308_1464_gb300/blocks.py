@@ -1,0 +1,314 @@
+"""A grid decomposed into blocks, one block per rank, stepped block by block.
+
+The update of a cell reads cells up to two away, its diagonal neighbours
+included through the transverse terms (LeVeque 2002, §21.8), so a block
+needs, before every step, two ghost layers from the blocks beside it; the
+global boundary keeps its boundary kinds, and a periodic direction split
+over several blocks wraps from the last block to the first.  The step size
+of the whole grid follows from the largest wave speed over all blocks (the
+variable time-step rule of the paper's "dynamic time stepping", §1.2,
+Table 1), one max-reduction per step.
+
+The ghost fill runs in two phases, x then y, so that the corner ghosts of a
+block come out as in the single-grid fill: phase x exchanges the two columns
+next to each shared x side (interior rows) and fills the physical x sides;
+phase y then exchanges the two rows next to each shared y side across the
+full padded width, x ghost columns included, and fills the physical y sides.
+
+This module is marshalling and message passing only.  Packing, unpacking,
+ghost fills and steps are done by a block's ``ops`` (``DeviceBlockOps``: the
+library's kernels through the C ABI); messages go through a transport
+(``DistTransport``: torch.distributed point-to-point, one rank per block) or,
+for every block held by one process, through ``exchange_local``.
+"""
+from __future__ import annotations
+
+import copy
+from dataclasses import dataclass
+
+from . import BC_GIVEN, BC_PERIODIC, Context, McError, MC_EINVAL
+
+XLO, XHI, YLO, YHI = 0, 1, 2, 3
+
+
+def split(n: int, parts: int):
+    """Sizes and offsets of `parts` near-equal pieces of n cells (the first
+    n % parts pieces one cell larger)."""
+    base, extra = divmod(n, parts)
+    sizes = [base + (1 if k < extra else 0) for k in range(parts)]
+    offsets = [sum(sizes[:k]) for k in range(parts)]
+    return sizes, offsets
+
+
+@dataclass(frozen=True)
+class Extent:
+    i0: int
+    j0: int
+    mx: int
+    my: int
+
+
+class Decomposition:
+    """px x py blocks of a global problem; rank r is block (r % px, r // px)."""
+
+    def __init__(self, problem, px: int, py: int):
+        if px < 1 or py < 1:
+            raise ValueError("px and py must be positive")
+        if problem.mx < 2 * px or problem.my < 2 * py:
+            raise ValueError(f"{problem.mx} x {problem.my} cells cannot give {px} x {py} blocks "
+                             "of at least 2 x 2 cells")
+        self.problem = problem
+        self.px, self.py = px, py
+        self.nx, self.ox = split(problem.mx, px)
+        self.ny, self.oy = split(problem.my, py)
+
+    @property
+    def nblocks(self) -> int:
+        return self.px * self.py
+
+    def coords(self, rank: int):
+        return rank % self.px, rank // self.px
+
+    def rank_of(self, bx: int, by: int) -> int:
+        return by * self.px + bx
+
+    def extent(self, rank: int) -> Extent:
+        bx, by = self.coords(rank)
+        return Extent(self.ox[bx], self.oy[by], self.nx[bx], self.ny[by])
+
+    def neighbour(self, rank: int, side: int):
+        """Rank whose interior provides the ghosts on `side`, or None where
+        the side keeps the global boundary kind (a periodic direction of a
+        single block wraps onto itself through its own boundary kind)."""
+        bx, by = self.coords(rank)
+        n = self.px if side < 2 else self.py
+        b = bx if side < 2 else by
+        b += -1 if side % 2 == 0 else 1
+        if 0 <= b < n:
+            pass
+        elif self.problem.bc[side] == BC_PERIODIC and n > 1:
+            b %= n
+        else:
+            return None
+        return self.rank_of(b, by) if side < 2 else self.rank_of(bx, b)
+
+    def local_problem(self, rank: int):
+        """The block's problem: its own size, MC_BC_GIVEN on shared sides."""
+        e = self.extent(rank)
+        p = copy.copy(self.problem)
+        p.mx, p.my = e.mx, e.my
+        for side in range(4):
+            if self.neighbour(rank, side) is not None:
+                p.bc[side] = BC_GIVEN
+        return p
+
+    def messages(self, rank: int, direction: int):
+        """The halo messages of one phase (direction 0: x, 1: y).
+
+        sends: (side, dst) -- the strip next to `side` of this block, for the
+        ghosts on the opposite side of dst; recvs: (side, src) -- the ghosts
+        on `side`.  A message's tag is the receiving side.  Sends are listed
+        in decreasing side order and receives in increasing order: with two
+        blocks in a periodic direction both sides of a block face the same
+        peer, and transports without tags match the messages of a pair in
+        posting order, which these orders keep consistent."""
+        sides = (2 * direction, 2 * direction + 1)
+        sends = [(s, self.neighbour(rank, s)) for s in reversed(sides)
+                 if self.neighbour(rank, s) is not None]
+        recvs = [(s, self.neighbour(rank, s)) for s in sides if self.neighbour(rank, s) is not None]
+        return sends, recvs
+
+
+class Block:
+    """One rank's block: its problem, its ops, and the halo buffers."""
+
+    def __init__(self, decomp: Decomposition, rank: int, ops):
+        self.decomp = decomp
+        self.rank = rank
+        self.ops = ops
+        self.problem = decomp.local_problem(rank)
+        self._send = {s: ops.alloc(ops.halo_elems(s)) for s in range(4)
+                      if decomp.neighbour(rank, s) is not None}
+        self._recv = {s: ops.alloc(ops.halo_elems(s)) for s in range(4)
+                      if decomp.neighbour(rank, s) is not None}
+
+    def outgoing(self, q, direction: int):
+        """Pack the strips of one phase: [(dst, tag, buffer)]."""
+        sends, _ = self.decomp.messages(self.rank, direction)
+        out = []
+        for side, dst in sends:
+            buf = self._send[side]
+            self.ops.pack(q, side, buf)
+            out.append((dst, side ^ 1, buf))
+        return out
+
+    def incoming(self, direction: int):
+        """Receive buffers of one phase: [(src, tag, buffer)]."""
+        _, recvs = self.decomp.messages(self.rank, direction)
+        return [(src, side, self._recv[side]) for side, src in recvs]
+
+    def finish(self, q, direction: int) -> None:
+        """Unpack the received strips of one phase, then fill the physical
+        sides of that direction."""
+        _, recvs = self.decomp.messages(self.rank, direction)
+        for side, _ in recvs:
+            self.ops.unpack(self._recv[side], side, q)
+        self.ops.fill_dir(q, direction)
+
+
+def exchange(block: Block, q, transport) -> None:
+    """The two-phase ghost fill of one rank's block."""
+    for direction in (0, 1):
+        out = block.outgoing(q, direction)
+        inc = block.incoming(direction)
+        transport.exchange(out, inc)
+        block.finish(q, direction)
+
+
+def exchange_local(blocks, qs) -> None:
+    """The two-phase ghost fill of every block, all held by this process."""
+    for direction in (0, 1):
+        mail = {}
+        for b, q in zip(blocks, qs):
+            for dst, tag, buf in b.outgoing(q, direction):
+                mail[(b.rank, dst, tag)] = buf
+        for b, q in zip(blocks, qs):
+            for src, tag, buf in b.incoming(direction):
+                b.ops.copy(mail.pop((src, b.rank, tag)), buf)
+            b.finish(q, direction)
+        if mail:
+            raise RuntimeError(f"unmatched halo messages: {sorted(mail)}")
+
+
+class Stepper:
+    """Steps of a decomposed grid with one global time step.
+
+    `blocks` are the blocks this process holds (one per rank with a
+    transport, or all of them with ``transport=None``); states are passed as
+    lists in the same order."""
+
+    def __init__(self, blocks, transport=None):
+        self.blocks = list(blocks)
+        self.transport = transport
+        if transport is not None and len(self.blocks) != 1:
+            raise ValueError("a transport serves one block per rank")
+
+    def fill(self, qs) -> None:
+        if self.transport is None:
+            exchange_local(self.blocks, qs)
+        else:
+            exchange(self.blocks[0], qs[0], self.transport)
+
+    def _max(self, values) -> float:
+        v = max(values)
+        return v if self.transport is None else self.transport.max(v)
+
+    def max_cell_speed(self, qs) -> float:
+        return self._max([b.ops.max_speed(q) for b, q in zip(self.blocks, qs)])
+
+    def step(self, qs_in, qs_out, dt: float) -> float:
+        """One step of every block with dt; returns the global smax of the
+        step's waves (Courant number = dt * smax)."""
+        self.fill(qs_in)
+        return self._max([b.ops.step(qi, qo, dt) for b, qi, qo in zip(self.blocks, qs_in, qs_out)])
+
+    def advance(self, qa, qb, nsteps: int, cfl_desired: float, cfl_max: float, t: float = 0.0,
+                dt: float | None = None):
+        """nsteps accepted steps with the variable time-step rule: an attempt
+        whose Courant number exceeds cfl_max is retaken with
+        dt = cfl_desired / smax; an accepted one proposes that dt for the
+        next.  Returns (t, dt, result_in_b, nrejected)."""
+        if dt is None:
+            dt = cfl_desired / self.max_cell_speed(qa)
+        cur, nxt = qa, qb
+        in_b, nacc, nrej = False, 0, 0
+        while nacc < nsteps:
+            if nacc + nrej > 100 * nsteps + 100:
+                raise McError(MC_EINVAL, "too many rejected steps")
+            smax = self.step(cur, nxt, dt)
+            if smax > 0 and dt * smax > cfl_max:
+                nrej += 1
+            else:
+                t += dt
+                nacc += 1
+                cur, nxt = nxt, cur
+                in_b = not in_b
+            if smax > 0:
+                dt = cfl_desired / smax
+        return t, dt, in_b, nrej
+
+
+class DistTransport:
+    """Halo messages and the speed maximum over torch.distributed (one rank
+    per block).  With the gloo backend device buffers are staged through
+    host memory; NCCL sends device buffers directly."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.backend = dist.get_backend(group)
+
+    def _stage(self, t):
+        return t.cpu() if (self.backend == "gloo" and t.is_cuda) else t
+
+    def exchange(self, sends, recvs) -> None:
+        import torch
+        dist = self.dist
+        if not sends and not recvs:
+            return
+        staged = [(src, tag, buf, self._stage(torch.empty_like(buf)) if buf.is_cuda and
+                   self.backend == "gloo" else buf) for src, tag, buf in recvs]
+        ops = [dist.P2POp(dist.isend, self._stage(buf), dst, self.group, tag)
+               for dst, tag, buf in sends]
+        ops += [dist.P2POp(dist.irecv, host, src, self.group, tag) for src, tag, _, host in staged]
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+        for _, _, buf, host in staged:
+            if host is not buf:
+                buf.copy_(host)
+
+    def max(self, value: float) -> float:
+        import torch
+        dist = self.dist
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=self.group)
+        return float(t.item())
+
+
+class DeviceBlockOps:
+    """A block's packing, unpacking, ghost fills and steps: the library's
+    kernels through the C ABI.  States are device addresses; halo buffers
+    are torch tensors on the context's device."""
+
+    def __init__(self, ctx: Context, stream: int = 0):
+        import torch
+        self.ctx = ctx
+        self.stream = stream
+        self.dtype = torch.float64 if ctx.layout.elem_bytes == 8 else torch.float32
+
+    def halo_elems(self, side: int) -> int:
+        return self.ctx.halo_elems(side)
+
+    def alloc(self, n: int):
+        import torch
+        return torch.empty(int(n), dtype=self.dtype, device="cuda")
+
+    def copy(self, src, dst) -> None:
+        dst.copy_(src)
+
+    def pack(self, q: int, side: int, buf) -> None:
+        self.ctx.halo_pack(q, side, buf.data_ptr(), self.stream)
+
+    def unpack(self, buf, side: int, q: int) -> None:
+        self.ctx.halo_unpack(buf.data_ptr(), side, q, self.stream)
+
+    def fill_dir(self, q: int, direction: int) -> None:
+        self.ctx.bc_fill_dir(q, direction, self.stream)
+
+    def step(self, q_in: int, q_out: int, dt: float) -> float:
+        return self.ctx.step(q_in, q_out, dt, True, self.stream)
+
+    def max_speed(self, q: int) -> float:
+        return self.ctx.max_cell_speed(q, self.stream)

@@ -217,6 +217,10 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
     if (npatch < 0 || npatch > 4096) return set_error(MC_EINVAL, "npatch out of range");
     if (coarse->solver == MC_ACOUSTICS_VAR)
         return set_error(MC_ENOTSUP, "refined patches do not carry material planes");
+    for (int k = 0; k < 4; k++)
+        if (coarse->bc[k] == MC_BC_GIVEN)
+            return set_error(MC_EINVAL, "the coarse grid's ghosts must come from its boundary kinds "
+                             "(MC_BC_GIVEN sides need a fill before every coarse step)");
     mc_layout clay;
     mc_status st = mc_layout_of(coarse, &clay);
     if (st != MC_OK) return st;

@@ -65,8 +65,11 @@ static mc_status validate(const mc_problem* p)
         return set_error(MC_EINVAL, "transverse must be 0, 1 or 2");
     if (p->efix != 0 && p->efix != 1) return set_error(MC_EINVAL, "efix must be 0 or 1");
     for (int k = 0; k < 4; k++)
-        if (p->bc[k] < MC_BC_PERIODIC || p->bc[k] > MC_BC_WALL)
+        if (p->bc[k] < MC_BC_PERIODIC || p->bc[k] > MC_BC_GIVEN)
             return set_error(MC_EINVAL, "unknown boundary kind %d on side %d", p->bc[k], k);
+    for (int k = 0; k < 4; k++)
+        if (p->bc[k] == MC_BC_GIVEN && (p->mx < 2 || p->my < 2))
+            return set_error(MC_EINVAL, "a grid with caller-filled ghost sides needs at least 2 x 2 cells");
     if ((p->bc[0] == MC_BC_PERIODIC) != (p->bc[1] == MC_BC_PERIODIC) ||
         (p->bc[2] == MC_BC_PERIODIC) != (p->bc[3] == MC_BC_PERIODIC))
         return set_error(MC_EINVAL, "periodic boundaries must be paired");
@@ -133,9 +136,22 @@ static cudaError_t maxspeed_launch(const mc_problem& p, const mc_layout& lay, co
     }
 }
 
+static bool has_given_side(const mc_problem& p)
+{
+    for (int k = 0; k < 4; k++)
+        if (p.bc[k] == MC_BC_GIVEN) return true;
+    return false;
+}
+
 cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
                       const int* cur_dev, cudaStream_t s)
 {
+    if (has_given_side(p)) {
+        // leave the caller's sides alone: x ghosts of the interior rows, then
+        // y ghosts across the full width, physical sides only
+        cudaError_t e = bc_dir_launch(p, lay, qa, qb, cur_dev, 0, s);
+        return e == cudaSuccess ? bc_dir_launch(p, lay, qa, qb, cur_dev, 1, s) : e;
+    }
     const long long total = 4LL * (p.mx + 4) + 4LL * p.my;
     int blocks = int((total + 255) / 256);
     if (blocks > 2048) blocks = 2048;
@@ -449,6 +465,45 @@ mc_status mc_bc_fill(mc_ctx* c, void* q, void* stream)
     return e == cudaSuccess ? MC_OK : cuda_error(e, "ghost fill launch");
 }
 
+mc_status mc_bc_fill_dir(mc_ctx* c, void* q, int32_t dir, void* stream)
+{
+    if (!c || !q) return set_error(MC_EINVAL, "NULL argument");
+    if (dir != 0 && dir != 1) return set_error(MC_EINVAL, "direction must be 0 (x) or 1 (y)");
+    cudaError_t e = bc_dir_launch(c->p, c->lay, q, q, nullptr, dir, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "directional ghost fill launch");
+}
+
+mc_status mc_halo_elems(const mc_problem* p, int32_t side, int64_t* elems)
+{
+    if (!elems) return set_error(MC_EINVAL, "NULL argument");
+    mc_status st = validate(p);
+    if (st != MC_OK) return st;
+    if (side < 0 || side > 3) return set_error(MC_EINVAL, "side must be 0..3");
+    if (p->mx < 2 || p->my < 2) return set_error(MC_EINVAL, "halo strips need at least 2 x 2 cells");
+    *elems = halo_elems(*p, side);
+    return MC_OK;
+}
+
+static mc_status halo_call(mc_ctx* c, const void* src, void* dst, int32_t side, bool pack,
+                           void* stream)
+{
+    if (!c || !src || !dst) return set_error(MC_EINVAL, "NULL argument");
+    if (side < 0 || side > 3) return set_error(MC_EINVAL, "side must be 0..3");
+    if (c->p.mx < 2 || c->p.my < 2) return set_error(MC_EINVAL, "halo strips need at least 2 x 2 cells");
+    cudaError_t e = halo_launch(c->p, c->lay, src, dst, side, pack, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, pack ? "halo pack launch" : "halo unpack launch");
+}
+
+mc_status mc_halo_pack(mc_ctx* c, const void* q, int32_t side, void* buf, void* stream)
+{
+    return halo_call(c, q, buf, side, true, stream);
+}
+
+mc_status mc_halo_unpack(mc_ctx* c, const void* buf, int32_t side, void* q, void* stream)
+{
+    return halo_call(c, buf, q, side, false, stream);
+}
+
 static mc_status read_status(mc_ctx* c, DevState* h, cudaStream_t s)
 {
     cudaError_t e = cudaMemcpyAsync(h, c->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s);
@@ -622,6 +677,9 @@ mc_status mc_advance(mc_ctx* c, void* qa, void* qb, int nsteps, double cfl_desir
     if (!c || !qa || !qb || !t_inout || !dt_inout || !result_in_b)
         return set_error(MC_EINVAL, "NULL argument");
     if (qa == qb) return set_error(MC_EINVAL, "qa and qb must differ");
+    if (has_given_side(c->p))
+        return set_error(MC_EINVAL, "sides of kind MC_BC_GIVEN need their ghosts written before "
+                         "every step: use mc_step");
     if (nsteps < 0 || nsteps > 1000000) return set_error(MC_EINVAL, "nsteps out of range");
     if (!(cfl_desired > 0.0) || !(cfl_max >= cfl_desired))
         return set_error(MC_EINVAL, "need 0 < cfl_desired <= cfl_max");

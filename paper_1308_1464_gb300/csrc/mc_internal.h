@@ -101,6 +101,13 @@ cudaError_t maxspeed_launch_euler_godunov(const mc_problem& p, const mc_layout& 
 cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
                       const int* cur_dev, cudaStream_t s);
 
+// halo strips and directional ghost fills of a decomposed grid's block (mc_halo.cu)
+long long halo_elems(const mc_problem& p, int side);
+cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* src, void* dst,
+                        int side, bool pack, cudaStream_t s);
+cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
+                          const int* cur_dev, int dir, cudaStream_t s);
+
 int ntasks_for(const mc_problem& p, int tile_rows, int* nbands);
 
 // error reporting

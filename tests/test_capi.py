@@ -52,7 +52,8 @@ def test_layout(L):
     dict(solver=7), dict(solver=0), dict(dtype=3), dict(mx=0), dict(my=-1), dict(limiter=5),
     dict(limiter=-1), dict(order=3), dict(transverse=3),
     dict(bc=(mc.BC_PERIODIC, mc.BC_WALL, 0, 0)), dict(dx=0.0), dict(param=(0.0, 0, 0, 0)),
-    dict(solver=mc.EULER_ROE, param=(1.0, 0, 0, 0)),
+    dict(solver=mc.EULER_ROE, param=(1.0, 0, 0, 0)), dict(bc=(4, 2, 2, 2)),
+    dict(mx=1, bc=(mc.BC_GIVEN, mc.BC_WALL, mc.BC_WALL, mc.BC_WALL)),
 ])
 def test_invalid_problems_rejected(L, kw):
     p = base_problem(**kw)
@@ -73,3 +74,17 @@ def test_null_arguments(L):
     assert L.mc_layout_of(None, None) == mc.MC_EINVAL
     assert L.mc_step(None, None, None, 0.1, None, None) == mc.MC_EINVAL
     assert L.mc_destroy(None) == mc.MC_OK
+
+
+def test_halo_strip_sizes(L):
+    """Strips of a block: two interior columns by my rows (x sides), two rows
+    across the padded width mx + 4 (y sides), all planes."""
+    p = base_problem(mx=30, my=7, bc=(mc.BC_GIVEN, mc.BC_WALL, mc.BC_GIVEN, mc.BC_GIVEN))
+    mc.layout_of(p)
+    n = ctypes.c_int64()
+    for side, want in ((0, 3 * 7 * 2), (1, 3 * 7 * 2), (2, 3 * 2 * 34), (3, 3 * 2 * 34)):
+        assert L.mc_halo_elems(ctypes.byref(p), side, ctypes.byref(n)) == mc.MC_OK
+        assert n.value == want
+    assert L.mc_halo_elems(ctypes.byref(p), 4, ctypes.byref(n)) == mc.MC_EINVAL
+    assert L.mc_halo_pack(None, None, 0, None, None) == mc.MC_EINVAL
+    assert L.mc_bc_fill_dir(None, None, 0, None) == mc.MC_EINVAL

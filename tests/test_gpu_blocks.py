@@ -1,0 +1,229 @@
+"""Blocks of a decomposed grid on the GPU: halo strips, directional ghost
+fills, and decomposed runs against the single grid.
+
+* mc_halo_pack / mc_halo_unpack move exactly the cells the strip layout
+  names (compared with slices of the downloaded array, bit for bit);
+* mc_bc_fill_dir(0) then (1) equals mc_bc_fill, and with MC_BC_GIVEN sides
+  the fill equals the oracle's, which leaves those sides alone;
+* a run over 2 x 2 and 3 x 2 blocks exchanging halos in one process equals
+  the single-grid run of the same kernels bit for bit (every cell reads the
+  same values; the global smax is the maximum of the same edge speeds), and
+  the oracle within the parity tolerance;
+* two gloo ranks on this one GPU, exchanging host-staged strips through
+  torch.distributed, give the same bits.  Their kernels never wait on each
+  other: every exchange is a host-side send and receive between launches.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1308_1464_gb300 as mc
+from gpu_util import TOL, embed, initial_state, problems, scaled_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1308_1464_gb300.blocks import (Block, Decomposition, DeviceBlockOps,  # noqa: E402
+                                          DistTransport, Stepper)
+from paper_1308_1464_gb300.state import DeviceState  # noqa: E402
+
+P, X, W, G = mc.BC_PERIODIC, mc.BC_EXTRAP, mc.BC_WALL, mc.BC_GIVEN
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1308_1464_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def random_state(ctx, seed):
+    """A state whose every element (ghosts and padding too) is random."""
+    s = DeviceState(ctx)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    vals = torch.rand(s.buf.numel() // (8 if s.t_dtype == torch.float64 else 4), generator=g,
+                      dtype=torch.float64) + 0.5
+    s.buf.view(s.t_dtype).copy_(vals.to(s.t_dtype).cuda())
+    return s
+
+
+@pytest.mark.parametrize("dtype", [mc.F32, mc.F64])
+def test_halo_strips(dtype):
+    mx, my = 37, 9
+    p, _ = problems("euler", mx, my, 0.1, 0.1, dtype, (G, G, G, G))
+    with mc.Context(p) as ctx:
+        s = random_state(ctx, 1)
+        full = s.with_ghosts()                                  # (meqn, my + 4, mx + 4)
+        for side in range(4):
+            n = ctx.halo_elems(side)
+            buf = torch.empty(n, dtype=s.t_dtype, device="cuda")
+            ctx.halo_pack(s.ptr, side, buf.data_ptr())
+            if side < 2:
+                cols = slice(2, 4) if side == 0 else slice(mx, mx + 2)
+                want = full[:, 2:2 + my, cols]
+            else:
+                rows = slice(2, 4) if side == 2 else slice(my, my + 2)
+                want = full[:, rows, :]
+            assert n == want.size
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(buf.cpu().numpy().reshape(want.shape), want)
+        # unpack fresh strips into the ghosts, nothing else changes
+        t = random_state(ctx, 2)
+        before = t.with_ghosts()
+        expect = before.copy()
+        for side in range(4):
+            n = ctx.halo_elems(side)
+            strip = (torch.arange(n, dtype=torch.float64) * 0.25 + side).to(s.t_dtype)
+            ctx.halo_unpack(strip.cuda().data_ptr(), side, t.ptr)
+            torch.cuda.synchronize()
+            if side < 2:
+                cols = slice(0, 2) if side == 0 else slice(mx + 2, mx + 4)
+                expect[:, 2:2 + my, cols] = strip.numpy().reshape(expect[:, 2:2 + my, cols].shape)
+            else:
+                rows = slice(0, 2) if side == 2 else slice(my + 2, my + 4)
+                expect[:, rows, :] = strip.numpy().reshape(expect[:, rows, :].shape)
+        np.testing.assert_array_equal(t.with_ghosts(), expect)
+
+
+@pytest.mark.parametrize("bc", [(P, P, P, P), (W, X, P, P), (X, W, W, X), (W, W, W, W)])
+@pytest.mark.parametrize("dtype", [mc.F32, mc.F64])
+def test_directional_fill_equals_fill(bc, dtype):
+    p, _ = problems("swe", 23, 14, 0.1, 0.1, dtype, bc)
+    with mc.Context(p) as ctx:
+        a, b = random_state(ctx, 3), random_state(ctx, 3)
+        ctx.bc_fill(a.ptr)
+        ctx.bc_fill_dir(b.ptr, 0)
+        ctx.bc_fill_dir(b.ptr, 1)
+        np.testing.assert_array_equal(a.with_ghosts(), b.with_ghosts())
+
+
+@pytest.mark.parametrize("bc", [(G, W, X, G), (G, G, P, P), (P, P, G, W), (G, G, G, G)])
+def test_fill_leaves_given_sides(bc):
+    p, op = problems("swe", 19, 12, 0.1, 0.1, mc.F64, bc)
+    with mc.Context(p) as ctx:
+        a = random_state(ctx, 4)
+        before = a.with_ghosts()
+        ctx.bc_fill(a.ptr)
+        want = oracle.bc_fill(op, before)                      # GIVEN sides untouched
+        np.testing.assert_array_equal(a.with_ghosts(), want)
+
+
+def test_given_sides_rejected_where_unsupported():
+    p, _ = problems("swe", 16, 16, 0.1, 0.1, mc.F32, (G, W, W, W))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        with pytest.raises(mc.McError):
+            ctx.advance(a.ptr, b.ptr, 1, 0.9, 1.0, 0.0, 1e-3)
+    narrow, _ = problems("swe", 1, 8, 0.1, 0.1, mc.F32, (G, W, W, W))
+    with pytest.raises(mc.McError):
+        mc.Context(narrow)                                     # a strip needs two columns
+
+
+def single_grid(p, q, nsteps, cfl=0.8):
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(q)
+        dt = cfl / ctx.max_cell_speed(a.ptr)
+        t, dt, in_b, nrej = ctx.advance(a.ptr, b.ptr, nsteps, cfl, 1.0, 0.0, dt)
+        return (b if in_b else a).download(), t
+
+
+def decomposed(p, q, px, py, nsteps, cfl=0.8):
+    d = Decomposition(p, px, py)
+    ctxs = [mc.Context(d.local_problem(r)) for r in range(d.nblocks)]
+    blocks = [Block(d, r, DeviceBlockOps(c)) for r, c in enumerate(ctxs)]
+    qa, qb = [], []
+    for r, c in enumerate(ctxs):
+        e = d.extent(r)
+        a, b = DeviceState(c).zero_(), DeviceState(c).zero_()
+        a.upload(q[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx])
+        qa.append(a)
+        qb.append(b)
+    t, dt, in_b, nrej = Stepper(blocks).advance([s.ptr for s in qa], [s.ptr for s in qb],
+                                                nsteps, cfl, 1.0)
+    out = np.zeros(q.shape, dtype=qa[0].np_dtype)
+    for r in range(d.nblocks):
+        e = d.extent(r)
+        out[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx] = (qb[r] if in_b else qa[r]).download()
+    for c in ctxs:
+        c.close()
+    return out, t
+
+
+CASES = [
+    ("swe", mc.F32, (W, W, W, W), 2, 2, 1),
+    ("swe", mc.F32, (P, P, W, X), 3, 2, 1),
+    ("euler", mc.F32, (X, X, X, X), 2, 3, 2),
+    ("euler", mc.F64, (P, P, P, P), 2, 2, 1),
+    ("acoustics", mc.F64, (P, P, P, P), 3, 3, 1),
+    ("advection", mc.F32, (P, P, X, W), 2, 2, 0),
+]
+
+
+@pytest.mark.parametrize("solver,dtype,bc,px,py,trans", CASES)
+def test_blocks_equal_single_grid(solver, dtype, bc, px, py, trans):
+    mx, my, nsteps = 75, 61, 4
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, op = problems(solver, mx, my, dx, dy, dtype, bc, transverse=trans)
+    qin = q.astype(np.float64 if dtype == mc.F64 else np.float32)
+    want, t_want = single_grid(p, qin, nsteps)
+    got, t = decomposed(p, qin, px, py, nsteps)
+    assert t == t_want
+    np.testing.assert_array_equal(got, want)
+    ref, _, _, _, flags = oracle.advance(op, embed(op, qin.astype(np.float64)), nsteps, 0.8, 1.0, 0.0,
+                                         0.8 / oracle.max_cell_speed(op, embed(op, qin.astype(np.float64))))
+    assert scaled_error(solver, got.astype(np.float64), ref[:, 2:-2, 2:-2]) <= TOL[dtype] * nsteps
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, args, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    solver, dtype, bc, px, py, mx, my, nsteps = args
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, _ = problems(solver, mx, my, dx, dy, dtype, bc)
+    qin = q.astype(np.float64 if dtype == mc.F64 else np.float32)
+    d = Decomposition(p, px, py)
+    e = d.extent(rank)
+    with mc.Context(d.local_problem(rank)) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx])
+        st = Stepper([Block(d, rank, DeviceBlockOps(ctx))], DistTransport())
+        t, dt, in_b, nrej = st.advance([a.ptr], [b.ptr], nsteps, 0.8, 1.0)
+        out[rank] = ((b if in_b else a).download(), t)
+    dist.destroy_process_group()
+
+
+def test_gloo_ranks_on_one_gpu_equal_single_grid():
+    import torch.multiprocessing as mp
+    solver, dtype, bc, px, py, mx, my, nsteps = "swe", mc.F32, (P, P, W, W), 2, 1, 64, 40, 3
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank, args=(2, _free_port(), (solver, dtype, bc, px, py, mx, my, nsteps), out),
+             nprocs=2, join=True)
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, _ = problems(solver, mx, my, dx, dy, dtype, bc)
+    want, t_want = single_grid(p, q.astype(np.float32), nsteps)
+    d = Decomposition(p, px, py)
+    got = np.zeros_like(want)
+    for r in range(2):
+        e = d.extent(r)
+        got[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx] = out[r][0]
+        assert out[r][1] == t_want
+    np.testing.assert_array_equal(got, want)
