@@ -241,6 +241,7 @@ struct mc_ctx {
     std::vector<GraphEntry> graphs;
     int next_slot;
     const mc_mlp* seed_net = nullptr;   // pressure seeds of the exact-solution solver, or none
+    int sms = 0;                        // SMs of the context's device
 };
 
 // the context's extras for every fused-step launch
@@ -248,6 +249,7 @@ static void launch_extras(const mc_ctx* c, SweepLaunch& L)
 {
     L.seed_net = c->seed_net ? c->seed_net->dev : nullptr;
     L.newton = c->dev->newton;
+    L.sms = c->sms;
 }
 
 static void drop_graphs(mc_ctx* c)
@@ -345,6 +347,12 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
     c->p = *p;
     layout_unchecked(p, &c->lay);
     c->tile_rows = default_tile_rows(*p);
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            c->sms = 0;
+    }
     cudaError_t e = cudaMalloc(&c->dev, sizeof(DevState));
     if (e != cudaSuccess) {
         delete c;

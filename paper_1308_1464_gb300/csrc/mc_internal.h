@@ -43,6 +43,7 @@ struct SweepLaunch {
     cudaStream_t stream;
     const void* seed_net = nullptr;            // MlpDev of a pressure-seed network (SEEDED solvers)
     unsigned long long* newton = nullptr;      // Newton update / solve counters, or null
+    int sms = 0;                               // SMs of the device (0: unknown, full CTAs)
 };
 
 // One launch of the fused step over many grids (mc_multi.cuh); grids and

@@ -705,10 +705,13 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     }
     __syncwarp();
 
+    // warps per CTA: SWEEP_WARPS, or fewer to spread a small grid's tasks
+    // over more SMs
+    const int nw = blockDim.x >> 5;
     bool failed = false, bad = false;
     T smx = T(0), smy = T(0);
-    for (int task = blockIdx.x * SWEEP_WARPS + warp; task < a.ntasks && !failed && map_ok;
-         task += gridDim.x * SWEEP_WARPS) {
+    for (int task = blockIdx.x * nw + warp; task < a.ntasks && !failed && map_ok;
+         task += gridDim.x * nw) {
         const int i0 = (task % a.nbands) * BAND_W;
         const int j0 = (task / a.nbands) * a.tile_rows;
         const int jend = min(j0 + a.tile_rows, a.my);

@@ -51,12 +51,19 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.newton_updates = RP::SEEDED ? L.newton : nullptr;
 
     const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (a.net ? seednet_smem_bytes() : 0);
-    int blocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
+    // a grid with fewer tasks than SWEEP_WARPS per SM gets smaller CTAs, so
+    // that its warps land on separate SMs instead of sharing a few
+    int wpb = SWEEP_WARPS;
+    if (L.sms > 0 && a.ntasks < L.sms * SWEEP_WARPS) {
+        wpb = (a.ntasks + L.sms - 1) / L.sms;
+        if (wpb < 1) wpb = 1;
+    }
+    int blocks = (a.ntasks + wpb - 1) / wpb;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
     if (is_fast_scheme(L.prob))
-        ctu_sweep_kernel<RP, true><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+        ctu_sweep_kernel<RP, true><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
     else
-        ctu_sweep_kernel<RP, false><<<blocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+        ctu_sweep_kernel<RP, false><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
     return cudaGetLastError();
 }
 
