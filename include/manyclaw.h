@@ -418,11 +418,17 @@ typedef struct mc_train_cfg {
     float lr, beta1, beta2, eps;   /* Adam (Kingma & Ba 2015) */
     uint64_t seed;          /* per-epoch row order */
     int32_t fit_norm;       /* 1: set mu/sigma from the features first */
+    float clip;             /* >= 1: a step's gradient is scaled down to at most clip
+                             * times the running mean of the (clipped) gradient
+                             * norms; 0: no clipping */
+    float lr_final;         /* learning rate of the last step: cosine decay from lr
+                             * over the call's steps (lr_final = lr: constant) */
 } mc_train_cfg;
 
 /* Trains the network on n rows (device features n x 10, targets n) with
- * minibatch Adam on the GPU (the same kernels as mc_mlp_grad).  Rows with a
- * non-finite feature or target are skipped.  Each epoch visits the rows in
+ * minibatch Adam on the GPU (the same kernels as mc_mlp_grad), optionally
+ * clipping each step's gradient norm and decaying the learning rate (see
+ * mc_train_cfg).  Rows with a non-finite feature or target are skipped.  Each epoch visits the rows in
  * the order i -> (a i + b) mod n with a coprime to n drawn from seed.
  * loss_per_epoch (host, nullable): mean loss of each epoch.  Synchronous. */
 mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const float* target,

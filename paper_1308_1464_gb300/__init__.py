@@ -277,7 +277,8 @@ MLP_NPARAM = MLP_NWEIGHT + 20
 class TrainCfg(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("epochs", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("fit_norm", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("fit_norm", ctypes.c_int32), ("clip", ctypes.c_float),
+                ("lr_final", ctypes.c_float)]
 
 
 class SeedNet:
@@ -318,8 +319,10 @@ class SeedNet:
 
     def train(self, n: int, features: int, target: int, batch: int = 8192, epochs: int = 10,
               lr: float = 2e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
-              seed: int = 1, fit_norm: bool = True, loss_out: int = 0, stream: int = 0) -> None:
-        cfg = TrainCfg(int(batch), int(epochs), lr, beta1, beta2, eps, int(seed), int(fit_norm))
+              seed: int = 1, fit_norm: bool = True, loss_out: int = 0, stream: int = 0,
+              clip: float = 2.0, lr_final: float | None = None) -> None:
+        cfg = TrainCfg(int(batch), int(epochs), lr, beta1, beta2, eps, int(seed), int(fit_norm),
+                       float(clip), float(lr if lr_final is None else lr_final))
         check(lib().mc_mlp_train(self._h, int(n), _VP(features), _VP(target), ctypes.byref(cfg),
                                  _VP(loss_out) if loss_out else None, _VP(stream)))
 

@@ -308,15 +308,48 @@ __global__ void zero_grad_kernel(MlpDev* d)
     if (blockIdx.x == 0 && threadIdx.x == 0) d->loss_sum = 0.0;
 }
 
-// Adam (Kingma & Ba 2015) on the FP32 master weights; also folds the step's
-// loss into the epoch total
+// Gradient clipping against the running mean of the gradient norms: a step
+// whose norm exceeds clip times that mean is scaled down to it, so that a
+// minibatch dominated by a few extreme rows (near-vacuum interfaces, whose
+// two-rarefaction guess collapses) cannot throw the weights far; the mean
+// follows the clipped norms (weight 0.01 per step).  One block.
+__global__ void clip_kernel(MlpDev* d, float clip)
+{
+    __shared__ float part[256];
+    float s = 0.f;
+    for (int k = threadIdx.x; k < MC_MLP_NWEIGHT; k += blockDim.x) s += d->grad[k] * d->grad[k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float norm = sqrtf(part[0]);
+        if (!isfinite(norm)) {
+            d->gscale = 0.f;               // a non-finite gradient is dropped
+            return;
+        }
+        float scale = 1.f, kept = norm;
+        if (d->gnorm_mean > 0.f && norm > clip * d->gnorm_mean) {
+            kept = clip * d->gnorm_mean;
+            scale = kept / norm;
+        }
+        d->gnorm_mean = d->gnorm_mean > 0.f ? 0.99f * d->gnorm_mean + 0.01f * kept : norm;
+        d->gscale = scale;
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights, on the gradient times
+// gscale; also folds the step's loss into the epoch total
 __global__ void adam_kernel(MlpDev* d, float lr, float b1, float b2, float eps, int t)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) d->loss_epoch += d->loss_sum;
     const float c1 = 1.f - powf(b1, float(t)), c2 = 1.f - powf(b2, float(t));
+    const float gs = d->gscale;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < MC_MLP_NWEIGHT;
          k += blockDim.x * gridDim.x) {
-        const float gr = d->grad[k];
+        const float gr = d->grad[k] * gs;
         const float m = b1 * d->adam_m[k] + (1.f - b1) * gr;
         const float v = b2 * d->adam_v[k] + (1.f - b2) * gr * gr;
         d->adam_m[k] = m;
@@ -433,6 +466,8 @@ mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const floa
     if (!(cfg->lr > 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
         !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
         return set_error(MC_EINVAL, "invalid Adam parameters");
+    if (!(cfg->clip == 0.f || cfg->clip >= 1.f) || !(cfg->lr_final > 0.f && cfg->lr_final <= cfg->lr))
+        return set_error(MC_EINVAL, "need clip = 0 or >= 1 and 0 < lr_final <= lr");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     if (cfg->fit_norm) {
@@ -456,6 +491,11 @@ mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const floa
     if (e != cudaSuccess) return cuda_error(e, "reading optimiser state");
     const long long batch = cfg->batch < n ? cfg->batch : n;
     const long long steps = (n + batch - 1) / batch;
+    const long long total = steps * cfg->epochs;
+    long long done = 0;
+    const float one = 1.f;
+    e = cudaMemcpyAsync(&net->dev->gscale, &one, sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "training set-up");
     uint64_t rs = cfg->seed * 0x9E3779B97F4A7C15ull + 1;
     for (int ep = 0; ep < cfg->epochs; ep++) {
         // row order of this epoch: k -> (a k + b) mod n with gcd(a, n) = 1
@@ -484,7 +524,13 @@ mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const floa
             e = train_launch(net->dev, a, s);
             if (e != cudaSuccess) return cuda_error(e, "training step");
             t++;
-            adam_kernel<<<(MC_MLP_NWEIGHT + 255) / 256, 256, 0, s>>>(net->dev, cfg->lr, cfg->beta1,
+            if (cfg->clip > 0.f) clip_kernel<<<1, 256, 0, s>>>(net->dev, cfg->clip);
+            // cosine decay from lr to lr_final over the steps of this call
+            const double frac = total > 1 ? double(done) / double(total - 1) : 1.0;
+            const float lr = float(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) *
+                                                       (1.0 + cos(3.141592653589793 * frac)));
+            done++;
+            adam_kernel<<<(MC_MLP_NWEIGHT + 255) / 256, 256, 0, s>>>(net->dev, lr, cfg->beta1,
                                                                      cfg->beta2, cfg->eps, t);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = mlp_pack(net->dev, s);

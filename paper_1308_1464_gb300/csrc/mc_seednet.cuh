@@ -33,6 +33,8 @@ struct MlpDev {
     double loss_sum;      // sum of squared residuals of the last gradient
     double loss_epoch;    // ... accumulated over an epoch by the optimiser
     int adam_t;
+    float gnorm_mean;     // running mean of the clipped gradient norms (0: none yet)
+    float gscale;         // factor the optimiser applies to the current gradient
 };
 
 // Rebuilds the BF16 weight copies from the FP32 parameters (mc_exact.cu).

@@ -27,8 +27,11 @@ def initial_params(mc, seed: int = 0) -> np.ndarray:
 
 
 def train_seed_net(ntrain: int = 1 << 22, epochs: int = 12, gamma: float = 1.4, offset: int = 1 << 26,
-                   batch: int = 16384, lr: float = 2e-3, seed: int = 3):
-    """-> (SeedNet, per-epoch losses, training seconds)."""
+                   batch: int = 16384, lr: float = 2e-3, seed: int = 3, clip: float = 2.0,
+                   lr_final: float = 4e-5):
+    """-> (SeedNet, per-epoch losses, training seconds).  Adam with each
+    step's gradient norm clipped to `clip` times its running mean and the
+    learning rate decayed from lr to lr_final (cosine)."""
     import torch
     import paper_1308_1464_gb300 as mc
     from paper_1308_1464_gb300 import workloads
@@ -50,6 +53,6 @@ def train_seed_net(ntrain: int = 1 << 22, epochs: int = 12, gamma: float = 1.4, 
     losses = np.zeros(epochs, dtype=np.float32)
     t0 = time.perf_counter()
     net.train(ntrain, feat.data_ptr(), tgt.data_ptr(), batch=batch, epochs=epochs, lr=lr, seed=seed,
-              loss_out=losses.ctypes.data)
+              loss_out=losses.ctypes.data, clip=clip, lr_final=lr_final)
     torch.cuda.synchronize()
     return net, losses, time.perf_counter() - t0
