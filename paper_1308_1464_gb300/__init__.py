@@ -304,11 +304,27 @@ class SeedNet:
         except Exception:
             pass
 
-    def set_params(self, host_ptr: int) -> None:
-        check(lib().mc_mlp_set_params(self._h, _VP(host_ptr)))
+    def set_params(self, params) -> None:
+        """params: a host array of MLP_NPARAM values (held for the duration of
+        the call), or the address of one."""
+        if isinstance(params, int):
+            check(lib().mc_mlp_set_params(self._h, _VP(params)))
+            return
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != MLP_NPARAM:
+            raise ValueError(f"expected {MLP_NPARAM} parameters, got {a.size}")
+        check(lib().mc_mlp_set_params(self._h, _VP(a.ctypes.data)))
 
-    def get_params(self, host_ptr: int) -> None:
-        check(lib().mc_mlp_get_params(self._h, _VP(host_ptr)))
+    def get_params(self, host_ptr: int | None = None):
+        """Copies the parameters to the address given, or returns a new array."""
+        if host_ptr is not None:
+            check(lib().mc_mlp_get_params(self._h, _VP(host_ptr)))
+            return None
+        import numpy as np
+        a = np.empty(MLP_NPARAM, dtype=np.float32)
+        check(lib().mc_mlp_get_params(self._h, _VP(a.ctypes.data)))
+        return a
 
     def forward(self, n: int, features: int, out: int, stream: int = 0) -> None:
         check(lib().mc_mlp_forward(self._h, int(n), _VP(features), _VP(out), _VP(stream)))

@@ -49,7 +49,7 @@ def train_seed_net(ntrain: int = 1 << 22, epochs: int = 12, gamma: float = 1.4, 
     tgt = torch.empty(ntrain, dtype=torch.float32, device="cuda")
     mc.mlp_features(ntrain, gamma, ptrs, p_star.data_ptr(), feat.data_ptr(), tgt.data_ptr())
     net = mc.SeedNet()
-    net.set_params(initial_params(mc).ctypes.data)
+    net.set_params(initial_params(mc))
     losses = np.zeros(epochs, dtype=np.float32)
     t0 = time.perf_counter()
     net.train(ntrain, feat.data_ptr(), tgt.data_ptr(), batch=batch, epochs=epochs, lr=lr, seed=seed,

@@ -135,3 +135,16 @@ def test_training_reduces_newton_iterations():
     print(f"mean Newton updates: learned {mean_m:.3f}, plain {mean_p:.3f}, fallback {fallback:.4f}")
     assert mean_m < mean_p
     assert fallback < 0.01
+
+
+def test_params_round_trip():
+    """set_params copies every value (the first ones included) from an array
+    it holds for the whole call, temporaries too; get_params returns them."""
+    from paper_1308_1464_gb300.seednet import initial_params
+    net = mc.SeedNet()
+    for seed in range(4):
+        net.set_params(initial_params(mc, seed=seed))      # a temporary array
+        np.testing.assert_array_equal(net.get_params(), initial_params(mc, seed=seed))
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(10, dtype=np.float32))
+    net.close()
