@@ -522,7 +522,7 @@ def bench_exact(args, rank, world):
         stats = torch.zeros(6, dtype=torch.int64, device="cuda")
         mc.riemann_exact(n, GAM, [s.data_ptr() for s in states], ps.data_ptr(), us.data_ptr(),
                          it.data_ptr(), fl.data_ptr(), mode, net, tol, 30, stats.data_ptr())
-        return ps, it, fl, stats
+        return ps, it, fl, stats, us
 
     from paper_1308_1464_gb300.seednet import train_seed_net
     ntrain, epochs = 1 << 22, 12
@@ -532,6 +532,8 @@ def bench_exact(args, rank, world):
     test = dev_states(n, offset=0)
     stream = torch.cuda.current_stream()
     out = {}
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.__enter__()
     for name, mode, nn in (("plain", mc.SEED_ADAPTIVE, None), ("learned", mc.SEED_MLP, net)):
         for _ in range(args.warmup):
             solve(test, mode, nn)
@@ -540,7 +542,7 @@ def bench_exact(args, rank, world):
         e0.record(stream)
         reps = max(1, args.steps)
         for _ in range(reps):
-            ps, it, fl, stats = solve(test, mode, nn)
+            ps, it, fl, stats, _ = solve(test, mode, nn)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
@@ -556,6 +558,30 @@ def bench_exact(args, rank, world):
             ok = fl.cpu().numpy() & 1 == 0
             a, c = ps.cpu().numpy()[ok], ps_plain.cpu().numpy()[ok]
             out["learned"]["max_rel_diff_vs_plain"] = float(np.max(np.abs(a - c) / np.abs(c)))
+    clk.__exit__(None, None, None)
+    # end to end through the public call: the six state arrays from pinned host
+    # memory, the learned-seed solve, p* and u* back to pinned host memory
+    host = [torch.from_numpy(a.astype(np.float32)).pin_memory()
+            for a in workloads.riemann_states(n, seed=1308, offset=0)]
+    h_ps = torch.empty(n, dtype=torch.float32).pin_memory()
+    h_us = torch.empty_like(h_ps).pin_memory()
+    dev = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(6)]
+    reps_e2e = 3
+    for rep in range(reps_e2e + 1):
+        if rep == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        for d, h in zip(dev, host):
+            d.copy_(h, non_blocking=True)
+        ps, _, _, _, us = solve(dev, mc.SEED_MLP, net)
+        h_ps.copy_(ps, non_blocking=True)
+        h_us.copy_(us, non_blocking=True)
+        torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    e2e = {"value": world * n * reps_e2e / el, "unit": "solves/s",
+           "h2d_bytes_per_step": 6 * 4 * n, "d2h_bytes_per_step": 2 * 4 * n,
+           "note": "six FP32 state arrays from pinned host memory, mc_riemann_exact with the "
+                   "learned seed, p* and u* back to pinned host memory; one step = 2^24 solves"}
     peak, kind = measured_peaks()
     ms = out["learned"]["ms"]
     cnt = ncu_exact()
@@ -584,8 +610,8 @@ def bench_exact(args, rank, world):
                    "train_rows": ntrain, "train_epochs": epochs, "train_s": round(train_s, 2),
                    "train_loss": [float(x) for x in losses]},
         "plain": out["plain"], "learned": out["learned"],
-        "roofline": roofline,
-        "gpu_launches": 1,
+        "roofline": roofline, "e2e": e2e,
+        "gpu_launches": 1, "clocks": clk.summary(),
     }
 
 
