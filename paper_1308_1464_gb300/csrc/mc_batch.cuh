@@ -73,7 +73,7 @@ __device__ __forceinline__ bool wait_counter(const unsigned* counter, unsigned t
     return true;
 }
 
-template <class RP, bool FAST>
+template <class RP, int MODE>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const BatchArgs<RP> a)
 {
     using T = typename RP::real;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         const int j0 = (t / d.nbands) * d.tile_rows;
         const int jend = min(j0 + d.tile_rows, d.my);
         T smx = T(0), smy = T(0);
-        if (!sweep_task<RP, true, FAST>(a.rp, map, qout, d.mx, d.my, d.ld_x, d.ld_field, a.x_offset, i0,
+        if (!sweep_task<RP, true, MODE>(a.rp, map, qout, d.mx, d.my, d.ld_x, d.ld_field, a.x_offset, i0,
                                   j0, jend, T(dt / d.dx), T(dt / d.dy), a.limiter, second, a.transverse,
                                   W, bad, smx, smy, a.status)) {
             tma_failed = true;

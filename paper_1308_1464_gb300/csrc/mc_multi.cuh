@@ -29,7 +29,7 @@ struct MultiArgs {
     int* status;
 };
 
-template <class RP, bool FAST>
+template <class RP, int MODE>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32) multi_sweep_kernel(const MultiArgs<RP> a)
 {
     using T = typename RP::real;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) multi_sweep_kernel(const Mul
         const int j0 = (t / g.nbands) * g.tile_rows;
         const int jend = min(j0 + g.tile_rows, g.my);
         T smx = T(0), smy = T(0);
-        failed = !sweep_task<RP, false, FAST>(a.rp, map, static_cast<T*>(g.q[a.cur ^ 1]), g.mx, g.my,
+        failed = !sweep_task<RP, false, MODE>(a.rp, map, static_cast<T*>(g.q[a.cur ^ 1]), g.mx, g.my,
                                               g.ld_x, g.ld_field, a.x_offset, i0, j0, jend, T(a.nux),
                                               T(a.nuy), a.limiter, second, a.transverse, W, bad, smx,
                                               smy, a.status);

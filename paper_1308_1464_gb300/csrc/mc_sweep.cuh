@@ -67,45 +67,63 @@ struct SweepArgs {
     unsigned long long* newton_updates;   // [0] Newton updates, [1] normal solves, or null
 };
 
-// phi(theta) with theta = dl / dr, branch-free (LeVeque 2002, eq. 6.39):
-// minmod (1), superbee (2), van Leer (3), MC (4) or none (0: phi = 1).  With a
-// compile-time limiter the selection folds away.  A zero wave (dr = 0) needs
-// no test: theta is then NaN or infinite, min/max return their other
-// operand, so phi stays in [0, 2] and multiplies a wave whose components are
-// all zero.  Van Leer's (theta + |theta|)/(1 + |theta|) is written as
-// 2 - 2/(1 + t) with t = max(theta, 0), which keeps that property.
-template <typename T>
-__device__ __forceinline__ T limiter_phi(int lim, T dl, T dr)
+// phi(theta) of K ratios theta = dl / dr at once (LeVeque 2002, eq. 6.39):
+// minmod (1), superbee (2), van Leer (3), MC (4) or none (0: phi = 1).  The
+// limiter is warp-uniform, so one branch selects the formula for all K
+// ratios; with a compile-time limiter the selection folds away.  A zero wave
+// (dr = 0) needs no test: theta is then NaN or infinite, min/max return their
+// other operand, so phi stays in [0, 2] and multiplies a wave whose
+// components are all zero.  Van Leer's (theta + |theta|)/(1 + |theta|) is
+// written as 2 - 2/(1 + t) with t = max(theta, 0), which keeps that property.
+template <int K, typename T>
+__device__ __forceinline__ void limiter_phis(int lim, const T (&th)[K], T (&phi)[K])
 {
-    const T th = dl * rcp_(dr);
-    T phi = T(1);
     if (lim == 4) {
-        phi = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th), T(2)), T(2) * th));
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            phi[k] = fmax(T(0), fmin(fmin(T(0.5) * (T(1) + th[k]), T(2)), T(2) * th[k]));
     } else if (lim == 1) {
-        phi = fmax(T(0), fmin(T(1), th));
+#pragma unroll
+        for (int k = 0; k < K; k++) phi[k] = fmax(T(0), fmin(T(1), th[k]));
     } else if (lim == 2) {
-        phi = fmax(T(0), fmax(fmin(T(1), T(2) * th), fmin(T(2), th)));
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            phi[k] = fmax(T(0), fmax(fmin(T(1), T(2) * th[k]), fmin(T(2), th[k])));
     } else if (lim == 3) {
-        const T t = fmax(th, T(0));
-        phi = T(2) - T(2) * rcp_(T(1) + t);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const T t = fmax(th[k], T(0));
+            phi[k] = T(2) - T(2) * rcp_(T(1) + t);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; k++) phi[k] = T(1);
     }
-    return phi;
 }
 
-// limiter_phi of an x-edge and a y-edge wave at once (FP32 pairs)
-__device__ __forceinline__ f2 limiter_phi_pair(int lim, f2 dl, f2 dr)
+// limiter_phis of K pairs (.x an x-edge wave, .y a y-edge wave)
+template <int K>
+__device__ __forceinline__ void limiter_phis_pair(int lim, const f2 (&th)[K], f2 (&phi)[K])
 {
-    const f2 th = p_mul(dl, p_rcp(dr));
-    f2 phi = p_set(1.f);
     if (lim == 4) {
-        const f2 a = p_fma(th, p_set(0.5f), p_set(0.5f)), b = p_add(th, th);
-        phi.x = fmaxf(0.f, fminf(fminf(a.x, 2.f), b.x));
-        phi.y = fmaxf(0.f, fminf(fminf(a.y, 2.f), b.y));
-    } else if (lim == 1 || lim == 2 || lim == 3) {
-        phi.x = limiter_phi(lim, dl.x, dr.x);
-        phi.y = limiter_phi(lim, dl.y, dr.y);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const f2 a = p_fma(th[k], p_set(0.5f), p_set(0.5f)), b = p_add(th[k], th[k]);
+            phi[k].x = fmaxf(0.f, fminf(fminf(a.x, 2.f), b.x));
+            phi[k].y = fmaxf(0.f, fminf(fminf(a.y, 2.f), b.y));
+        }
+    } else {
+        float tx[K], ty[K], px[K], py[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            tx[k] = th[k].x;
+            ty[k] = th[k].y;
+        }
+        limiter_phis<K>(lim, tx, px);
+        limiter_phis<K>(lim, ty, py);
+#pragma unroll
+        for (int k = 0; k < K; k++) phi[k] = make_float2(px[k], py[k]);
     }
-    return phi;
 }
 
 // Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage;
@@ -128,9 +146,11 @@ struct WarpRing {
 // sides: x ghosts negate component 1, y ghosts component 2, corners both), so
 // the next step needs no separate ghost fill.
 //
-// FAST compiles the common scheme (MC limiter, second order, transverse
-// splits of the fluctuations) with those choices fixed; otherwise they are
-// read at run time.
+// MODE_FAST compiles the common scheme (MC limiter, second order, transverse
+// splits of the fluctuations) with those choices fixed; MODE_TRANS2 fixes
+// second order with transverse option 2 and MODE_GENERAL transverse option
+// 0 or 1 (option 2 at first order is option 1); the other choices are read
+// at run time.
 //
 // Transverse option 2 splits each edge's whole contribution to a cell
 // (A+dQ - F into the high cell, A-dQ + F into the low one, F the limited
@@ -140,7 +160,7 @@ struct WarpRing {
 // the part entering row k+1 joins F of row k+1 as before, and the part
 // entering row k is added to row k's carried x-edge terms just before row k
 // is updated.
-template <class RP, bool WALL_GHOSTS, bool FAST>
+template <class RP, bool WALL_GHOSTS, int MODE>
 __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real* __restrict__ qout, int mx, int my,
                                            long long ld_x, long long ld_field, long long x_offset,
@@ -150,10 +170,11 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real& smx, typename RP::real& smy,
                                            int* status)
 {
+    constexpr bool FAST = MODE == MODE_FAST;
+    constexpr bool trans2 = MODE == MODE_TRANS2;
     const int limiter = FAST ? 4 : limiter_rt;
-    const bool second = FAST ? true : second_rt;
-    const bool trans = FAST ? true : transverse_rt != 0;
-    const bool trans2 = FAST ? false : (transverse_rt == 2 && second_rt);
+    const bool second = MODE != MODE_GENERAL ? true : second_rt;
+    const bool trans = MODE != MODE_GENERAL ? true : transverse_rt != 0;
     using T = typename RP::real;
     // N conserved fields; NP state planes (with material planes after them)
     constexpr int N = RP::NEQ, NW = RP::NW, NP = RP::NPLANE;
@@ -453,35 +474,41 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     // frame: .x the x-edge, .y the y-edge (component m of the
                     // frame is component frame_comp(m, 1) of the y-edge state)
                     const f2 nnu = make_float2(-nux, -nuy);
-                    f2 FG[N];
+                    f2 FG[N], th[NW], phi[NW];
 #pragma unroll
                     for (int m = 0; m < N; m++) FG[m] = p_set(0.f);
 #pragma unroll
                     for (int p = 0; p < NW; p++) {
                         const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
                         const bool upl = sy1[p] > T(0);
-                        f2 dl = p_set(0.f), dr = p_set(0.f), LW[N];
+                        f2 dl = p_set(0.f), dr = p_set(0.f);
 #pragma unroll
                         for (int m = 0; m < N; m++) {
                             if (!RP::template wave_nz<0>(p, m)) continue;
                             const int my_ = frame_comp(m, 1);
-                            LW[m] = make_float2(Wx[p][m], Wy1[p][my_]);
+                            const f2 lw = make_float2(Wx[p][m], Wy1[p][my_]);
                             const float wux = shfl(Wx[p][m], src);
                             if constexpr (CD) {
                                 dl.x += wux * Wx[p][m];
                             } else {
                                 const float wuy = upl ? Wy0[p][my_] : Wy2[p][my_];
-                                dl = p_fma(make_float2(wux, wuy), LW[m], dl);
+                                dl = p_fma(make_float2(wux, wuy), lw, dl);
                             }
-                            dr = p_fma(LW[m], LW[m], dr);
+                            dr = p_fma(lw, lw, dr);
                         }
                         if constexpr (CD) dl.y = upl ? dlo[p] : dhi[p];
+                        th[p] = p_mul(dl, p_rcp(dr));
+                    }
+                    limiter_phis_pair<NW>(limiter, th, phi);
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
                         const f2 as = make_float2(fabsf(sxw[p]), fabsf(sy1[p]));
                         const f2 cf = p_mul(p_mul(p_mul(p_set(0.5f), as), p_fma(nnu, as, p_set(1.f))),
-                                            limiter_phi_pair(limiter, dl, dr));
+                                            phi[p]);
 #pragma unroll
                         for (int m = 0; m < N; m++)
-                            if (RP::template wave_nz<0>(p, m)) FG[m] = p_fma(cf, LW[m], FG[m]);
+                            if (RP::template wave_nz<0>(p, m))
+                                FG[m] = p_fma(cf, make_float2(Wx[p][m], Wy1[p][frame_comp(m, 1)]), FG[m]);
                     }
 #pragma unroll
                     for (int m = 0; m < N; m++) {
@@ -489,6 +516,9 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                         Gn[frame_comp(m, 1)] = FG[m].y;
                     }
                 } else {
+                    // ratios of all waves of both edges (x: 0..NW-1, y:
+                    // NW..2NW-1), then one branch on the limiter
+                    T th[2 * NW], phi[2 * NW];
 #pragma unroll
                     for (int p = 0; p < NW; p++) {
                         const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
@@ -500,11 +530,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                             dl += wu * Wx[p][m];
                             dr += Wx[p][m] * Wx[p][m];
                         }
-                        const T as = fabs(sxw[p]);
-                        const T cf = T(0.5) * as * (T(1) - nux * as) * limiter_phi(limiter, dl, dr);
-#pragma unroll
-                        for (int m = 0; m < N; m++)
-                            if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
+                        th[p] = dl * rcp_(dr);
                     }
 #pragma unroll
                     for (int p = 0; p < NW; p++) {
@@ -517,8 +543,21 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                             dr += Wy1[p][m] * Wy1[p][m];
                         }
                         if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
+                        th[NW + p] = dl * rcp_(dr);
+                    }
+                    limiter_phis<2 * NW>(limiter, th, phi);
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
+                        const T as = fabs(sxw[p]);
+                        const T cf = T(0.5) * as * (T(1) - nux * as) * phi[p];
+#pragma unroll
+                        for (int m = 0; m < N; m++)
+                            if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
+                    }
+#pragma unroll
+                    for (int p = 0; p < NW; p++) {
                         const T as = fabs(sy1[p]);
-                        const T cf = T(0.5) * as * (T(1) - nuy * as) * limiter_phi(limiter, dl, dr);
+                        const T cf = T(0.5) * as * (T(1) - nuy * as) * phi[NW + p];
 #pragma unroll
                         for (int m = 0; m < N; m++)
                             if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
@@ -667,7 +706,7 @@ __device__ __forceinline__ WarpRing warp_ring(unsigned char* smem, int es, int n
 // The fused step over one grid.  The tensor maps of the two state buffers
 // live in device global memory (64-byte aligned, written by the host before
 // the launch); the kernel takes plain pointers to them.
-template <class RP, bool FAST>
+template <class RP, int MODE>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
 {
@@ -715,7 +754,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
         const int i0 = (task % a.nbands) * BAND_W;
         const int j0 = (task / a.nbands) * a.tile_rows;
         const int jend = min(j0 + a.tile_rows, a.my);
-        failed = !sweep_task<RP, false, FAST>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
+        failed = !sweep_task<RP, false, MODE>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
                                          a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
                                          a.transverse, W, bad, smx, smy, a.status);
     }

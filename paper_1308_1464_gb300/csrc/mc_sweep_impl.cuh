@@ -16,10 +16,14 @@ inline int seednet_smem_bytes()
     return int(sizeof(MlpShared)) + SWEEP_WARPS * 32 * XP * 2 + SWEEP_WARPS * 32 * 4;
 }
 
-// the scheme the FAST kernels compile in: MC limiter, second order, transverse
-inline bool is_fast_scheme(const mc_problem& p)
+// the compile-time scheme of a problem's fused step: MODE_FAST for MC,
+// second order, transverse option 1; MODE_TRANS2 for second order with
+// transverse option 2; MODE_GENERAL otherwise
+inline int scheme_mode(const mc_problem& p)
 {
-    return p.limiter == MC_LIM_MC && p.order == 2 && p.transverse == 1;
+    if (p.limiter == MC_LIM_MC && p.order == 2 && p.transverse == 1) return MODE_FAST;
+    if (p.order == 2 && p.transverse == 2) return MODE_TRANS2;
+    return MODE_GENERAL;
 }
 
 template <class RP>
@@ -60,10 +64,16 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     }
     int blocks = (a.ntasks + wpb - 1) / wpb;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
-    if (is_fast_scheme(L.prob))
-        ctu_sweep_kernel<RP, true><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
-    else
-        ctu_sweep_kernel<RP, false><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+    switch (scheme_mode(L.prob)) {
+    case MODE_FAST:
+        ctu_sweep_kernel<RP, MODE_FAST><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+        break;
+    case MODE_TRANS2:
+        ctu_sweep_kernel<RP, MODE_TRANS2><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+        break;
+    default:
+        ctu_sweep_kernel<RP, MODE_GENERAL><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+    }
     return cudaGetLastError();
 }
 
@@ -74,10 +84,13 @@ cudaError_t sweep_prepare_t()
 {
     using T = typename RP::real;
     const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (RP::SEEDED ? seednet_smem_bytes() : 0);
-    cudaError_t e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, true>,
+    cudaError_t e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, MODE_FAST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, false>,
+        e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, MODE_TRANS2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, MODE_GENERAL>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
@@ -127,10 +140,16 @@ cudaError_t batch_launch_t(const BatchLaunch& L)
 {
     using T = typename RP::real;
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
-    if (is_fast_scheme(L.proto))
-        batch_sweep_kernel<RP, true><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
-    else
-        batch_sweep_kernel<RP, false><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+    switch (scheme_mode(L.proto)) {
+    case MODE_FAST:
+        batch_sweep_kernel<RP, MODE_FAST><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+        break;
+    case MODE_TRANS2:
+        batch_sweep_kernel<RP, MODE_TRANS2><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+        break;
+    default:
+        batch_sweep_kernel<RP, MODE_GENERAL><<<L.blocks, SWEEP_WARPS * 32, smem, L.stream>>>(batch_args<RP>(L));
+    }
     return cudaGetLastError();
 }
 
@@ -149,13 +168,16 @@ cudaError_t batch_occupancy_t(int* ctas)
 {
     using T = typename RP::real;
     constexpr int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE);
-    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP, true>,
+    cudaError_t e = cudaFuncSetAttribute(batch_sweep_kernel<RP, MODE_FAST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_sweep_kernel<RP, false>,
+        e = cudaFuncSetAttribute(batch_sweep_kernel<RP, MODE_TRANS2>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_sweep_kernel<RP, MODE_GENERAL>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, batch_sweep_kernel<RP, true>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, batch_sweep_kernel<RP, MODE_FAST>,
                                                          SWEEP_WARPS * 32, smem);
 }
 
@@ -182,14 +204,21 @@ cudaError_t multi_launch_t(const MultiLaunch& L)
     long long blocks = (L.total + SWEEP_WARPS - 1) / SWEEP_WARPS;
     if (blocks < 1) blocks = 1;
     cudaError_t e;
-    if (is_fast_scheme(L.prob)) {
-        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    switch (scheme_mode(L.prob)) {
+    case MODE_FAST:
+        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, MODE_FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            multi_sweep_kernel<RP, true><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            multi_sweep_kernel<RP, MODE_FAST><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
+        break;
+    case MODE_TRANS2:
+        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, MODE_TRANS2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            multi_sweep_kernel<RP, false><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
+            multi_sweep_kernel<RP, MODE_TRANS2><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
+        break;
+    default:
+        e = cudaFuncSetAttribute(multi_sweep_kernel<RP, MODE_GENERAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            multi_sweep_kernel<RP, MODE_GENERAL><<<(unsigned)blocks, SWEEP_WARPS * 32, smem, L.stream>>>(a);
     }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }

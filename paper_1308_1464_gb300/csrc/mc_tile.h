@@ -36,6 +36,8 @@ __host__ __device__ constexpr int sweep_smem_bytes(int es, int neq)
 {
     return 128 + SWEEP_WARPS * NSTAGE * stage_bytes(es, neq);
 }
+// compile-time schemes of the fused step (see sweep_task)
+constexpr int MODE_GENERAL = 0, MODE_TRANS2 = 1, MODE_FAST = 2;
 constexpr int DEFAULT_TILE_ROWS = 64;
 // attempts per captured graph of the time-step loop
 constexpr int GRAPH_CHUNK = 50;
