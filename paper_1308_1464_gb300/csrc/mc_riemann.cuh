@@ -103,7 +103,6 @@ struct AcousticsRP {
     // the sweep keeps the y-edge waves of the row below (not their products)
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
-    static constexpr bool PAIR_LIMITER = false;
     static constexpr bool SEEDED = false;   // no external pressure seed
 
     __device__ __forceinline__ void cell_speeds(const T*, T& sx, T& sy) const { sx = sy = c; }
@@ -168,7 +167,6 @@ struct AcousticsVarRP {
     __host__ __device__ static constexpr bool wave_nz(int, int m) { return m != 2 - DIR; }
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
-    static constexpr bool PAIR_LIMITER = false;
     static constexpr bool SEEDED = false;   // no external pressure seed
     bool efix;  // unused: linear
     struct Lin { T cl, cr; };
@@ -226,7 +224,6 @@ struct AdvectionRP {
     __host__ __device__ static constexpr bool wave_nz(int, int) { return true; }
     static constexpr bool CARRY_DOT = false;
     static constexpr bool PAIRED = false;   // scalar solves only
-    static constexpr bool PAIR_LIMITER = false;
     static constexpr bool SEEDED = false;   // no external pressure seed
     T u, v;
     bool efix;  // unused: linear
@@ -277,8 +274,9 @@ struct SweRP {
     // tangential momentum
     template <int DIR>
     __host__ __device__ static constexpr bool wave_nz(int p, int m) { return p != 1 || m == 2 - DIR; }
-    // the sweep keeps the y-edge waves of the row below (measured faster here)
-    static constexpr bool CARRY_DOT = false;
+    // the sweep carries the limiter dot products of the y-edge waves with
+    // those of the row below (measured 1-3% faster than carrying the waves)
+    static constexpr bool CARRY_DOT = true;
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
 
@@ -368,7 +366,6 @@ struct SweRP {
     // edge-normal frame (component 1 normal, 2 tangential momentum); the
     // same arithmetic as normal<0> / transverse<0>, two edges per instruction
     static constexpr bool PAIRED = sizeof(T) == 4;
-    static constexpr bool PAIR_LIMITER = false;
     static constexpr bool SEEDED = false;   // no external pressure seed
     struct LinP { f2 u, v, c, r2c; };
     // the scalar linearised state of half h (x-edge 0, y-edge 1)
@@ -519,7 +516,6 @@ struct EulerRP {
     // its 12 wave components (measured faster here)
     static constexpr bool CARRY_DOT = true;
     static constexpr bool PAIRED = sizeof(T) == 4;
-    static constexpr bool PAIR_LIMITER = true;
     static constexpr bool SEEDED = false;   // no external pressure seed
     // max over the edge's waves of |s|: speeds u - c, u, u + c with c > 0
     __device__ __forceinline__ T max_speed(const Lin& L) const { return fabs(L.u) + L.c; }
@@ -855,7 +851,6 @@ struct EulerGodunovRP : EulerRP<T> {
     using Base::gamma;
     using Base::gm1;
     static constexpr bool PAIRED = false;   // scalar solves only
-    static constexpr bool PAIR_LIMITER = false;
     // accepts a pressure seed for Newton (normal_seeded), e.g. the learned one
     static constexpr bool SEEDED = true;
     static constexpr bool CARRY_DOT = true;

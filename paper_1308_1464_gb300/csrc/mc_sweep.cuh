@@ -101,31 +101,6 @@ __device__ __forceinline__ void limiter_phis(int lim, const T (&th)[K], T (&phi)
     }
 }
 
-// limiter_phis of K pairs (.x an x-edge wave, .y a y-edge wave)
-template <int K>
-__device__ __forceinline__ void limiter_phis_pair(int lim, const f2 (&th)[K], f2 (&phi)[K])
-{
-    if (lim == 4) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const f2 a = p_fma(th[k], p_set(0.5f), p_set(0.5f)), b = p_add(th[k], th[k]);
-            phi[k].x = fmaxf(0.f, fminf(fminf(a.x, 2.f), b.x));
-            phi[k].y = fmaxf(0.f, fminf(fminf(a.y, 2.f), b.y));
-        }
-    } else {
-        float tx[K], ty[K], px[K], py[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            tx[k] = th[k].x;
-            ty[k] = th[k].y;
-        }
-        limiter_phis<K>(lim, tx, px);
-        limiter_phis<K>(lim, ty, py);
-#pragma unroll
-        for (int k = 0; k < K; k++) phi[k] = make_float2(px[k], py[k]);
-    }
-}
-
 // Per-warp TMA ring: NSTAGE stages of one box each, one mbarrier per stage;
 // with a seed network also the CTA's shared copy of it and the warp's scratch
 // tiles for its inference, and the Newton counters.
@@ -469,99 +444,51 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 #pragma unroll
             for (int m = 0; m < N; m++) Fn[m] = Gn[m] = T(0);
             if (second) {
-                if constexpr (RP::PAIRED && RP::PAIR_LIMITER) {
-                    // both limiters as one pair, indexed in the edge-normal
-                    // frame: .x the x-edge, .y the y-edge (component m of the
-                    // frame is component frame_comp(m, 1) of the y-edge state)
-                    const f2 nnu = make_float2(-nux, -nuy);
-                    f2 FG[N], th[NW], phi[NW];
+                // ratios of all waves of both edges (x: 0..NW-1, y:
+                // NW..2NW-1), then one branch on the limiter
+                T th[2 * NW], phi[2 * NW];
 #pragma unroll
-                    for (int m = 0; m < N; m++) FG[m] = p_set(0.f);
-#pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
-                        const bool upl = sy1[p] > T(0);
-                        f2 dl = p_set(0.f), dr = p_set(0.f);
-#pragma unroll
-                        for (int m = 0; m < N; m++) {
-                            if (!RP::template wave_nz<0>(p, m)) continue;
-                            const int my_ = frame_comp(m, 1);
-                            const f2 lw = make_float2(Wx[p][m], Wy1[p][my_]);
-                            const float wux = shfl(Wx[p][m], src);
-                            if constexpr (CD) {
-                                dl.x += wux * Wx[p][m];
-                            } else {
-                                const float wuy = upl ? Wy0[p][my_] : Wy2[p][my_];
-                                dl = p_fma(make_float2(wux, wuy), lw, dl);
-                            }
-                            dr = p_fma(lw, lw, dr);
-                        }
-                        if constexpr (CD) dl.y = upl ? dlo[p] : dhi[p];
-                        th[p] = p_mul(dl, p_rcp(dr));
-                    }
-                    limiter_phis_pair<NW>(limiter, th, phi);
-#pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const f2 as = make_float2(fabsf(sxw[p]), fabsf(sy1[p]));
-                        const f2 cf = p_mul(p_mul(p_mul(p_set(0.5f), as), p_fma(nnu, as, p_set(1.f))),
-                                            phi[p]);
-#pragma unroll
-                        for (int m = 0; m < N; m++)
-                            if (RP::template wave_nz<0>(p, m))
-                                FG[m] = p_fma(cf, make_float2(Wx[p][m], Wy1[p][frame_comp(m, 1)]), FG[m]);
-                    }
+                for (int p = 0; p < NW; p++) {
+                    const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
+                    T dl = T(0), dr = T(0);
 #pragma unroll
                     for (int m = 0; m < N; m++) {
-                        Fn[m] = FG[m].x;
-                        Gn[frame_comp(m, 1)] = FG[m].y;
+                        if (!RP::template wave_nz<0>(p, m)) continue;
+                        const T wu = shfl(Wx[p][m], src);
+                        dl += wu * Wx[p][m];
+                        dr += Wx[p][m] * Wx[p][m];
                     }
-                } else {
-                    // ratios of all waves of both edges (x: 0..NW-1, y:
-                    // NW..2NW-1), then one branch on the limiter
-                    T th[2 * NW], phi[2 * NW];
+                    th[p] = dl * rcp_(dr);
+                }
 #pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
-                        T dl = T(0), dr = T(0);
+                for (int p = 0; p < NW; p++) {
+                    const bool upl = sy1[p] > T(0);
+                    T dl = T(0), dr = T(0);
 #pragma unroll
-                        for (int m = 0; m < N; m++) {
-                            if (!RP::template wave_nz<0>(p, m)) continue;
-                            const T wu = shfl(Wx[p][m], src);
-                            dl += wu * Wx[p][m];
-                            dr += Wx[p][m] * Wx[p][m];
-                        }
-                        th[p] = dl * rcp_(dr);
+                    for (int m = 0; m < N; m++) {
+                        if (!RP::template wave_nz<1>(p, m)) continue;
+                        if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
+                        dr += Wy1[p][m] * Wy1[p][m];
                     }
+                    if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
+                    th[NW + p] = dl * rcp_(dr);
+                }
+                limiter_phis<2 * NW>(limiter, th, phi);
 #pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const bool upl = sy1[p] > T(0);
-                        T dl = T(0), dr = T(0);
+                for (int p = 0; p < NW; p++) {
+                    const T as = fabs(sxw[p]);
+                    const T cf = T(0.5) * as * (T(1) - nux * as) * phi[p];
 #pragma unroll
-                        for (int m = 0; m < N; m++) {
-                            if (!RP::template wave_nz<1>(p, m)) continue;
-                            if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
-                            dr += Wy1[p][m] * Wy1[p][m];
-                        }
-                        if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
-                        th[NW + p] = dl * rcp_(dr);
-                    }
-                    limiter_phis<2 * NW>(limiter, th, phi);
+                    for (int m = 0; m < N; m++)
+                        if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
+                }
 #pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const T as = fabs(sxw[p]);
-                        const T cf = T(0.5) * as * (T(1) - nux * as) * phi[p];
+                for (int p = 0; p < NW; p++) {
+                    const T as = fabs(sy1[p]);
+                    const T cf = T(0.5) * as * (T(1) - nuy * as) * phi[NW + p];
 #pragma unroll
-                        for (int m = 0; m < N; m++)
-                            if (RP::template wave_nz<0>(p, m)) Fn[m] += cf * Wx[p][m];
-                    }
-#pragma unroll
-                    for (int p = 0; p < NW; p++) {
-                        const T as = fabs(sy1[p]);
-                        const T cf = T(0.5) * as * (T(1) - nuy * as) * phi[NW + p];
-#pragma unroll
-                        for (int m = 0; m < N; m++)
-                            if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
-                    }
+                    for (int m = 0; m < N; m++)
+                        if (RP::template wave_nz<1>(p, m)) Gn[m] += cf * Wy1[p][m];
                 }
             }
             if (trans2) {
