@@ -220,7 +220,9 @@ def _amr_lib():
         L.mcref_amr_average_down.argtypes = [P, ctypes.c_int, AP, ctypes.c_int, DPP, _D]
         L.mcref_amr_average_down.restype = None
         L.mcref_amr_step.argtypes = [P, ctypes.c_int, AP, ctypes.c_int, _D, _D, DPP, ctypes.c_double,
-                                     ctypes.c_int]
+                                     ctypes.c_int, ctypes.c_int]
+        L.mcref_edge_flux.argtypes = [P, _D, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.mcref_edge_flux.restype = None
         L._amr_ready = True
     return L
 
@@ -256,17 +258,29 @@ def amr_average_down(coarse: Problem, ratio, patches, qf, qc):
     return qc
 
 
-def amr_step(coarse: Problem, ratio, patches, qc, qf, dt, nthreads=1):
+def amr_step(coarse: Problem, ratio, patches, qc, qf, dt, nthreads=1, reflux=False):
     """One coarse step with ratio fine steps per patch -> (qc_new, flags); the
-    patch arrays in the list qf are advanced in place."""
+    patch arrays in the list qf are advanced in place.  reflux: correct the
+    coarse cells outside the patches with the mean fine fluxes."""
     qc = _f64(qc)
     out = np.zeros_like(qc)
     for a in qf:
         assert a.dtype == np.float64 and a.flags.c_contiguous
     ptrs = (_D * max(1, len(qf)))(*[_p(a) for a in qf])
     flags = _amr_lib().mcref_amr_step(ctypes.byref(coarse.c()), int(ratio), _patch_array(patches),
-                                      len(patches), _p(qc), _p(out), ptrs, float(dt), int(nthreads))
+                                      len(patches), _p(qc), _p(out), ptrs, float(dt), int(bool(reflux)),
+                                      int(nthreads))
     return out, flags
+
+
+def edge_flux(prob: Problem, q, dt: float, direction: int, i: int, j: int):
+    """Flux through the edge of `direction` with high cell (i, j) implied by
+    the step of q (ghosts filled) with dt."""
+    q = _f64(q)
+    F = np.zeros(prob.meqn)
+    _amr_lib().mcref_edge_flux(ctypes.byref(prob.c()), _p(q), float(dt), int(direction), int(i),
+                               int(j), _p(F))
+    return F
 
 
 def exact_sample(gamma, rl, ul, pl, rr, ur, pr, pstar, ustar):

@@ -198,9 +198,18 @@ void mcref_amr_fill_ghosts(const mcref_problem* pc, int ratio, const double* qc0
 void mcref_amr_average_down(const mcref_problem* pc, int ratio, const mcref_amr_patch* pts,
                             int npatch, double* const* qf, double* qc);
 /* One coarse step of dt with ratio fine steps of dt/ratio on every patch
- * (Berger-Oliger); qf[p] are updated in place, qc_out gets filled ghosts. */
+ * (Berger-Oliger); qf[p] are updated in place, qc_out gets filled ghosts.
+ * reflux != 0: the coarse cells outside the patches get the flux correction
+ * of Berger & Colella (coarse flux replaced by the mean fine flux). */
 int mcref_amr_step(const mcref_problem* pc, int ratio, const mcref_amr_patch* pts, int npatch,
-                   const double* qc_in, double* qc_out, double** qf, double dt, int nthreads);
+                   const double* qc_in, double* qc_out, double** qf, double dt, int reflux,
+                   int nthreads);
+/* The flux through one edge implied by the step of q (filled ghosts) with dt:
+ * f(Q_low) + A-dQ + limited correction + transverse terms, so that a cell's
+ * update is minus the difference of its edges' fluxes.  dir 0: x-edge with
+ * high cell (i, j); dir 1: y-edge with high cell (i, j).  F: meqn values. */
+void mcref_edge_flux(const mcref_problem* p, const double* q, double dt, int dir, int i, int j,
+                     double* F);
 
 #ifdef __cplusplus
 }

@@ -174,3 +174,98 @@ def test_refinement_improves_an_advected_pulse(oracle_mod):
     # the covered coarse cells are the averages of the patch
     np.testing.assert_allclose(qco[0, 2 + cj0: 2 + cj0 + ch, 2 + ci0: 2 + ci0 + cw],
                                qfs[0][0, 2:-2, 2:-2].reshape(ch, r, cw, r).mean(axis=(1, 3)), atol=1e-14)
+
+
+# ---- the edge flux and refluxing --------------------------------------------
+
+def _random_state(oracle_mod, solver, mx, my, seed):
+    rng = np.random.default_rng(seed)
+    if solver == "advection":
+        return rng.uniform(0, 1, (1, my, mx))
+    if solver == "acoustics":
+        return rng.uniform(-1, 1, (3, my, mx))
+    if solver == "swe":
+        return np.stack([1 + 0.5 * rng.uniform(0, 1, (my, mx)), 0.3 * rng.uniform(-1, 1, (my, mx)),
+                         0.3 * rng.uniform(-1, 1, (my, mx))])
+    rho = 1 + 0.5 * rng.uniform(0, 1, (my, mx))
+    return np.stack([rho, 0.4 * rho * rng.uniform(-1, 1, (my, mx)), 0.4 * rho * rng.uniform(-1, 1, (my, mx)),
+                     2.5 + rng.uniform(0, 1, (my, mx))])
+
+
+def _prob(oracle_mod, solver, mx, my, bc, limiter=4, order=2, transverse=1):
+    sid = {"advection": oracle_mod.ADVECTION, "acoustics": oracle_mod.ACOUSTICS, "swe": oracle_mod.SWE,
+           "euler": oracle_mod.EULER}[solver]
+    param = {"advection": (1.0, -0.6, 0, 0), "acoustics": (1.0, 4.0, 0, 0), "swe": (9.81, 0, 0, 0),
+             "euler": (1.4, 0, 0, 0)}[solver]
+    return oracle_mod.Problem(sid, mx, my, 1.0 / mx, 1.0 / my, limiter=limiter, order=order,
+                              transverse=transverse, bc=bc, param=param)
+
+
+@pytest.mark.parametrize("solver,limiter,order,transverse", [
+    ("advection", 4, 2, 1), ("acoustics", 1, 2, 2), ("swe", 4, 2, 1), ("swe", 3, 2, 2),
+    ("euler", 4, 2, 1), ("euler", 2, 1, 0), ("euler", 4, 2, 2)])
+def test_edge_fluxes_reproduce_the_step(oracle_mod, solver, limiter, order, transverse):
+    """Minus the difference of the edge fluxes, computed edge by edge from
+    the stencil, is the step's update of every cell (step.c builds it from
+    whole-grid work arrays instead)."""
+    mx, my = 9, 7
+    p = _prob(oracle_mod, solver, mx, my, (BCX, 2, BCP, BCP), limiter, order, transverse)
+    q = np.zeros(p.shape)
+    q[:, 2:-2, 2:-2] = _random_state(oracle_mod, solver, mx, my, 11)
+    q = oracle_mod.bc_fill(p, q)
+    dt = 0.6 / oracle_mod.max_cell_speed(p, q)
+    want, _, flags = oracle_mod.step(p, q, dt)
+    assert flags == 0
+    Fx = np.array([[oracle_mod.edge_flux(p, q, dt, 0, i, j) for i in range(mx + 1)] for j in range(my)])
+    Fy = np.array([[oracle_mod.edge_flux(p, q, dt, 1, i, j) for i in range(mx)] for j in range(my + 1)])
+    got = q[:p.meqn, 2:-2, 2:-2] - dt / p.dx * np.moveaxis(Fx[:, 1:] - Fx[:, :-1], 2, 0) \
+        - dt / p.dy * np.moveaxis(Fy[1:] - Fy[:-1], 2, 0)
+    scale = np.abs(q[:p.meqn]).max()
+    np.testing.assert_allclose(got, want[:p.meqn, 2:-2, 2:-2], atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("solver", ["advection", "swe", "euler"])
+def test_refluxing_conserves(oracle_mod, solver):
+    """On a periodic coarse grid the sum over all coarse cells is conserved
+    to rounding with the flux correction, and not without it."""
+    mx, my, r = 16, 14, 2
+    p = _prob(oracle_mod, solver, mx, my, (BCP,) * 4)
+    q0 = np.zeros(p.shape)
+    q0[:, 2:-2, 2:-2] = _random_state(oracle_mod, solver, mx, my, 5)
+    patches = [(3, 2, 4, 5), (9, 6, 4, 4), (2, 9, 5, 3)]
+    dt = 0.4 / oracle_mod.max_cell_speed(p, oracle_mod.bc_fill(p, q0))
+    drift = {}
+    for reflux in (False, True):
+        qc = q0.copy()
+        qf = []
+        for (ci0, cj0, cw, ch) in patches:
+            a = np.zeros(oracle_mod.fine_problem(p, r, (ci0, cj0, cw, ch)).shape)
+            a[:, 2:-2, 2:-2] = np.repeat(np.repeat(q0[:, 2 + cj0: 2 + cj0 + ch, 2 + ci0: 2 + ci0 + cw], r, 1), r, 2)
+            qf.append(a)
+        s0 = q0[:, 2:-2, 2:-2].sum(axis=(1, 2))
+        for _ in range(3):
+            qc, flags = oracle_mod.amr_step(p, r, patches, qc, qf, dt, reflux=reflux)
+            assert flags == 0
+        drift[reflux] = np.abs(qc[:, 2:-2, 2:-2].sum(axis=(1, 2)) - s0).max() / np.abs(s0).max()
+    assert drift[True] < 1e-13, drift
+    assert drift[False] > 1e3 * max(drift[True], 1e-16), drift
+
+
+def test_refluxing_keeps_uniform_state_and_single_grid(oracle_mod):
+    """A uniform state stays uniform; ratio 1 with one patch over the whole
+    grid has no corrected edge and is the single-grid step."""
+    mx, my = 10, 8
+    p = _prob(oracle_mod, "swe", mx, my, (2, 2, 2, 2))
+    qc = np.zeros(p.shape)
+    qc[0] = 1.3
+    qf = [np.zeros(oracle_mod.fine_problem(p, 2, pt).shape) for pt in [(2, 2, 3, 3), (6, 2, 3, 4)]]
+    for a in qf:
+        a[0] = 1.3
+    out, _ = oracle_mod.amr_step(p, 2, [(2, 2, 3, 3), (6, 2, 3, 4)], qc, qf, 0.02, reflux=True)
+    np.testing.assert_allclose(out[:, 2:-2, 2:-2], qc[:, 2:-2, 2:-2], atol=1e-14)
+    q = np.zeros(p.shape)
+    q[:, 2:-2, 2:-2] = _random_state(oracle_mod, "swe", mx, my, 2)
+    dt = 0.5 / oracle_mod.max_cell_speed(p, oracle_mod.bc_fill(p, q))
+    single, _, _ = oracle_mod.step(p, q, dt)
+    amr, _ = oracle_mod.amr_step(p, 1, [(0, 0, mx, my)], q, [q.copy()], dt, reflux=True)
+    np.testing.assert_allclose(amr, single, atol=1e-14)
