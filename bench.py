@@ -407,9 +407,9 @@ def bench_amr(args, rank, world):
     """Shallow-water dam break on a 4096^2 coarse grid (FP32, walls) with
     ratio-2 patches of 128^2 coarse cells over the ring 0.3 <= r <= 0.7 that
     the waves cross: K coarse steps of mc_amr_advance (two fine steps per
-    patch each), against a uniformly fine 8192^2 grid advanced over the same
-    simulated time with the fused step alone.  The coarse state and the patch
-    states together exceed the L2."""
+    patch each, conservative coupling by refluxing), against a uniformly fine
+    8192^2 grid advanced over the same simulated time with the fused step
+    alone.  The coarse state and the patch states together exceed the L2."""
     import torch
     import paper_1308_1464_gb300 as mc
     from paper_1308_1464_gb300 import workloads
@@ -439,7 +439,7 @@ def bench_amr(args, rank, world):
                 v[:, 2:-2, x0: x0 + fp.mx] = torch.from_numpy(np.repeat(np.repeat(sub, r, 1), r, 2)).cuda()
                 patches.append((bi * blk, bj * blk, blk, blk, a.data_ptr(), b.data_ptr()))
                 fine.append((a, b))
-    amr = mc.Amr(p, r, patches)
+    amr = mc.Amr(p, r, patches, reflux=True)
     smax = ctx.max_cell_speed(qa.ptr)
     dt = 0.8 / smax
     K = args.steps
@@ -483,7 +483,7 @@ def bench_amr(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "shallow-water dam break, 4096^2 coarse fp32 walls, ratio-2 patches "
-                               "of 128^2 coarse cells over the ring 0.3 <= r <= 0.7, CFL 0.8",
+                               "of 128^2 coarse cells over the ring 0.3 <= r <= 0.7, refluxing, CFL 0.8",
                    "patches": len(patches), "fine_cells": fine_cells,
                    "l2": "inputs larger than L2 (%d MB coarse state, %d MB of patch states)"
                          % (int(ctx.layout.bytes) // 10**6,
@@ -491,9 +491,10 @@ def bench_amr(args, rank, world):
         "uniform_fine": {"grid": f"{r * nc}x{r * nc}", "ms_for_same_time": fms,
                          "amr_ms": ms, "amr_speedup": fms / ms},
         # per coarse step: ghost fill + fused step (coarse), ghost fill of the
-        # new coarse state, ratio x (patch ghosts + one multi-patch fused step),
-        # average down
-        "gpu_launches": K * (2 + 1 + 2 * r + 1),
+        # new coarse state, the coarse boundary fluxes, ratio x (patch ghosts +
+        # fine boundary fluxes + one multi-patch fused step), average down, the
+        # flux correction (one launch per edge class) and a last ghost fill
+        "gpu_launches": K * (2 + 1 + 1 + 3 * r + 1 + 4 + 1),
         "clocks": clk.summary(),
     }
 

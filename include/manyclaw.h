@@ -168,6 +168,14 @@ mc_status mc_amr_fine_problem(const mc_problem* coarse, int32_t ratio, const mc_
                               mc_problem* out);
 mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_patch* patches,
                         int32_t npatch, mc_amr** out);
+/* Conservative coupling (off by default): after each coarse step the coarse
+ * cells outside the patches take dt/d times the difference between the flux
+ * the coarse step put through their patch-boundary edge and the mean of the
+ * fine fluxes through it over the fine steps (Berger & Colella 1989; the flux
+ * of an edge is f(Q_low) + A-dQ plus the limited correction and transverse
+ * terms).  Edges on the domain boundary and edges between two patches are not
+ * corrected.  on: 0 or 1. */
+mc_status mc_amr_set_reflux(mc_amr* amr, int32_t on);
 mc_status mc_amr_destroy(mc_amr* amr);
 /* nsteps coarse steps of dt.  The coarse state alternates between qc_a and
  * qc_b (coarse_in_b: which holds the result); every patch's state is in its

@@ -96,6 +96,7 @@ def lib():
         L.mc_amr_create.argtypes = [P, ctypes.c_int32, ctypes.POINTER(AmrPatch), ctypes.c_int32,
                                     ctypes.POINTER(_VP)]
         L.mc_amr_destroy.argtypes = [_VP]
+        L.mc_amr_set_reflux.argtypes = [_VP, ctypes.c_int32]
         L.mc_amr_advance.argtypes = [_VP, _VP, _VP, ctypes.c_int32, ctypes.c_double,
                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _VP]
         L.mc_newton_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -438,11 +439,16 @@ class Amr:
     """Refined patches on a coarse grid (mc_amr_*).  patches: list of
     (ci0, cj0, cw, ch, qa_ptr, qb_ptr)."""
 
-    def __init__(self, coarse: Problem, ratio: int, patches):
+    def __init__(self, coarse: Problem, ratio: int, patches, reflux: bool = False):
         arr = (AmrPatch * max(1, len(patches)))(*[AmrPatch(*pt) for pt in patches])
         h = _VP()
         check(lib().mc_amr_create(ctypes.byref(coarse), int(ratio), arr, len(patches), ctypes.byref(h)))
         self._h = h
+        self.set_reflux(reflux)
+
+    def set_reflux(self, on: bool) -> None:
+        """Flux correction of the coarse cells outside the patches."""
+        check(lib().mc_amr_set_reflux(self._h, int(bool(on))))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

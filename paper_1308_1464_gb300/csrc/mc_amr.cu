@@ -12,9 +12,15 @@
 // cell's value plus MC-limited slopes, a conservative reconstruction.
 // The patches' steps are one launch of the fused step over all of them
 // (mc_multi.cuh).  Afterwards one kernel replaces every covered coarse cell by
-// the mean of its fine cells.  There is no refluxing.  Everything is enqueued
-// on the caller's stream; the only synchronisation is the status check at
-// the end.
+// the mean of its fine cells.  With refluxing on (mc_amr_set_reflux), the
+// coarse cells outside the patches get the flux correction of Berger &
+// Colella: the flux the coarse step put through each patch-boundary edge is
+// recorded (mc_edge_flux.cuh), the fine fluxes through the same edge are
+// subtracted over the fine steps with weight 1/ratio^2 each, and the outside
+// cell receives dt/d times the difference.  Edges on the domain boundary and
+// edges whose outside cell lies in another patch are not corrected.
+// Everything is enqueued on the caller's stream; the only synchronisation is
+// the status check at the end.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -22,6 +28,7 @@
 #include <new>
 #include <vector>
 
+#include "mc_edge_flux.cuh"
 #include "mc_internal.h"
 #include "mc_multi.cuh"
 
@@ -46,6 +53,71 @@ struct AmrArgs {
     long long c_ldx, c_ldf;
     double alpha;
 };
+
+// A coarse edge on a patch boundary that gets the flux correction: normal
+// dir, high cell (ci, cj), the outside coarse cell (oi, oj) and the sign of
+// its update from this edge (+1: the edge is the cell's high edge), the
+// patch, and the high cell (fi, fj) of the first of the ratio fine edges
+// along it in the patch's local indices.
+struct RefluxEdge {
+    int dir, ci, cj, oi, oj, sgn, patch, fi, fj;
+};
+
+template <class RP>
+__global__ void amr_coarse_flux_kernel(const RP rp, const StateView<typename RP::real> V,
+                                       const RefluxEdge* E, int n, typename RP::real dtdx,
+                                       typename RP::real dtdy, const EdgeScheme S, double* D)
+{
+    using T = typename RP::real;
+    constexpr int N = RP::NEQ;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        T F[N];
+        if (E[e].dir == 0) edge_flux<RP, 0>(rp, V, E[e].ci, E[e].cj, dtdx, dtdy, S, F);
+        else edge_flux<RP, 1>(rp, V, E[e].ci, E[e].cj, dtdy, dtdx, S, F);
+#pragma unroll
+        for (int m = 0; m < N; m++) D[(long long)e * N + m] = double(F[m]);
+    }
+}
+
+template <class RP>
+__global__ void amr_fine_flux_kernel(const RP rp, const AmrPatchDev* P, int cur, long long x_offset,
+                                     const RefluxEdge* E, int n, int ratio, typename RP::real dtdx,
+                                     typename RP::real dtdy, const EdgeScheme S, double* D)
+{
+    using T = typename RP::real;
+    constexpr int N = RP::NEQ;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const AmrPatchDev& d = P[E[e].patch];
+        const StateView<T> V{static_cast<const T*>(d.q[cur]), d.ld_x, d.ld_field, x_offset};
+        double acc[N];
+#pragma unroll
+        for (int m = 0; m < N; m++) acc[m] = 0.0;
+        for (int t = 0; t < ratio; t++) {
+            T F[N];
+            if (E[e].dir == 0) edge_flux<RP, 0>(rp, V, E[e].fi, E[e].fj + t, dtdx, dtdy, S, F);
+            else edge_flux<RP, 1>(rp, V, E[e].fi + t, E[e].fj, dtdy, dtdx, S, F);
+#pragma unroll
+            for (int m = 0; m < N; m++) acc[m] += double(F[m]);
+        }
+        const double w = 1.0 / (double(ratio) * ratio);
+#pragma unroll
+        for (int m = 0; m < N; m++) D[(long long)e * N + m] -= w * acc[m];
+    }
+}
+
+// the correction of the outside cells of edges [begin, end), whose outside
+// cells are distinct (one normal and sign class)
+template <typename T>
+__global__ void amr_reflux_kernel(T* qc, long long ldx, long long ldf, long long x_offset,
+                                  const RefluxEdge* E, int begin, int end, int meqn, double dtdx,
+                                  double dtdy, const double* D)
+{
+    for (int e = begin + blockIdx.x * blockDim.x + threadIdx.x; e < end; e += gridDim.x * blockDim.x) {
+        T* c = qc + (long long)(E[e].oj + 2) * ldx + x_offset + E[e].oi;
+        const double f = E[e].sgn * (E[e].dir == 0 ? dtdx : dtdy);
+        for (int m = 0; m < meqn; m++) c[m * ldf] += T(f * D[(long long)e * meqn + m]);
+    }
+}
 
 __device__ __forceinline__ int floordiv_(int a, int b)
 {
@@ -167,7 +239,132 @@ struct mc_amr {
     int* status = nullptr;
     long long nghost = 0, ncell = 0, ntask = 0;
     int fine_in_b = 0;   // which buffer of every patch holds its current state
+    int reflux = 0;
+    RefluxEdge* edges = nullptr;  // corrected edges, grouped by (dir, sgn) class
+    int nedge = 0;
+    int cls[5] = {0, 0, 0, 0, 0}; // class boundaries in edges
+    double* D = nullptr;          // nedge x meqn flux differences
 };
+
+namespace {
+
+bool covered_by(const std::vector<mc_amr_patch>& P, int i, int j)
+{
+    for (const auto& a : P)
+        if (i >= a.ci0 && i < a.ci0 + a.cw && j >= a.cj0 && j < a.cj0 + a.ch) return true;
+    return false;
+}
+
+// the corrected edges of all patches, grouped by (dir, sgn): x-edges whose
+// outside cell lies below in x (+1), above (-1), then the y-edges alike
+std::vector<RefluxEdge> reflux_edges(const mc_problem& pc, int ratio, const std::vector<mc_amr_patch>& P,
+                                     int* cls)
+{
+    std::vector<RefluxEdge> out;
+    for (int c = 0; c < 4; c++) {
+        cls[c] = (int)out.size();
+        const int dir = c / 2, sgn = c % 2 == 0 ? 1 : -1;
+        for (int p = 0; p < (int)P.size(); p++) {
+            const mc_amr_patch& a = P[p];
+            const int len = dir == 0 ? a.ch : a.cw;
+            for (int k = 0; k < len; k++) {
+                RefluxEdge e;
+                e.dir = dir;
+                e.sgn = sgn;
+                e.patch = p;
+                if (dir == 0) {
+                    e.cj = e.oj = a.cj0 + k;
+                    e.ci = sgn > 0 ? a.ci0 : a.ci0 + a.cw;
+                    e.oi = sgn > 0 ? a.ci0 - 1 : a.ci0 + a.cw;
+                    e.fi = sgn > 0 ? 0 : ratio * a.cw;
+                    e.fj = ratio * k;
+                } else {
+                    e.ci = e.oi = a.ci0 + k;
+                    e.cj = sgn > 0 ? a.cj0 : a.cj0 + a.ch;
+                    e.oj = sgn > 0 ? a.cj0 - 1 : a.cj0 + a.ch;
+                    e.fi = ratio * k;
+                    e.fj = sgn > 0 ? 0 : ratio * a.ch;
+                }
+                if (e.oi < 0 || e.oi >= pc.mx || e.oj < 0 || e.oj >= pc.my) continue;
+                if (covered_by(P, e.oi, e.oj)) continue;
+                out.push_back(e);
+            }
+        }
+    }
+    cls[4] = (int)out.size();
+    return out;
+}
+
+int grid_of(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 4096) b = 4096;
+    return b < 1 ? 1 : int(b);
+}
+
+// coarse (record the coarse step's fluxes from its filled input q) or fine
+// (subtract the fluxes of every patch's current buffer `cur`)
+template <class RP>
+cudaError_t flux_launch_t(const mc_amr* A, bool coarse, const void* q, int cur, double dt, cudaStream_t s)
+{
+    using T = typename RP::real;
+    RP rp;
+    rp.setup(A->coarse.param, A->coarse.efix);
+    const EdgeScheme S{A->coarse.limiter, A->coarse.order >= 2, A->coarse.transverse};
+    const int blocks = grid_of(A->nedge, 128);
+    if (coarse) {
+        const StateView<T> V{static_cast<const T*>(q), A->clay.ld_x, A->clay.ld_field, A->clay.x_offset};
+        amr_coarse_flux_kernel<RP><<<blocks, 128, 0, s>>>(rp, V, A->edges, A->nedge, T(dt / A->coarse.dx),
+                                                           T(dt / A->coarse.dy), S, A->D);
+    } else {
+        amr_fine_flux_kernel<RP><<<blocks, 128, 0, s>>>(rp, A->desc, cur, A->clay.x_offset, A->edges, A->nedge,
+                                                         A->ratio, T(dt / A->ratio / A->fine.dx),
+                                                         T(dt / A->ratio / A->fine.dy), S, A->D);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t flux_launch_dtype(const mc_amr* A, bool coarse, const void* q, int cur, double dt, cudaStream_t s)
+{
+    switch (A->coarse.solver) {
+    case MC_ACOUSTICS: return flux_launch_t<AcousticsRP<T>>(A, coarse, q, cur, dt, s);
+    case MC_SWE_ROE: return flux_launch_t<SweRP<T>>(A, coarse, q, cur, dt, s);
+    case MC_ADVECTION: return flux_launch_t<AdvectionRP<T>>(A, coarse, q, cur, dt, s);
+    case MC_EULER_GODUNOV: return flux_launch_t<EulerGodunovRP<T>>(A, coarse, q, cur, dt, s);
+    default: return flux_launch_t<EulerRP<T>>(A, coarse, q, cur, dt, s);
+    }
+}
+
+cudaError_t flux_launch(const mc_amr* A, bool coarse, const void* q, int cur, double dt, cudaStream_t s)
+{
+    if (A->nedge == 0) return cudaSuccess;
+    return A->clay.elem_bytes == 8 ? flux_launch_dtype<double>(A, coarse, q, cur, dt, s)
+                                   : flux_launch_dtype<float>(A, coarse, q, cur, dt, s);
+}
+
+cudaError_t reflux_apply(const mc_amr* A, void* qc, double dt, cudaStream_t s)
+{
+    const int meqn = solver_meqn(A->coarse.solver);
+    for (int c = 0; c < 4; c++) {
+        const int b = A->cls[c], e = A->cls[c + 1];
+        if (e <= b) continue;
+        const int blocks = grid_of(e - b, 128);
+        if (A->clay.elem_bytes == 8)
+            amr_reflux_kernel<double><<<blocks, 128, 0, s>>>(static_cast<double*>(qc), A->clay.ld_x, A->clay.ld_field,
+                                                             A->clay.x_offset, A->edges, b, e, meqn,
+                                                             dt / A->coarse.dx, dt / A->coarse.dy, A->D);
+        else
+            amr_reflux_kernel<float><<<blocks, 128, 0, s>>>(static_cast<float*>(qc), A->clay.ld_x, A->clay.ld_field,
+                                                            A->clay.x_offset, A->edges, b, e, meqn,
+                                                            dt / A->coarse.dx, dt / A->coarse.dy, A->D);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
 
 static void amr_free(mc_amr* a)
 {
@@ -178,6 +375,8 @@ static void amr_free(mc_amr* a)
     cudaFree(a->maps);
     cudaFree(a->prefix);
     cudaFree(a->status);
+    cudaFree(a->edges);
+    cudaFree(a->D);
     delete a;
 }
 
@@ -325,7 +524,30 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
             return cuda_error(e, "patch descriptors");
         }
     }
+    {
+        std::vector<RefluxEdge> edges = reflux_edges(*coarse, ratio, A->patches, A->cls);
+        A->nedge = (int)edges.size();
+        if (A->nedge > 0) {
+            const int meqn = solver_meqn(coarse->solver);
+            cudaError_t e = cudaMalloc(&A->edges, sizeof(RefluxEdge) * A->nedge);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(A->edges, edges.data(), sizeof(RefluxEdge) * A->nedge, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&A->D, sizeof(double) * (size_t)A->nedge * meqn);
+            if (e != cudaSuccess) {
+                amr_free(A);
+                return cuda_error(e, "reflux edges");
+            }
+        }
+    }
     *out = A;
+    return MC_OK;
+}
+
+mc_status mc_amr_set_reflux(mc_amr* A, int32_t on)
+{
+    if (!A) return set_error(MC_EINVAL, "NULL argument");
+    if (on != 0 && on != 1) return set_error(MC_EINVAL, "reflux must be 0 or 1");
+    A->reflux = on;
     return MC_OK;
 }
 
@@ -361,9 +583,14 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
     for (int n = 0; n < nsteps; n++) {
         void* qin = cb ? qc_b : qc_a;
         void* qout = cb ? qc_a : qc_b;
+        const bool rf = A->reflux && np > 0 && A->nedge > 0;
         mc_status st = mc_step(A->cctx, qin, qout, dt, nullptr, stream);   // fills qin's ghosts
         if (st == MC_OK) st = mc_bc_fill(A->cctx, qout, stream);
         if (st != MC_OK) return st;
+        if (rf) {
+            cudaError_t e = flux_launch(A, true, qin, 0, dt, s);
+            if (e != cudaSuccess) return cuda_error(e, "coarse boundary fluxes");
+        }
         a.qc0 = qin;
         a.qc1 = qout;
         for (int sub = 0; sub < A->ratio && np > 0; sub++) {
@@ -373,6 +600,10 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
             else amr_ghost_kernel<float><<<gblocks > 0 ? gblocks : 1, 256, 0, s>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_error(e, "patch ghost fill");
+            if (rf) {
+                e = flux_launch(A, false, nullptr, fb, dt, s);
+                if (e != cudaSuccess) return cuda_error(e, "fine boundary fluxes");
+            }
             M.cur = fb;
             e = multi_launch(M);
             if (e != cudaSuccess) return cuda_error(e, "patch steps");
@@ -384,6 +615,12 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
             else amr_average_kernel<float><<<ablocks > 0 ? ablocks : 1, 256, 0, s>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_error(e, "average down");
+            if (rf) {
+                e = reflux_apply(A, qout, dt, s);
+                if (e != cudaSuccess) return cuda_error(e, "flux correction");
+            }
+            st = mc_bc_fill(A->cctx, qout, stream);
+            if (st != MC_OK) return st;
         }
         cb ^= 1;
     }

@@ -5,7 +5,9 @@ every patch, ghost layers from neighbouring patches or the interpolated
 coarse state, covered coarse cells averaged down) are compared with the
 oracle's two-level step on the same rounded input.  One coarse step chains
 ratio + 1 fused steps, so the FP32 bound is the per-step tolerance times
-(ratio + 1).
+(ratio + 1).  With refluxing the coarse cells outside the patches also get
+the flux correction, and on a periodic FP64 grid the coarse sum is conserved
+to rounding.
 """
 import numpy as np
 import pytest
@@ -62,8 +64,9 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("reflux", [False, True])
 @pytest.mark.parametrize("solver,dtype,bc,ratio,patches", CASES)
-def test_amr_parity(solver, dtype, bc, ratio, patches):
+def test_amr_parity(solver, dtype, bc, ratio, patches, reflux):
     mx, my = 18, 14
     q, dx, dy = initial_state(solver, mx, my, seed=6)
     p, op = problems(solver, mx, my, dx, dy, dtype, bc)
@@ -89,7 +92,7 @@ def test_amr_parity(solver, dtype, bc, ratio, patches):
         fprobs.append(fp)
         flays.append(fl)
     amr = mc.Amr(p, ratio, [(ci0, cj0, cw, ch, a.data_ptr(), b.data_ptr())
-                            for (ci0, cj0, cw, ch), (a, b) in zip(patches, fbufs)])
+                            for (ci0, cj0, cw, ch), (a, b) in zip(patches, fbufs)], reflux=reflux)
     # oracle state
     oqc = qo.copy()
     oqf = []
@@ -105,7 +108,7 @@ def test_amr_parity(solver, dtype, bc, ratio, patches):
         c_in_b, f_in_b = amr.advance(ca.data_ptr() if cur_a else cb.data_ptr(),
                                      cb.data_ptr() if cur_a else ca.data_ptr(), 1, dt)
         cur_a = not cur_a
-        oqc, flags = oracle.amr_step(op, ratio, opatches, oqc, oqf, dt)
+        oqc, flags = oracle.amr_step(op, ratio, opatches, oqc, oqf, dt, reflux=reflux)
         assert flags == 0
         got_c = interior(ca if cur_a else cb, lay, p)
         assert scaled_error(solver, got_c, oqc[:, 2:-2, 2:-2]) <= tol * (step + 1), step
@@ -123,3 +126,32 @@ def test_amr_rejects_bad_patches():
         mc.Amr(p, 2, [(8, 0, 4, 4, fake, fake * 2)])          # leaves the interior
     with pytest.raises(mc.McError):
         mc.Amr(p, 2, [(0, 0, 4, 4, fake, fake * 2), (3, 3, 4, 4, fake * 3, fake * 4)])   # overlap
+
+
+@pytest.mark.parametrize("solver,trans", [("swe", 1), ("euler", 2), ("advection", 0)])
+def test_reflux_conserves_on_the_gpu(solver, trans):
+    """Periodic FP64 coarse grid, three separated patches: the sum over the
+    coarse cells stays at its initial value to rounding with refluxing."""
+    mx, my, ratio = 24, 20, 2
+    q, dx, dy = initial_state(solver, mx, my, seed=3)
+    p, op = problems(solver, mx, my, dx, dy, mc.F64, (P, P, P, P), transverse=trans)
+    patches = [(3, 2, 5, 6), (12, 9, 6, 5), (4, 13, 7, 4)]
+    dt = 0.4 / oracle.max_cell_speed(op, oracle.bc_fill(op, embed(op, q)))
+    ca, lay = dev_array(p)
+    cb, _ = dev_array(p)
+    upload_interior(ca, lay, p, q)
+    bufs = []
+    for (ci0, cj0, cw, ch) in patches:
+        fp = mc.amr_fine_problem(p, ratio, ci0, cj0, cw, ch)
+        a, fl = dev_array(fp)
+        b, _ = dev_array(fp)
+        upload_interior(a, fl, fp, np.repeat(np.repeat(q[:, cj0: cj0 + ch, ci0: ci0 + cw], ratio, 1), ratio, 2))
+        bufs.append((a, b))
+    amr = mc.Amr(p, ratio, [(ci0, cj0, cw, ch, a.data_ptr(), b.data_ptr())
+                            for (ci0, cj0, cw, ch), (a, b) in zip(patches, bufs)], reflux=True)
+    c_in_b, _ = amr.advance(ca.data_ptr(), cb.data_ptr(), 4, dt)
+    got = interior(cb if c_in_b else ca, lay, p)
+    meqn = op.meqn
+    s0, s1 = q[:meqn].sum(axis=(1, 2)), got[:meqn].sum(axis=(1, 2))
+    assert np.abs(s1 - s0).max() <= 1e-12 * np.abs(q[:meqn]).sum(axis=(1, 2)).max(), (s0, s1)
+    amr.close()
