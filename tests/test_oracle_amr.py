@@ -11,7 +11,10 @@ spatial and temporal interpolation.  Pinned independently of amr.c:
 * ratio 1 with one patch over the whole grid is exactly the single-grid step;
 * a uniform state stays uniform;
 * refining the region an advected pulse crosses brings the result closer to
-  a uniformly fine run than the coarse grid alone.
+  a uniformly fine run than the coarse grid alone;
+* the pointwise edge flux reproduces the step (minus its differences is each
+  cell's update), and refluxing with it conserves the coarse sum on a
+  periodic grid to rounding.
 """
 import numpy as np
 import pytest
