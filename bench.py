@@ -398,7 +398,7 @@ def bench_batch(args, rank, world):
                    "cells": cells, "tune_policy": policy, "tune_ms": tune_ms,
                    "l2": "inputs larger than L2 (%.0f MB per state)" % (ps.nbytes / 1e6)},
         "plain": {"value": cells * K / (ms_plain * 1e-3), "ms_per_step": ms_plain / K,
-                  "launches": 3 * 2000 * K},
+                  "launches_per_step": 3 * 2000, "timed_steps": per_launch},
         "batched_over_plain": ms_plain / ms,
         "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
