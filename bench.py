@@ -231,6 +231,20 @@ def ncu_exact():
     return None
 
 
+def ncu_fp64(workload: str):
+    """FP64 counts of the fused step of an FP64 workload from the committed
+    ncu summary, if taken on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_fp64.json")) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("source_hash") == sweep_source_hash():
+            return e
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def ncu_traffic(workload: str):
     """DRAM bytes per launch of the fused step from the committed ncu summary,
     if it was taken on the current kernel sources."""
@@ -794,6 +808,19 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.workload),
                 "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
                 "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
+    f64 = ncu_fp64(args.workload) if p.dtype == mc.F64 else None
+    if f64 is not None:
+        # an FP64 step is bound by the FP64 pipe: counted FP64 flops over the
+        # live kernel time, against the nominal FP64 rate
+        tf = f64["fp64_flops_per_launch"] / (kms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": round(tf / FP64_NOMINAL_TFLOPS, 4),
+                    "traffic": f64["dram_bytes_per_launch"], "kernel": "ctu_sweep_kernel",
+                    "kernel_ms": round(kms, 4), "fp64_pipe_active_pct": f64["fp64_pipe_active_pct"],
+                    "hbm_frac": round(achieved / peak, 4),
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak is on record)",
+                    "flops_source": "FP64 thread instructions of one launch counted by ncu on these "
+                                    "sources (FMA = 2 flops, add and multiply = 1)"}
     # end to end through the host-buffer C-ABI call (pinned host memory)
     e2e = None
     if not args.no_e2e:
