@@ -103,3 +103,21 @@ def test_nonphysical_state_is_reported():
         q2, _, _ = initial_state("swe", 40, 30, seed=1)
         a.upload(q2)
         ctx.step(a.ptr, b.ptr, 1e-4)
+
+
+def test_usage_example_runs():
+    """The usage example of the package documentation: a lake at rest stays
+    at rest over 100 steps of the time-step loop."""
+    p = mc.Problem.make(mc.SWE_ROE, 512, 512, 1 / 256, 1 / 256, dtype=mc.F32,
+                        bc=(mc.BC_WALL,) * 4, param=(9.81, 0, 0, 0))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        q0 = np.zeros((3, 512, 512), np.float32)
+        q0[0] = 1.0
+        a.upload(q0)
+        dt = 0.9 / ctx.max_cell_speed(a.ptr)
+        t, dt, in_b, nrej = ctx.advance(a.ptr, b.ptr, 100, 0.9, 1.0, 0.0, dt)
+        q = (b if in_b else a).download()
+    assert nrej == 0 and t > 0
+    np.testing.assert_array_equal(q[0], 1.0)
+    np.testing.assert_array_equal(q[1:], 0.0)
