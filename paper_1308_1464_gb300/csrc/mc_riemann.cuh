@@ -1017,12 +1017,14 @@ struct EulerGodunovRP : EulerRP<T> {
         const bool seeded = pseed >= T(1e-6) * pmin && pseed <= T(1e6) * pmax;   // false for NaN
         T ps = seeded ? pseed : fmax(p0, pmin * T(1e-6));
         int updates = 0;
+        // branch values and slopes at the last iterate pprev, kept for u*
+        T fl = T(0), fdl = T(0), fr = T(0), fdr = T(0), pprev = ps;
         for (int pass = seeded ? 0 : 1; pass < 2; pass++) {
             bool conv = false;
             for (int it = 0; it < 40; it++) {
-                T fl, fdl, fr, fdr;
                 fK(ps, rl, pl, cl, fl, fdl);
                 fK(ps, rr, pr, cr, fr, fdr);
+                pprev = ps;
                 T pn = ps - (fl + fr + du) * rcp_(fdl + fdr);
                 pn = fmax(pn, pmin * T(1e-8));
                 updates++;
@@ -1033,10 +1035,11 @@ struct EulerGodunovRP : EulerRP<T> {
             if (conv) break;
             if (pass == 0) ps = fmax(p0, pmin * T(1e-6));   // the seeded run failed: restart from the guess
         }
-        T fl, fdl, fr, fdr;
-        fK(ps, rl, pl, cl, fl, fdl);
-        fK(ps, rr, pr, cr, fr, fdr);
-        const T us = T(0.5) * (ul + ur) + T(0.5) * (fr - fl);
+        // u* = (u_l + u_r)/2 + (f_R(p*) - f_L(p*))/2 (Toro eq. 4.9), with the
+        // branches taken at p* to first order from the last iterate: the
+        // final step moved p by at most tol p, so the neglected term is of
+        // order (tol p)^2 and two more branch evaluations are saved
+        const T us = T(0.5) * (ul + ur) + T(0.5) * ((fr - fl) + (fdr - fdl) * (ps - pprev));
 
         // waves and speeds, in the edge frame, then to the physical frame
         T qL[4], qSL[4], qSR[4], qR[4];
