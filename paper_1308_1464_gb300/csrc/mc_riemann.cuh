@@ -1035,7 +1035,7 @@ struct EulerGodunovRP : EulerRP<T> {
             if (conv) break;
             if (pass == 0) ps = fmax(p0, pmin * T(1e-6));   // the seeded run failed: restart from the guess
         }
-        // u* = (u_l + u_r)/2 + (f_R(p*) - f_L(p*))/2 (Toro eq. 4.9), with the
+        // u* = (u_l + u_r)/2 + (f_R(p*) - f_L(p*))/2 (Toro, ch. 4), with the
         // branches taken at p* to first order from the last iterate: the
         // final step moved p by at most tol p, so the neglected term is of
         // order (tol p)^2 and two more branch evaluations are saved
