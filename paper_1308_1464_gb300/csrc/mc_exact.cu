@@ -6,8 +6,8 @@
 //            A_K = 2 / ((gamma+1) rho_K), B_K = (gamma-1)/(gamma+1) p_K,
 //   f_K(p) = 2 c_K/(gamma-1) ((p/p_K)^z - 1),      p <= p_K (rarefaction),
 //            z = (gamma-1)/(2 gamma),
-// and u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2.  Newton runs in FP64;
-// seeds are Toro's PV, TR and TS guesses (ch. 9) or the network's proposal
+// and u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2.  Newton runs in FP64 with
+// at most one power per update (p^(z-1), shared by the two sides); seeds are Toro's PV, TR and TS guesses (ch. 9) or the network's proposal
 // p_TR exp(net(x)).  One thread per interface; a warp evaluates the network
 // for its 32 interfaces together on the tensor cores.
 #include <cuda_runtime.h>
@@ -35,46 +35,66 @@ struct ExactArgs {
 };
 
 struct Side {
-    double rho, u, p, c, A, B, kr, ik;
+    // iA = 1/A_K, ipz = p_K^-z, ikr = p_K^(1-z) / (rho_K c_K)
+    double rho, u, p, c, B, iA, kr, ipz, ikr;
 };
 
-__device__ __forceinline__ Side make_side(double gamma, double rho, double u, double p)
+// One division, one reciprocal square root and one power per side: c and
+// 1/c come from the same rsqrt, 1/A_K needs none.
+__device__ __forceinline__ Side make_side(double gamma, double z, double rho, double u, double p)
 {
     Side s;
     s.rho = rho;
     s.u = u;
     s.p = p;
-    s.c = sqrt(gamma * p / rho);
-    s.A = 2.0 / ((gamma + 1.0) * rho);
+    const double irho = 1.0 / rho;
+    const double c2 = gamma * p * irho;
+    const double rc = rsqrt(c2);
+    s.c = c2 * rc;
     s.B = (gamma - 1.0) / (gamma + 1.0) * p;
+    s.iA = 0.5 * (gamma + 1.0) * rho;
     s.kr = 2.0 * s.c / (gamma - 1.0);
-    s.ik = 1.0 / (rho * s.c);
+    s.ipz = pow(p, -z);
+    s.ikr = irho * rc * p * s.ipz;
     return s;
 }
 
-__device__ __forceinline__ void branch(const Side& s, double p, double z, double& f, double& fd)
+// f_K and f_K' at p; w = p^(z-1) is shared by both sides (only read on the
+// rarefaction branch).  Shock: sqrt(A/(B+p)) = rsqrt((B+p)/A) and
+// 1/(B+p) = q^2/A.  Rarefaction: (p/p_K)^z = w p p_K^-z and
+// f_K' = (p/p_K)^(z-1) / (rho_K c_K) = w p_K^(1-z) / (rho_K c_K).
+__device__ __forceinline__ void branch(const Side& s, double p, double w, double& f, double& fd)
 {
     if (p > s.p) {
-        const double q = sqrt(s.A / (s.B + p));
-        f = (p - s.p) * q;
-        fd = q * (1.0 - 0.5 * (p - s.p) / (s.B + p));
+        const double q = rsqrt((s.B + p) * s.iA);
+        const double dp = p - s.p;
+        f = dp * q;
+        fd = q * (1.0 - 0.5 * dp * q * q * s.iA);
     } else {
-        const double r = p / s.p;
-        const double pz = pow(r, z);
-        f = s.kr * (pz - 1.0);
-        fd = s.ik * pz / r;   // (p/p_K)^(-(gamma+1)/(2 gamma)) = (p/p_K)^z / (p/p_K)
+        f = s.kr * (w * p * s.ipz - 1.0);
+        fd = s.ikr * w;
     }
 }
 
-// Newton from p0; returns true on convergence, counts updates in it
+// The last Newton evaluation: f_K, f_K' at the iterate p it was taken at.
+struct NewtonEval {
+    double p, fl, fdl, fr, fdr;
+};
+
+// Newton from p0; returns true on convergence, counts updates in it.  The
+// power p^(z-1) is formed once per update, and only when a side of some lane
+// of the warp is on its rarefaction branch.
 __device__ __forceinline__ bool newton(const Side& L, const Side& R, double z, double p0,
-                                       double tol, int max_iter, double& ps, int& it)
+                                       double tol, int max_iter, double& ps, int& it,
+                                       NewtonEval& ev)
 {
     double p = p0;
     for (int k = 0; k < max_iter; k++) {
+        const double w = (p <= L.p || p <= R.p) ? pow(p, z - 1.0) : 0.0;
         double fl, fdl, fr, fdr;
-        branch(L, p, z, fl, fdl);
-        branch(R, p, z, fr, fdr);
+        branch(L, p, w, fl, fdl);
+        branch(R, p, w, fr, fdr);
+        ev = NewtonEval{p, fl, fdl, fr, fdr};
         double pn = p - (fl + fr + (R.u - L.u)) / (fdl + fdr);
         if (pn < PFLOOR) pn = PFLOOR;
         it++;
@@ -82,7 +102,7 @@ __device__ __forceinline__ bool newton(const Side& L, const Side& R, double z, d
             ps = p;
             return false;
         }
-        if (fabs(pn - p) / pn < tol) {
+        if (fabs(pn - p) < tol * pn) {   // pn > 0: |dp| / p_{k+1} < tol
             ps = pn;
             return true;
         }
@@ -92,20 +112,29 @@ __device__ __forceinline__ bool newton(const Side& L, const Side& R, double z, d
     return false;
 }
 
+// u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2 (Toro, ch. 4), with f_K(p*)
+// carried from the last Newton evaluation at p to p* to first order: on
+// convergence |p* - p| < tol p*, so the omitted term is O(tol^2) of the
+// pressure scale.
+__device__ __forceinline__ double star_velocity(const Side& L, const Side& R, double ps,
+                                                const NewtonEval& ev)
+{
+    const double d = ps - ev.p;
+    return 0.5 * (L.u + R.u) + 0.5 * ((ev.fr - ev.fl) + (ev.fdr - ev.fdl) * d);
+}
+
 struct Seeds {
     double pv_raw, pv, tr, ts, adaptive, pvtr;
 };
 
-__device__ __forceinline__ Seeds seeds(double gamma, const Side& L, const Side& R)
+__device__ __forceinline__ Seeds seeds(double gamma, double z, const Side& L, const Side& R)
 {
     Seeds s;
     const double du = R.u - L.u;
-    const double z = 0.5 * (gamma - 1.0) / gamma;
     s.pv_raw = 0.5 * (L.p + R.p) - 0.125 * du * (L.rho + R.rho) * (L.c + R.c);
     s.pv = s.pv_raw < PFLOOR ? PFLOOR : s.pv_raw;
-    s.tr = pow((L.c + R.c - 0.5 * (gamma - 1.0) * du) / (L.c / pow(L.p, z) + R.c / pow(R.p, z)),
-               1.0 / z);
-    const double gl = sqrt(L.A / (L.B + s.pv)), gr = sqrt(R.A / (R.B + s.pv));
+    s.tr = pow((L.c + R.c - 0.5 * (gamma - 1.0) * du) / (L.c * L.ipz + R.c * R.ipz), 1.0 / z);
+    const double gl = rsqrt((L.B + s.pv) * L.iA), gr = rsqrt((R.B + s.pv) * R.iA);
     s.ts = (gl * L.p + gr * R.p - du) / (gl + gr);
     if (s.ts < PFLOOR) s.ts = PFLOOR;
     const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
@@ -157,14 +186,14 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
         const bool valid = i < a.n;
         Side L, R;
         if (valid) {
-            L = make_side(gamma, a.rl[i], a.ul[i], a.pl[i]);
-            R = make_side(gamma, a.rr[i], a.ur[i], a.pr[i]);
+            L = make_side(gamma, z, a.rl[i], a.ul[i], a.pl[i]);
+            R = make_side(gamma, z, a.rr[i], a.ur[i], a.pr[i]);
         } else {
-            L = make_side(gamma, 1.0, 0.0, 1.0);
+            L = make_side(gamma, z, 1.0, 0.0, 1.0);
             R = L;
         }
         const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
-        Seeds sd = seeds(gamma, L, R);
+        Seeds sd = seeds(gamma, z, L, R);
         double p0;
         switch (a.seed_mode) {
         case MC_SEED_PV: p0 = sd.pv; break;
@@ -175,6 +204,7 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
         }
         int flag = 0, it = 0;
         double ps = 0.0;
+        NewtonEval ev{};
         bool done = false;
         if (MLP) {
             float x[10];
@@ -191,7 +221,7 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
                 const double prop = sd.tr * exp(double(o));
                 const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
                 if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
-                    newton(L, R, z, prop, a.tol, a.max_iter, ps, it)) {
+                    newton(L, R, z, prop, a.tol, a.max_iter, ps, it, ev)) {
                     done = true;
                 } else {
                     flag |= MC_RS_FALLBACK;
@@ -205,15 +235,10 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
                 it = 0;
                 ps = 0.0;
             } else if (!done) {
-                if (!newton(L, R, z, p0, a.tol, a.max_iter, ps, it)) flag |= MC_RS_NOCONV;
+                if (!newton(L, R, z, p0, a.tol, a.max_iter, ps, it, ev)) flag |= MC_RS_NOCONV;
             }
             double us = __longlong_as_double(0x7ff8000000000000LL);   // NaN for vacuum
-            if (!vacuum) {
-                double fl, fdl, fr, fdr;
-                branch(L, ps, z, fl, fdl);
-                branch(R, ps, z, fr, fdr);
-                us = 0.5 * (L.u + R.u) + 0.5 * (fr - fl);
-            }
+            if (!vacuum) us = star_velocity(L, R, ps, ev);
             a.ps[i] = float(ps);
             a.us[i] = float(us);
             if (a.iters) a.iters[i] = uint8_t(it > 255 ? 255 : it);
@@ -256,11 +281,12 @@ __global__ void features_kernel(long long n, double gamma, const float* rl, cons
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const Side L = make_side(gamma, rl[i], ul[i], pl[i]);
-        const Side R = make_side(gamma, rr[i], ur[i], pr[i]);
+        const double z = 0.5 * (gamma - 1.0) / gamma;
+        const Side L = make_side(gamma, z, rl[i], ul[i], pl[i]);
+        const Side R = make_side(gamma, z, rr[i], ur[i], pr[i]);
         const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
         float x[10];
-        const Seeds sd = seeds(gamma, L, R);
+        const Seeds sd = seeds(gamma, z, L, R);
         raw_features(L, R, sd, x);
         const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
