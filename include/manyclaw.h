@@ -187,8 +187,9 @@ mc_status mc_amr_advance(mc_amr* amr, void* qc_a, void* qc_b, int32_t nsteps, do
 
 /* Pressure seeds for the exact-solution Euler solver (MC_EULER_GODUNOV): with
  * a trained seed network attached (see mc_mlp_* below), a normal solve of the
- * fused step whose jump is too strong for Toro's PV guess (the adaptive rule
- * would leave PV) starts Newton from the network's proposal p_TR exp(net(x)),
+ * fused step across a strong jump (pressure ratio 2 or more, where Toro's
+ * adaptive rule leaves the PV guess) starts Newton from the network's
+ * proposal p_TR exp(net(x)),
  * evaluated per warp on the tensor cores when any lane of the warp needs it;
  * it restarts from Toro's adaptive guess when the proposal is implausible or
  * does not converge (the Riemann kernel stays pointwise, as the paper keeps

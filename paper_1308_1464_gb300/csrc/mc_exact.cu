@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
             }
             const float o = mlp_infer_warp(*net, x, xs, outs);
             if (!vacuum && valid) {
-                const double prop = sd.tr * exp(double(o));
+                // a seed: FP32 accuracy of the factor is ample, and an FP64 exp
+                // would cost as much as a Newton update
+                const double prop = sd.tr * double(expf(o));
                 const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
                 if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
                     newton(L, R, z, prop, a.tol, a.max_iter, ps, it, ev)) {

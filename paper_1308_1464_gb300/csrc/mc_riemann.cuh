@@ -22,22 +22,24 @@ __device__ __forceinline__ T tmax0(T a) { return a > T(0) ? a : T(0); }
 
 // Reciprocal, square root and reciprocal square root.  FP32 uses the
 // hardware approximations (rcp/sqrt/rsqrt.approx: at most about 2 ulp, far
-// inside the FP32 parity tolerance); FP64 keeps correctly rounded division
-// and square root.
+// inside the FP32 parity tolerance); FP64 keeps correctly rounded square
+// roots and reciprocals, so every kernel that inlines them gets the same
+// bits (an FP64 rsqrt is not correctly rounded, and its inlined form
+// differed between kernels).
 __device__ __forceinline__ float rcp_(float x)
 {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ double rcp_(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float rsqrt_(float x)
 {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return __drcp_rn(__dsqrt_rn(x)); }
 __device__ __forceinline__ float sqrt_(float x)
 {
     float r;
@@ -885,22 +887,27 @@ struct EulerGodunovRP : EulerRP<T> {
         p = gm1 * (q[3] - T(0.5) * r * (un * un + ut * ut));
         c = sqrt_(gamma * p * ir);
     }
+    // a mild jump: p_max < 2 p_min, the pressure-ratio part of Toro's
+    // adaptive rule.  There the PV or TR/TS guess already lies close to p*,
+    // and the network is not consulted.  (Kinetic energy (m_1^2 + m_2^2) /
+    // (2 rho) does not depend on the edge's direction.)
+    __device__ __forceinline__ bool seed_mild(const T* ql, const T* qr) const
+    {
+        const T pl = gm1 * (ql[3] - T(0.5) * (ql[1] * ql[1] + ql[2] * ql[2]) * rcp_(ql[0]));
+        const T pr = gm1 * (qr[3] - T(0.5) * (qr[1] * qr[1] + qr[2] * qr[2]) * rcp_(qr[0]));
+        return fmax(pl, pr) < T(2) * fmin(pl, pr);
+    }
     // the seed network's ten raw inputs of the edge's normal problem (ln rho,
     // ln p, ln c of both sides, du, du/(c_L + c_R), ln p_TR, ln max(p_PV,
     // 1e-6)) and the two-rarefaction guess p_TR its output multiplies
-    // pv_ok: Toro's adaptive rule would keep the PV guess (p_max < 2 p_min and
-    // p_PV within [p_min, p_max]), i.e. the edge's jump is mild
     template <int DIR>
-    __device__ __forceinline__ void seed_features(const T* ql, const T* qr, float (&x)[10], float& ptr,
-                                                  bool& pv_ok) const
+    __device__ __forceinline__ void seed_features(const T* ql, const T* qr, float (&x)[10], float& ptr) const
     {
         T rl, ul, vl, pl, cl, rr, ur, vr, pr, cr;
         prim<DIR>(ql, rl, ul, vl, pl, cl);
         prim<DIR>(qr, rr, ur, vr, pr, cr);
         const T du = ur - ul;
         const T pv = T(0.5) * (pl + pr) - T(0.125) * du * (rl + rr) * (cl + cr);
-        const T pmin = fmin(pl, pr), pmax = fmax(pl, pr);
-        pv_ok = pmax < T(2) * pmin && pv >= pmin && pv <= pmax;
         const T tr = pow_((cl + cr - T(0.5) * gm1 * du) * rcp_(cl * pow_(pl, -z) + cr * pow_(pr, -z)), rz);
         x[0] = __logf(float(rl));
         x[1] = __logf(float(rr));

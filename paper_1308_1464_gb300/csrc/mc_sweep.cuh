@@ -375,17 +375,17 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             typename RP::Lin Ly;
             bool bady = false;
             // pressure seeds of the two normal problems from the network, for
-            // edges whose jump is too strong for the PV guess (Toro's rule);
-            // the whole warp evaluates it (x-edges, then y-edges), and only
-            // when one of its lanes has such an edge
+            // edges with a strong jump (pressure ratio 2 or more); the whole
+            // warp evaluates it (x-edges, then y-edges), and only when one of
+            // its lanes has such an edge
             T seed_x = T(0), seed_y = T(0);
             if constexpr (RP::SEEDED) {
                 if (W.net) {
-                    float fx[10], fy[10], trx, try_;
-                    bool okx, oky;
-                    rp.template seed_features<0>(ql1, qc1, fx, trx, okx);
-                    rp.template seed_features<1>(qc1, qc2, fy, try_, oky);
+                    const bool okx = rp.seed_mild(ql1, qc1), oky = rp.seed_mild(qc1, qc2);
                     if (__any_sync(0xffffffffu, !(okx && oky))) {
+                        float fx[10], fy[10], trx, try_;
+                        rp.template seed_features<0>(ql1, qc1, fx, trx);
+                        rp.template seed_features<1>(qc1, qc2, fy, try_);
 #pragma unroll
                         for (int m = 0; m < 10; m++) {
                             fx[m] = (fx[m] - W.net->mu[m]) / W.net->sig[m];
