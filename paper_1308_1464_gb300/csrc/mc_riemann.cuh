@@ -295,9 +295,21 @@ struct SweRP {
         efix = ef != 0;
     }
 
+    // the sweep may pass each state's 1/sqrt(h), formed once per cell
+    static constexpr bool RS_CACHE = true;
+    __device__ __forceinline__ T rs_of(const T* q) const { return rsqrt_(q[0]); }
+
     template <int DIR>
     __device__ __forceinline__ void normal(const T* ql, const T* qr, T (&W)[NW][NEQ], T (&s)[NW],
                                            T* amdq, T* apdq, Lin& L, bool& bad) const
+    {
+        normal_rs<DIR>(ql, qr, rsqrt_(ql[0]), rsqrt_(qr[0]), W, s, amdq, apdq, L, bad);
+    }
+
+    // the normal solve given rsl = 1/sqrt(h_l) and rsr = 1/sqrt(h_r)
+    template <int DIR>
+    __device__ __forceinline__ void normal_rs(const T* ql, const T* qr, T rsl, T rsr, T (&W)[NW][NEQ],
+                                              T (&s)[NW], T* amdq, T* apdq, Lin& L, bool& bad) const
     {
         constexpr int un = 1 + DIR, ut = 2 - DIR;
         const T hl = ql[0], hr = qr[0];
@@ -306,7 +318,6 @@ struct SweRP {
         bad = bad || !(hl > T(0) && hr > T(0));
         // Roe average: sqrt(h) u = hu / sqrt(h), so one reciprocal square
         // root per state gives both weights
-        const T rsl = rsqrt_(hl), rsr = rsqrt_(hr);
         const T w = rcp_(hl * rsl + hr * rsr);
         const T u = (ql[un] * rsl + qr[un] * rsr) * w;
         const T v = (ql[ut] * rsl + qr[ut] * rsr) * w;

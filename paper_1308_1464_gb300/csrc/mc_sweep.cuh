@@ -40,6 +40,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mc_device.cuh"
 #include "mc_riemann.cuh"
 #include "mc_seednet.cuh"
@@ -66,6 +68,50 @@ struct SweepArgs {
     const MlpDev* net;                    // pressure-seed network, or null (solvers with SEEDED)
     unsigned long long* newton_updates;   // [0] Newton updates, [1] normal solves, or null
 };
+
+// Solvers that take each state's 1/sqrt(h) from the caller (RS_CACHE):
+// the scalar sweep forms it once per cell and carries it down the march,
+// instead of twice per edge.
+template <class RP, class = void>
+struct rs_cache : std::false_type {};
+template <class RP>
+struct rs_cache<RP, std::void_t<decltype(RP::RS_CACHE)>> : std::bool_constant<RP::RS_CACHE> {};
+
+// theta = dl / dr of K waves.  FP32: one hardware reciprocal each.  FP64:
+// one correctly rounded reciprocal for all K (simultaneous inversion: prefix
+// products of the dr, the reciprocal of their product, then each 1/dr_k as
+// that reciprocal times the other factors), where a division costs about as
+// much as eight multiplications.  A zero wave (dr = 0, so dl = 0) takes
+// dr = 1 and theta = 0; a product outside [1e-290, 1e290] falls back to K
+// reciprocals.  Results differ from dl / dr by a few ulp.
+template <int K, typename T>
+__device__ __forceinline__ void ratios(const T (&dl)[K], const T (&dr)[K], T (&th)[K])
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < K; k++) th[k] = dl[k] * rcp_(dr[k]);
+    } else {
+        T d[K], pre[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) d[k] = dr[k] > T(0) ? dr[k] : T(1);
+        pre[0] = d[0];
+#pragma unroll
+        for (int k = 1; k < K; k++) pre[k] = pre[k - 1] * d[k];
+        const T P = pre[K - 1];
+        if (P > T(1e-290) && P < T(1e290)) {
+            T r = rcp_(P);
+#pragma unroll
+            for (int k = K - 1; k >= 1; k--) {
+                th[k] = dl[k] * (r * pre[k - 1]);
+                r *= d[k];
+            }
+            th[0] = dl[0] * r;
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; k++) th[k] = dl[k] * rcp_(d[k]);
+        }
+    }
+}
 
 // phi(theta) of K ratios theta = dl / dr at once (LeVeque 2002, eq. 6.39):
 // minmod (1), superbee (2), van Leer (3), MC (4) or none (0: phi = 1).  The
@@ -247,6 +293,13 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         }
     }
     if (!fetch(rbase, qc1, ql1)) return false;
+    // 1/sqrt(h) of qc1 and ql1 for RS_CACHE solvers
+    constexpr bool RSC = rs_cache<RP>::value && !RP::PAIRED;
+    T rs_c1 = T(0), rs_l1 = T(0);
+    if constexpr (RSC) {
+        rs_c1 = rp.rs_of(qc1);
+        rs_l1 = rp.rs_of(ql1);
+    }
 
     // transverse splits.  A y-edge fluctuation entering the cell of column c
     // whose plane vector is `cell`; with material planes the split needs that
@@ -283,6 +336,11 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             for (int q = 0; q < RP::NAUX; q++) ql0[N + q] = shfl_up1(qc0[N + q]);
         }
         if (!fetch(k + 2, qc2, ql2)) return false;
+        T rs_c2 = T(0), rs_l2 = T(0);
+        if constexpr (RSC) {
+            rs_c2 = rp.rs_of(qc2);
+            rs_l2 = rp.rs_of(ql2);
+        }
 
         // ---- y-edge between rows k+1 and k+2 of column c, x-edge c-1/2 of row k+1
         T Wy2[NW][N], sy2[NW], bm2[N], bp2[N];
@@ -376,29 +434,33 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             bool bady = false;
             // pressure seeds of the two normal problems from the network, for
             // edges with a strong jump (pressure ratio 2 or more); the whole
-            // warp evaluates it (x-edges, then y-edges), and only when one of
-            // its lanes has such an edge
+            // warp evaluates it for its x-edges when one of its lanes has
+            // such an x-edge, and likewise for the y-edges
             T seed_x = T(0), seed_y = T(0);
             if constexpr (RP::SEEDED) {
                 if (W.net) {
                     const bool okx = rp.seed_mild(ql1, qc1), oky = rp.seed_mild(qc1, qc2);
-                    if (__any_sync(0xffffffffu, !(okx && oky))) {
-                        float fx[10], fy[10], trx, try_;
-                        rp.template seed_features<0>(ql1, qc1, fx, trx);
-                        rp.template seed_features<1>(qc1, qc2, fy, try_);
+                    if (__any_sync(0xffffffffu, !okx)) {
+                        float f[10], tr;
+                        rp.template seed_features<0>(ql1, qc1, f, tr);
 #pragma unroll
-                        for (int m = 0; m < 10; m++) {
-                            fx[m] = (fx[m] - W.net->mu[m]) / W.net->sig[m];
-                            fy[m] = (fy[m] - W.net->mu[m]) / W.net->sig[m];
-                        }
-                        const float ox = mlp_infer_warp(*W.net, fx, W.xs, W.outs);
-                        const float oy = mlp_infer_warp(*W.net, fy, W.xs, W.outs);
-                        if (!okx) seed_x = T(trx * __expf(ox));
-                        if (!oky) seed_y = T(try_ * __expf(oy));
+                        for (int m = 0; m < 10; m++) f[m] = (f[m] - W.net->mu[m]) / W.net->sig[m];
+                        const float o = mlp_infer_warp(*W.net, f, W.xs, W.outs);
+                        if (!okx) seed_x = T(tr * __expf(o));
+                    }
+                    if (__any_sync(0xffffffffu, !oky)) {
+                        float f[10], tr;
+                        rp.template seed_features<1>(qc1, qc2, f, tr);
+#pragma unroll
+                        for (int m = 0; m < 10; m++) f[m] = (f[m] - W.net->mu[m]) / W.net->sig[m];
+                        const float o = mlp_infer_warp(*W.net, f, W.xs, W.outs);
+                        if (!oky) seed_y = T(tr * __expf(o));
                     }
                 }
                 newton_n += rp.template normal_seeded<1>(qc1, qc2, seed_y, Wy2, sy2, bm2, bp2, Ly, bady);
                 newton_s += 1;
+            } else if constexpr (RSC) {
+                rp.template normal_rs<1>(qc1, qc2, rs_c1, rs_c2, Wy2, sy2, bm2, bp2, Ly, bady);
             } else {
                 rp.template normal<1>(qc1, qc2, Wy2, sy2, bm2, bp2, Ly, bady);
             }
@@ -420,6 +482,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 if constexpr (RP::SEEDED) {
                     newton_n += rp.template normal_seeded<0>(ql1, qc1, seed_x, Wx, sxw, amdq1, apdq1, Lx, badx);
                     newton_s += 1;
+                } else if constexpr (RSC) {
+                    rp.template normal_rs<0>(ql1, qc1, rs_l1, rs_c1, Wx, sxw, amdq1, apdq1, Lx, badx);
                 } else {
                     rp.template normal<0>(ql1, qc1, Wx, sxw, amdq1, apdq1, Lx, badx);
                 }
@@ -446,33 +510,34 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             if (second) {
                 // ratios of all waves of both edges (x: 0..NW-1, y:
                 // NW..2NW-1), then one branch on the limiter
-                T th[2 * NW], phi[2 * NW];
+                T dl[2 * NW], dr[2 * NW], th[2 * NW], phi[2 * NW];
 #pragma unroll
                 for (int p = 0; p < NW; p++) {
                     const int src = (sxw[p] > T(0) ? lane - 1 : lane + 1) & 31;
-                    T dl = T(0), dr = T(0);
+                    dl[p] = dr[p] = T(0);
 #pragma unroll
                     for (int m = 0; m < N; m++) {
                         if (!RP::template wave_nz<0>(p, m)) continue;
                         const T wu = shfl(Wx[p][m], src);
-                        dl += wu * Wx[p][m];
-                        dr += Wx[p][m] * Wx[p][m];
+                        dl[p] += wu * Wx[p][m];
+                        dr[p] += Wx[p][m] * Wx[p][m];
                     }
-                    th[p] = dl * rcp_(dr);
                 }
 #pragma unroll
                 for (int p = 0; p < NW; p++) {
                     const bool upl = sy1[p] > T(0);
-                    T dl = T(0), dr = T(0);
+                    T dly = T(0), dry = T(0);
 #pragma unroll
                     for (int m = 0; m < N; m++) {
                         if (!RP::template wave_nz<1>(p, m)) continue;
-                        if constexpr (!CD) dl += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
-                        dr += Wy1[p][m] * Wy1[p][m];
+                        if constexpr (!CD) dly += (upl ? Wy0[p][m] : Wy2[p][m]) * Wy1[p][m];
+                        dry += Wy1[p][m] * Wy1[p][m];
                     }
-                    if constexpr (CD) dl = upl ? dlo[p] : dhi[p];
-                    th[NW + p] = dl * rcp_(dr);
+                    if constexpr (CD) dly = upl ? dlo[p] : dhi[p];
+                    dl[NW + p] = dly;
+                    dr[NW + p] = dry;
                 }
+                ratios<2 * NW>(dl, dr, th);
                 limiter_phis<2 * NW>(limiter, th, phi);
 #pragma unroll
                 for (int p = 0; p < NW; p++) {
@@ -570,6 +635,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
         for (int m = 0; m < NP; m++) {
             qc0[m] = qc1[m]; qc1[m] = qc2[m]; ql1[m] = ql2[m];
         }
+        rs_c1 = rs_c2;
+        rs_l1 = rs_l2;
 #pragma unroll
         for (int m = 0; m < N; m++) {
             Z0[m] = dqy_n[m] - Gn[m];

@@ -129,13 +129,15 @@ def test_tiny_and_odd_grids(mx, my, solver, dtype, bc, trans):
 
 
 @pytest.mark.parametrize("solver,dtype,trans", [("swe", mc.F32, 1), ("euler", mc.F64, 1),
-                                                ("swe", mc.F32, 2), ("euler", mc.F32, 2)])
+                                                ("swe", mc.F32, 2), ("euler", mc.F32, 2),
+                                                ("acoustics", mc.F64, 1), ("swe", mc.F64, 1)])
 def test_tile_shape_invariance(solver, dtype, trans):
-    """Results do not depend on the tile height: bitwise equal outputs."""
+    """Results do not depend on the tile height, down to one row per warp
+    task (the small grids' tiles): bitwise equal outputs."""
     mx, my = 100, 130
     q, dx, dy = initial_state(solver, mx, my, seed=9)
     p, op = problems(solver, mx, my, dx, dy, dtype, (W, X, X, W), transverse=trans)
-    outs = [run_step(p, op, q, tile_rows=t)[0] for t in (8, 17, 64, 256)]
+    outs = [run_step(p, op, q, tile_rows=t)[0] for t in (8, 1, 2, 3, 5, 17, 64, 256)]
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
 
