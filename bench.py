@@ -303,7 +303,7 @@ def cpu_baseline(wl, budget_s=12.0):
         q, smax, _ = oracle.step(op, q, dt, nthreads=cores)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 200:
+        if el >= budget_s or steps >= (200 if n >= 1024 else 10000):
             break
     return {"value": n * n * steps / el, "unit": "cell-updates/s", "cores": cores,
             "kind": "oracle",
