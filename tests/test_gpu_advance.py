@@ -121,3 +121,38 @@ def test_usage_example_runs():
     assert nrej == 0 and t > 0
     np.testing.assert_array_equal(q[0], 1.0)
     np.testing.assert_array_equal(q[1:], 0.0)
+
+
+@pytest.mark.parametrize("dtype", [mc.F64, mc.F32])
+def test_degenerate_waves(dtype):
+    """Zero and vanishing waves.  A lake at rest (every jump zero, so every
+    wave and every limiter ratio's denominator is zero) stays exactly at
+    rest.  FP64: momenta of 1e-60 give squared wave norms near 1e-120, whose
+    product over a cell's six waves leaves the normal range; the step stays
+    finite and equal to the oracle's."""
+    n = 96
+    W = mc.BC_WALL
+    p, op = problems("swe", n, n, 1 / 64, 1 / 64, dtype, (W, W, W, W))
+    npdt = np.float64 if dtype == mc.F64 else np.float32
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        q0 = np.zeros((3, n, n), npdt)
+        q0[0] = 1.0
+        a.upload(q0)
+        ctx.step(a.ptr, b.ptr, 0.002)
+        q = b.download()
+        np.testing.assert_array_equal(q[0], 1.0)
+        np.testing.assert_array_equal(q[1:], 0.0)
+        if dtype == mc.F64:
+            rng = np.random.default_rng(60)
+            q1 = q0.copy()
+            q1[1] = 1e-60 * rng.uniform(-1, 1, (n, n))
+            a.upload(q1)
+            ctx.step(a.ptr, b.ptr, 0.002)
+            got = b.download()
+            assert np.isfinite(got).all()
+            want, _, _ = oracle.step(op, embed(op, q1), 0.002)
+            want = want[:, 2:-2, 2:-2]
+            np.testing.assert_array_equal(got[0], want[0])
+            assert np.abs(got[1:] - want[1:]).max() <= 1e-12 * 1e-60
+            assert np.abs(got[1]).max() > 1e-61
