@@ -351,15 +351,23 @@ def run_reference(args, wl):
 
 
 def bench_batch(args, rank, world):
-    """2000 uneven shallow-water patches (sides log-uniform in [16, 256]), FP32,
-    walls, per-patch dt at CFL 0.9: K steps in one persistent launch inside a
-    CUDA graph with autotuned work splits, against one launch per patch per
-    step on the same GPU."""
+    """2000 uneven shallow-water patches (sides log-uniform in [16, 256]) per
+    GPU, FP32, walls, per-patch dt at CFL 0.9: K steps in one persistent
+    launch inside a CUDA graph with autotuned work splits, against one launch
+    per patch per step on the same GPU.  With N ranks the 2000 N patches of
+    the seeded set are shared by greedy longest-processing-time on cell
+    count; the patches are independent, so the ranks exchange nothing but
+    the slowest rank's time."""
     import torch
     import paper_1308_1464_gb300 as mc
     from paper_1308_1464_gb300 import autotune, workloads
+    from paper_1308_1464_gb300.blocks import lpt_shards
     from paper_1308_1464_gb300.state import PatchSet
-    pats_w = workloads.swe_patches(2000)
+    nall = 2000 * world
+    sizes_all = workloads.swe_patches(nall, with_state=False)
+    cells_all = sum(q.nx * q.ny for q in sizes_all)
+    mine = lpt_shards([q.nx * q.ny for q in sizes_all], world)[rank]
+    pats_w = workloads.swe_patches(nall, only=mine)
     pats = [(p.nx, p.ny, p.grid.dx, p.grid.dy, p.grid.q) for p in pats_w]
     cells = sum(p[0] * p[1] for p in pats)
     proto = mc.Problem.make(mc.SWE_ROE, 16, 16, 1 / 128, 1 / 128, dtype=mc.F32,
@@ -367,7 +375,7 @@ def bench_batch(args, rank, world):
     ps = PatchSet(proto, pats)
     b = mc.Batch(proto, ps.pointers())
     sizes = [(p[0], p[1]) for p in pats]
-    cache = os.path.join(tempfile.gettempdir(), "manyclaw_batch_tune.json")
+    cache = os.path.join(tempfile.gettempdir(), "manyclaw_batch_tune%s.json" % (f"_r{rank}" if world > 1 else ""))
     policy, tune_ms = autotune.tune_batch(b, sizes, ps.reset, nsteps=4, cache_path=cache)
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
@@ -380,6 +388,8 @@ def bench_batch(args, rank, world):
         ps.reset()
         b.advance(per_launch, 0.9, stream=sh)
     ps.reset()
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -388,31 +398,36 @@ def bench_batch(args, rank, world):
             b.advance(per_launch, 0.9, stream=sh)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     ps.reset()
     b.advance_plain(2, 0.9, stream=sh)       # warm the per-patch path
     ps.reset()
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     b.advance_plain(per_launch, 0.9, stream=sh)
     p1.record(stream)
     torch.cuda.synchronize()
-    ms_plain = p0.elapsed_time(p1) * K / per_launch
-    value = cells * K / (ms * 1e-3)
-    alg = 2 * cells * 3 * 4 * K
+    ms_plain = max_over_ranks(p0.elapsed_time(p1), world, "cuda") * K / per_launch
+    value = cells_all * K / (ms * 1e-3)
+    alg = 2 * cells * 3 * 4 * K     # this rank's bytes (the roofline is per GPU)
     peak, kind = measured_peaks()
     b.close()
     return {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "2000 uneven shallow-water patches (16..256 per side), fp32, walls, "
-                               "per-patch dt CFL 0.9, 20 steps per persistent launch in a CUDA graph",
-                   "cells": cells, "tune_policy": policy, "tune_ms": tune_ms,
+        "config": {"workload": "2000 uneven shallow-water patches (16..256 per side) per GPU, fp32, "
+                               "walls, per-patch dt CFL 0.9, 20 steps per persistent launch in a "
+                               "CUDA graph",
+                   "cells": cells_all, "patches": nall, "tune_policy": policy, "tune_ms": tune_ms,
+                   "parallelism": ("patches shared by LPT on cell count, %d ranks" % world
+                                   if world > 1 else "single"),
                    "l2": "inputs larger than L2 (%.0f MB per state)" % (ps.nbytes / 1e6)},
-        "plain": {"value": cells * K / (ms_plain * 1e-3), "ms_per_step": ms_plain / K,
-                  "launches_per_step": 3 * 2000, "timed_steps": per_launch},
+        "plain": {"value": cells_all * K / (ms_plain * 1e-3), "ms_per_step": ms_plain / K,
+                  "launches_per_step": 3 * len(pats), "timed_steps": per_launch},
         "batched_over_plain": ms_plain / ms,
         "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
@@ -467,6 +482,8 @@ def bench_amr(args, rank, world):
     sh = stream.cuda_stream
     for _ in range(args.warmup):
         amr.advance(qa.ptr, qb.ptr, 2, dt, sh)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -474,7 +491,7 @@ def bench_amr(args, rank, world):
         amr.advance(qa.ptr, qb.ptr, K, dt, sh)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     fine_cells = len(patches) * (r * blk) ** 2
     updates = K * (nc * nc + r * fine_cells)
     # the same simulated time on a uniformly fine grid: r K fused steps of dt / r
@@ -487,6 +504,8 @@ def bench_amr(args, rank, world):
     cf.bc_fill(fa.ptr, sh)
     for _ in range(3):
         cf.sweep(fa.ptr, fb.ptr, dt / r, sh)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
@@ -495,7 +514,7 @@ def bench_amr(args, rank, world):
         cf.step(src.ptr, dst.ptr, dt / r, want_smax=False, stream=sh)
     f1.record(stream)
     torch.cuda.synchronize()
-    fms = f0.elapsed_time(f1)
+    fms = max_over_ranks(f0.elapsed_time(f1), world, "cuda")
     amr.close()
     return {
         "metric": "cell-updates/s", "value": world * updates / (ms * 1e-3), "unit": "cell-updates/s",
@@ -505,6 +524,7 @@ def bench_amr(args, rank, world):
         "config": {"workload": "shallow-water dam break, 4096^2 coarse fp32 walls, ratio-2 patches "
                                "of 128^2 coarse cells over the ring 0.3 <= r <= 0.7, refluxing, CFL 0.8",
                    "patches": len(patches), "fine_cells": fine_cells,
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%d MB coarse state, %d MB of patch states)"
                          % (int(ctx.layout.bytes) // 10**6,
                             sum(int(a.numel()) for a, _ in fine) // 10**6)},
@@ -550,7 +570,10 @@ def bench_exact(args, rank, world):
     net, losses, train_s = train_seed_net(ntrain=ntrain, epochs=epochs, gamma=GAM)
 
     n = 1 << 24
-    test = dev_states(n, offset=0)
+    # rank r solves its own block of draws, disjoint from the others' and from
+    # the training draws at [2^26, 2^26 + 2^22)
+    off = rank * n if (rank + 1) * n <= (1 << 26) else (1 << 27) + rank * n
+    test = dev_states(n, offset=off)
     stream = torch.cuda.current_stream()
     out = {}
     clk = ClockSampler(torch.cuda.current_device())
@@ -558,6 +581,8 @@ def bench_exact(args, rank, world):
     for name, mode, nn in (("plain", mc.SEED_ADAPTIVE, None), ("learned", mc.SEED_MLP, net)):
         for _ in range(args.warmup):
             solve(test, mode, nn)
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -566,10 +591,10 @@ def bench_exact(args, rank, world):
             ps, it, fl, stats, _ = solve(test, mode, nn)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda") / reps
         st = stats.cpu().numpy()
         nonvac = st[0] - st[1]
-        out[name] = {"solves_per_s": n / (ms * 1e-3), "ms": ms,
+        out[name] = {"solves_per_s": world * n / (ms * 1e-3), "ms": ms,
                      "mean_newton_updates": float(st[4] / max(nonvac, 1)),
                      "fallback_rate": float(st[2] / max(nonvac, 1)), "vacuum": int(st[1]),
                      "not_converged": int(st[3])}
@@ -583,7 +608,7 @@ def bench_exact(args, rank, world):
     # end to end through the public call: the six state arrays from pinned host
     # memory, the learned-seed solve, p* and u* back to pinned host memory
     host = [torch.from_numpy(a.astype(np.float32)).pin_memory()
-            for a in workloads.riemann_states(n, seed=1308, offset=0)]
+            for a in workloads.riemann_states(n, seed=1308, offset=off)]
     h_ps = torch.empty(n, dtype=torch.float32).pin_memory()
     h_us = torch.empty_like(h_ps).pin_memory()
     dev = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(6)]
@@ -598,7 +623,7 @@ def bench_exact(args, rank, world):
         h_ps.copy_(ps, non_blocking=True)
         h_us.copy_(us, non_blocking=True)
         torch.cuda.synchronize()
-    el = time.perf_counter() - t0
+    el = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda") * 1e-3
     e2e = {"value": world * n * reps_e2e / el, "unit": "solves/s",
            "h2d_bytes_per_step": 6 * 4 * n, "d2h_bytes_per_step": 2 * 4 * n,
            "note": "six FP32 state arrays from pinned host memory, mc_riemann_exact with the "

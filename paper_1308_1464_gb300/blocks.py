@@ -31,6 +31,25 @@ from . import BC_GIVEN, BC_PERIODIC, Context, McError, MC_EINVAL
 XLO, XHI, YLO, YHI = 0, 1, 2, 3
 
 
+def lpt_shards(weights, nparts: int):
+    """Independent units (patches, interfaces) shared among nparts ranks by
+    greedy longest processing time: units in decreasing weight, each to the
+    currently lightest part (ties go to the lower part index).  Each shard
+    lists its units in increasing index order.  The heaviest part is at most
+    4/3 - 1/(3 nparts) times the best possible (Graham's bound)."""
+    import heapq
+    if nparts < 1:
+        raise ValueError("nparts must be >= 1")
+    order = sorted(range(len(weights)), key=lambda k: (-weights[k], k))
+    heap = [(0, part) for part in range(nparts)]
+    shards = [[] for _ in range(nparts)]
+    for k in order:
+        load, part = heapq.heappop(heap)
+        shards[part].append(k)
+        heapq.heappush(heap, (load + weights[k], part))
+    return [sorted(s) for s in shards]
+
+
 def split(n: int, parts: int):
     """Sizes and offsets of `parts` near-equal pieces of n cells (the first
     n % parts pieces one cell larger)."""

@@ -162,16 +162,18 @@ def patch_sizes(npatch: int = 2000, seed: int = DEFAULT_SEED, lo: int = 16, hi: 
 
 
 def swe_patches(npatch: int = 2000, seed: int = DEFAULT_SEED, h_cell: float = 1.0 / 128.0,
-                with_state: bool = True):
+                with_state: bool = True, only=None):
     """Uneven shallow-water patches with a Gaussian hump h = 1 + 0.5 exp(-50 r^2).
 
     Patch k covers [0, nx h_cell] x [0, ny h_cell]; the hump centre is drawn
-    uniformly inside it.  Momentum is zero.
+    uniformly inside it.  Momentum is zero.  ``only`` (indices into the
+    npatch patches) returns just those patches, in that order, each as in
+    the whole set.
     """
     nxs, nys = patch_sizes(npatch, seed)
     c = uniform(seed, S_PATCH_CENTRE, np.arange(2 * npatch, dtype=np.uint64)).reshape(npatch, 2)
     out = []
-    for k in range(npatch):
+    for k in (range(npatch) if only is None else only):
         nx, ny = int(nxs[k]), int(nys[k])
         if not with_state:
             out.append(Patch(nx, ny, None))

@@ -239,3 +239,36 @@ def test_gloo_ranks_equal_single_grid(solver, bc, px, py):
     got = gather(d, [out[r][0] for r in range(world)], q.shape[0])
     assert all(out[r][1] == t_want for r in range(world))
     np.testing.assert_array_equal(got, want)
+
+
+def test_lpt_shards():
+    """Greedy longest-processing-time sharing of independent units: every
+    unit in exactly one shard, shards sorted, the list-scheduling bound
+    (heaviest part <= total / parts + (1 - 1/parts) largest unit), one part =
+    everything, and the textbook instance where LPT misses the optimum."""
+    from paper_1308_1464_gb300.blocks import lpt_shards
+    rng = np.random.default_rng(5)
+    for parts in (1, 2, 3, 8):
+        w = [int(x) for x in rng.integers(1, 5000, 997)]
+        shards = lpt_shards(w, parts)
+        assert len(shards) == parts
+        flat = sorted(k for s in shards for k in s)
+        assert flat == list(range(len(w)))
+        assert all(s == sorted(s) for s in shards)
+        loads = [sum(w[k] for k in s) for s in shards]
+        assert max(loads) <= sum(w) / parts + (1 - 1 / parts) * max(w)
+    assert lpt_shards([3, 1, 2], 1) == [[0, 1, 2]]
+    # textbook case: 3, 3, 2, 2, 2 on two machines, LPT gives 7 against the optimum 6
+    loads = sorted(sum([3, 3, 2, 2, 2][k] for k in s) for s in lpt_shards([3, 3, 2, 2, 2], 2))
+    assert loads == [5, 7]
+
+
+def test_patch_subset_matches_whole_set():
+    """A rank's share of the seeded patch set equals those patches of the
+    whole set."""
+    from paper_1308_1464_gb300 import workloads
+    whole = workloads.swe_patches(40)
+    some = workloads.swe_patches(40, only=[3, 17, 39])
+    for k, p in zip([3, 17, 39], some):
+        assert (p.nx, p.ny) == (whole[k].nx, whole[k].ny)
+        np.testing.assert_array_equal(p.grid.q, whole[k].grid.q)
