@@ -7,7 +7,8 @@
 //   f_K(p) = 2 c_K/(gamma-1) ((p/p_K)^z - 1),      p <= p_K (rarefaction),
 //            z = (gamma-1)/(2 gamma),
 // and u* = (u_L + u_R)/2 + (f_R(p*) - f_L(p*))/2.  Newton runs in FP64 with
-// at most one power per update (p^(z-1), shared by the two sides); seeds are Toro's PV, TR and TS guesses (ch. 9) or the network's proposal
+// at most one power per update (p^(z-1), shared by the two sides, and formed
+// without FP64 pow when 1/z is an integer, see Powers); seeds are Toro's PV, TR and TS guesses (ch. 9) or the network's proposal
 // p_TR exp(net(x)).  One thread per interface; a warp evaluates the network
 // for its 32 interfaces together on the tensor cores.
 #include <cuda_runtime.h>
@@ -23,8 +24,71 @@ namespace mc {
 
 constexpr double PFLOOR = 1e-12;
 
+// The powers of the pressure functions, p^-z, p^(z-1) and x^(1/z) with
+// z = (gamma-1)/(2 gamma).  When 1/z = 2 gamma/(gamma-1) is an integer n
+// (gamma = 1.4: 7; 5/3: 5) they need no FP64 pow: x^(1/z) = x^n by
+// repeated squaring, and v = p^(-1/n) by Newton's method on p v^n = 1,
+// v <- v + v (1 - p v^n) / n, from an FP32 start (the relative error e
+// becomes about (n+1)/2 e^2 per step, so two steps from FP32 reach FP64
+// rounding), then p^(z-1) = v^(n-1).  Otherwise, and for p outside
+// [1e-30, 1e30], FP64 pow.
+struct Powers {
+    double z;
+    int n;         // 1/z when an integer in [2, 32], else 0
+    double invn;   // 1/n
+};
+
+__host__ inline Powers make_powers(double gamma)
+{
+    Powers w;
+    w.z = 0.5 * (gamma - 1.0) / gamma;
+    const double rz = 2.0 * gamma / (gamma - 1.0);
+    const long k = lround(rz);
+    w.n = (k >= 2 && k <= 32 && fabs(rz - double(k)) <= 1e-9 * rz) ? int(k) : 0;
+    w.invn = w.n ? 1.0 / w.n : 0.0;
+    return w;
+}
+
+__device__ __forceinline__ double ipow(double v, int k)
+{
+    double r = 1.0;
+    while (k) {
+        if (k & 1) r *= v;
+        v *= v;
+        k >>= 1;
+    }
+    return r;
+}
+
+// p^(-1/n), p > 0
+__device__ __forceinline__ double inv_root(const Powers& w, double p)
+{
+    if (!(p > 1e-30 && p < 1e30)) return pow(p, -w.invn);
+    double v = double(powf(float(p), -float(w.invn)));
+#pragma unroll
+    for (int s = 0; s < 2; s++) v = fma(v * w.invn, fma(-p, ipow(v, w.n), 1.0), v);
+    return v;
+}
+
+__device__ __forceinline__ double pow_mz(const Powers& w, double p)
+{
+    return w.n ? inv_root(w, p) : pow(p, -w.z);
+}
+
+__device__ __forceinline__ double pow_zm1(const Powers& w, double p)
+{
+    return w.n ? ipow(inv_root(w, p), w.n - 1) : pow(p, w.z - 1.0);
+}
+
+__device__ __forceinline__ double pow_rz(const Powers& w, double x)
+{
+    if (!w.n) return pow(x, 1.0 / w.z);
+    return x > 0.0 ? ipow(x, w.n) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
 struct ExactArgs {
     long long n;
+    Powers pw;
     double gamma, tol;
     int max_iter, seed_mode;
     const float *rl, *ul, *pl, *rr, *ur, *pr;
@@ -41,7 +105,8 @@ struct Side {
 
 // One division, one reciprocal square root and one power per side: c and
 // 1/c come from the same rsqrt, 1/A_K needs none.
-__device__ __forceinline__ Side make_side(double gamma, double z, double rho, double u, double p)
+__device__ __forceinline__ Side make_side(double gamma, const Powers& pw, double rho, double u,
+                                          double p)
 {
     Side s;
     s.rho = rho;
@@ -54,7 +119,7 @@ __device__ __forceinline__ Side make_side(double gamma, double z, double rho, do
     s.B = (gamma - 1.0) / (gamma + 1.0) * p;
     s.iA = 0.5 * (gamma + 1.0) * rho;
     s.kr = 2.0 * s.c / (gamma - 1.0);
-    s.ipz = pow(p, -z);
+    s.ipz = pow_mz(pw, p);
     s.ikr = irho * rc * p * s.ipz;
     return s;
 }
@@ -84,13 +149,13 @@ struct NewtonEval {
 // Newton from p0; returns true on convergence, counts updates in it.  The
 // power p^(z-1) is formed once per update, and only when a side of some lane
 // of the warp is on its rarefaction branch.
-__device__ __forceinline__ bool newton(const Side& L, const Side& R, double z, double p0,
+__device__ __forceinline__ bool newton(const Side& L, const Side& R, const Powers& pw, double p0,
                                        double tol, int max_iter, double& ps, int& it,
                                        NewtonEval& ev)
 {
     double p = p0;
     for (int k = 0; k < max_iter; k++) {
-        const double w = (p <= L.p || p <= R.p) ? pow(p, z - 1.0) : 0.0;
+        const double w = (p <= L.p || p <= R.p) ? pow_zm1(pw, p) : 0.0;
         double fl, fdl, fr, fdr;
         branch(L, p, w, fl, fdl);
         branch(R, p, w, fr, fdr);
@@ -127,13 +192,13 @@ struct Seeds {
     double pv_raw, pv, tr, ts, adaptive, pvtr;
 };
 
-__device__ __forceinline__ Seeds seeds(double gamma, double z, const Side& L, const Side& R)
+__device__ __forceinline__ Seeds seeds(double gamma, const Powers& pw, const Side& L, const Side& R)
 {
     Seeds s;
     const double du = R.u - L.u;
     s.pv_raw = 0.5 * (L.p + R.p) - 0.125 * du * (L.rho + R.rho) * (L.c + R.c);
     s.pv = s.pv_raw < PFLOOR ? PFLOOR : s.pv_raw;
-    s.tr = pow((L.c + R.c - 0.5 * (gamma - 1.0) * du) / (L.c * L.ipz + R.c * R.ipz), 1.0 / z);
+    s.tr = pow_rz(pw, (L.c + R.c - 0.5 * (gamma - 1.0) * du) / (L.c * L.ipz + R.c * R.ipz));
     const double gl = rsqrt((L.B + s.pv) * L.iA), gr = rsqrt((R.B + s.pv) * R.iA);
     s.ts = (gl * L.p + gr * R.p - du) / (gl + gr);
     if (s.ts < PFLOOR) s.ts = PFLOOR;
@@ -177,7 +242,8 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
         outs = reinterpret_cast<float*>(smem + sizeof(MlpShared) + 4 * 32 * XP * 2) + warp * 32;
         __syncthreads();
     }
-    const double gamma = a.gamma, z = 0.5 * (gamma - 1.0) / gamma;
+    const double gamma = a.gamma;
+    const Powers pw = a.pw;
     long long c_n = 0, c_vac = 0, c_fb = 0, c_nc = 0, c_it = 0, c_max = 0;
     const long long nchunks = (a.n + 31) / 32;
     for (long long ch = (long long)blockIdx.x * 4 + warp; ch < nchunks;
@@ -186,14 +252,14 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
         const bool valid = i < a.n;
         Side L, R;
         if (valid) {
-            L = make_side(gamma, z, a.rl[i], a.ul[i], a.pl[i]);
-            R = make_side(gamma, z, a.rr[i], a.ur[i], a.pr[i]);
+            L = make_side(gamma, pw, a.rl[i], a.ul[i], a.pl[i]);
+            R = make_side(gamma, pw, a.rr[i], a.ur[i], a.pr[i]);
         } else {
-            L = make_side(gamma, z, 1.0, 0.0, 1.0);
+            L = make_side(gamma, pw, 1.0, 0.0, 1.0);
             R = L;
         }
         const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
-        Seeds sd = seeds(gamma, z, L, R);
+        Seeds sd = seeds(gamma, pw, L, R);
         double p0;
         switch (a.seed_mode) {
         case MC_SEED_PV: p0 = sd.pv; break;
@@ -223,7 +289,7 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
                 const double prop = sd.tr * double(expf(o));
                 const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
                 if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
-                    newton(L, R, z, prop, a.tol, a.max_iter, ps, it, ev)) {
+                    newton(L, R, pw, prop, a.tol, a.max_iter, ps, it, ev)) {
                     done = true;
                 } else {
                     flag |= MC_RS_FALLBACK;
@@ -237,7 +303,7 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
                 it = 0;
                 ps = 0.0;
             } else if (!done) {
-                if (!newton(L, R, z, p0, a.tol, a.max_iter, ps, it, ev)) flag |= MC_RS_NOCONV;
+                if (!newton(L, R, pw, p0, a.tol, a.max_iter, ps, it, ev)) flag |= MC_RS_NOCONV;
             }
             double us = __longlong_as_double(0x7ff8000000000000LL);   // NaN for vacuum
             if (!vacuum) us = star_velocity(L, R, ps, ev);
@@ -277,18 +343,17 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
 
 constexpr int EXACT_SMEM_MLP = (int)sizeof(MlpShared) + 4 * 32 * XP * 2 + 4 * 32 * 4;
 
-__global__ void features_kernel(long long n, double gamma, const float* rl, const float* ul,
+__global__ void features_kernel(long long n, double gamma, Powers pw, const float* rl, const float* ul,
                                 const float* pl, const float* rr, const float* ur,
                                 const float* pr, const float* ps, float* feat, float* target)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const double z = 0.5 * (gamma - 1.0) / gamma;
-        const Side L = make_side(gamma, z, rl[i], ul[i], pl[i]);
-        const Side R = make_side(gamma, z, rr[i], ur[i], pr[i]);
+        const Side L = make_side(gamma, pw, rl[i], ul[i], pl[i]);
+        const Side R = make_side(gamma, pw, rr[i], ur[i], pr[i]);
         const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
         float x[10];
-        const Seeds sd = seeds(gamma, z, L, R);
+        const Seeds sd = seeds(gamma, pw, L, R);
         raw_features(L, R, sd, x);
         const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
@@ -396,7 +461,7 @@ mc_status mc_mlp_features(int64_t n, double gamma, const float* rho_l, const flo
     long long blocks = (n + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     features_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        n, gamma, rho_l, u_l, p_l, rho_r, u_r, p_r, p_star, features, target);
+        n, gamma, make_powers(gamma), rho_l, u_l, p_l, rho_r, u_r, p_r, p_star, features, target);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MC_OK : cuda_error(e, "features launch");
 }
@@ -417,7 +482,7 @@ mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const fl
     if (seed_mode < MC_SEED_ADAPTIVE || seed_mode > MC_SEED_MLP)
         return set_error(MC_EINVAL, "unknown seed mode %d", seed_mode);
     if (seed_mode == MC_SEED_MLP && !net) return set_error(MC_EINVAL, "MLP seed needs a network");
-    ExactArgs a{n, gamma, tol, max_iter, seed_mode, rho_l, u_l, p_l, rho_r, u_r, p_r,
+    ExactArgs a{n, make_powers(gamma), gamma, tol, max_iter, seed_mode, rho_l, u_l, p_l, rho_r, u_r, p_r,
                 p_star, u_star, iters, flags, net ? net->dev : nullptr, stats};
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);

@@ -28,7 +28,7 @@ def built():
     oracle.build()
 
 
-def gpu_solve(states32, seed_mode=mc.SEED_ADAPTIVE, net=None, tol=1e-8, max_iter=30):
+def gpu_solve(states32, seed_mode=mc.SEED_ADAPTIVE, net=None, tol=1e-8, max_iter=30, gamma=GAMMA):
     n = states32[0].size
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in states32]
     ps = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -36,7 +36,7 @@ def gpu_solve(states32, seed_mode=mc.SEED_ADAPTIVE, net=None, tol=1e-8, max_iter
     it = torch.empty(n, dtype=torch.uint8, device="cuda")
     fl = torch.empty_like(it)
     stats = torch.zeros(6, dtype=torch.int64, device="cuda")
-    mc.riemann_exact(n, GAMMA, [d.data_ptr() for d in dev], ps.data_ptr(), us.data_ptr(),
+    mc.riemann_exact(n, gamma, [d.data_ptr() for d in dev], ps.data_ptr(), us.data_ptr(),
                      it.data_ptr(), fl.data_ptr(), seed_mode, net, tol, max_iter, stats.data_ptr())
     torch.cuda.synchronize()
     return (ps.cpu().numpy(), us.cpu().numpy(), it.cpu().numpy().astype(np.int32),
@@ -73,6 +73,22 @@ def test_plain_seeds_match_oracle(mode):
     assert stats[1] == int(((fl & mc.RS_VACUUM) != 0).sum())
     assert stats[3] == int(((fl & mc.RS_NOCONV) != 0).sum())
     assert stats[4] == int(it.sum()) and stats[5] == int(it.max())
+
+
+@pytest.mark.parametrize("gamma", [5.0 / 3.0, 1.3, 2.0])
+def test_other_gammas_match_oracle(gamma):
+    """2 gamma / (gamma - 1) = 5 and 4 (integer: the powers come from roots
+    and products) and 8.67 (not an integer: FP64 pow); the same parity as at
+    gamma = 1.4."""
+    st = f32_states(20011, seed=22)
+    ps, us, it, fl, stats = gpu_solve(st, mc.SEED_ADAPTIVE, gamma=gamma)
+    r = [a.astype(np.float64) for a in st]
+    ref = oracle.exact_batch(gamma, *r, seed_mode=oracle.SEED_ADAPTIVE)
+    cl, cr = np.sqrt(gamma * r[2] / r[0]), np.sqrt(gamma * r[5] / r[3])
+    vac = 2.0 / (gamma - 1.0) * (cl + cr) <= r[4] - r[1]
+    np.testing.assert_array_equal((fl & mc.RS_VACUUM) != 0, vac)
+    compare(st, ps, us, it, fl, ref)
+    assert stats[3] == 0
 
 
 def test_vacuum_criterion_and_edge_cases():
