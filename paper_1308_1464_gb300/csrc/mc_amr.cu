@@ -25,6 +25,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -39,14 +40,13 @@ struct AmrPatchDev {
     int fw, fh;                  // fine interior size (ratio cw x ratio ch)
     long long ld_x, ld_field;    // fine layout
     void* q[2];                  // the patch's two state buffers
-    long long ghost_begin;       // first ghost cell of this patch in the flat count
-    long long cell_begin;        // first covered coarse cell in the flat count
+    int nb_begin, nb_count;      // the patches that reach into its ghost layers (AmrArgs::nb)
 };
 
 struct AmrArgs {
     const AmrPatchDev* P;
+    const int* nb;               // neighbour lists, ascending patch index
     int npatch, ratio, nplane, cur;
-    long long nghost, ncell;
     long long x_offset;          // element offset of cell 0 within a row (same for all layouts)
     const void* qc0;             // coarse state before its step (ghosts filled)
     const void* qc1;             // ... after its step (ghosts filled); average-down target
@@ -141,58 +141,58 @@ __global__ void amr_ghost_kernel(const AmrArgs a)
     const T* qc0 = static_cast<const T*>(a.qc0);
     const T* qc1 = static_cast<const T*>(a.qc1);
     const T alpha = T(a.alpha);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.nghost;
-         t += (long long)gridDim.x * blockDim.x) {
-        int p = 0;
-        while (p + 1 < a.npatch && a.P[p + 1].ghost_begin <= t) p++;
+    // patches along y of the grid, each patch's ghost cells along x
+    for (int p = blockIdx.y; p < a.npatch; p += gridDim.y) {
         const AmrPatchDev& P = a.P[p];
-        const long long g = t - P.ghost_begin;
-        const int rowlen = P.fw + 4;
-        int fi, fj;
-        if (g < 2LL * rowlen) {                       // two rows below
-            fj = int(g / rowlen) - 2;
-            fi = int(g % rowlen) - 2;
-        } else if (g < 4LL * rowlen) {                // two rows above
-            const long long h = g - 2LL * rowlen;
-            fj = P.fh + int(h / rowlen);
-            fi = int(h % rowlen) - 2;
-        } else {                                      // two columns each side of the interior rows
-            const long long h = g - 4LL * rowlen;
-            fj = int(h >> 2);
-            const int k = int(h & 3);
-            fi = k < 2 ? k - 2 : P.fw + k - 2;
-        }
-        const int gx = a.ratio * P.ci0 + fi, gy = a.ratio * P.cj0 + fj;
-        T* dst = static_cast<T*>(P.q[a.cur]) + (long long)(fj + 2) * P.ld_x + a.x_offset + fi;
-        // another patch covering this fine cell?
-        int src = -1, si = 0, sj = 0;
-        for (int q = 0; q < a.npatch && src < 0; q++) {
-            if (q == p) continue;
-            const int qi = gx - a.ratio * a.P[q].ci0, qj = gy - a.ratio * a.P[q].cj0;
-            if (qi >= 0 && qi < a.P[q].fw && qj >= 0 && qj < a.P[q].fh) {
-                src = q;
-                si = qi;
-                sj = qj;
+        const int nghost = 4 * (P.fw + 4) + 4 * P.fh;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nghost; g += gridDim.x * blockDim.x) {
+            const int rowlen = P.fw + 4;
+            int fi, fj;
+            if (g < 2LL * rowlen) {                       // two rows below
+                fj = int(g / rowlen) - 2;
+                fi = int(g % rowlen) - 2;
+            } else if (g < 4LL * rowlen) {                // two rows above
+                const long long h = g - 2LL * rowlen;
+                fj = P.fh + int(h / rowlen);
+                fi = int(h % rowlen) - 2;
+            } else {                                      // two columns each side of the interior rows
+                const long long h = g - 4LL * rowlen;
+                fj = int(h >> 2);
+                const int k = int(h & 3);
+                fi = k < 2 ? k - 2 : P.fw + k - 2;
             }
-        }
-        if (src >= 0) {
-            const AmrPatchDev& Q = a.P[src];
-            const T* s0 = static_cast<const T*>(Q.q[a.cur]) + (long long)(sj + 2) * Q.ld_x + a.x_offset + si;
-            for (int m = 0; m < a.nplane; m++) dst[m * P.ld_field] = s0[m * Q.ld_field];
-            continue;
-        }
-        // the coarse reconstruction at the fine cell centre
-        const int cx = floordiv_(gx, a.ratio), cy = floordiv_(gy, a.ratio);
-        const T ox = (T(gx - a.ratio * cx) + T(0.5)) / T(a.ratio) - T(0.5);
-        const T oy = (T(gy - a.ratio * cy) + T(0.5)) / T(a.ratio) - T(0.5);
-        const long long c = (long long)(cy + 2) * a.c_ldx + a.x_offset + cx;
-        for (int m = 0; m < a.nplane; m++) {
-            const long long b = m * a.c_ldf + c;
-            auto qt = [&](long long o) { return (T(1) - alpha) * qc0[b + o] + alpha * qc1[b + o]; };
-            const T q = qt(0);
-            const T sx = mc_slope(q - qt(-1), qt(1) - q);
-            const T sy = mc_slope(q - qt(-a.c_ldx), qt(a.c_ldx) - q);
-            dst[m * P.ld_field] = q + ox * sx + oy * sy;
+            const int gx = a.ratio * P.ci0 + fi, gy = a.ratio * P.cj0 + fj;
+            T* dst = static_cast<T*>(P.q[a.cur]) + (long long)(fj + 2) * P.ld_x + a.x_offset + fi;
+            // another patch covering this fine cell? (only the neighbours can)
+            int src = -1, si = 0, sj = 0;
+            for (int n = 0; n < P.nb_count && src < 0; n++) {
+                const int q = a.nb[P.nb_begin + n];
+                const int qi = gx - a.ratio * a.P[q].ci0, qj = gy - a.ratio * a.P[q].cj0;
+                if (qi >= 0 && qi < a.P[q].fw && qj >= 0 && qj < a.P[q].fh) {
+                    src = q;
+                    si = qi;
+                    sj = qj;
+                }
+            }
+            if (src >= 0) {
+                const AmrPatchDev& Q = a.P[src];
+                const T* s0 = static_cast<const T*>(Q.q[a.cur]) + (long long)(sj + 2) * Q.ld_x + a.x_offset + si;
+                for (int m = 0; m < a.nplane; m++) dst[m * P.ld_field] = s0[m * Q.ld_field];
+                continue;
+            }
+            // the coarse reconstruction at the fine cell centre
+            const int cx = floordiv_(gx, a.ratio), cy = floordiv_(gy, a.ratio);
+            const T ox = (T(gx - a.ratio * cx) + T(0.5)) / T(a.ratio) - T(0.5);
+            const T oy = (T(gy - a.ratio * cy) + T(0.5)) / T(a.ratio) - T(0.5);
+            const long long c = (long long)(cy + 2) * a.c_ldx + a.x_offset + cx;
+            for (int m = 0; m < a.nplane; m++) {
+                const long long b = m * a.c_ldf + c;
+                auto qt = [&](long long o) { return (T(1) - alpha) * qc0[b + o] + alpha * qc1[b + o]; };
+                const T q = qt(0);
+                const T sx = mc_slope(q - qt(-1), qt(1) - q);
+                const T sy = mc_slope(q - qt(-a.c_ldx), qt(a.c_ldx) - q);
+                dst[m * P.ld_field] = q + ox * sx + oy * sy;
+            }
         }
     }
 }
@@ -201,22 +201,21 @@ template <typename T>
 __global__ void amr_average_kernel(const AmrArgs a)
 {
     T* qc = static_cast<T*>(const_cast<void*>(a.qc1));
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.ncell;
-         t += (long long)gridDim.x * blockDim.x) {
-        int p = 0;
-        while (p + 1 < a.npatch && a.P[p + 1].cell_begin <= t) p++;
+    for (int p = blockIdx.y; p < a.npatch; p += gridDim.y) {
         const AmrPatchDev& P = a.P[p];
-        const long long k = t - P.cell_begin;
-        const int ci = int(k % P.cw), cj = int(k / P.cw);
-        const T* f = static_cast<const T*>(P.q[a.cur]);
-        const T inv = T(1) / T(a.ratio * a.ratio);
-        for (int m = 0; m < a.nplane; m++) {
-            T s = T(0);
-            for (int bj = 0; bj < a.ratio; bj++)
-                for (int bi = 0; bi < a.ratio; bi++)
-                    s += f[m * P.ld_field + (long long)(a.ratio * cj + bj + 2) * P.ld_x + a.x_offset +
-                           a.ratio * ci + bi];
-            qc[m * a.c_ldf + (long long)(P.cj0 + cj + 2) * a.c_ldx + a.x_offset + P.ci0 + ci] = s * inv;
+        const int ncell = P.cw * P.ch;
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncell; k += gridDim.x * blockDim.x) {
+            const int ci = k % P.cw, cj = k / P.cw;
+            const T* f = static_cast<const T*>(P.q[a.cur]);
+            const T inv = T(1) / T(a.ratio * a.ratio);
+            for (int m = 0; m < a.nplane; m++) {
+                T s = T(0);
+                for (int bj = 0; bj < a.ratio; bj++)
+                    for (int bi = 0; bi < a.ratio; bi++)
+                        s += f[m * P.ld_field + (long long)(a.ratio * cj + bj + 2) * P.ld_x + a.x_offset +
+                               a.ratio * ci + bi];
+                qc[m * a.c_ldf + (long long)(P.cj0 + cj + 2) * a.c_ldx + a.x_offset + P.ci0 + ci] = s * inv;
+            }
         }
     }
 }
@@ -233,11 +232,13 @@ struct mc_amr {
     std::vector<mc_amr_patch> patches;
     std::vector<AmrPatchDev> host_desc;
     AmrPatchDev* desc = nullptr;
+    int* nb = nullptr;            // neighbour lists of the patches (AmrPatchDev::nb_begin)
     MultiGrid* grids = nullptr;   // the patches for the multi-grid fused step
     CUtensorMap* maps = nullptr;  // two per patch (64-byte aligned device array)
     long long* prefix = nullptr;
     int* status = nullptr;
-    long long nghost = 0, ncell = 0, ntask = 0;
+    int max_ghost = 0, max_cell = 0;   // largest per-patch ghost and covered-cell counts
+    long long ntask = 0;
     int fine_in_b = 0;   // which buffer of every patch holds its current state
     int reflux = 0;
     RefluxEdge* edges = nullptr;  // corrected edges, grouped by (dir, sgn) class
@@ -371,6 +372,7 @@ static void amr_free(mc_amr* a)
     if (!a) return;
     if (a->cctx) mc_destroy(a->cctx);
     cudaFree(a->desc);
+    cudaFree(a->nb);
     cudaFree(a->grids);
     cudaFree(a->maps);
     cudaFree(a->prefix);
@@ -446,7 +448,7 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
         amr_free(A);
         return st;
     }
-    long long g = 0, c = 0, tk = 0;
+    long long tk = 0;
     std::vector<MultiGrid> grids;
     std::vector<CUtensorMap> maps(2 * (size_t)(npatch > 0 ? npatch : 1));
     std::vector<long long> prefix(1, 0);
@@ -491,15 +493,29 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
         d.ld_field = fl.ld_field;
         d.q[0] = patches[p].qa;
         d.q[1] = patches[p].qb;
-        d.ghost_begin = g;
-        d.cell_begin = c;
-        g += 4LL * (fp.mx + 4) + 4LL * fp.my;
-        c += (long long)d.cw * d.ch;
+        d.nb_begin = d.nb_count = 0;
+        A->max_ghost = std::max(A->max_ghost, 4 * (fp.mx + 4) + 4 * fp.my);
+        A->max_cell = std::max(A->max_cell, d.cw * d.ch);
         A->host_desc.push_back(d);
     }
-    A->nghost = g;
-    A->ncell = c;
     A->ntask = tk;
+    // neighbour lists: the patches whose cells fall in a patch's two fine
+    // ghost layers, in ascending index order
+    std::vector<int> nbl;
+    for (int p = 0; p < npatch; p++) {
+        AmrPatchDev& d = A->host_desc[p];
+        d.nb_begin = (int)nbl.size();
+        const long long x0 = (long long)ratio * d.ci0 - 2, x1 = (long long)ratio * d.ci0 + d.fw + 2;
+        const long long y0 = (long long)ratio * d.cj0 - 2, y1 = (long long)ratio * d.cj0 + d.fh + 2;
+        for (int q = 0; q < npatch; q++) {
+            if (q == p) continue;
+            const AmrPatchDev& e = A->host_desc[q];
+            const long long u0 = (long long)ratio * e.ci0, u1 = u0 + e.fw;
+            const long long v0 = (long long)ratio * e.cj0, v1 = v0 + e.fh;
+            if (u0 < x1 && x0 < u1 && v0 < y1 && y0 < v1) nbl.push_back(q);
+        }
+        d.nb_count = (int)nbl.size() - d.nb_begin;
+    }
     cudaError_t e0 = cudaMalloc(&A->status, sizeof(int));
     if (e0 == cudaSuccess) e0 = cudaMemset(A->status, 0, sizeof(int));
     if (e0 != cudaSuccess) {
@@ -510,6 +526,9 @@ mc_status mc_amr_create(const mc_problem* coarse, int32_t ratio, const mc_amr_pa
         cudaError_t e = cudaMalloc(&A->desc, sizeof(AmrPatchDev) * npatch);
         if (e == cudaSuccess)
             e = cudaMemcpy(A->desc, A->host_desc.data(), sizeof(AmrPatchDev) * npatch, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&A->nb, sizeof(int) * (nbl.size() + 1));
+        if (e == cudaSuccess && !nbl.empty())
+            e = cudaMemcpy(A->nb, nbl.data(), sizeof(int) * nbl.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMalloc(&A->grids, sizeof(MultiGrid) * npatch);
         if (e == cudaSuccess)
             e = cudaMemcpy(A->grids, grids.data(), sizeof(MultiGrid) * npatch, cudaMemcpyHostToDevice);
@@ -573,13 +592,16 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
     a.npatch = np;
     a.ratio = A->ratio;
     a.nplane = (int)A->clay.meqn;
-    a.nghost = A->nghost;
-    a.ncell = A->ncell;
+    a.nb = A->nb;
     a.x_offset = A->clay.x_offset;
     a.c_ldx = A->clay.ld_x;
     a.c_ldf = A->clay.ld_field;
-    const int gblocks = (int)((A->nghost + 255) / 256 > 4096 ? 4096 : (A->nghost + 255) / 256);
-    const int ablocks = (int)((A->ncell + 255) / 256 > 4096 ? 4096 : (A->ncell + 255) / 256);
+    // one grid row of blocks per patch (patches beyond 65535 wrap), enough
+    // blocks along x for the largest patch
+    const dim3 ggrid((unsigned)std::max(1, std::min(64, (A->max_ghost + 255) / 256)),
+                     (unsigned)std::max(1, std::min(np, 65535)));
+    const dim3 agrid((unsigned)std::max(1, std::min(64, (A->max_cell + 255) / 256)),
+                     (unsigned)std::max(1, std::min(np, 65535)));
     for (int n = 0; n < nsteps; n++) {
         void* qin = cb ? qc_b : qc_a;
         void* qout = cb ? qc_a : qc_b;
@@ -596,8 +618,8 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
         for (int sub = 0; sub < A->ratio && np > 0; sub++) {
             a.cur = fb;
             a.alpha = double(sub) / A->ratio;
-            if (es == 8) amr_ghost_kernel<double><<<gblocks > 0 ? gblocks : 1, 256, 0, s>>>(a);
-            else amr_ghost_kernel<float><<<gblocks > 0 ? gblocks : 1, 256, 0, s>>>(a);
+            if (es == 8) amr_ghost_kernel<double><<<ggrid, 256, 0, s>>>(a);
+            else amr_ghost_kernel<float><<<ggrid, 256, 0, s>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_error(e, "patch ghost fill");
             if (rf) {
@@ -611,8 +633,8 @@ mc_status mc_amr_advance(mc_amr* A, void* qc_a, void* qc_b, int32_t nsteps, doub
         }
         if (np > 0) {
             a.cur = fb;
-            if (es == 8) amr_average_kernel<double><<<ablocks > 0 ? ablocks : 1, 256, 0, s>>>(a);
-            else amr_average_kernel<float><<<ablocks > 0 ? ablocks : 1, 256, 0, s>>>(a);
+            if (es == 8) amr_average_kernel<double><<<agrid, 256, 0, s>>>(a);
+            else amr_average_kernel<float><<<agrid, 256, 0, s>>>(a);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_error(e, "average down");
             if (rf) {
