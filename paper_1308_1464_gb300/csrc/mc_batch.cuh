@@ -150,57 +150,62 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);
 }
 
-// Initial ghost fill (walls) and cell-speed maximum of every patch: one
-// block per patch.
+// Initial ghost fill (walls) and cell-speed maximum of every patch: a row
+// of gridDim.x blocks per patch (patches beyond gridDim.y wrap around),
+// which share its ghost cells and its rows.
 template <class RP>
-__global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, long long x_offset,
-                                  int stride, unsigned long long* smax)
+__global__ void batch_init_kernel(const RP rp, const PatchDesc* patches, int npatch,
+                                  long long x_offset, int stride, unsigned long long* smax)
 {
     using T = typename RP::real;
-    const PatchDesc d = patches[blockIdx.x];
-    T* q = static_cast<T*>(d.qa);
-    // ghosts: x of interior rows, then y over the full width (corners)
-    const int W = d.mx + 4;
-    const int nghost = 4 * W + 4 * d.my;
-    for (int g = threadIdx.x; g < nghost; g += blockDim.x) {
-        int i, j;
-        if (g < 4 * W) {
-            const int jr = g / W;
-            j = jr < 2 ? jr - 2 : d.my + jr - 2;
-            i = g - jr * W - 2;
-        } else {
-            const int u = g - 4 * W;
-            j = u >> 2;
-            const int ir = u & 3;
-            i = ir < 2 ? ir - 2 : d.mx + ir - 2;
-        }
-        bool fx = false, fy = false;
-        const int si = bc_map(i, d.mx, BC_WALL_KIND, BC_WALL_KIND, fx);
-        const int sj = bc_map(j, d.my, BC_WALL_KIND, BC_WALL_KIND, fy);
-        for (int m = 0; m < RP::NPLANE; m++) {
-            T v = q[m * d.ld_field + (long long)(sj + 2) * d.ld_x + x_offset + si];
-            if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
-            q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i] = v;
-        }
-    }
-    // cell-speed maxima (see max_cell_speed_kernel): warps take rows
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    T msx = T(0), msy = T(0);
-    for (int j = threadIdx.x >> 5; j < d.my; j += nw) {
-        const T* row = q + (long long)(j + 2) * d.ld_x + x_offset;
-        for (int i = lane; i < d.mx; i += 32) {
-            T qq[RP::NPLANE];
-            for (int m = 0; m < RP::NPLANE; m++) qq[m] = row[m * d.ld_field + i];
-            T sx, sy;
-            rp.cell_speeds(qq, sx, sy);
-            msx = fmax(msx, sx);
-            msy = fmax(msy, sy);
+    const int wid = blockIdx.x * nw + (threadIdx.x >> 5), nwarp = gridDim.x * nw;
+    for (int pi = blockIdx.y; pi < npatch; pi += gridDim.y) {
+        const PatchDesc d = patches[pi];
+        T* q = static_cast<T*>(d.qa);
+        // ghosts: x of interior rows, then y over the full width (corners)
+        const int W = d.mx + 4;
+        const int nghost = 4 * W + 4 * d.my;
+        for (int g = tid; g < nghost; g += nthr) {
+            int i, j;
+            if (g < 4 * W) {
+                const int jr = g / W;
+                j = jr < 2 ? jr - 2 : d.my + jr - 2;
+                i = g - jr * W - 2;
+            } else {
+                const int u = g - 4 * W;
+                j = u >> 2;
+                const int ir = u & 3;
+                i = ir < 2 ? ir - 2 : d.mx + ir - 2;
+            }
+            bool fx = false, fy = false;
+            const int si = bc_map(i, d.mx, BC_WALL_KIND, BC_WALL_KIND, fx);
+            const int sj = bc_map(j, d.my, BC_WALL_KIND, BC_WALL_KIND, fy);
+            for (int m = 0; m < RP::NPLANE; m++) {
+                T v = q[m * d.ld_field + (long long)(sj + 2) * d.ld_x + x_offset + si];
+                if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
+                q[m * d.ld_field + (long long)(j + 2) * d.ld_x + x_offset + i] = v;
+            }
         }
-    }
-    double v = fmax(double(msx) / d.dx, double(msy) / d.dy);
+        // cell-speed maxima (see max_cell_speed_kernel): warps take rows
+        T msx = T(0), msy = T(0);
+        for (int j = wid; j < d.my; j += nwarp) {
+            const T* row = q + (long long)(j + 2) * d.ld_x + x_offset;
+            for (int i = lane; i < d.mx; i += 32) {
+                T qq[RP::NPLANE];
+                for (int m = 0; m < RP::NPLANE; m++) qq[m] = row[m * d.ld_field + i];
+                T sx, sy;
+                rp.cell_speeds(qq, sx, sy);
+                msx = fmax(msx, sx);
+                msy = fmax(msy, sy);
+            }
+        }
+        double v = fmax(double(msx) / d.dx, double(msy) / d.dy);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&smax[(long long)blockIdx.x * stride], v);
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) atomic_max_nonneg(&smax[(long long)pi * stride], v);
+    }
 }
 
 }  // namespace mc

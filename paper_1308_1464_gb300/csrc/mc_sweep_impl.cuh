@@ -158,8 +158,10 @@ cudaError_t batch_init_t(const BatchLaunch& L)
 {
     RP rp;
     rp.setup(L.proto.param, L.proto.efix);
-    batch_init_kernel<RP><<<L.npatch, 256, 0, L.stream>>>(rp, L.patches, L.x_offset, L.nsteps + 1,
-                                                          L.smax);
+    // four blocks per patch (a patch has at most a few hundred rows)
+    const dim3 grid(4, (unsigned)(L.npatch < 1 ? 1 : L.npatch < 65535 ? L.npatch : 65535));
+    batch_init_kernel<RP><<<grid, 256, 0, L.stream>>>(rp, L.patches, L.npatch, L.x_offset,
+                                                     L.nsteps + 1, L.smax);
     return cudaGetLastError();
 }
 
