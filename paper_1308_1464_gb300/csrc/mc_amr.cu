@@ -210,10 +210,26 @@ __global__ void amr_average_kernel(const AmrArgs a)
             const T inv = T(1) / T(a.ratio * a.ratio);
             for (int m = 0; m < a.nplane; m++) {
                 T s = T(0);
-                for (int bj = 0; bj < a.ratio; bj++)
-                    for (int bi = 0; bi < a.ratio; bi++)
-                        s += f[m * P.ld_field + (long long)(a.ratio * cj + bj + 2) * P.ld_x + a.x_offset +
-                               a.ratio * ci + bi];
+                const long long base = m * P.ld_field + (long long)(a.ratio * cj + 2) * P.ld_x + a.x_offset +
+                                       a.ratio * ci;
+                bool done = false;
+                if constexpr (sizeof(T) == 4) {
+                    if (a.ratio == 2) {
+                        // the fine pair of a row in one 8-byte load: rows are
+                        // 128-byte padded and cell 0 sits at element 4, so base
+                        // is even; the same summation order as the loop
+                        const float2 u = *reinterpret_cast<const float2*>(f + base);
+                        const float2 w = *reinterpret_cast<const float2*>(f + base + P.ld_x);
+                        s += u.x;
+                        s += u.y;
+                        s += w.x;
+                        s += w.y;
+                        done = true;
+                    }
+                }
+                if (!done)
+                    for (int bj = 0; bj < a.ratio; bj++)
+                        for (int bi = 0; bi < a.ratio; bi++) s += f[base + (long long)bj * P.ld_x + bi];
                 qc[m * a.c_ldf + (long long)(P.cj0 + cj + 2) * a.c_ldx + a.x_offset + P.ci0 + ci] = s * inv;
             }
         }
