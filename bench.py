@@ -770,10 +770,15 @@ def main():
         from paper_1308_1464_gb300 import _build
         rank, world, local = dist_info()
         torch.cuda.set_device(local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
         _build.build()
         line = {"batch": bench_batch, "exact": bench_exact, "amr": bench_amr}[args.workload](args, rank, world)
         if rank == 0:
             print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
