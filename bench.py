@@ -539,6 +539,17 @@ def bench_amr(args, rank, world):
     }
 
 
+TRAIN_OFFSET, TRAIN_ROWS = 1 << 26, 1 << 22   # the seed network's training draws
+
+
+def exact_offset(rank: int, n: int) -> int:
+    """First draw of rank r's n interfaces: blocks disjoint across ranks and
+    from the training draws [TRAIN_OFFSET, TRAIN_OFFSET + TRAIN_ROWS)."""
+    if (rank + 1) * n <= TRAIN_OFFSET:
+        return rank * n
+    return 2 * TRAIN_OFFSET + rank * n
+
+
 def bench_exact(args, rank, world):
     """2^24 exact Euler Riemann problems (rho in [0.01, 10], p in [0.01, 100]
     log-uniform, |u| <= 5), FP64 Newton to |dp|/p < 1e-8: the plain adaptive
@@ -566,13 +577,12 @@ def bench_exact(args, rank, world):
         return ps, it, fl, stats, us
 
     from paper_1308_1464_gb300.seednet import train_seed_net
-    ntrain, epochs = 1 << 22, 12
-    net, losses, train_s = train_seed_net(ntrain=ntrain, epochs=epochs, gamma=GAM)
+    ntrain, epochs = TRAIN_ROWS, 12
+    net, losses, train_s = train_seed_net(ntrain=ntrain, epochs=epochs, gamma=GAM,
+                                          offset=TRAIN_OFFSET)
 
     n = 1 << 24
-    # rank r solves its own block of draws, disjoint from the others' and from
-    # the training draws at [2^26, 2^26 + 2^22)
-    off = rank * n if (rank + 1) * n <= (1 << 26) else (1 << 27) + rank * n
+    off = exact_offset(rank, n)
     test = dev_states(n, offset=off)
     stream = torch.cuda.current_stream()
     out = {}

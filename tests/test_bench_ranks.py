@@ -43,3 +43,15 @@ def test_single_rank_passthrough():
     import bench
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.replica_throughput(2.0, 1, 100, 10) == pytest.approx(100 * 10 / 2e-3)
+
+
+def test_exact_draw_blocks_are_disjoint():
+    """Each rank's 2^24 exact-solver interfaces come from its own block of
+    draws, apart from every other rank's and from the training draws."""
+    import bench
+    n = 1 << 24
+    blocks = [(bench.exact_offset(r, n), bench.exact_offset(r, n) + n) for r in range(16)]
+    blocks.append((bench.TRAIN_OFFSET, bench.TRAIN_OFFSET + bench.TRAIN_ROWS))
+    blocks.sort()
+    assert all(a1 <= b0 for (a0, a1), (b0, b1) in zip(blocks, blocks[1:]))
+    assert bench.exact_offset(0, n) == 0
