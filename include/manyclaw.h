@@ -265,21 +265,22 @@ mc_status mc_sweep(mc_ctx* ctx, const void* q_in, void* q_out, double dt, void* 
 
 /* mc_step without a context and without allocating device memory.  The paper
  * has no counterpart; this exists for callers that cannot call cudaMalloc --
- * code running while a stream is being captured into a graph, plug-ins handed
- * a fixed device-memory budget by their host, and loops that must not risk
- * the device-wide synchronisation that allocating or freeing can cause.  It
- * performs the same ghost fill and fused step as mc_step (same results) and
- * keeps its scratch -- speed maximum, status word and the tensor map of q_in,
- * 192 bytes -- in a 256-byte static device array that every device loading
- * the library holds until the process exits.  Problems are validated as by
- * mc_layout_of and rejected with MC_EINVAL and a message; the scratch does not
- * grow with the grid, so every valid grid fits.  The first call on a device
- * (with that device current) looks up the array's device address and raises
- * the kernels' shared-memory limits; make that first call before any stream
- * capture.  The array is shared by all calls and keeps the previous call's
- * contents (the call clears what must start at zero): calls that overlap on
- * the GPU, from other streams or host threads, race on it.  smax_out and the
- * status report behave as in mc_step (synchronising when smax_out != NULL). */
+ * plug-ins whose host hands them a fixed device-memory budget and owns every
+ * allocation, and loops that must not risk the device-wide synchronisation
+ * that allocating or freeing can cause.  It performs the same ghost fill and
+ * fused step as mc_step (same results) and keeps its scratch -- speed
+ * maximum, status word and the tensor map of q_in, 192 bytes -- in a 256-byte
+ * static device array that every device loading the library holds until the
+ * process exits.  Problems are validated as by mc_layout_of and rejected with
+ * MC_EINVAL and a message; the scratch does not grow with the grid, so every
+ * grid mc_layout_of accepts fits.  The first call on a device (with that
+ * device current) looks up the array's device address and raises the dynamic
+ * shared-memory limits of every solver's kernels; if that set-up fails the
+ * call returns MC_ECUDA and the next call retries it.  The array is shared by
+ * all calls and keeps the previous call's contents (each call clears what
+ * must start at zero): calls that overlap on the GPU, from other streams or
+ * host threads, race on it.  smax_out and the status report behave as in
+ * mc_step (the call synchronises the stream when smax_out != NULL). */
 mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_out, double dt,
                           double* smax_out, void* stream);
 

@@ -113,6 +113,19 @@ static cudaError_t solver_batch_occupancy(const mc_problem& p, int* ctas)
     }
 }
 
+// dynamic shared-memory limits of the per-patch (plain) form's fused step
+static cudaError_t solver_sweep_prepare(const mc_problem& p)
+{
+    switch (p.solver) {
+    case MC_ACOUSTICS: return sweep_prepare_acoustics(p.dtype);
+    case MC_SWE_ROE: return sweep_prepare_swe(p.dtype);
+    case MC_ADVECTION: return sweep_prepare_advection(p.dtype);
+    case MC_ACOUSTICS_VAR: return sweep_prepare_acoustics_var(p.dtype);
+    case MC_EULER_GODUNOV: return sweep_prepare_euler_godunov(p.dtype);
+    default: return sweep_prepare_euler(p.dtype);
+    }
+}
+
 static void free_batch(mc_batch* b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -311,9 +324,7 @@ mc_status mc_batch_create(const mc_problem* proto, const mc_patch* patches, int3
     if (e == cudaSuccess) e = solver_batch_occupancy(*proto, &ctas);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = sweep_prepare_swe(proto->dtype);   // (plain form) smem limits
-    if (e == cudaSuccess) e = sweep_prepare_acoustics(proto->dtype);
-    if (e == cudaSuccess) e = sweep_prepare_euler(proto->dtype);
+    if (e == cudaSuccess) e = solver_sweep_prepare(*proto);   // the plain form's smem limits
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_error(e, "batch set-up");

@@ -1,10 +1,10 @@
 // mc_noalloc.cu -- mc_step_noalloc: one unsplit step that allocates no
 // device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph, hosts that hand a plug-in a fixed device-memory
-// budget, and latency-critical loops that must not risk the implicit device
-// synchronisation that allocation and release can cause.  mc_step needs a
+// Some callers cannot call cudaMalloc: plug-ins whose host hands them a fixed
+// device-memory budget and owns every allocation, and latency-critical loops
+// that must not risk the implicit device synchronisation that allocating and
+// freeing can cause.  mc_step needs a
 // context (mc_create allocates its device scratch), so this entry point runs
 // the same ghost fill and fused step with their scratch -- the running
 // maximum of the edge speeds, the device status word and the tensor map the
@@ -50,34 +50,60 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // Per-device set-up, done by the first call on each device (with that device
-// current): the device address of the scratch array and the fused kernels'
-// shared-memory limits.  The host symbol g_noalloc_scratch is only a host-side
-// stand-in; kernels must be given the address obtained here.
+// current): the device address of the scratch array and the dynamic
+// shared-memory limits of every solver's fused kernels in both precisions
+// (several need more than the 48 KB default).  The host symbol
+// g_noalloc_scratch is only a host-side stand-in; kernels must be given the
+// address obtained here.  A set-up that fails is not remembered: the next
+// call tries again.
 struct DeviceSetup {
-    std::once_flag once;
-    cudaError_t err = cudaSuccess;
+    bool done = false;
     NoallocScratch* scratch = nullptr;
 };
 DeviceSetup g_setup[MAX_DEVICES];
+std::mutex g_setup_mutex;
 std::once_flag g_encode_once;
 EncodeTiledFn g_encode = nullptr;
 
 cudaError_t setup_device(int dev, NoallocScratch** out)
 {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup& s = g_setup[dev];
-    std::call_once(s.once, [&s]() {
+    if (!s.done) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         for (int dtype = MC_F32; e == cudaSuccess && dtype <= MC_F64; dtype++) {
-            e = sweep_prepare_acoustics(dtype);
-            if (e == cudaSuccess) e = sweep_prepare_swe(dtype);
-            if (e == cudaSuccess) e = sweep_prepare_euler(dtype);
+            cudaError_t (*prep[])(int) = {sweep_prepare_acoustics, sweep_prepare_swe,
+                                          sweep_prepare_euler, sweep_prepare_advection,
+                                          sweep_prepare_acoustics_var, sweep_prepare_euler_godunov};
+            for (auto f : prep)
+                if (e == cudaSuccess) e = f(dtype);
         }
-        s.err = e;
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return e;
+        }
         s.scratch = static_cast<NoallocScratch*>(p);
-    });
+        s.done = true;
+    }
     *out = s.scratch;
-    return s.err;
+    return cudaSuccess;
+}
+
+// Starts a call: clears the speed maximum and the status word left by the
+// previous call and stores this call's tensor map.  The map travels as a
+// kernel argument (copied at launch), so no host buffer has to outlive the
+// call.
+__global__ void noalloc_begin_kernel(NoallocScratch* s, const CUtensorMap map)
+{
+    const int t = threadIdx.x;
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(&map);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(&s->map);
+    if (t < int(sizeof(CUtensorMap) / 8)) dst[t] = src[t];
+    if (t == 0) {
+        s->smax_bits = 0ull;
+        s->status = 0;
+    }
 }
 
 }  // namespace
@@ -96,11 +122,9 @@ extern "C" mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_ou
     if (reinterpret_cast<uintptr_t>(q_in) % 16 || reinterpret_cast<uintptr_t>(q_out) % 16)
         return set_error(MC_EINVAL, "state pointers must be 16-byte aligned");
     if (!(dt >= 0.0) || !isfinite(dt)) return set_error(MC_EINVAL, "dt must be finite and >= 0");
-    // The scratch a call needs does not grow with the grid; larger records
-    // than the array holds are refused.
-    if (sizeof(NoallocScratch) > NOALLOC_SCRATCH_BYTES)
-        return set_error(MC_EINVAL, "step scratch (%zu bytes) exceeds the %zu-byte static array",
-                         sizeof(NoallocScratch), NOALLOC_SCRATCH_BYTES);
+    // The scratch a call needs does not grow with the grid (the static_assert
+    // above keeps the record inside the array), so every grid that
+    // mc_layout_of accepts fits; larger grids were refused there.
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -118,7 +142,7 @@ extern "C" mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_ou
     });
     if (!g_encode) return set_error(MC_ECUDA, "driver entry point cuTensorMapEncodeTiled unavailable");
 
-    // tensor map of q_in, encoded on the host and copied into the array
+    // tensor map of q_in, encoded on the host and stored into the array
     const int es = (int)lay.elem_bytes;
     cuuint64_t dims[3] = {(cuuint64_t)lay.ld_x, (cuuint64_t)(p->my + 4), (cuuint64_t)lay.meqn};
     cuuint64_t strides[2] = {(cuuint64_t)(lay.ld_x * es), (cuuint64_t)(lay.ld_field * es)};
@@ -135,9 +159,8 @@ extern "C" mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_ou
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: the maximum and the
     // status word must start from zero; the map is rewritten every call
-    e = cudaMemsetAsync(scratch, 0, offsetof(NoallocScratch, map), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&scratch->map, &map, sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
+    noalloc_begin_kernel<<<1, 32, 0, s>>>(scratch, map);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = bc_launch(*p, lay, q_in, q_in, nullptr, s);
     if (e != cudaSuccess) return cuda_error(e, "ghost fill");
     const int rows = DEFAULT_TILE_ROWS;
