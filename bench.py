@@ -197,6 +197,24 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_unit_peaks():
+    """The execution-unit rates of profiles/peaks_gb300.json (bench.py --peaks
+    on a GB300 of this pool), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "peaks_gb300.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
+
+
+def fp64_peak():
+    """(TFLOP/s, source) of the FP64 fused multiply-add: measured if on record."""
+    pk = measured_unit_peaks()
+    if pk and "dfma" in pk:
+        return pk["dfma"]["value"], "measured DFMA rate (profiles/peaks_gb300.json)"
+    return FP64_NOMINAL_TFLOPS, "nominal GB300 FP64 rate"
+
+
 def sweep_source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1308_1464_gb300", "csrc")
@@ -305,10 +323,24 @@ def cpu_baseline(wl, budget_s=12.0):
         el = time.perf_counter() - t0
         if el >= budget_s or steps >= (200 if n >= 1024 else 10000):
             break
-    return {"value": n * n * steps / el, "unit": "cell-updates/s", "cores": cores,
-            "kind": "oracle",
-            "sample": f"{steps} FP64 oracle steps of the same problem on a {n}x{n} grid "
-                      f"(OpenMP over rows, {cores} threads), {el:.1f} s"}
+    rec = {"value": n * n * steps / el, "unit": "cell-updates/s", "cores": cores,
+           "kind": "oracle",
+           "sample": f"{steps} FP64 oracle steps of the same problem on a {n}x{n} grid "
+                     f"(OpenMP over rows, {cores} threads), {el:.1f} s"}
+    # the plain oracle on one core, a shorter sample of the same grid
+    q1 = np.zeros(op.shape)
+    q1[:, 2:-2, 2:-2] = g.q
+    s1, t1 = 0, time.perf_counter()
+    while True:
+        q1, _, _ = oracle.step(op, q1, dt, nthreads=1)
+        s1 += 1
+        e1 = time.perf_counter() - t1
+        if e1 >= budget_s / 3 or s1 >= 50:
+            break
+    rec["single_thread"] = {"value": n * n * s1 / e1, "unit": "cell-updates/s", "cores": 1,
+                            "sample": f"{s1} FP64 oracle steps on the {n}x{n} grid, one thread, "
+                                      f"{e1:.1f} s"}
+    return rec
 
 
 def run_reference(args, wl):
@@ -399,6 +431,21 @@ def bench_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    # one launch per step over all patches (the same kernel, one step per
+    # launch, the launches of a call in one graph): the step-synchronous form
+    ps.reset()
+    b.advance_steps(per_launch, 0.9, stream=sh)   # builds its graph
+    ps.reset()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(launches):
+        b.advance_steps(per_launch, 0.9, stream=sh)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms_steps = max_over_ranks(s0.elapsed_time(s1), world, "cuda")
     ps.reset()
     b.advance_plain(2, 0.9, stream=sh)       # warm the per-patch path
     ps.reset()
@@ -423,11 +470,17 @@ def bench_batch(args, rank, world):
                                "walls, per-patch dt CFL 0.9, 20 steps per persistent launch in a "
                                "CUDA graph",
                    "cells": cells_all, "patches": nall, "tune_policy": policy, "tune_ms": tune_ms,
+                   "tuned_over_as_created": round(tune_ms["as_created"] / min(tune_ms.values()), 4),
                    "parallelism": ("patches shared by LPT on cell count, %d ranks" % world
                                    if world > 1 else "single"),
                    "l2": "inputs larger than L2 (%.0f MB per state)" % (ps.nbytes / 1e6)},
+        "per_step_launch": {"value": cells_all * K / (ms_steps * 1e-3), "ms_per_step": ms_steps / K,
+                            "launches_per_step": 1,
+                            "note": "the same kernel, one launch per step over all patches, "
+                                    "a call's launches in one CUDA graph"},
         "plain": {"value": cells_all * K / (ms_plain * 1e-3), "ms_per_step": ms_plain / K,
                   "launches_per_step": 3 * len(pats), "timed_steps": per_launch},
+        "batched_over_per_step_launch": ms_steps / ms,
         "batched_over_plain": ms_plain / ms,
         "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
@@ -571,7 +624,7 @@ def bench_exact(args, rank, world):
         us = torch.empty_like(ps)
         it = torch.empty(n, dtype=torch.uint8, device="cuda")
         fl = torch.empty_like(it)
-        stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+        stats = torch.zeros(8, dtype=torch.int64, device="cuda")
         mc.riemann_exact(n, GAM, [s.data_ptr() for s in states], ps.data_ptr(), us.data_ptr(),
                          it.data_ptr(), fl.data_ptr(), mode, net, tol, 30, stats.data_ptr())
         return ps, it, fl, stats, us
@@ -588,7 +641,10 @@ def bench_exact(args, rank, world):
     out = {}
     clk = ClockSampler(torch.cuda.current_device())
     clk.__enter__()
-    for name, mode, nn in (("plain", mc.SEED_ADAPTIVE, None), ("learned", mc.SEED_MLP, net)):
+    arms = (("plain", mc.SEED_ADAPTIVE, None), ("learned", mc.SEED_MLP, net),
+            ("plain_mixed", mc.SEED_ADAPTIVE | mc.NEWTON_MIXED, None),
+            ("learned_mixed", mc.SEED_MLP | mc.NEWTON_MIXED, net))
+    for name, mode, nn in arms:
         for _ in range(args.warmup):
             solve(test, mode, nn)
         if world > 1:
@@ -608,15 +664,27 @@ def bench_exact(args, rank, world):
                      "mean_newton_updates": float(st[4] / max(nonvac, 1)),
                      "fallback_rate": float(st[2] / max(nonvac, 1)), "vacuum": int(st[1]),
                      "not_converged": int(st[3])}
+        if mode & mc.NEWTON_MIXED:
+            out[name]["mean_fp32_updates"] = float(st[6] / max(nonvac, 1))
+            out[name]["mean_fp64_updates"] = float(st[7] / max(nonvac, 1))
         if name == "plain":
             ps_plain = ps.clone()
         else:
             ok = fl.cpu().numpy() & 1 == 0
             a, c = ps.cpu().numpy()[ok], ps_plain.cpu().numpy()[ok]
-            out["learned"]["max_rel_diff_vs_plain"] = float(np.max(np.abs(a - c) / np.abs(c)))
+            out[name]["max_rel_diff_vs_plain"] = float(np.max(np.abs(a - c) / np.abs(c)))
     clk.__exit__(None, None, None)
-    # end to end through the public call: the six state arrays from pinned host
-    # memory, the learned-seed solve, p* and u* back to pinned host memory
+    e2e = None
+    if not getattr(args, "light", False):
+        e2e = exact_e2e(n, off, world, solve, net, mc)
+    return exact_record(args, out, e2e, world, n, ntrain, epochs, train_s, losses, clk)
+
+
+def exact_e2e(n, off, world, solve, net, mc):
+    """End to end through the public call: the six state arrays from pinned
+    host memory, the learned-seed solve, p* and u* back to pinned host memory."""
+    import torch
+    from paper_1308_1464_gb300 import workloads
     host = [torch.from_numpy(a.astype(np.float32)).pin_memory()
             for a in workloads.riemann_states(n, seed=1308, offset=off)]
     h_ps = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -629,27 +697,33 @@ def bench_exact(args, rank, world):
             t0 = time.perf_counter()
         for d, h in zip(dev, host):
             d.copy_(h, non_blocking=True)
-        ps, _, _, _, us = solve(dev, mc.SEED_MLP, net)
+        ps, _, _, _, us = solve(dev, mc.SEED_MLP | mc.NEWTON_MIXED, net)
         h_ps.copy_(ps, non_blocking=True)
         h_us.copy_(us, non_blocking=True)
         torch.cuda.synchronize()
     el = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda") * 1e-3
-    e2e = {"value": world * n * reps_e2e / el, "unit": "solves/s",
-           "h2d_bytes_per_step": 6 * 4 * n, "d2h_bytes_per_step": 2 * 4 * n,
-           "note": "six FP32 state arrays from pinned host memory, mc_riemann_exact with the "
-                   "learned seed, p* and u* back to pinned host memory; one step = 2^24 solves"}
+    return {"value": world * n * reps_e2e / el, "unit": "solves/s",
+            "h2d_bytes_per_step": 6 * 4 * n, "d2h_bytes_per_step": 2 * 4 * n,
+            "note": "six FP32 state arrays from pinned host memory, mc_riemann_exact with the "
+                    "learned seed, p* and u* back to pinned host memory; one step = 2^24 solves"}
+
+
+def exact_record(args, out, e2e, world, n, ntrain, epochs, train_s, losses, clk):
     peak, kind = measured_peaks()
-    ms = out["learned"]["ms"]
+    # the headline arm: the learned seed, FP32 Newton stage and FP64 finish (the same
+    # |dp|/p < 1e-8 test in FP64)
+    ms = out["learned_mixed"]["ms"]
     cnt = ncu_exact()
     if cnt is not None and "learned" in cnt:
         # FP64-pipe bound: flops counted by ncu on these sources over the live time
         c = cnt["learned"]
         achieved = c["fp64_flops_per_launch"] / (ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4),
+        pk64, pk64_src = fp64_peak()
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": pk64,
+                    "unit": "TFLOP/s", "frac": round(achieved / pk64, 4),
                     "traffic": c["dram_bytes_per_launch"], "kernel": "exact_kernel<true>",
                     "fp64_pipe_active_pct": c["fp64_pipe_active_pct"],
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak is on record)",
+                    "peak_source": pk64_src,
                     "flops_source": "FP64 thread instructions of one launch counted by ncu on "
                                     "these sources (FMA = 2 flops, add and multiply = 1)"}
     else:
@@ -658,17 +732,76 @@ def bench_exact(args, rank, world):
                     "frac": round(34 * n / (ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
                     "kernel": "exact_kernel<true>", "note": "FP64-ALU bound; bytes not binding"}
     return {
-        "metric": "Riemann solves/s", "value": out["learned"]["solves_per_s"],
+        "metric": "Riemann solves/s", "value": out["learned_mixed"]["solves_per_s"],
         "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 Newton, f32 io, bf16 network", "data": "synthetic",
+        "dtype": "f32 then f64 Newton, f32 io, bf16 network", "data": "synthetic",
         "config": {"workload": "2^24 exact Euler Riemann problems, gamma 1.4, tol 1e-8",
                    "train_rows": ntrain, "train_epochs": epochs, "train_s": round(train_s, 2),
                    "train_loss": [float(x) for x in losses]},
         "plain": out["plain"], "learned": out["learned"],
+        "plain_mixed": out["plain_mixed"], "learned_mixed": out["learned_mixed"],
         "roofline": roofline, "e2e": e2e,
         "gpu_launches": 1, "clocks": clk.summary(),
     }
+
+
+PEAK_KINDS = [("ffma", 0, "TFLOP/s", 1e12), ("ffma2", 1, "TFLOP/s", 1e12), ("dfma", 2, "TFLOP/s", 1e12),
+              ("rsqrt", 3, "Gresults/s", 1e9), ("rcp", 4, "Gresults/s", 1e9),
+              ("iadd", 5, "T thread-inst/s", 1e12), ("issue", 6, "T thread-inst/s", 1e12)]
+
+
+def bench_peaks(args):
+    """Throughput of the execution units on all SMs (mc_peak_run), each kind
+    timed by CUDA events over 5 launches of about 25 ms, clocks sampled."""
+    import torch
+    import paper_1308_1464_gb300 as mc
+    from paper_1308_1464_gb300 import _build
+    torch.cuda.set_device(0)
+    _build.build()
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"sms": sms, "device": props.name, "blocks_per_sm": 8, "threads_per_block": 256}
+    with ClockSampler(0) as clk:
+        for name, kind, unit, scale in PEAK_KINDS:
+            iters = 64
+            for _ in range(8):   # grow until one launch takes about 25 ms
+                mc.peak_run(kind, 8, iters, sink.data_ptr(), sh)
+                e0.record(stream)
+                mc.peak_run(kind, 8, iters, sink.data_ptr(), sh)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if ms > 15.0:
+                    break
+                iters = int(iters * min(16.0, 25.0 / max(ms, 1e-3)))
+            e0.record(stream)
+            ops = 0.0
+            for _ in range(5):
+                ops += mc.peak_run(kind, 8, iters, sink.data_ptr(), sh)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"value": round(ops / (ms * 1e-3) / scale, 3), "unit": unit,
+                         "ms_per_launch": round(ms / 5, 3), "iters": iters}
+            if ms / 5 < 1.0:   # the loop did not take the time its count implies
+                out[name]["value"] = None
+                out[name]["note"] = "launch too short to be the counted work; not a rate"
+    out["clocks"] = clk.summary()
+    mhz = out["clocks"].get("sm_mhz") or 0
+    if mhz:
+        # warp instructions issued per cycle per SM (4 schedulers: at most 4)
+        out["issue"]["warp_inst_per_clk_per_sm"] = round(
+            out["issue"]["value"] * 1e12 / 32 / sms / (mhz * 1e6), 3)
+    line = {"metric": "peak throughput", "peaks": out}
+    if args.peaks_out:
+        with open(args.peaks_out, "w") as f:
+            json.dump(out, f, indent=1)
+    print(json.dumps(line))
 
 
 def time_large_grid(args, wl, ctx, a, b, q0, dt0, stream, sh, world):
@@ -759,53 +892,14 @@ def time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh, world):
     return total, 0, clk.summary(), kms / reps, note
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS) + ["batch", "exact", "amr"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
-                    help="profiling aid: run K stand-alone fused steps (mc_step) and exit")
-    args = ap.parse_args()
-    if args.workload in ("batch", "exact", "amr"):
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is timed "
-                              "for the grid workloads only"}))
-            return
-        import torch
-        from paper_1308_1464_gb300 import _build
-        rank, world, local = dist_info()
-        torch.cuda.set_device(local)
-        if world > 1:
-            import torch.distributed as dist
-            dist.init_process_group("nccl")
-        _build.build()
-        line = {"batch": bench_batch, "exact": bench_exact, "amr": bench_amr}[args.workload](args, rank, world)
-        if rank == 0:
-            print(json.dumps(line))
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    wl = WORKLOADS[args.workload]
-    if args.impl == "reference":
-        return run_reference(args, wl)
-    assert args.warmup >= 3, "at least 3 warm-up steps"
-
+def bench_grid(args, wl, rank, world, sub=False):
+    """One grid workload: K time steps in one timed region (graph-captured
+    mc_advance) or runs of a few steps after an L2 flush for a state smaller
+    than the L2, plus the fused step alone; with sub, the record of a further
+    configuration (no end-to-end or CPU-baseline legs)."""
     import torch
     import paper_1308_1464_gb300 as mc
-    from paper_1308_1464_gb300 import _build
     from paper_1308_1464_gb300.state import DeviceState
-
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    _build.build()
 
     p, g = make_problem(mc, wl)
     n_cells = p.mx * p.my
@@ -825,7 +919,7 @@ def main():
         torch.cuda.synchronize()
         print(json.dumps({"kernel_only": args.kernel_only, "workload": wl["desc"]}))
         ctx.close()
-        return
+        return None
 
     l2 = L2Flush(torch)
     if lay.bytes < l2.l2_bytes:
@@ -853,17 +947,18 @@ def main():
         # an FP64 step is bound by the FP64 pipe: counted FP64 flops over the
         # live kernel time, against the nominal FP64 rate
         tf = f64["fp64_flops_per_launch"] / (kms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": round(tf / FP64_NOMINAL_TFLOPS, 4),
+        pk64, pk64_src = fp64_peak()
+        roofline = {"bound": "alu", "achieved": round(tf, 4), "peak": pk64,
+                    "unit": "TFLOP/s", "frac": round(tf / pk64, 4),
                     "traffic": f64["dram_bytes_per_launch"], "kernel": "ctu_sweep_kernel",
                     "kernel_ms": round(kms, 4), "fp64_pipe_active_pct": f64["fp64_pipe_active_pct"],
                     "hbm_frac": round(achieved / peak, 4),
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak is on record)",
+                    "peak_source": pk64_src,
                     "flops_source": "FP64 thread instructions of one launch counted by ncu on these "
                                     "sources (FMA = 2 flops, add and multiply = 1)"}
     # end to end through the host-buffer C-ABI call (pinned host memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not sub:
         host0 = torch.from_numpy(q0).pin_memory()
         hostq = torch.empty_like(host0).pin_memory()
         nsteps_e2e = 100
@@ -909,7 +1004,7 @@ def main():
         ctx.set_seed_net(None)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sub:
         cpu = cpu_baseline(wl)
 
     if rank == 0:
@@ -927,8 +1022,114 @@ def main():
         }
         if seeds is not None:
             line["pressure_seed"] = seeds
-        print(json.dumps(line))
     ctx.close()
+    return line if rank == 0 else None
+
+
+
+
+def compact(line, keep=("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",
+                         "riemann_solves_per_s", "roofline", "clocks", "gpu_launches")):
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line.get("config", {}).get("workload")
+    return out
+
+
+def bench_configs(args):
+    """The further configurations of the benchmark (acoustics 128^2 FP64, the
+    dam break in FP64, Euler four quadrants in FP32, 2000 batched patches,
+    2^24 exact Riemann problems), each timed briefly on this GPU with CUDA
+    events and its own clock record, as sub-records of the one JSON line."""
+    import copy
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.light = 20, 5, True
+    out = {}
+    for key, name in (("acoustics_128_fp64", "acoustics"), ("swe_4096_fp64", "swe64"),
+                      ("euler_4096_fp32", "euler32")):
+        t0 = time.perf_counter()
+        out[key] = compact(bench_grid(sub, WORKLOADS[name], 0, 1, sub=True))
+        out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+    t0 = time.perf_counter()
+    bl = bench_batch(sub, 0, 1)
+    rec = compact(bl)
+    for k in ("per_step_launch", "plain", "batched_over_per_step_launch", "batched_over_plain"):
+        rec[k] = bl[k]
+    rec["tune_policy"] = bl["config"].get("tune_policy")
+    rec["tuned_over_as_created"] = bl["config"].get("tuned_over_as_created")
+    rec["wall_s"] = round(time.perf_counter() - t0, 1)
+    out["batch_2000_fp32"] = rec
+    t0 = time.perf_counter()
+    ex = bench_exact(sub, 0, 1)
+    rec = compact(ex)
+    for k in ("plain", "learned", "plain_mixed", "learned_mixed"):
+        rec[k] = ex[k]
+    rec["train_s"] = ex["config"].get("train_s")
+    rec["wall_s"] = round(time.perf_counter() - t0, 1)
+    out["exact_2p24"] = rec
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="swe32", choices=sorted(WORKLOADS) + ["batch", "exact", "amr"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the records of the further configurations in the default run")
+    ap.add_argument("--peaks", action="store_true",
+                    help="time the execution-unit microbenchmarks (FFMA, FFMA2, DFMA, MUFU, issue) and exit")
+    ap.add_argument("--peaks-out", default="", help="with --peaks: also write the JSON to this file")
+    ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
+                    help="profiling aid: run K stand-alone fused steps (mc_step) and exit")
+    ap.add_argument("--n", type=int, default=0,
+                    help="profiling aid: grid of n x n cells in place of the workload's (with --kernel-only)")
+    args = ap.parse_args()
+    if args.peaks:
+        return bench_peaks(args)
+    if args.workload in ("batch", "exact", "amr"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is timed "
+                              "for the grid workloads only"}))
+            return
+        import torch
+        from paper_1308_1464_gb300 import _build
+        rank, world, local = dist_info()
+        torch.cuda.set_device(local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        _build.build()
+        line = {"batch": bench_batch, "exact": bench_exact, "amr": bench_amr}[args.workload](args, rank, world)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    from paper_1308_1464_gb300 import _build
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    if args.n and args.kernel_only:
+        wl = dict(wl, n=args.n)
+    line = bench_grid(args, wl, rank, world)
+    if line is not None and args.workload == "swe32" and world == 1 and not args.no_configs:
+        line["configs"] = bench_configs(args)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
 

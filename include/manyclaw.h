@@ -106,7 +106,17 @@ typedef struct mc_problem {
     int32_t bc[4];       /* boundary kinds at xlo, xhi, ylo, yhi (MC_BC_*) */
     double dx, dy;       /* cell sizes, > 0 */
     double param[4];     /* acoustics: rho, K | shallow water: g | Euler: gamma |
-                          * advection: u, v */
+                          * advection: u, v.  Shallow water and Euler, FP32
+                          * only: param[3] = tau of the FP64 guard (0: the
+                          * default 1e-3; negative: guard off).  A guarded
+                          * edge -- across a near-dry or near-vacuum front
+                          * (smaller depth or density below tau times the
+                          * larger) or, for Euler, with Roe sound speed
+                          * c^2 < tau (gamma - 1) H (cold, high-Mach flow) --
+                          * has its normal solve and transverse splits
+                          * computed in FP64; with the guard on, the speeds
+                          * and split of a transonic entropy fix are formed
+                          * in FP64 too (mc_guard_stats counts the edges). */
 } mc_problem;
 
 typedef struct mc_layout {
@@ -203,6 +213,13 @@ mc_status mc_set_seed_net(mc_ctx* ctx, const mc_mlp* net);
  * reset != 0 zeroes the counters afterwards). */
 mc_status mc_newton_stats(mc_ctx* ctx, int64_t* updates, int64_t* solves, int32_t reset, void* stream);
 
+/* Interior edges whose normal solve the FP64 guard of an FP32 shallow-water
+ * or Euler step recomputed (see mc_problem.param[3]; paper §1.2, "local
+ * precision": precision spent only where the state needs it), counted over
+ * this context's fused steps since the last reset.  Synchronises the stream;
+ * reset != 0 zeroes the counter afterwards. */
+mc_status mc_guard_stats(mc_ctx* ctx, int64_t* edges, int32_t reset, void* stream);
+
 /* Host <-> device copies between a dense interior array (meqn x my x mx,
  * x fastest, the problem's dtype) and a device state in the library layout.
  * Asynchronous on stream. */
@@ -284,6 +301,27 @@ mc_status mc_sweep(mc_ctx* ctx, const void* q_in, void* q_out, double dt, void* 
 mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_out, double dt,
                           double* smax_out, void* stream);
 
+/* ---- Throughput microbenchmarks (no counterpart in the paper) -----------
+ * The step kernels are bound by instruction issue and by their arithmetic
+ * pipes, not by HBM alone; these launches measure the denominators of those
+ * rooflines on the device at hand.  mc_peak_run launches one kernel of `kind`
+ * with blocks_per_sm blocks of 256 threads on every SM of the current device
+ * (the SM count the device reports); every thread runs `iters` loop
+ * iterations of 16 steps of 8 independent dependency chains.  *ops_out (host)
+ * receives the operations of the launch: flops for MC_PEAK_FFMA, _FFMA2
+ * (packed FP32 pairs) and _DFMA (2 per fused multiply-add), results for
+ * MC_PEAK_RSQRT and _RCP (the FP32 hardware approximations), and thread
+ * instructions for MC_PEAK_IADD (integer multiply-adds) and MC_PEAK_ISSUE
+ * (independent FP32 multiply-adds, which issue at the full rate of one warp
+ * instruction per scheduler and cycle: the issue ceiling).  The caller times
+ * the launch (events on `stream`).  sink: a device float the kernel writes
+ * only for impossible results (keeps the chains from being optimised away).
+ * Asynchronous; MC_EINVAL for a bad kind or size. */
+enum { MC_PEAK_FFMA = 0, MC_PEAK_FFMA2 = 1, MC_PEAK_DFMA = 2, MC_PEAK_RSQRT = 3, MC_PEAK_RCP = 4,
+       MC_PEAK_IADD = 5, MC_PEAK_ISSUE = 6, MC_PEAK_NKINDS = 7 };
+mc_status mc_peak_run(int32_t kind, int32_t blocks_per_sm, int64_t iters, float* sink,
+                      double* ops_out, void* stream);
+
 /* max over interior cells of max((|u|+c)/dx, (|v|+c)/dy), synchronising. */
 mc_status mc_max_cell_speed(mc_ctx* ctx, const void* q, double* smax_out, void* stream);
 
@@ -350,6 +388,14 @@ mc_status mc_batch_advance(mc_batch* b, int32_t nsteps, double cfl, double* t_ou
  * fused step per patch), for comparison; bitwise equal interiors. */
 mc_status mc_batch_advance_plain(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
                                  int* result_in_b, void* stream);
+/* The same computation as one launch per step over all patches (the
+ * persistent kernel restricted to one step per launch, all nsteps launches
+ * captured in one CUDA graph, after the same ghost fill and cell-speed pass):
+ * the launch boundary orders the steps instead of per-patch completion
+ * counters.  Bitwise equal interiors; for comparison with mc_batch_advance.
+ * Synchronous. */
+mc_status mc_batch_advance_steps(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
+                                 int* result_in_b, void* stream);
 /* Failure-detection hook for tests (no counterpart in the paper): during the
  * next mc_batch_advance only, the tasks of `patch` wait for one more finished
  * task of their previous step than will ever exist.  Their bounded waits give
@@ -377,6 +423,14 @@ mc_status mc_batch_inject_stall(mc_batch* b, int32_t patch);
  * ------------------------------------------------------------------------ */
 enum { MC_SEED_ADAPTIVE = 0, MC_SEED_PV = 1, MC_SEED_TR = 2, MC_SEED_TS = 3, MC_SEED_PVTR = 4,
        MC_SEED_MLP = 5 };
+/* Added to a seed mode: Newton first iterates in FP32 from the seed (the
+ * network's proposal included) until |dp|/p < 1e-5 (at most 12 updates; a
+ * stalled or failed FP32 stage hands over its last finite iterate, else the
+ * FP64 adaptive guess), then FP64 updates finish with the same stopping test
+ * |p_{k+1} - p_k| / p_{k+1} < tol, usually two of them.  iters counts the
+ * updates of both stages; stats then needs 8 entries, [6] the FP32 and [7]
+ * the FP64 updates.  (GB300's FP64 rate is 1/73 of its FP32 rate.) */
+enum { MC_NEWTON_MIXED = 16 };
 enum { MC_RS_OK = 0, MC_RS_VACUUM = 1, MC_RS_NOCONV = 2, MC_RS_FALLBACK = 4 };
 
 /* Seed network: 10 features -> 64 -> 64 -> 1 (ReLU), BF16 weights and FP32
@@ -446,7 +500,8 @@ mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const floa
 
 /* stats (nullable): device int64[6], accumulated (the caller zeroes it):
  * interfaces, vacuum, fallback, not converged, total Newton updates,
- * largest per-interface count. */
+ * largest per-interface count; with MC_NEWTON_MIXED 8 entries, [6] FP32 and
+ * [7] FP64 updates. */
 mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const float* u_l,
                            const float* p_l, const float* rho_r, const float* u_r,
                            const float* p_r, float* p_star, float* u_star, uint8_t* iters,

@@ -101,6 +101,7 @@ def lib():
                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _VP]
         L.mc_newton_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                       ctypes.c_int32, _VP]
+        L.mc_guard_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _VP]
         L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_download.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
@@ -111,6 +112,7 @@ def lib():
         L.mc_step.argtypes = [_VP, _VP, _VP, ctypes.c_double, _DP, _VP]
         L.mc_sweep.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP]
         L.mc_step_noalloc.argtypes = [P, _VP, _VP, ctypes.c_double, _DP, _VP]
+        L.mc_peak_run.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP, _DP, _VP]
         L.mc_max_cell_speed.argtypes = [_VP, _VP, _DP, _VP]
         L.mc_advance.argtypes = [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  _DP, _DP, _IP, _IP, _VP]
@@ -129,7 +131,7 @@ def lib():
         L.mc_batch_destroy.argtypes = [_VP]
         L.mc_batch_set_tile_rows.argtypes = [_VP, ctypes.c_void_p]
         L.mc_batch_inject_stall.argtypes = [_VP, ctypes.c_int32]
-        for fn in (L.mc_batch_advance, L.mc_batch_advance_plain):
+        for fn in (L.mc_batch_advance, L.mc_batch_advance_plain, L.mc_batch_advance_steps):
             fn.argtypes = [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, _IP, _VP]
         L.mc_riemann_exact.argtypes = [ctypes.c_int64, ctypes.c_double] + [_VP] * 10 + [
             ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int, _VP, _VP]
@@ -192,6 +194,12 @@ class Context:
         """Attach a SeedNet (or None) to the exact-solution Euler solver."""
         self._seed_net = net   # keep it alive while attached
         check(lib().mc_set_seed_net(self._h, net.handle if net is not None else None))
+
+    def guard_stats(self, reset: bool = True, stream: int = 0) -> int:
+        """Interior edges the FP64 guard recomputed since the last reset."""
+        n = ctypes.c_int64()
+        check(lib().mc_guard_stats(self._h, ctypes.byref(n), int(reset), _VP(stream)))
+        return n.value
 
     def newton_stats(self, reset: bool = True, stream: int = 0):
         """(Newton updates, normal solves) counted since the last reset."""
@@ -270,6 +278,7 @@ def header_functions(path: str = HEADER) -> list[str]:
 # ---------------------------------------------------------------- exact solver
 
 SEED_ADAPTIVE, SEED_PV, SEED_TR, SEED_TS, SEED_PVTR, SEED_MLP = range(6)
+NEWTON_MIXED = 16   # added to a seed mode: FP32 Newton stage, then FP64 updates
 RS_OK, RS_VACUUM, RS_NOCONV, RS_FALLBACK = 0, 1, 2, 4
 MLP_NWEIGHT = 16 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 MLP_NPARAM = MLP_NWEIGHT + 20
@@ -372,6 +381,17 @@ def step_noalloc(problem: Problem, q_in: int, q_out: int, dt: float, want_smax: 
     return smax.value if want_smax else None
 
 
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA, PEAK_RSQRT, PEAK_RCP, PEAK_IADD, PEAK_ISSUE = range(7)
+
+
+def peak_run(kind: int, blocks_per_sm: int, iters: int, sink: int, stream: int = 0) -> float:
+    """mc_peak_run: launch one throughput microbenchmark; returns its operation count."""
+    ops = ctypes.c_double(0.0)
+    check(lib().mc_peak_run(int(kind), int(blocks_per_sm), int(iters), _VP(sink), ctypes.byref(ops),
+                            _VP(stream)))
+    return ops.value
+
+
 # ---------------------------------------------------------------- batched patches
 
 class PatchC(ctypes.Structure):
@@ -420,6 +440,10 @@ class Batch:
     def inject_stall(self, patch: int) -> None:
         """Test hook: the next advance's waits for this patch run out (MC_ETIMEOUT)."""
         check(lib().mc_batch_inject_stall(self._h, int(patch)))
+
+    def advance_steps(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
+        """One launch per step over all patches, in a graph -> (t per patch or None, result_in_b)."""
+        return self._run(lib().mc_batch_advance_steps, nsteps, cfl, want_t, stream)
 
     def advance_plain(self, nsteps: int, cfl: float = 0.9, want_t: bool = False, stream: int = 0):
         """One launch per patch per step -> (t per patch or None, result_in_b)."""

@@ -64,6 +64,9 @@ struct mc_batch {
     cudaGraphExec_t exec = nullptr;
     int exec_steps = -1;
     double exec_cfl = 0.0;
+    cudaGraphExec_t exec_ps = nullptr;   // the one-launch-per-step form
+    int exec_ps_steps = -1;
+    double exec_ps_cfl = 0.0;
     int stall_patch = -1;           // fault injection for the next advance
 };
 
@@ -126,9 +129,17 @@ static cudaError_t solver_sweep_prepare(const mc_problem& p)
     }
 }
 
-static void free_batch(mc_batch* b)
+static void drop_exec(mc_batch* b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->exec_ps) cudaGraphExecDestroy(b->exec_ps);
+    b->exec = b->exec_ps = nullptr;
+    b->exec_steps = b->exec_ps_steps = -1;
+}
+
+static void free_batch(mc_batch* b)
+{
+    drop_exec(b);
     if (b->capture) cudaStreamDestroy(b->capture);
     cudaFree(b->d_patches);
     cudaFree(b->d_maps);
@@ -151,11 +162,7 @@ static mc_status upload_tables(mc_batch* b)
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_prefix, b->prefix.data(), sizeof(long long) * (b->npatch + 1),
                        cudaMemcpyHostToDevice);
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        b->exec_steps = -1;
-    }
+    drop_exec(b);
     return e == cudaSuccess ? MC_OK : cuda_error(e, "uploading patch tables");
 }
 
@@ -164,17 +171,17 @@ static mc_status ensure_steps(mc_batch* b, int nsteps)
     if (nsteps <= b->cap_steps) return MC_OK;
     cudaFree(b->d_smax);
     cudaFree(b->d_dt);
+    cudaFree(b->d_next);
     b->d_smax = nullptr;
     b->d_dt = nullptr;
+    b->d_next = nullptr;
     cudaError_t e = cudaMalloc(&b->d_smax, sizeof(unsigned long long) * (size_t)b->npatch * (nsteps + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_dt, sizeof(double) * (size_t)b->npatch * nsteps);
+    // one work counter per launch of the one-launch-per-step form
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned long long) * (size_t)nsteps);
     if (e != cudaSuccess) return cuda_error(e, "allocating per-step arrays");
     b->cap_steps = nsteps;
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        b->exec_steps = -1;
-    }
+    drop_exec(b);
     return MC_OK;
 }
 
@@ -187,6 +194,8 @@ static BatchLaunch make_launch(mc_batch* b, int nsteps, double cfl, cudaStream_t
     L.prefix = b->d_prefix;
     L.npatch = b->npatch;
     L.nsteps = nsteps;
+    L.step0 = 0;
+    L.nsteps_all = nsteps;
     L.tasks_per_step = b->prefix[b->npatch];
     L.x_offset = b->x_offset;
     L.cfl = cfl;
@@ -407,6 +416,54 @@ mc_status mc_batch_advance(mc_batch* b, int32_t nsteps, double cfl, double* t_ou
         cudaError_t e2 = upload_desc(b, -1);
         if (e2 != cudaSuccess && st == MC_OK) st = cuda_error(e2, "restoring patch descriptors");
     }
+    if (st == MC_OK && result_in_b) *result_in_b = nsteps & 1;
+    return st;
+}
+
+mc_status mc_batch_advance_steps(mc_batch* b, int32_t nsteps, double cfl, double* t_out,
+                                 int* result_in_b, void* stream)
+{
+    if (!b) return set_error(MC_EINVAL, "NULL batch");
+    if (nsteps < 1 || nsteps > 100000) return set_error(MC_EINVAL, "nsteps out of range");
+    if (!(cfl > 0.0 && cfl <= 1.0)) return set_error(MC_EINVAL, "need 0 < cfl <= 1");
+    mc_status st = ensure_steps(b, nsteps);
+    if (st != MC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!b->exec_ps || b->exec_ps_steps != nsteps || b->exec_ps_cfl != cfl) {
+        if (b->exec_ps) cudaGraphExecDestroy(b->exec_ps);
+        b->exec_ps = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_error(e, "begin capture");
+        BatchLaunch L = make_launch(b, nsteps, cfl, b->capture);
+        cudaError_t e2 = cudaMemsetAsync(b->d_smax, 0,
+                                         sizeof(unsigned long long) * (size_t)b->npatch * (nsteps + 1),
+                                         b->capture);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(b->d_done, 0, sizeof(unsigned) * b->npatch, b->capture);
+        if (e2 == cudaSuccess)
+            e2 = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long) * (size_t)nsteps, b->capture);
+        if (e2 == cudaSuccess) e2 = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->capture);
+        if (e2 == cudaSuccess) e2 = solver_batch_init(L);
+        // one launch per step over all patches, each with its own counter
+        L.nsteps = 1;
+        for (int k = 0; k < nsteps && e2 == cudaSuccess; k++) {
+            L.step0 = k;
+            e2 = solver_batch_launch(L);
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->capture, &graph);
+        if (e2 != cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec_ps, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec_ps = nullptr;
+            return cuda_error(e, "capturing the per-step launches");
+        }
+        b->exec_ps_steps = nsteps;
+        b->exec_ps_cfl = cfl;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec_ps, s);
+    if (e != cudaSuccess) return cuda_error(e, "per-step graph launch");
+    st = finish(b, nsteps, t_out, s);
     if (st == MC_OK && result_in_b) *result_in_b = nsteps & 1;
     return st;
 }

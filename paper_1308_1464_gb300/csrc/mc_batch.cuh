@@ -35,15 +35,16 @@ struct BatchArgs {
     const PatchDesc* patches;
     const CUtensorMap* maps;        // two per patch: [2p] of qa, [2p + 1] of qb
     const long long* prefix;        // npatch + 1 cumulative task counts
-    int npatch, nsteps;
+    int npatch, nsteps;             // steps of this launch
+    int step0, nsteps_all;          // its first step; steps of the whole advance
     long long tasks_per_step;
     long long x_offset;
     double cfl;
     int limiter, order, transverse;
-    unsigned long long* smax;       // npatch x (nsteps + 1): [p][0] initial cell speeds, [p][s+1] step s
-    double* dt_used;                // npatch x nsteps
+    unsigned long long* smax;       // npatch x (nsteps_all + 1): [p][0] initial cell speeds, [p][s+1] step s
+    double* dt_used;                // npatch x nsteps_all
     unsigned int* done;             // npatch: tasks completed so far
-    unsigned long long* next_item;  // work counter
+    unsigned long long* next_item;  // work counters, one per launch (indexed by step0)
     int* status;
 };
 
@@ -74,20 +75,22 @@ __device__ __forceinline__ bool wait_counter(const unsigned* counter, unsigned t
 }
 
 template <class RP, int MODE>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const BatchArgs<RP> a)
+__global__ void __launch_bounds__(SWEEP_WARPS * 32, min_ctas<RP>::value) batch_sweep_kernel(const BatchArgs<RP> a)
 {
     using T = typename RP::real;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
     const bool second = a.order >= 2;
-    const long long total = (long long)a.nsteps * a.tasks_per_step;
-    const int stride = a.nsteps + 1;
+    // items of this launch: steps [step0, step0 + nsteps), in step order
+    const long long first = (long long)a.step0 * a.tasks_per_step;
+    const long long total = first + (long long)a.nsteps * a.tasks_per_step;
+    const int stride = a.nsteps_all + 1;
     bool dep_failed = false, tma_failed = false, bad = false;
 
     for (;;) {
         long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(a.next_item, 1ull);
+        if (lane == 0) item = first + (long long)atomicAdd(&a.next_item[a.step0], 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total) break;
         const int s = int(item / a.tasks_per_step);
@@ -139,7 +142,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32) batch_sweep_kernel(const Bat
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) {
             atomic_max_nonneg(&a.smax[(long long)p * stride + s + 1], v);
-            if (t == 0) a.dt_used[(long long)p * a.nsteps + s] = dt;
+            if (t == 0) a.dt_used[(long long)p * a.nsteps_all + s] = dt;
             __threadfence();
             atomicAdd(&a.done[p], 1u);
         }

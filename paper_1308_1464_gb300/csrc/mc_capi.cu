@@ -251,13 +251,42 @@ struct mc_ctx {
     int next_slot;
     const mc_mlp* seed_net = nullptr;   // pressure seeds of the exact-solution solver, or none
     int sms = 0;                        // SMs of the context's device
+    int* gq_tasks = nullptr;            // task list of the FP64 guard's queue (FP32 pair solvers)
+    int gq_cap = 0;
 };
+
+// FP32 shallow-water and Euler steps carry the FP64 guard
+static bool has_guard(const mc_problem& p)
+{
+    return p.dtype == MC_F32 && (p.solver == MC_SWE_ROE || p.solver == MC_EULER_ROE);
+}
+
+// The guard queue's task list holds one entry per task of the current tile
+// shape; without it the guard kernel recomputes every task of a step that
+// queued one.
+static void ensure_guard_list(mc_ctx* c)
+{
+    if (!has_guard(c->p)) return;
+    int nb = 0;
+    const int need = ntasks_for(c->p, c->tile_rows, &nb);
+    if (need <= c->gq_cap) return;
+    if (c->gq_tasks) cudaFree(c->gq_tasks);
+    c->gq_tasks = nullptr;
+    c->gq_cap = 0;
+    if (cudaMalloc(&c->gq_tasks, sizeof(int) * (size_t)need) == cudaSuccess) c->gq_cap = need;
+    else (void)cudaGetLastError();
+}
 
 // the context's extras for every fused-step launch
 static void launch_extras(const mc_ctx* c, SweepLaunch& L)
 {
     L.seed_net = c->seed_net ? c->seed_net->dev : nullptr;
     L.newton = c->dev->newton;
+    L.guard = &c->dev->guard;
+    if (has_guard(c->p)) {
+        L.gq = &c->dev->gq;
+        L.gq_tasks = c->gq_tasks;
+    }
     L.sms = c->sms;
 }
 
@@ -393,6 +422,7 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
         return set_error(MC_ECUDA, "driver entry point cuTensorMapEncodeTiled unavailable");
     }
     c->encode = reinterpret_cast<EncodeTiledFn>(fn);
+    ensure_guard_list(c);
     *out = c;
     return MC_OK;
 }
@@ -404,6 +434,7 @@ mc_status mc_destroy(mc_ctx* c)
     cudaStreamDestroy(c->capture);
     cudaFree(c->dmaps);
     cudaFree(c->dev);
+    if (c->gq_tasks) cudaFree(c->gq_tasks);
     delete c;
     return MC_OK;
 }
@@ -415,6 +446,7 @@ mc_status mc_set_tile_rows(mc_ctx* c, int rows)
     if (rows < 1 || rows > 4096) return set_error(MC_EINVAL, "tile rows %d out of range", rows);
     if (rows != c->tile_rows) drop_graphs(c);
     c->tile_rows = rows;
+    ensure_guard_list(c);
     return MC_OK;
 }
 
@@ -439,6 +471,19 @@ mc_status mc_newton_stats(mc_ctx* c, int64_t* updates, int64_t* solves, int32_t 
     if (e != cudaSuccess) return cuda_error(e, "Newton counters");
     *updates = (int64_t)h[0];
     *solves = (int64_t)h[1];
+    return MC_OK;
+}
+
+mc_status mc_guard_stats(mc_ctx* c, int64_t* edges, int32_t reset, void* stream)
+{
+    if (!c || !edges) return set_error(MC_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, &c->dev->guard, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(&c->dev->guard, 0, sizeof(h), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "guard counter");
+    *edges = (int64_t)h;
     return MC_OK;
 }
 

@@ -228,7 +228,129 @@ __device__ __forceinline__ void raw_features(const Side& L, const Side& R, const
     x[9] = logf(float(fmax(sd.pv_raw, 1e-6)));
 }
 
-template <bool MLP>
+// ---- The FP32 stage (MC_NEWTON_MIXED).  GB300 runs FP64 at 1/73 of its
+// FP32 rate, so Newton first iterates in FP32 from the seed until
+// |dp|/p < TOL32, and FP64 updates (newton above, same stopping test
+// |p_{k+1} - p_k| / p_{k+1} < tol) finish from there: two of them in the
+// usual case, since the FP32 iterate is within about 1e-6 of p* and one FP64
+// update squares that relative error.  The FP32 sides, guesses and powers
+// use the hardware base-2 logarithm and exponential (relative error a few
+// 1e-7), ample for a stage whose result is only a starting point.
+constexpr float TOL32 = 1e-5f;
+constexpr int MAX32 = 12;
+
+__device__ __forceinline__ float pow32(float x, float y)
+{
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y * l));
+    return r;
+}
+
+struct Side32 {
+    float rho, u, p, c, B, iA, kr, ipz, ikr;
+};
+
+__device__ __forceinline__ Side32 make_side32(float gamma, float z, float rho, float u, float p)
+{
+    Side32 s;
+    s.rho = rho;
+    s.u = u;
+    s.p = p;
+    const float irho = 1.0f / rho;
+    const float c2 = gamma * p * irho;
+    const float rc = rsqrtf(c2);
+    s.c = c2 * rc;
+    s.B = (gamma - 1.0f) / (gamma + 1.0f) * p;
+    s.iA = 0.5f * (gamma + 1.0f) * rho;
+    s.kr = 2.0f * s.c / (gamma - 1.0f);
+    s.ipz = pow32(p, -z);
+    s.ikr = irho * rc * p * s.ipz;
+    return s;
+}
+
+__device__ __forceinline__ void branch32(const Side32& s, float p, float w, float& f, float& fd)
+{
+    if (p > s.p) {
+        const float q = rsqrtf((s.B + p) * s.iA);
+        const float dp = p - s.p;
+        f = dp * q;
+        fd = q * (1.0f - 0.5f * dp * q * q * s.iA);
+    } else {
+        f = s.kr * (w * p * s.ipz - 1.0f);
+        fd = s.ikr * w;
+    }
+}
+
+struct Seeds32 {
+    float pv_raw, pv, tr, ts, adaptive, pvtr;
+};
+
+__device__ __forceinline__ Seeds32 seeds32(float gamma, float z, const Side32& L, const Side32& R)
+{
+    Seeds32 s;
+    const float fl = float(PFLOOR);
+    const float du = R.u - L.u;
+    s.pv_raw = 0.5f * (L.p + R.p) - 0.125f * du * (L.rho + R.rho) * (L.c + R.c);
+    s.pv = s.pv_raw < fl ? fl : s.pv_raw;
+    const float x = (L.c + R.c - 0.5f * (gamma - 1.0f) * du) / (L.c * L.ipz + R.c * R.ipz);
+    s.tr = x > 0.0f ? pow32(x, 1.0f / z) : __int_as_float(0x7fc00000);
+    const float gl = rsqrtf((L.B + s.pv) * L.iA), gr = rsqrtf((R.B + s.pv) * R.iA);
+    s.ts = (gl * L.p + gr * R.p - du) / (gl + gr);
+    if (s.ts < fl) s.ts = fl;
+    const float pmin = fminf(L.p, R.p), pmax = fmaxf(L.p, R.p);
+    const bool pv_ok = pmax / pmin < 2.0f && s.pv >= pmin && s.pv <= pmax;
+    s.adaptive = pv_ok ? s.pv : (s.pv < pmin ? s.tr : s.ts);
+    s.pvtr = pv_ok ? s.pv : s.tr;
+    return s;
+}
+
+__device__ __forceinline__ void raw_features32(const Side32& L, const Side32& R, const Seeds32& sd,
+                                               float (&x)[10])
+{
+    const float du = R.u - L.u;
+    x[0] = logf(L.rho);
+    x[1] = logf(R.rho);
+    x[2] = logf(L.p);
+    x[3] = logf(R.p);
+    x[4] = logf(L.c);
+    x[5] = logf(R.c);
+    x[6] = du;
+    x[7] = du / (L.c + R.c);
+    x[8] = logf(sd.tr);
+    x[9] = logf(fmaxf(sd.pv_raw, 1e-6f));
+}
+
+// FP32 Newton from p0 until |dp|/p < TOL32 (true) or MAX32 updates (false,
+// ps the last finite iterate); updates counted in it.
+__device__ __forceinline__ bool newton32(const Side32& L, const Side32& R, float z, float p0,
+                                         float& ps, int& it)
+{
+    float p = p0;
+    const float fl = float(PFLOOR);
+    for (int k = 0; k < MAX32; k++) {
+        const float w = (p <= L.p || p <= R.p) ? pow32(p, z - 1.0f) : 0.0f;
+        float f1, d1, f2, d2;
+        branch32(L, p, w, f1, d1);
+        branch32(R, p, w, f2, d2);
+        float pn = p - (f1 + f2 + (R.u - L.u)) / (d1 + d2);
+        if (pn < fl) pn = fl;
+        it++;
+        if (!isfinite(pn)) {
+            ps = p;
+            return false;
+        }
+        if (fabsf(pn - p) < TOL32 * pn) {
+            ps = pn;
+            return true;
+        }
+        p = pn;
+    }
+    ps = p;
+    return false;
+}
+
+template <bool MLP, bool MIXED>
 __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -244,7 +366,8 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
     }
     const double gamma = a.gamma;
     const Powers pw = a.pw;
-    long long c_n = 0, c_vac = 0, c_fb = 0, c_nc = 0, c_it = 0, c_max = 0;
+    long long c_n = 0, c_vac = 0, c_fb = 0, c_nc = 0, c_it = 0, c_max = 0, c_it32 = 0, c_it64 = 0;
+    const float g32 = float(gamma), z32 = float(pw.z);
     const long long nchunks = (a.n + 31) / 32;
     for (long long ch = (long long)blockIdx.x * 4 + warp; ch < nchunks;
          ch += (long long)gridDim.x * 4) {
@@ -259,41 +382,97 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
             R = L;
         }
         const bool vacuum = 2.0 / (gamma - 1.0) * (L.c + R.c) <= R.u - L.u;
-        Seeds sd = seeds(gamma, pw, L, R);
-        double p0;
-        switch (a.seed_mode) {
-        case MC_SEED_PV: p0 = sd.pv; break;
-        case MC_SEED_TR: p0 = sd.tr; break;
-        case MC_SEED_TS: p0 = sd.ts; break;
-        case MC_SEED_PVTR: p0 = sd.pvtr; break;
-        default: p0 = sd.adaptive; break;
-        }
-        int flag = 0, it = 0;
-        double ps = 0.0;
+        int flag = 0, it = 0, it32 = 0;
+        double ps = 0.0, p0 = 0.0;
         NewtonEval ev{};
         bool done = false;
-        if (MLP) {
-            float x[10];
-            if (!vacuum && valid) {
-                raw_features(L, R, sd, x);
-#pragma unroll
-                for (int k = 0; k < 10; k++) x[k] = (x[k] - net->mu[k]) / net->sig[k];
-            } else {
-#pragma unroll
-                for (int k = 0; k < 10; k++) x[k] = 0.0f;
+        if constexpr (MIXED) {
+            // FP32 stage from the seed (or the network's proposal), then FP64
+            const Side32 L32 = valid ? make_side32(g32, z32, a.rl[i], a.ul[i], a.pl[i])
+                                     : make_side32(g32, z32, 1.0f, 0.0f, 1.0f);
+            const Side32 R32 = valid ? make_side32(g32, z32, a.rr[i], a.ur[i], a.pr[i]) : L32;
+            const Seeds32 sd = seeds32(g32, z32, L32, R32);
+            float p32;
+            switch (a.seed_mode & 15) {
+            case MC_SEED_PV: p32 = sd.pv; break;
+            case MC_SEED_TR: p32 = sd.tr; break;
+            case MC_SEED_TS: p32 = sd.ts; break;
+            case MC_SEED_PVTR: p32 = sd.pvtr; break;
+            default: p32 = sd.adaptive; break;
             }
-            const float o = mlp_infer_warp(*net, x, xs, outs);
-            if (!vacuum && valid) {
-                // a seed: FP32 accuracy of the factor is ample, and an FP64 exp
-                // would cost as much as a Newton update
-                const double prop = sd.tr * double(expf(o));
-                const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
-                if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
-                    newton(L, R, pw, prop, a.tol, a.max_iter, ps, it, ev)) {
-                    done = true;
+            float ps32 = 0.0f;
+            bool have32 = false;
+            if (MLP) {
+                float x[10];
+                if (!vacuum && valid) {
+                    raw_features32(L32, R32, sd, x);
+#pragma unroll
+                    for (int k = 0; k < 10; k++) x[k] = (x[k] - net->mu[k]) / net->sig[k];
                 } else {
-                    flag |= MC_RS_FALLBACK;
-                    p0 = sd.adaptive;
+#pragma unroll
+                    for (int k = 0; k < 10; k++) x[k] = 0.0f;
+                }
+                const float o = mlp_infer_warp(*net, x, xs, outs);
+                if (!vacuum && valid) {
+                    const float prop = sd.tr * expf(o);
+                    const float pmin = fminf(L32.p, R32.p), pmax = fmaxf(L32.p, R32.p);
+                    if (isfinite(prop) && prop >= 1e-6f * pmin && prop <= 1e6f * pmax &&
+                        newton32(L32, R32, z32, prop, ps32, it32)) {
+                        have32 = true;
+                    } else {
+                        flag |= MC_RS_FALLBACK;
+                        p32 = sd.adaptive;
+                    }
+                }
+            }
+            if (valid && !vacuum) {
+                if (!have32) {
+                    float q = 0.0f;
+                    // a stalled FP32 stage still leaves a close start
+                    have32 = newton32(L32, R32, z32, p32, q, it32) || (isfinite(q) && q > 0.0f);
+                    ps32 = q;
+                }
+                // FP64 from the FP32 iterate, else from the FP64 adaptive guess
+                const double start = have32 ? double(ps32) : seeds(gamma, pw, L, R).adaptive;
+                int it64 = 0;
+                if (!newton(L, R, pw, start, a.tol, a.max_iter, ps, it64, ev)) flag |= MC_RS_NOCONV;
+                done = true;
+                it = it32 + it64;
+                c_it32 += it32;
+                c_it64 += it64;
+            }
+        } else {
+            Seeds sd = seeds(gamma, pw, L, R);
+            switch (a.seed_mode) {
+            case MC_SEED_PV: p0 = sd.pv; break;
+            case MC_SEED_TR: p0 = sd.tr; break;
+            case MC_SEED_TS: p0 = sd.ts; break;
+            case MC_SEED_PVTR: p0 = sd.pvtr; break;
+            default: p0 = sd.adaptive; break;
+            }
+            if (MLP) {
+                float x[10];
+                if (!vacuum && valid) {
+                    raw_features(L, R, sd, x);
+#pragma unroll
+                    for (int k = 0; k < 10; k++) x[k] = (x[k] - net->mu[k]) / net->sig[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 10; k++) x[k] = 0.0f;
+                }
+                const float o = mlp_infer_warp(*net, x, xs, outs);
+                if (!vacuum && valid) {
+                    // a seed: FP32 accuracy of the factor is ample, and an FP64 exp
+                    // would cost as much as a Newton update
+                    const double prop = sd.tr * double(expf(o));
+                    const double pmin = fmin(L.p, R.p), pmax = fmax(L.p, R.p);
+                    if (isfinite(prop) && prop >= 1e-6 * pmin && prop <= 1e6 * pmax &&
+                        newton(L, R, pw, prop, a.tol, a.max_iter, ps, it, ev)) {
+                        done = true;
+                    } else {
+                        flag |= MC_RS_FALLBACK;
+                        p0 = sd.adaptive;
+                    }
                 }
             }
         }
@@ -327,6 +506,8 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
             c_fb += __shfl_xor_sync(0xffffffffu, c_fb, o);
             c_nc += __shfl_xor_sync(0xffffffffu, c_nc, o);
             c_it += __shfl_xor_sync(0xffffffffu, c_it, o);
+            c_it32 += __shfl_xor_sync(0xffffffffu, c_it32, o);
+            c_it64 += __shfl_xor_sync(0xffffffffu, c_it64, o);
             long long m = __shfl_xor_sync(0xffffffffu, c_max, o);
             c_max = c_max > m ? c_max : m;
         }
@@ -337,6 +518,10 @@ __global__ void __launch_bounds__(128) exact_kernel(const ExactArgs a)
             atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[3]), (unsigned long long)c_nc);
             atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[4]), (unsigned long long)c_it);
             atomicMax(reinterpret_cast<unsigned long long*>(&a.stats[5]), (unsigned long long)c_max);
+            if (MIXED) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[6]), (unsigned long long)c_it32);
+                atomicAdd(reinterpret_cast<unsigned long long*>(&a.stats[7]), (unsigned long long)c_it64);
+            }
         }
     }
 }
@@ -479,10 +664,12 @@ mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const fl
     if (!(gamma > 1.0)) return set_error(MC_EINVAL, "gamma must be > 1");
     if (!(tol > 0.0) || max_iter < 1 || max_iter > 255)
         return set_error(MC_EINVAL, "need tol > 0 and 1 <= max_iter <= 255");
-    if (seed_mode < MC_SEED_ADAPTIVE || seed_mode > MC_SEED_MLP)
+    const bool mixed = (seed_mode & MC_NEWTON_MIXED) != 0;
+    const int base = seed_mode & ~MC_NEWTON_MIXED;
+    if (base < MC_SEED_ADAPTIVE || base > MC_SEED_MLP)
         return set_error(MC_EINVAL, "unknown seed mode %d", seed_mode);
-    if (seed_mode == MC_SEED_MLP && !net) return set_error(MC_EINVAL, "MLP seed needs a network");
-    ExactArgs a{n, make_powers(gamma), gamma, tol, max_iter, seed_mode, rho_l, u_l, p_l, rho_r, u_r, p_r,
+    if (base == MC_SEED_MLP && !net) return set_error(MC_EINVAL, "MLP seed needs a network");
+    ExactArgs a{n, make_powers(gamma), gamma, tol, max_iter, base, rho_l, u_l, p_l, rho_r, u_r, p_r,
                 p_star, u_star, iters, flags, net ? net->dev : nullptr, stats};
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -492,14 +679,20 @@ mc_status mc_riemann_exact(int64_t n, double gamma, const float* rho_l, const fl
     const long long cap = (long long)sms * 16;
     if (blocks > cap) blocks = cap;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (seed_mode == MC_SEED_MLP) {
-        cudaError_t e = cudaFuncSetAttribute(exact_kernel<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             EXACT_SMEM_MLP);
+    if (base == MC_SEED_MLP) {
+        cudaError_t e = mixed ? cudaFuncSetAttribute(exact_kernel<true, true>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     EXACT_SMEM_MLP)
+                              : cudaFuncSetAttribute(exact_kernel<true, false>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     EXACT_SMEM_MLP);
         if (e != cudaSuccess) return cuda_error(e, "exact solver set-up");
-        exact_kernel<true><<<(unsigned)blocks, 128, EXACT_SMEM_MLP, s>>>(a);
+        if (mixed) exact_kernel<true, true><<<(unsigned)blocks, 128, EXACT_SMEM_MLP, s>>>(a);
+        else exact_kernel<true, false><<<(unsigned)blocks, 128, EXACT_SMEM_MLP, s>>>(a);
+    } else if (mixed) {
+        exact_kernel<false, true><<<(unsigned)blocks, 128, 0, s>>>(a);
     } else {
-        exact_kernel<false><<<(unsigned)blocks, 128, 0, s>>>(a);
+        exact_kernel<false, false><<<(unsigned)blocks, 128, 0, s>>>(a);
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MC_OK : cuda_error(e, "exact solver launch");

@@ -43,6 +43,9 @@ struct SweepLaunch {
     cudaStream_t stream;
     const void* seed_net = nullptr;            // MlpDev of a pressure-seed network (SEEDED solvers)
     unsigned long long* newton = nullptr;      // Newton update / solve counters, or null
+    unsigned long long* guard = nullptr;       // FP64-guard edge counter, or null
+    void* gq = nullptr;                        // GuardQueue of the FP64 guard, or null (no guard)
+    int* gq_tasks = nullptr;                   // its task list (ntasks entries), or null: all tasks
     int sms = 0;                               // SMs of the device (0: unknown, full CTAs)
 };
 
@@ -128,6 +131,7 @@ struct BatchLaunch {
     const CUtensorMap* maps;
     const long long* prefix;
     int npatch, nsteps;
+    int step0 = 0, nsteps_all = 0;   // first step of the launch; steps of the whole advance
     long long tasks_per_step;
     long long x_offset;
     double cfl;

@@ -14,8 +14,11 @@
 // the bias sums stay on the CUDA cores in FP32.  The transposed operands of
 // the weight-gradient products (H1^T, X^T as A; D2, D1 as B) are staged in
 // shared memory, transposed, so that every fragment is one 32-bit load.
-// Per-CTA gradients accumulate in shared memory and are added to the
-// network's FP32 gradient once per CTA.
+// Gradients accumulate per warp in shared memory (contributions of several
+// lanes to one weight are first summed by shuffles in a fixed order), the
+// warps' sums are added in warp order into a per-CTA partial, and a second
+// kernel adds the partials in CTA order: no float atomics, so a training run
+// is bitwise reproducible.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -37,8 +40,8 @@ struct TrainShared {
     float b1[NH], b2[NH], w3r[NH];
     float mu[10], sig[10];
     float b3;
-    float g[MC_MLP_NWEIGHT];                  // CTA gradient
-    float loss;
+    float g[TW][MC_MLP_NWEIGHT];              // per-warp gradients
+    float loss[TW];
     struct Warp {
         __nv_bfloat16 xs[16 * XP];            // X, row major (A of layer 1)
         __nv_bfloat16 xT[16 * BP];            // X^T  [feature][row]
@@ -95,16 +98,23 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
             S.mu[k] = d->params[P_MU + k];
             S.sig[k] = d->params[P_SIG + k];
         }
-        for (int k = threadIdx.x; k < MC_MLP_NWEIGHT; k += blockDim.x) S.g[k] = 0.f;
-        if (threadIdx.x == 0) {
-            S.b3 = d->params[P_B3];
-            S.loss = 0.f;
-        }
+        float* g0 = &S.g[0][0];
+        for (int k = threadIdx.x; k < TW * MC_MLP_NWEIGHT; k += blockDim.x) g0[k] = 0.f;
+        if (threadIdx.x < TW) S.loss[threadIdx.x] = 0.f;
+        if (threadIdx.x == 0) S.b3 = d->params[P_B3];
     }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     TrainShared::Warp& W = S.w[warp];
+    float* G = S.g[warp];
+    // sum over the eight lanes of one t (lanes t, t + 4, ..., t + 28), fixed order
+    auto sum_g = [](float v) {
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        return v;
+    };
     const long long nchunk = (a.rows + 15) / 16;
     for (long long ch = (long long)blockIdx.x * TW + warp; ch < nchunk;
          ch += (long long)gridDim.x * TW) {
@@ -203,9 +213,12 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
         const float vg = W.valid[g], vg8 = W.valid[g + 8];
         const float rg = (og - W.y[g]) * vg, rg8 = (og8 - W.y[g + 8]) * vg8;
         const float dg = 2.f * rg * a.inv_batch, dg8 = 2.f * rg8 * a.inv_batch;
-        if (t == 0) {
-            atomicAdd(&S.loss, rg * rg + rg8 * rg8);
-            atomicAdd(&S.g[P_B3], dg + dg8);
+        {
+            const float l = sum_g(rg * rg + rg8 * rg8), b = sum_g(dg + dg8);
+            if (lane == 0) {
+                S.loss[warp] += l;
+                G[P_B3] += b;
+            }
         }
         float d2[8][4];
         uint32_t ad2[4][4];
@@ -213,14 +226,19 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
         for (int nt = 0; nt < 8; nt++) {
             const int k0 = nt * 8 + 2 * t;
             const float w0 = S.w3r[k0], w1 = S.w3r[k0 + 1];
-            atomicAdd(&S.g[P_W3 + k0], h2[nt][0] * dg + h2[nt][2] * dg8);
-            atomicAdd(&S.g[P_W3 + k0 + 1], h2[nt][1] * dg + h2[nt][3] * dg8);
+            const float gw0 = sum_g(h2[nt][0] * dg + h2[nt][2] * dg8);
+            const float gw1 = sum_g(h2[nt][1] * dg + h2[nt][3] * dg8);
             d2[nt][0] = h2[nt][0] > 0.f ? dg * w0 : 0.f;
             d2[nt][1] = h2[nt][1] > 0.f ? dg * w1 : 0.f;
             d2[nt][2] = h2[nt][2] > 0.f ? dg8 * w0 : 0.f;
             d2[nt][3] = h2[nt][3] > 0.f ? dg8 * w1 : 0.f;
-            atomicAdd(&S.g[P_B2 + k0], d2[nt][0] + d2[nt][2]);
-            atomicAdd(&S.g[P_B2 + k0 + 1], d2[nt][1] + d2[nt][3]);
+            const float gb0 = sum_g(d2[nt][0] + d2[nt][2]), gb1 = sum_g(d2[nt][1] + d2[nt][3]);
+            if (g == 0) {
+                G[P_W3 + k0] += gw0;
+                G[P_W3 + k0 + 1] += gw1;
+                G[P_B2 + k0] += gb0;
+                G[P_B2 + k0 + 1] += gb1;
+            }
             ad2[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16x2(d2[nt][0], d2[nt][1]);
             ad2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2(d2[nt][2], d2[nt][3]);
             W.d2T[k0 * BP + g] = __float2bfloat16_rn(d2[nt][0]);
@@ -244,10 +262,11 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
                 const __nv_bfloat16* bb = &W.d2T[(nt * 8 + g) * BP + 2 * t];
                 mma_bf16_16816(c, ah, ld_pair(bb), ld_pair(bb + 8));
                 const int k0 = nt * 8 + 2 * t;
-                atomicAdd(&S.g[P_W2 + j0 * NH + k0], c[0]);
-                atomicAdd(&S.g[P_W2 + j0 * NH + k0 + 1], c[1]);
-                atomicAdd(&S.g[P_W2 + (j0 + 8) * NH + k0], c[2]);
-                atomicAdd(&S.g[P_W2 + (j0 + 8) * NH + k0 + 1], c[3]);
+                // each lane owns its four weights of this tile
+                G[P_W2 + j0 * NH + k0] += c[0];
+                G[P_W2 + j0 * NH + k0 + 1] += c[1];
+                G[P_W2 + (j0 + 8) * NH + k0] += c[2];
+                G[P_W2 + (j0 + 8) * NH + k0 + 1] += c[3];
             }
         }
         // D1 = (D2 W2^T) . [H1 > 0]
@@ -262,8 +281,13 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
             const int j0 = nt * 8 + 2 * t;
             const float e0 = h1[nt][0] > 0.f ? c[0] : 0.f, e1 = h1[nt][1] > 0.f ? c[1] : 0.f;
             const float e2 = h1[nt][2] > 0.f ? c[2] : 0.f, e3 = h1[nt][3] > 0.f ? c[3] : 0.f;
-            atomicAdd(&S.g[P_B1 + j0], e0 + e2);
-            atomicAdd(&S.g[P_B1 + j0 + 1], e1 + e3);
+            {
+                const float b0 = sum_g(e0 + e2), b1 = sum_g(e1 + e3);
+                if (g == 0) {
+                    G[P_B1 + j0] += b0;
+                    G[P_B1 + j0 + 1] += b1;
+                }
+            }
             W.d1T[j0 * BP + g] = __float2bfloat16_rn(e0);
             W.d1T[(j0 + 1) * BP + g] = __float2bfloat16_rn(e1);
             W.d1T[j0 * BP + g + 8] = __float2bfloat16_rn(e2);
@@ -283,19 +307,46 @@ __global__ void __launch_bounds__(TW * 32) mlp_train_kernel(const TrainArgs a)
                 const __nv_bfloat16* bb = &W.d1T[(nt * 8 + g) * BP + 2 * t];
                 mma_bf16_16816(c, axt, ld_pair(bb), ld_pair(bb + 8));
                 const int j0 = nt * 8 + 2 * t;
-                atomicAdd(&S.g[P_W1 + g * NH + j0], c[0]);
-                atomicAdd(&S.g[P_W1 + g * NH + j0 + 1], c[1]);
-                atomicAdd(&S.g[P_W1 + (g + 8) * NH + j0], c[2]);
-                atomicAdd(&S.g[P_W1 + (g + 8) * NH + j0 + 1], c[3]);
+                G[P_W1 + g * NH + j0] += c[0];
+                G[P_W1 + g * NH + j0 + 1] += c[1];
+                G[P_W1 + (g + 8) * NH + j0] += c[2];
+                G[P_W1 + (g + 8) * NH + j0 + 1] += c[3];
             }
         }
         __syncwarp();
     }
     if (!a.backward) return;
     __syncthreads();
-    for (int k = threadIdx.x; k < MC_MLP_NWEIGHT; k += blockDim.x)
-        if (S.g[k] != 0.f) atomicAdd(&a.net->grad[k], S.g[k]);
-    if (threadIdx.x == 0) atomicAdd(&a.net->loss_sum, (double)S.loss);
+    // this CTA's partial: the warps' sums in warp order
+    float* part = a.net->gpart + (size_t)blockIdx.x * MC_MLP_NWEIGHT;
+    for (int k = threadIdx.x; k < MC_MLP_NWEIGHT; k += blockDim.x) {
+        float v = S.g[0][k];
+#pragma unroll
+        for (int w = 1; w < TW; w++) v += S.g[w][k];
+        part[k] = v;
+    }
+    if (threadIdx.x == 0) {
+        double l = 0.0;
+        for (int w = 0; w < TW; w++) l += double(S.loss[w]);
+        a.net->lpart[blockIdx.x] = l;
+    }
+}
+
+// The gradient and loss of a training launch: its CTAs' partials added in
+// CTA order.
+__global__ void reduce_grad_kernel(MlpDev* d, int nparts)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < MC_MLP_NWEIGHT;
+         k += blockDim.x * gridDim.x) {
+        float v = 0.f;
+        for (int b = 0; b < nparts; b++) v += d->gpart[(size_t)b * MC_MLP_NWEIGHT + k];
+        d->grad[k] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double l = 0.0;
+        for (int b = 0; b < nparts; b++) l += d->lpart[b];
+        d->loss_sum = l;
+    }
 }
 
 constexpr int TRAIN_SMEM = (int)sizeof(TrainShared);
@@ -358,9 +409,15 @@ __global__ void adam_kernel(MlpDev* d, float lr, float b1, float b2, float eps, 
     }
 }
 
-// mean / standard deviation of the finite feature rows (FP64 sums)
-__global__ void moments_kernel(long long n, const float* feat, double* sums)
+// mean / standard deviation of the finite feature rows (FP64 sums): each
+// block writes its 21 sums (feature sums, sums of squares, count), reduced
+// within the block in a fixed order; set_norm_kernel adds the blocks' sums
+// in block order
+constexpr int MOMENT_THREADS = 256;
+__global__ void __launch_bounds__(MOMENT_THREADS) moments_kernel(long long n, const float* feat,
+                                                                 double* sums)
 {
+    __shared__ double red[MOMENT_THREADS];
     double s[10], q[10], cnt = 0.0;
 #pragma unroll
     for (int f = 0; f < 10; f++) s[f] = q[f] = 0.0;
@@ -381,21 +438,31 @@ __global__ void moments_kernel(long long n, const float* feat, double* sums)
             q[f] += double(x[f]) * x[f];
         }
     }
-#pragma unroll
-    for (int f = 0; f < 10; f++) {
-        atomicAdd(&sums[f], s[f]);
-        atomicAdd(&sums[10 + f], q[f]);
+    for (int v = 0; v < 21; v++) {
+        red[threadIdx.x] = v < 10 ? s[v] : (v < 20 ? q[v - 10] : cnt);
+        __syncthreads();
+        for (int w = MOMENT_THREADS / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sums[(size_t)blockIdx.x * 21 + v] = red[0];
+        __syncthreads();
     }
-    atomicAdd(&sums[20], cnt);
 }
 
-__global__ void set_norm_kernel(MlpDev* d, const double* sums)
+__global__ void set_norm_kernel(MlpDev* d, const double* sums, int nblocks)
 {
     const int f = threadIdx.x;
     if (f >= 10) return;
-    const double cnt = sums[20] > 0.0 ? sums[20] : 1.0;
-    const double mu = sums[f] / cnt;
-    const double var = sums[10 + f] / cnt - mu * mu;
+    double sf = 0.0, qf = 0.0, c = 0.0;
+    for (int b = 0; b < nblocks; b++) {
+        sf += sums[(size_t)b * 21 + f];
+        qf += sums[(size_t)b * 21 + 10 + f];
+        c += sums[(size_t)b * 21 + 20];
+    }
+    const double cnt = c > 0.0 ? c : 1.0;
+    const double mu = sf / cnt;
+    const double var = qf / cnt - mu * mu;
     d->params[P_MU + f] = float(mu);
     d->params[P_SIG + f] = float(var > 1e-12 ? sqrt(var) : 1.0);
 }
@@ -408,12 +475,14 @@ static cudaError_t train_launch(MlpDev* dev, const TrainArgs& a, cudaStream_t s)
     const long long nchunk = (a.rows + 15) / 16;
     long long blocks = (nchunk + TW - 1) / TW;
     if (blocks > sms) blocks = sms;
+    if (blocks > TRAIN_MAX_CTAS) blocks = TRAIN_MAX_CTAS;
     if (blocks < 1) blocks = 1;
     cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, TRAIN_SMEM);
     if (e != cudaSuccess) return e;
-    (void)dev;
     mlp_train_kernel<<<(unsigned)blocks, TW * 32, TRAIN_SMEM, s>>>(a);
+    if (a.backward)
+        reduce_grad_kernel<<<(MC_MLP_NWEIGHT + 255) / 256, 256, 0, s>>>(dev, (int)blocks);
     return cudaGetLastError();
 }
 
@@ -472,13 +541,12 @@ mc_status mc_mlp_train(mc_mlp* net, int64_t n, const float* features, const floa
     cudaError_t e = cudaSuccess;
     if (cfg->fit_norm) {
         double* sums = nullptr;
-        e = cudaMallocAsync(&sums, 21 * sizeof(double), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, 21 * sizeof(double), s);
+        long long blocks = (n + MOMENT_THREADS - 1) / MOMENT_THREADS;
+        if (blocks > 1024) blocks = 1024;
+        e = cudaMallocAsync(&sums, 21 * sizeof(double) * (size_t)blocks, s);
         if (e == cudaSuccess) {
-            long long blocks = (n + 255) / 256;
-            if (blocks > 1024) blocks = 1024;
-            moments_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, features, sums);
-            set_norm_kernel<<<1, 32, 0, s>>>(net->dev, sums);
+            moments_kernel<<<(unsigned)blocks, MOMENT_THREADS, 0, s>>>(n, features, sums);
+            set_norm_kernel<<<1, 32, 0, s>>>(net->dev, sums, (int)blocks);
             e = cudaGetLastError();
             cudaFreeAsync(sums, s);
         }

@@ -30,7 +30,7 @@ struct MultiArgs {
 };
 
 template <class RP, int MODE>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32) multi_sweep_kernel(const MultiArgs<RP> a)
+__global__ void __launch_bounds__(SWEEP_WARPS * 32, min_ctas<RP>::value) multi_sweep_kernel(const MultiArgs<RP> a)
 {
     using T = typename RP::real;
     extern __shared__ __align__(128) unsigned char smem[];

@@ -26,15 +26,17 @@
 namespace mc {
 namespace {
 
-// Scratch of one call: the running speed maximum, the status word and the
-// tensor map of q_in (which the TMA reads from device memory) -- 192 bytes,
+// Scratch of one call: the running speed maximum, the status word, the FP64
+// guard's queue counters (FP32 shallow water and Euler) and the tensor map of
+// q_in (which the TMA reads from device memory) -- 192 bytes,
 // inside an array of NOALLOC_SCRATCH_BYTES that every device loading the
 // library keeps until the process exits.
 constexpr size_t NOALLOC_SCRATCH_BYTES = 256;
 struct NoallocScratch {
     unsigned long long smax_bits;
     int status;
-    int pad[13];
+    unsigned guard_queue[2];   // count and done of the FP64 guard's queue (no task list)
+    int pad[11];
     CUtensorMap map;   // 64-byte aligned
 };
 static_assert(offsetof(NoallocScratch, map) % 64 == 0, "tensor map alignment");
@@ -103,6 +105,7 @@ __global__ void noalloc_begin_kernel(NoallocScratch* s, const CUtensorMap map)
     if (t == 0) {
         s->smax_bits = 0ull;
         s->status = 0;
+        s->guard_queue[0] = s->guard_queue[1] = 0u;
     }
 }
 
@@ -166,6 +169,9 @@ extern "C" mc_status mc_step_noalloc(const mc_problem* p, void* q_in, void* q_ou
     const int rows = DEFAULT_TILE_ROWS;
     SweepLaunch L{*p, lay, &scratch->map, &scratch->map, q_in, q_out, nullptr, nullptr, dt,
                   &scratch->smax_bits, &scratch->status, rows, 0, s};
+    // the FP64 guard recomputes every task of a step that queued one (the
+    // array has no room for a task list)
+    L.gq = scratch->guard_queue;
     switch (p->solver) {
     case MC_ACOUSTICS: e = sweep_launch_acoustics(L); break;
     case MC_SWE_ROE: e = sweep_launch_swe(L); break;

@@ -262,6 +262,32 @@ struct AdvectionRP {
     }
 };
 
+// ---------------------------------------------------------------- FP64 guard
+// FP32 runs recompute a few edges in FP64: edges across a near-dry or
+// near-vacuum front (the smaller depth or density below tau times the
+// larger), Euler edges whose Roe sound speed is a vanishing part of the
+// enthalpy (c^2 < tau (gamma - 1) H: cold, high-Mach flow, where c^2 is the
+// difference of two nearly equal terms), and the speeds and the split of a
+// transonic entropy fix.  An Edge64 carries one such edge's results, in the
+// edge-normal frame (component 1 the normal momentum), rounded to FP32.
+struct Edge64 {
+    float W[3][4];
+    float s[3];
+    float am[4], ap[4];
+    float lin[6];             // the linearised state (solver's Lin fields in order)
+    float tm[4], tp[4];       // transverse split of am (B-, B+)
+    float um[4], up[4];       // ... and of ap
+    bool bad;
+};
+// the normal solve (and, with trans, both transverse splits) of one edge in
+// FP64; a and b are the left and right states in the edge-normal frame
+static __device__ __forceinline__ Edge64 swe_edge64(double g, bool efix, const float (&a)[3],
+                                                 const float (&b)[3], bool trans);
+static __device__ __forceinline__ Edge64 euler_edge64(double gamma, bool efix, const float (&a)[4],
+                                                   const float (&b)[4], bool trans);
+// default relative threshold of the guard (param[3] = 0)
+constexpr float GUARD_TAU_DEFAULT = 1e-3f;
+
 // ---------------------------------------------------------------- shallow water
 template <typename T>
 struct SweRP {
@@ -271,6 +297,8 @@ struct SweRP {
     static constexpr bool POSITIVE = true;    // depth h > 0
     T g;
     bool efix;
+    double gd;        // g in FP64 (guarded edges)
+    float gtau;       // FP32 guard threshold; negative: guard off
     struct Lin { T u, v, c, r2c; };
     // component m of wave p can be non-zero: the shear wave moves only the
     // tangential momentum
@@ -293,6 +321,38 @@ struct SweRP {
     {
         g = T(param[0]);
         efix = ef != 0;
+        gd = param[0];
+        gtau = param[3] == 0.0 ? GUARD_TAU_DEFAULT : float(param[3]);
+    }
+    __host__ __device__ __forceinline__ bool guard_on() const { return sizeof(T) == 4 && gtau >= 0.f; }
+    // an edge across a near-dry front: the smaller depth below gtau times
+    // the larger
+    __device__ __forceinline__ bool near_dry(float hl, float hr) const
+    {
+        return (hl < gtau * hr) | (hr < gtau * hl);
+    }
+    // Harten-Hyman for a wave with states (ha, hua) on its left and (hb,
+    // hub) on its right, characteristic speed hu/h + sg sqrt(g h) (sg = -1:
+    // the 1-wave, +1: the 3-wave), Roe speed sroe: if the speeds straddle
+    // zero, k = beta lam_a with beta = (lam_b - sroe) / (lam_b - lam_a), the
+    // left-going part; otherwise k is left as it is.  F64: the speeds and
+    // the split in FP64 (the guard's recompute of an FP32 step).
+    // Returns true (FP32 form) when a speed lies within gtau times cref (the
+    // Roe sound speed) of zero: a near-sonic edge for the FP64 guard.
+    template <bool F64 = false>
+    __device__ __forceinline__ bool hh_fix(T ha, T hua, T hb, T hub, T sg, T sroe, T cref, T& k) const
+    {
+        if constexpr (F64) {
+            const double la = double(hua) / double(ha) + double(sg) * sqrt(gd * double(ha));
+            const double lb = double(hub) / double(hb) + double(sg) * sqrt(gd * double(hb));
+            if (la < 0.0 && lb > 0.0) k = T((lb - double(sroe)) / (lb - la) * la);
+            return false;
+        } else {
+            const T la = hua * rcp_(ha) + sg * sqrt_(g * ha);
+            const T lb = hub * rcp_(hb) + sg * sqrt_(g * hb);
+            if (la < T(0) && lb > T(0)) k = (lb - sroe) * rcp_(lb - la) * la;
+            return fabs(la) < T(gtau) * cref || fabs(lb) < T(gtau) * cref;
+        }
     }
 
     // the sweep may pass each state's 1/sqrt(h), formed once per cell
@@ -348,19 +408,11 @@ struct SweRP {
             const T hul = ql[un], hum = ql[un] + W[0][un], hm = hl + W[0][0];
             const bool l_neg = hul <= T(0) || hul * hul < g * hl * hl * hl;
             const bool r_pos = hm > T(0) && hum > T(0) && hum * hum > g * hm * hm * hm;
-            if (l_neg && r_pos) {
-                const T lam_l = hul * rcp_(hl) - sqrt_(g * hl);
-                const T lam_r = hum * rcp_(hm) - sqrt_(g * hm);
-                if (lam_l < T(0) && lam_r > T(0)) k0 = (lam_r - s[0]) * rcp_(lam_r - lam_l) * lam_l;
-            }
+            if (l_neg && r_pos) hh_fix(hl, hul, hm, hum, T(-1), s[0], c, k0);
             const T hur = qr[un], hun = qr[un] - W[2][un], hn = hr - W[2][0];
             const bool n_neg = hn > T(0) && hun < T(0) && hun * hun > g * hn * hn * hn;
             const bool rr_pos = hur >= T(0) || hur * hur < g * hr * hr * hr;
-            if (n_neg && rr_pos) {
-                const T ll = hun * rcp_(hn) + sqrt_(g * hn);
-                const T lr = hur * rcp_(hr) + sqrt_(g * hr);
-                if (ll < T(0) && lr > T(0)) k2 = (lr - s[2]) * rcp_(lr - ll) * ll;
-            }
+            if (n_neg && rr_pos) hh_fix(hn, hun, hr, hur, T(1), s[2], c, k2);
         }
         // A-dQ = sum_p k_p W^p, A+dQ = sum_p (s^p - k_p) W^p (k_p = min(s^p, 0)
         // unless the entropy fix replaced it), over the non-zero components
@@ -380,6 +432,8 @@ struct SweRP {
     // same arithmetic as normal<0> / transverse<0>, two edges per instruction
     static constexpr bool PAIRED = sizeof(T) == 4;
     static constexpr bool SEEDED = false;   // no external pressure seed
+    // FP32: three resident CTAs of four warps per SM (at most 168 registers)
+    static constexpr int MIN_CTAS = sizeof(T) == 4 ? 3 : 1;
     struct LinP { f2 u, v, c, r2c; };
     // the scalar linearised state of half h (x-edge 0, y-edge 1)
     __device__ __forceinline__ Lin lin_half(const LinP& P, int h) const
@@ -391,9 +445,13 @@ struct SweRP {
         return fabs(half(L.u, h)) + half(L.c, h);
     }
 
+    // hh: bit h set when half h met a near-sonic transonic wave (a speed
+    // within gtau times the Roe sound speed of zero); F64FIX: the transonic
+    // fix's speeds and split in FP64
+    template <bool F64FIX = false>
     __device__ __forceinline__ void normal_pair(const f2* ql, const f2* qr, f2 (&W)[NW][NEQ],
                                                 f2 (&s)[NW], f2* amdq, f2* apdq, LinP& L,
-                                                bool& badx, bool& bady) const
+                                                bool& badx, bool& bady, int& hh) const
     {
         const f2 hl = ql[0], hr = qr[0];
         badx = badx || !(hl.x > 0.f && hr.x > 0.f);
@@ -422,39 +480,39 @@ struct SweRP {
 
         f2 k0 = p_min0(sm), k2 = p_min0(sp);
         if (efix) {
-            // the transonic tests of normal(), both halves at once and free of
-            // branches; the rare transonic edge then takes one branch
+            // the transonic tests of normal(), both halves at once.  A wave
+            // can be transonic only if its intermediate state moves faster
+            // than sound (rightward for the 1-wave, leftward for the 3-wave);
+            // those two tests come first, and the tests of the outer states
+            // only for a lane where one of them holds
             const f2 gs = p_set(g);
-            const f2 hul = ql[1], hum = p_add(ql[1], W[0][1]), hm = p_add(hl, a1);
-            const f2 hur = qr[1], hun = p_sub(qr[1], W[2][1]), hn = p_sub(hr, a3);
-            const f2 hul2 = p_mul(hul, hul), gl3 = p_mul(p_mul(p_mul(gs, hl), hl), hl);
+            const f2 hum = p_add(ql[1], W[0][1]), hm = p_add(hl, a1);
+            const f2 hun = p_sub(qr[1], W[2][1]), hn = p_sub(hr, a3);
             const f2 hum2 = p_mul(hum, hum), gm3 = p_mul(p_mul(p_mul(gs, hm), hm), hm);
             const f2 hun2 = p_mul(hun, hun), gn3 = p_mul(p_mul(p_mul(gs, hn), hn), hn);
-            const f2 hur2 = p_mul(hur, hur), gr3 = p_mul(p_mul(p_mul(gs, hr), hr), hr);
-            bool t0[2], t2[2];
+            bool r_pos[2], n_neg[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const bool l_neg = (half(hul, h) <= 0.f) | (half(hul2, h) < half(gl3, h));
-                const bool r_pos = (half(hm, h) > 0.f) & (half(hum, h) > 0.f) & (half(hum2, h) > half(gm3, h));
-                const bool n_neg = (half(hn, h) > 0.f) & (half(hun, h) < 0.f) & (half(hun2, h) > half(gn3, h));
-                const bool rr_pos = (half(hur, h) >= 0.f) | (half(hur2, h) < half(gr3, h));
-                t0[h] = l_neg & r_pos;
-                t2[h] = n_neg & rr_pos;
+                r_pos[h] = (half(hm, h) > 0.f) & (half(hum, h) > 0.f) & (half(hum2, h) > half(gm3, h));
+                n_neg[h] = (half(hn, h) > 0.f) & (half(hun, h) < 0.f) & (half(hun2, h) > half(gn3, h));
             }
-            if (t0[0] | t0[1] | t2[0] | t2[1]) {
+            if (r_pos[0] | r_pos[1] | n_neg[0] | n_neg[1]) {
+                const f2 hul = ql[1], hur = qr[1];
+                const f2 hul2 = p_mul(hul, hul), gl3 = p_mul(p_mul(p_mul(gs, hl), hl), hl);
+                const f2 hur2 = p_mul(hur, hur), gr3 = p_mul(p_mul(p_mul(gs, hr), hr), hr);
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    if (t0[h]) {
-                        const float lam_l = half(hul, h) * rcp_(half(hl, h)) - sqrt_(g * half(hl, h));
-                        const float lam_r = half(hum, h) * rcp_(half(hm, h)) - sqrt_(g * half(hm, h));
-                        if (lam_l < 0.f && lam_r > 0.f)
-                            half(k0, h) = (lam_r - half(sm, h)) * rcp_(lam_r - lam_l) * lam_l;
+                    const bool l_neg = (half(hul, h) <= 0.f) | (half(hul2, h) < half(gl3, h));
+                    const bool rr_pos = (half(hur, h) >= 0.f) | (half(hur2, h) < half(gr3, h));
+                    if (l_neg & r_pos[h]) {
+                        if (hh_fix<F64FIX>(half(hl, h), half(hul, h), half(hm, h), half(hum, h), -1.f,
+                                           half(sm, h), half(c, h), half(k0, h)))
+                            hh |= 1 << h;
                     }
-                    if (t2[h]) {
-                        const float ll = half(hun, h) * rcp_(half(hn, h)) + sqrt_(g * half(hn, h));
-                        const float lr = half(hur, h) * rcp_(half(hr, h)) + sqrt_(g * half(hr, h));
-                        if (ll < 0.f && lr > 0.f)
-                            half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                    if (n_neg[h] & rr_pos) {
+                        if (hh_fix<F64FIX>(half(hn, h), half(hun, h), half(hr, h), half(hur, h), 1.f,
+                                           half(sp, h), half(c, h), half(k2, h)))
+                            hh |= 1 << h;
                     }
                 }
             }
@@ -490,6 +548,53 @@ struct SweRP {
         bp[1] = p_fma(bp[0], v, q2);
     }
 
+    // The FP64 guard of a pair: bit h set when half h is a near-dry edge.
+    __device__ __forceinline__ int guard_mask(const f2* ql, const f2* qr, const LinP&) const
+    {
+        if (!guard_on()) return 0;
+        const f2 tl = p_mul(ql[0], p_set(gtau)), tr = p_mul(qr[0], p_set(gtau));
+        return ((ql[0].x < tr.x) | (qr[0].x < tl.x)) | (((ql[0].y < tr.y) | (qr[0].y < tl.y)) << 1);
+    }
+    // Replaces the results of the guarded halves by their FP64 solve (and,
+    // with trans, their FP64 transverse splits).
+    __device__ __forceinline__ void guard_redo(const f2* ql, const f2* qr, int gm, bool trans,
+                                               f2 (&W)[NW][NEQ], f2 (&s)[NW], f2* am, f2* ap,
+                                               LinP& L, f2* Tm, f2* Tp, f2* Um, f2* Up, bool& badx,
+                                               bool& bady) const
+    {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (!((gm >> h) & 1)) continue;
+            float a[NEQ], b[NEQ];
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) {
+                a[m] = half(ql[m], h);
+                b[m] = half(qr[m], h);
+            }
+            const Edge64 e = swe_edge64(gd, efix, a, b, trans);
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) {
+#pragma unroll
+                for (int p = 0; p < NW; p++) half(W[p][m], h) = e.W[p][m];
+                half(am[m], h) = e.am[m];
+                half(ap[m], h) = e.ap[m];
+                if (trans) {
+                    half(Tm[m], h) = e.tm[m];
+                    half(Tp[m], h) = e.tp[m];
+                    half(Um[m], h) = e.um[m];
+                    half(Up[m], h) = e.up[m];
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NW; p++) half(s[p], h) = e.s[p];
+            half(L.u, h) = e.lin[0];
+            half(L.v, h) = e.lin[1];
+            half(L.c, h) = e.lin[2];
+            half(L.r2c, h) = e.lin[3];
+            (h ? bady : badx) = e.bad;
+        }
+    }
+
     template <int DIR>
     __device__ __forceinline__ void transverse(const Lin& L, const T* a, T* bm, T* bp) const
     {
@@ -521,6 +626,8 @@ struct EulerRP {
     static constexpr bool POSITIVE = true;    // density rho > 0
     T gamma, gm1;
     bool efix;
+    double gd, gm1d;  // gamma and gamma - 1 in FP64 (guarded edges)
+    float gtau;       // FP32 guard threshold; negative: guard off
     struct Lin { T u, v, H, c, rc, gc2; };
     // every component of every wave can be non-zero
     template <int DIR>
@@ -548,6 +655,54 @@ struct EulerRP {
         gamma = T(param[0]);
         gm1 = T(param[0] - 1.0);
         efix = ef != 0;
+        gd = param[0];
+        gm1d = param[0] - 1.0;
+        gtau = param[3] == 0.0 ? GUARD_TAU_DEFAULT : float(param[3]);
+    }
+    __host__ __device__ __forceinline__ bool guard_on() const { return sizeof(T) == 4 && gtau >= 0.f; }
+    // an edge the guard recomputes: across a near-vacuum front (the smaller
+    // density below gtau times the larger; also for a density that is not a
+    // positive number)
+    __device__ __forceinline__ bool guarded(float rl, float rr) const
+    {
+        return !(rl >= gtau * rr) | !(rr >= gtau * rl);
+    }
+    // u_n + sgn c of a conserved state in FP64; false if not physical
+    template <int DIR>
+    __device__ __forceinline__ bool cspeed64(const T* q, double sgn, double& lam) const
+    {
+        constexpr int un = 1 + DIR, ut = 2 - DIR;
+        const double r = q[0];
+        if (!(r > 0.0)) return false;
+        const double u = double(q[un]) / r, v = double(q[ut]) / r;
+        const double p = gm1d * (double(q[3]) - 0.5 * r * (u * u + v * v));
+        if (!(p > 0.0)) return false;
+        lam = u + sgn * sqrt(gd * p / r);
+        return true;
+    }
+    // Harten-Hyman for a wave with states qa on its left and qb on its
+    // right, characteristic speed u + sgn c, Roe speed sroe: if both states
+    // are physical and their speeds straddle zero, k = beta lam_a, beta =
+    // (lam_b - sroe) / (lam_b - lam_a); otherwise k is left as it is.  F64:
+    // the speeds and the split in FP64 (the guard's recompute of an FP32
+    // step).
+    // Returns true (FP32 form) when a speed lies within gtau times cref (the
+    // Roe sound speed) of zero: a near-sonic edge for the FP64 guard.
+    template <int DIR, bool F64 = false>
+    __device__ __forceinline__ bool hh_fix(const T* qa, const T* qb, T sgn, T sroe, T cref, T& k) const
+    {
+        if constexpr (F64) {
+            double la, lb;
+            if (cspeed64<DIR>(qa, double(sgn), la) && cspeed64<DIR>(qb, double(sgn), lb) && la < 0.0 &&
+                lb > 0.0)
+                k = T((lb - double(sroe)) / (lb - la) * la);
+            return false;
+        } else {
+            T la = T(0), lb = T(0);
+            const bool ok = cspeed<DIR>(qa, sgn, la) && cspeed<DIR>(qb, sgn, lb);
+            if (ok && la < T(0) && lb > T(0)) k = (lb - sroe) * rcp_(lb - la) * la;
+            return ok && (fabs(la) < T(gtau) * cref || fabs(lb) < T(gtau) * cref);
+        }
     }
 
     // speed u_n -+ c of a conserved state; false if not physical
@@ -644,20 +799,12 @@ struct EulerRP {
             T qm[NEQ];
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = ql[m] + W[0][m];
-            if (slower_than_sound<DIR>(ql, false) && faster_than_sound<DIR>(qm, true)) {
-                T ll, lr;
-                if (cspeed<DIR>(ql, T(-1), ll) && cspeed<DIR>(qm, T(-1), lr) && ll < T(0) &&
-                    lr > T(0))
-                    k0 = (lr - s[0]) * rcp_(lr - ll) * ll;
-            }
+            if (slower_than_sound<DIR>(ql, false) && faster_than_sound<DIR>(qm, true))
+                hh_fix<DIR>(ql, qm, T(-1), s[0], c, k0);
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = qr[m] - W[2][m];
-            if (faster_than_sound<DIR>(qm, false) && slower_than_sound<DIR>(qr, true)) {
-                T ll, lr;
-                if (cspeed<DIR>(qm, T(1), ll) && cspeed<DIR>(qr, T(1), lr) && ll < T(0) &&
-                    lr > T(0))
-                    k2 = (lr - s[2]) * rcp_(lr - ll) * ll;
-            }
+            if (faster_than_sound<DIR>(qm, false) && slower_than_sound<DIR>(qr, true))
+                hh_fix<DIR>(qm, qr, T(1), s[2], c, k2);
         }
         const T k1 = tmin0(s[1]);
 #pragma unroll
@@ -705,9 +852,13 @@ struct EulerRP {
         return fabs(half(L.u, h)) + half(L.c, h);
     }
 
+    // hh: bit h set when half h met a near-sonic transonic wave (a speed
+    // within gtau times the Roe sound speed of zero); F64FIX: the transonic
+    // fix's speeds and split in FP64
+    template <bool F64FIX = false>
     __device__ __forceinline__ void normal_pair(const f2* ql, const f2* qr, f2 (&W)[NW][NEQ],
                                                 f2 (&s)[NW], f2* amdq, f2* apdq, LinP& L,
-                                                bool& badx, bool& bady) const
+                                                bool& badx, bool& bady, int& hh) const
     {
         const f2 h2 = p_set(0.5f), g1 = p_set(gm1);
         const f2 rl = ql[0], rr = qr[0];
@@ -787,9 +938,8 @@ struct EulerRP {
                             qa[m] = half(ql[m], h);
                             qb[m] = half(qm0[m], h);
                         }
-                        float ll, lr;
-                        if (cspeed<0>(qa, -1.f, ll) && cspeed<0>(qb, -1.f, lr) && ll < 0.f && lr > 0.f)
-                            half(k0, h) = (lr - half(sm, h)) * rcp_(lr - ll) * ll;
+                        if (hh_fix<0, F64FIX>(qa, qb, -1.f, half(sm, h), half(c, h), half(k0, h)))
+                            hh |= 1 << h;
                     }
                     if (t2[h]) {
 #pragma unroll
@@ -797,9 +947,8 @@ struct EulerRP {
                             qa[m] = half(qm2[m], h);
                             qb[m] = half(qr[m], h);
                         }
-                        float ll, lr;
-                        if (cspeed<0>(qa, 1.f, ll) && cspeed<0>(qb, 1.f, lr) && ll < 0.f && lr > 0.f)
-                            half(k2, h) = (lr - half(sp, h)) * rcp_(lr - ll) * ll;
+                        if (hh_fix<0, F64FIX>(qa, qb, 1.f, half(sp, h), half(c, h), half(k2, h)))
+                            hh |= 1 << h;
                     }
                 }
             }
@@ -845,7 +994,141 @@ struct EulerRP {
             bp[3] = p_fma(m1, e1, p_fma(me, ke, p_fma(ms, v, p_mul(m4, e4))));
         }
     }
+
+    // The FP64 guard of a pair: bit h set when half h is guarded.
+    __device__ __forceinline__ int guard_mask(const f2* ql, const f2* qr, const LinP& L) const
+    {
+        if (!guard_on()) return 0;
+        return int(guarded(ql[0].x, qr[0].x)) | (int(guarded(ql[0].y, qr[0].y)) << 1);
+    }
+    // Replaces the results of the guarded halves by their FP64 solve (and,
+    // with trans, their FP64 transverse splits).
+    __device__ __forceinline__ void guard_redo(const f2* ql, const f2* qr, int gm, bool trans,
+                                               f2 (&W)[NW][NEQ], f2 (&s)[NW], f2* am, f2* ap,
+                                               LinP& L, f2* Tm, f2* Tp, f2* Um, f2* Up, bool& badx,
+                                               bool& bady) const
+    {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (!((gm >> h) & 1)) continue;
+            float a[NEQ], b[NEQ];
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) {
+                a[m] = half(ql[m], h);
+                b[m] = half(qr[m], h);
+            }
+            const Edge64 e = euler_edge64(gd, efix, a, b, trans);
+#pragma unroll
+            for (int m = 0; m < NEQ; m++) {
+#pragma unroll
+                for (int p = 0; p < NW; p++) half(W[p][m], h) = e.W[p][m];
+                half(am[m], h) = e.am[m];
+                half(ap[m], h) = e.ap[m];
+                if (trans) {
+                    half(Tm[m], h) = e.tm[m];
+                    half(Tp[m], h) = e.tp[m];
+                    half(Um[m], h) = e.um[m];
+                    half(Up[m], h) = e.up[m];
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NW; p++) half(s[p], h) = e.s[p];
+            half(L.u, h) = e.lin[0];
+            half(L.v, h) = e.lin[1];
+            half(L.H, h) = e.lin[2];
+            half(L.c, h) = e.lin[3];
+            half(L.rc, h) = e.lin[4];
+            half(L.gc2, h) = e.lin[5];
+            (h ? bady : badx) = !(a[0] > 0.f && b[0] > 0.f) || e.bad;
+        }
+    }
 };
+
+// ---------------------------------------------------------------- FP64 guard: edge solves
+static __device__ __forceinline__ Edge64 swe_edge64(double g, bool efix, const float (&a)[3],
+                                                 const float (&b)[3], bool trans)
+{
+    SweRP<double> r;
+    r.g = g;
+    r.gd = g;
+    r.efix = efix;
+    r.gtau = -1.f;
+    double ql[3], qr[3], W[3][3], s[3], am[3], ap[3];
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        ql[m] = a[m];
+        qr[m] = b[m];
+    }
+    typename SweRP<double>::Lin L;
+    bool bad = false;
+    r.template normal<0>(ql, qr, W, s, am, ap, L, bad);
+    Edge64 e{};
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) e.W[p][m] = float(W[p][m]);
+        e.am[m] = float(am[m]);
+        e.ap[m] = float(ap[m]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; p++) e.s[p] = float(s[p]);
+    e.lin[0] = float(L.u); e.lin[1] = float(L.v); e.lin[2] = float(L.c); e.lin[3] = float(L.r2c);
+    if (trans) {
+        double t1[3], t2[3];
+        r.template transverse<0>(L, am, t1, t2);
+#pragma unroll
+        for (int m = 0; m < 3; m++) { e.tm[m] = float(t1[m]); e.tp[m] = float(t2[m]); }
+        r.template transverse<0>(L, ap, t1, t2);
+#pragma unroll
+        for (int m = 0; m < 3; m++) { e.um[m] = float(t1[m]); e.up[m] = float(t2[m]); }
+    }
+    e.bad = bad;
+    return e;
+}
+
+static __device__ __forceinline__ Edge64 euler_edge64(double gamma, bool efix, const float (&a)[4],
+                                                   const float (&b)[4], bool trans)
+{
+    EulerRP<double> r;
+    r.gamma = gamma;
+    r.gm1 = gamma - 1.0;
+    r.gd = gamma;
+    r.gm1d = gamma - 1.0;
+    r.efix = efix;
+    r.gtau = -1.f;
+    double ql[4], qr[4], W[3][4], s[3], am[4], ap[4];
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        ql[m] = a[m];
+        qr[m] = b[m];
+    }
+    typename EulerRP<double>::Lin L;
+    bool bad = false;
+    r.template normal<0>(ql, qr, W, s, am, ap, L, bad);
+    Edge64 e{};
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) e.W[p][m] = float(W[p][m]);
+        e.am[m] = float(am[m]);
+        e.ap[m] = float(ap[m]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; p++) e.s[p] = float(s[p]);
+    e.lin[0] = float(L.u); e.lin[1] = float(L.v); e.lin[2] = float(L.H);
+    e.lin[3] = float(L.c); e.lin[4] = float(L.rc); e.lin[5] = float(L.gc2);
+    if (trans) {
+        double t1[4], t2[4];
+        r.template transverse<0>(L, am, t1, t2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) { e.tm[m] = float(t1[m]); e.tp[m] = float(t2[m]); }
+        r.template transverse<0>(L, ap, t1, t2);
+#pragma unroll
+        for (int m = 0; m < 4; m++) { e.um[m] = float(t1[m]); e.up[m] = float(t2[m]); }
+    }
+    e.bad = bad;
+    return e;
+}
 
 // ---------------------------------------------------------------- Euler, exact solution
 // Godunov normal solve: the exact Riemann solution of the normal problem

@@ -21,6 +21,9 @@ constexpr int W1P = 24, W2P = 72, XP = 24;
 
 // Device-resident network: master FP32 parameters, BF16 copies in the
 // layouts the mma fragments read, and the optimiser state.
+// CTAs of one training launch at most (their partial gradients live in MlpDev)
+constexpr int TRAIN_MAX_CTAS = 256;
+
 struct MlpDev {
     float params[MC_MLP_NPARAM];
     __nv_bfloat16 w1t[NH * W1P];   // [out][in]: W1 transposed, 16 inputs used
@@ -35,6 +38,10 @@ struct MlpDev {
     int adam_t;
     float gnorm_mean;     // running mean of the clipped gradient norms (0: none yet)
     float gscale;         // factor the optimiser applies to the current gradient
+    // per-CTA partial gradients and losses of one training launch, summed in
+    // CTA order into grad and loss_sum (deterministic: no float atomics)
+    float gpart[TRAIN_MAX_CTAS * MC_MLP_NWEIGHT];
+    double lpart[TRAIN_MAX_CTAS];
 };
 
 // Rebuilds the BF16 weight copies from the FP32 parameters (mc_exact.cu).

@@ -49,6 +49,13 @@
 
 namespace mc {
 
+// Tasks of one fused step that met a guarded or transonic edge: the step
+// kernel counts (and lists) them, the guard kernel recomputes them and its
+// last block resets the queue for the next step.
+struct GuardQueue {
+    unsigned count, done;
+};
+
 template <class RP>
 struct SweepArgs {
     using T = typename RP::real;
@@ -67,6 +74,9 @@ struct SweepArgs {
     int* status;
     const MlpDev* net;                    // pressure-seed network, or null (solvers with SEEDED)
     unsigned long long* newton_updates;   // [0] Newton updates, [1] normal solves, or null
+    unsigned long long* guard_edges;      // edges recomputed in FP64 (FP32 pair solvers), or null
+    GuardQueue* gq;                       // tasks the FP64 guard recomputes, or null (no guard)
+    int* gq_tasks;                        // their indices (capacity ntasks), or null: all tasks
 };
 
 // Solvers that take each state's 1/sqrt(h) from the caller (RS_CACHE):
@@ -76,6 +86,19 @@ template <class RP, class = void>
 struct rs_cache : std::false_type {};
 template <class RP>
 struct rs_cache<RP, std::void_t<decltype(RP::RS_CACHE)>> : std::bool_constant<RP::RS_CACHE> {};
+
+// The FP64 guard of FP32 pair solvers inside a task: none (the batched and
+// multi-grid forms), detect (mark a task that meets a guarded or transonic
+// edge), redo (recompute those edges in FP64).
+constexpr int GUARD_NONE = 0, GUARD_DETECT = 1, GUARD_REDO = 2;
+
+// Resident CTAs per SM the fused kernels are compiled for (a register cap):
+// a solver's MIN_CTAS, else 1.  The FP64 guard's rare path would otherwise
+// set the register count of the whole kernel.
+template <class RP, class = void>
+struct min_ctas : std::integral_constant<int, 1> {};
+template <class RP>
+struct min_ctas<RP, std::void_t<decltype(RP::MIN_CTAS)>> : std::integral_constant<int, RP::MIN_CTAS> {};
 
 // theta = dl / dr of K waves.  FP32: one hardware reciprocal each.  FP64:
 // one correctly rounded reciprocal for all K (simultaneous inversion: prefix
@@ -158,6 +181,7 @@ struct WarpRing {
     __nv_bfloat16* xs = nullptr;
     float* outs = nullptr;
     unsigned long long* newton = nullptr;
+    unsigned long long* guard = nullptr;   // count of edges recomputed in FP64, or null
 };
 
 // One warp task: the rows [j0, jend) of the band of columns starting at i0
@@ -181,7 +205,7 @@ struct WarpRing {
 // the part entering row k+1 joins F of row k+1 as before, and the part
 // entering row k is added to row k's carried x-edge terms just before row k
 // is updated.
-template <class RP, bool WALL_GHOSTS, int MODE>
+template <class RP, bool WALL_GHOSTS, int MODE, int GUARD = GUARD_NONE>
 __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real* __restrict__ qout, int mx, int my,
                                            long long ld_x, long long ld_field, long long x_offset,
@@ -189,7 +213,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                                            typename RP::real nuy, int limiter_rt, bool second_rt,
                                            int transverse_rt, WarpRing& W, bool& bad,
                                            typename RP::real& smx, typename RP::real& smy,
-                                           int* status)
+                                           int* status, bool* flagged = nullptr)
 {
     constexpr bool FAST = MODE == MODE_FAST;
     constexpr bool trans2 = MODE == MODE_TRANS2;
@@ -233,27 +257,37 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 
     // fetch row r of columns c and c-1 into registers; a stage goes back to
     // the TMA once its last row has been read
-    auto fetch = [&](int r, T* qc, T* ql) -> bool {
-        const int rel = r - rbase, f = rel / RS, rr = rel - f * RS, st = f % NSTAGE;
-        if (rr == 0) {
-            const bool ok = mbar_wait_bounded(&W.bars[st], (W.phase >> st) & 1u);
+    // Rows are fetched strictly in order (rbase, rbase + 1, ...), so the ring
+    // position is kept as counters: fr the row within the stage, fs the
+    // stage, ff the stage's fill index, frow the lane's element of the row.
+    int fr = 0, fs = 0, ff = 0;
+    const T* frow = reinterpret_cast<const T*>(W.ring) + sx;
+    auto fetch = [&](int, T* qc, T* ql) -> bool {
+        if (fr == 0) {
+            const bool ok = mbar_wait_bounded(&W.bars[fs], (W.phase >> fs) & 1u);
             if (!__all_sync(0xffffffffu, ok)) return false;
-            W.phase ^= 1u << st;
+            W.phase ^= 1u << fs;
         }
-        const T* row = reinterpret_cast<const T*>(W.ring + st * SB) + rr * BW;
 #pragma unroll
         for (int m = 0; m < NP; m++) {
-            qc[m] = row[m * RS * BW + sx];
-            ql[m] = row[m * RS * BW + sx - 1];
+            qc[m] = frow[m * RS * BW];
+            ql[m] = frow[m * RS * BW - 1];
         }
-        if (rr == RS - 1) {
+        if (fr == RS - 1) {
             __syncwarp();
-            const int fn = f + NSTAGE;
+            const int fn = ff + NSTAGE;
             if (lane == 0 && fn < nfill) {
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&W.bars[st], TB);
-                tma_load_3d(W.ring + st * SB, map, &W.bars[st], box_x, rbase + fn * RS + 2, 0);
+                mbar_arrive_expect_tx(&W.bars[fs], TB);
+                tma_load_3d(W.ring + fs * SB, map, &W.bars[fs], box_x, rbase + fn * RS + 2, 0);
             }
+            ff++;
+            fs = fs == NSTAGE - 1 ? 0 : fs + 1;
+            fr = 0;
+            frow = reinterpret_cast<const T*>(W.ring + fs * SB) + sx;
+        } else {
+            fr++;
+            frow += BW;
         }
         return true;
     };
@@ -326,6 +360,9 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     };
 
     int newton_n = 0, newton_s = 0;   // Newton updates and solves of this lane (SEEDED solvers)
+    int guard_n = 0;                  // interior edges this lane recomputed in FP64
+    bool task_flag = false;           // a near-sonic transonic edge met (GUARD_DETECT)
+    float g_lo = 3.0e38f, g_hi = 0.0f;   // range of the first field (GUARD_DETECT)
     for (int k = j0 - 3; k < jend; k++) {
         T qc2[NP], ql2[NP];
         // material of cell (c-1, k), the neighbour below where A-dQ of x-edge
@@ -336,6 +373,14 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             for (int q = 0; q < RP::NAUX; q++) ql0[N + q] = shfl_up1(qc0[N + q]);
         }
         if (!fetch(k + 2, qc2, ql2)) return false;
+        if constexpr (GUARD == GUARD_DETECT) {
+            // the range of the first field (depth, density) over the cells
+            // this lane reads: the guard's near-dry test is a ratio of two
+            // of them, so a task whose range stays within 1/tau has no
+            // near-dry edge
+            g_lo = fminf(g_lo, fminf(float(qc2[0]), float(ql2[0])));
+            g_hi = fmaxf(g_hi, fmaxf(float(qc2[0]), float(ql2[0])));
+        }
         T rs_c2 = T(0), rs_l2 = T(0);
         if constexpr (RSC) {
             rs_c2 = rp.rs_of(qc2);
@@ -385,7 +430,48 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             f2 W2[NW][N], s2[NW], am2[N], ap2[N];
             typename RP::LinP L2;
             bool badx = false, bady = false;
-            rp.normal_pair(QL, QR, W2, s2, am2, ap2, L2, badx, bady);
+            int hh = 0;
+            rp.template normal_pair<GUARD == GUARD_REDO>(QL, QR, W2, s2, am2, ap2, L2, badx, bady, hh);
+            const bool trans1 = trans && !trans2;
+            f2 Tm[N], Tp[N], Um[N], Up[N];
+            if (trans1) {
+                rp.transverse_pair(L2, am2, Tm, Tp);
+                rp.transverse_pair(L2, ap2, Um, Up);
+            }
+            const bool yin = ye_lane && k + 2 >= 0 && k + 2 <= my;
+            const bool xin = xe_lane && k + 1 >= 0 && k + 1 < my;
+            // FP32 runs with the FP64 guard: in the step kernel a task with a
+            // guarded or transonic edge is only marked (its speeds and flags
+            // are left out, and the guard kernel recomputes it); the guard
+            // kernel recomputes those edges in FP64
+            if constexpr (GUARD != GUARD_NONE) {
+                // only edges between cells of the ghosted grid: lanes of the
+                // last band past column mx + 1 hold no state (zeros), and
+                // would look near-dry
+                const bool gvalid = c >= -1 && c <= mx + 1;
+                if constexpr (GUARD == GUARD_DETECT) {
+                    // near-sonic transonic edges here; near-dry edges by the
+                    // task's depth range (below)
+                    if (gvalid && hh != 0) task_flag = true;
+                } else {
+                    const int gm = gvalid ? rp.guard_mask(QL, QR, L2) : 0;
+                    if (gm) {
+                        rp.guard_redo(QL, QR, gm, trans1, W2, s2, am2, ap2, L2, Tm, Tp, Um, Up, badx,
+                                      bady);
+                        // count each interior edge once: the x-edge c-1/2 of
+                        // row k+1 and the y-edge below row k+2 belong to the
+                        // task whose output lanes and rows hold column c and
+                        // that row (the grid's last edges to its last band
+                        // and tile)
+                        const bool own_c = lane >= 1 && lane <= BAND_W;
+                        const bool xown =
+                            ((own_c && c <= mx) || (lane == BAND_W + 1 && c == mx && i0 + BAND_W == mx)) &&
+                            k + 1 >= j0 && k + 1 < jend;
+                        const bool yown = own_c && c < mx && k + 2 >= j0 && (k + 2 < jend || k + 2 == my);
+                        guard_n += int((gm & 1) && xown) + int((gm & 2) && yown);
+                    }
+                }
+            }
 #pragma unroll
             for (int p = 0; p < NW; p++) {
                 sxw[p] = s2[p].x;
@@ -407,9 +493,6 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 Lx_cur = rp.lin_half(L2, 0);
                 Ly_cur = rp.lin_half(L2, 1);
             } else if (trans) {
-                f2 Tm[N], Tp[N], Um[N], Up[N];
-                rp.transverse_pair(L2, am2, Tm, Tp);
-                rp.transverse_pair(L2, ap2, Um, Up);
 #pragma unroll
                 for (int m = 0; m < N; m++) {
                     BmAm1[m] = Tm[m].x; BpAm1[m] = Tp[m].x;
@@ -418,16 +501,10 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                     nPm[frame_comp(m, 1)] = Um[m].y; nPp[frame_comp(m, 1)] = Up[m].y;
                 }
             }
-            {
-                const bool in = ye_lane && k + 2 >= 0 && k + 2 <= my;
-                bad |= in && bady;
-                smy = fmax(smy, in ? rp.max_speed(L2, 1) : T(0));
-            }
-            {
-                const bool in = xe_lane && k + 1 >= 0 && k + 1 < my;
-                bad |= in && badx;
-                smx = fmax(smx, in ? rp.max_speed(L2, 0) : T(0));
-            }
+            bad |= yin && bady;
+            smy = fmax(smy, yin ? rp.max_speed(L2, 1) : T(0));
+            bad |= xin && badx;
+            smx = fmax(smx, xin ? rp.max_speed(L2, 0) : T(0));
             y_tail();
         } else {
             typename RP::Lin Ly;
@@ -659,6 +736,28 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             }
         }
     }
+    if constexpr (GUARD == GUARD_DETECT) {
+        if (flagged) {
+            if (c > mx + 1) {   // no state in these lanes
+                g_lo = 3.0e38f;
+                g_hi = 0.0f;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                g_lo = fminf(g_lo, __shfl_xor_sync(0xffffffffu, g_lo, o));
+                g_hi = fmaxf(g_hi, __shfl_xor_sync(0xffffffffu, g_hi, o));
+            }
+            const bool dry = rp.guard_on() && !(g_lo >= rp.gtau * g_hi);
+            *flagged = dry || __any_sync(0xffffffffu, task_flag && rp.guard_on());
+        }
+    }
+    if constexpr (GUARD == GUARD_REDO) {
+        if (W.guard && __any_sync(0xffffffffu, guard_n != 0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) guard_n += __shfl_xor_sync(0xffffffffu, guard_n, o);
+            if (lane == 0) atomicAdd(W.guard, (unsigned long long)guard_n);
+        }
+    }
     if constexpr (RP::SEEDED) {
         if (W.newton) {
 #pragma unroll
@@ -701,7 +800,7 @@ __device__ __forceinline__ WarpRing warp_ring(unsigned char* smem, int es, int n
 // live in device global memory (64-byte aligned, written by the host before
 // the launch); the kernel takes plain pointers to them.
 template <class RP, int MODE>
-__global__ void __launch_bounds__(SWEEP_WARPS * 32)
+__global__ void __launch_bounds__(SWEEP_WARPS * 32, min_ctas<RP>::value)
     ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
 {
     using T = typename RP::real;
@@ -722,6 +821,7 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
         }
     }
 
+    W.guard = a.guard_edges;
     const int cur = a.cur ? *a.cur : 0;
     const CUtensorMap* map = cur ? map_b : map_a;
     T* __restrict__ qout = cur ? a.qa : a.qb;
@@ -743,14 +843,30 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     const int nw = blockDim.x >> 5;
     bool failed = false, bad = false;
     T smx = T(0), smy = T(0);
+    // FP32 pair solvers detect the edges of the FP64 guard: a task that
+    // meets one is queued for the guard kernel and contributes neither its
+    // speeds nor its flags here (the guard kernel's recompute does)
+    constexpr int GD = RP::PAIRED ? GUARD_DETECT : GUARD_NONE;
     for (int task = blockIdx.x * nw + warp; task < a.ntasks && !failed && map_ok;
          task += gridDim.x * nw) {
         const int i0 = (task % a.nbands) * BAND_W;
         const int j0 = (task / a.nbands) * a.tile_rows;
         const int jend = min(j0 + a.tile_rows, a.my);
-        failed = !sweep_task<RP, false, MODE>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
-                                         a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
-                                         a.transverse, W, bad, smx, smy, a.status);
+        bool fl = false, tb = false;
+        T tx = T(0), ty = T(0);
+        failed = !sweep_task<RP, false, MODE, GD>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
+                                             a.x_offset, i0, j0, jend, nux, nuy, a.limiter, second,
+                                             a.transverse, W, tb, tx, ty, a.status, &fl);
+        if (fl && a.gq) {
+            if (lane == 0) {
+                const unsigned slot = atomicAdd(&a.gq->count, 1u);
+                if (a.gq_tasks) a.gq_tasks[slot] = task;
+            }
+        } else {
+            bad |= tb;
+            smx = fmax(smx, tx);
+            smy = fmax(smy, ty);
+        }
     }
 
     if (failed) {
@@ -762,6 +878,67 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) atomic_max_nonneg(a.smax_bits, v);
+}
+
+// The guard kernel of an FP32 pair solver's step: recomputes the queued
+// tasks (all tasks when the queue keeps no list) with the guarded and
+// transonic edges in FP64, contributes their speeds and flags, and resets the
+// queue.  Launched after the step kernel on the same stream; with an empty
+// queue every block returns at once.
+template <class RP, int MODE>
+__global__ void __launch_bounds__(SWEEP_WARPS * 32)
+    ctu_guard_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
+{
+    using T = typename RP::real;
+    const unsigned n = a.gq->count;
+    if (n == 0) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
+    W.guard = a.guard_edges;
+    const int cur = a.cur ? *a.cur : 0;
+    const CUtensorMap* map = cur ? map_b : map_a;
+    T* __restrict__ qout = cur ? a.qa : a.qb;
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+    const T nux = T(dt / a.dx), nuy = T(dt / a.dy);
+    const bool second = a.order >= 2;
+    const bool map_ok = (reinterpret_cast<uintptr_t>(map) & 63) == 0;
+    if (!map_ok && lane == 0) atomicOr(a.status, ST_BADARG);
+    if (lane == 0 && map_ok) acquire_tensormap(map);
+    __syncwarp();
+    const int nw = blockDim.x >> 5;
+    const int total = a.gq_tasks ? int(n) : a.ntasks;
+    bool failed = false, bad = false;
+    T smx = T(0), smy = T(0);
+    for (int idx = blockIdx.x * nw + warp; idx < total && !failed && map_ok; idx += gridDim.x * nw) {
+        const int task = a.gq_tasks ? a.gq_tasks[idx] : idx;
+        const int i0 = (task % a.nbands) * BAND_W;
+        const int j0 = (task / a.nbands) * a.tile_rows;
+        const int jend = min(j0 + a.tile_rows, a.my);
+        failed = !sweep_task<RP, false, MODE, GUARD_REDO>(a.rp, map, qout, a.mx, a.my, a.ld_x,
+                                                          a.ld_field, a.x_offset, i0, j0, jend, nux,
+                                                          nuy, a.limiter, second, a.transverse, W,
+                                                          bad, smx, smy, a.status);
+    }
+    if (failed) {
+        drain_ring(W);
+        if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, ST_NONPHYS);
+    double v = fmax(double(smx) / a.dx, double(smy) / a.dy);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomic_max_nonneg(a.smax_bits, v);
+    // the last block to finish empties the queue for the next step
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.gq->done, 1u) == gridDim.x - 1) {
+            a.gq->count = 0;
+            a.gq->done = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ------------------------------------------------------------------ ghosts
@@ -831,6 +1008,8 @@ struct DevState {
     double dt, t, cfl_last, cfl_maxseen;
     int cur, nacc, nrej, status;
     unsigned long long newton[2];   // Newton updates and normal solves (exact-solution solver)
+    unsigned long long guard;       // interior edges of FP32 steps recomputed in FP64
+    GuardQueue gq;                  // tasks queued for the FP64 guard's recompute
 };
 
 // ------------------------------------------------------------------ cell speeds

@@ -53,6 +53,9 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.status = L.status;
     a.net = RP::SEEDED ? static_cast<const MlpDev*>(L.seed_net) : nullptr;
     a.newton_updates = RP::SEEDED ? L.newton : nullptr;
+    a.guard_edges = RP::PAIRED ? L.guard : nullptr;
+    a.gq = RP::PAIRED ? static_cast<GuardQueue*>(L.gq) : nullptr;
+    a.gq_tasks = RP::PAIRED ? L.gq_tasks : nullptr;
 
     const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (a.net ? seednet_smem_bytes() : 0);
     // a grid with fewer tasks than SWEEP_WARPS per SM gets smaller CTAs, so
@@ -64,7 +67,8 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     }
     int blocks = (a.ntasks + wpb - 1) / wpb;
     if (L.max_blocks > 0 && blocks > L.max_blocks) blocks = L.max_blocks;
-    switch (scheme_mode(L.prob)) {
+    const int mode = scheme_mode(L.prob);
+    switch (mode) {
     case MODE_FAST:
         ctu_sweep_kernel<RP, MODE_FAST><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
         break;
@@ -73,6 +77,26 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
         break;
     default:
         ctu_sweep_kernel<RP, MODE_GENERAL><<<blocks, wpb * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+    }
+    if constexpr (RP::PAIRED) {
+        // the FP64 guard's recompute of the tasks the step queued
+        if (a.gq && a.rp.guard_on()) {
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            int gblocks = (a.ntasks + SWEEP_WARPS - 1) / SWEEP_WARPS;
+            const int cap = 2 * (L.sms > 0 ? L.sms : 152);
+            if (gblocks > cap) gblocks = cap;
+            switch (mode) {
+            case MODE_FAST:
+                ctu_guard_kernel<RP, MODE_FAST><<<gblocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+                break;
+            case MODE_TRANS2:
+                ctu_guard_kernel<RP, MODE_TRANS2><<<gblocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+                break;
+            default:
+                ctu_guard_kernel<RP, MODE_GENERAL><<<gblocks, SWEEP_WARPS * 32, smem, L.stream>>>(L.map_a, L.map_b, a);
+            }
+        }
     }
     return cudaGetLastError();
 }
@@ -92,6 +116,17 @@ cudaError_t sweep_prepare_t()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ctu_sweep_kernel<RP, MODE_GENERAL>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (RP::PAIRED) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ctu_guard_kernel<RP, MODE_FAST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ctu_guard_kernel<RP, MODE_TRANS2>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(ctu_guard_kernel<RP, MODE_GENERAL>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
     return e;
 }
 
@@ -121,6 +156,8 @@ BatchArgs<RP> batch_args(const BatchLaunch& L)
     a.prefix = L.prefix;
     a.npatch = L.npatch;
     a.nsteps = L.nsteps;
+    a.step0 = L.step0;
+    a.nsteps_all = L.nsteps_all > 0 ? L.nsteps_all : L.nsteps;
     a.tasks_per_step = L.tasks_per_step;
     a.x_offset = L.x_offset;
     a.cfl = L.cfl;
@@ -161,7 +198,8 @@ cudaError_t batch_init_t(const BatchLaunch& L)
     // four blocks per patch (a patch has at most a few hundred rows)
     const dim3 grid(4, (unsigned)(L.npatch < 1 ? 1 : L.npatch < 65535 ? L.npatch : 65535));
     batch_init_kernel<RP><<<grid, 256, 0, L.stream>>>(rp, L.patches, L.npatch, L.x_offset,
-                                                     L.nsteps + 1, L.smax);
+                                                     (L.nsteps_all > 0 ? L.nsteps_all : L.nsteps) + 1,
+                                                     L.smax);
     return cudaGetLastError();
 }
 

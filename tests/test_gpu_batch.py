@@ -1,5 +1,6 @@
 """GPU checks of the batched persistent step (mc_batch_advance): bitwise equal
-to the per-patch launch loop, and per patch equal to the oracle advancing the
+to the per-patch launch loop and to one launch per step over all patches
+(mc_batch_advance_steps), and per patch equal to the oracle advancing the
 same patch with its own dt sequence (dt_k = cfl / smax_{k-1})."""
 import numpy as np
 import pytest
@@ -67,16 +68,18 @@ def test_batched_equals_plain_and_oracle(dtype):
     pats = small_patches(23, seed=5)
     nsteps, cfl = 7, 0.9
     res = {}
-    for form in ("batched", "plain"):
+    for form in ("batched", "plain", "steps"):
         ps = PatchSet(proto(dtype), pats)
         b = mc.Batch(proto(dtype), ps.pointers())
         b.set_tile_rows([8 + 8 * (k % 3) for k in range(len(pats))])   # uneven splits
-        t, inb = (b.advance if form == "batched" else b.advance_plain)(nsteps, cfl, want_t=True)
+        run = {"batched": b.advance, "plain": b.advance_plain, "steps": b.advance_steps}[form]
+        t, inb = run(nsteps, cfl, want_t=True)
         res[form] = (ps.interiors(inb), t)
         b.close()
-    for qa, qb in zip(res["batched"][0], res["plain"][0]):
-        np.testing.assert_array_equal(qa, qb)
-    assert res["batched"][1] == res["plain"][1]
+    for form in ("plain", "steps"):
+        for qa, qb in zip(res["batched"][0], res[form][0]):
+            np.testing.assert_array_equal(qa, qb)
+        assert res["batched"][1] == res[form][1]
     tol = 1e-11 if dtype == mc.F64 else 2e-5 * nsteps
     for k, (mx, my, dx, dy, q) in enumerate(pats):
         qin = q.astype(np.float32).astype(np.float64) if dtype == mc.F32 else q
@@ -144,4 +147,25 @@ def test_bounded_wait_reports_timeout_and_batch_recovers():
     ref = ps.interiors(inb2)
     for a, c in zip(got, ref):
         np.testing.assert_array_equal(a, c)
+    b.close()
+
+
+def test_tuned_split_is_bitwise_equal_to_untuned():
+    """The autotuner changes only the work split: the tuned batch gives the
+    same interiors and times, bit for bit, as the batch as created."""
+    from paper_1308_1464_gb300 import autotune
+    pats = small_patches(31, seed=9)
+    sizes = [(p[0], p[1]) for p in pats]
+    ps = PatchSet(proto(mc.F32), pats)
+    b = mc.Batch(proto(mc.F32), ps.pointers())
+    nsteps = 6
+    t0, inb0 = b.advance(nsteps, 0.9, want_t=True)
+    q0 = ps.interiors(inb0)
+    desc, timings = autotune.tune_batch(b, sizes, ps.reset, nsteps=2, repeats=1)
+    assert len(timings) > len(autotune.POLICIES)
+    ps.reset()
+    t1, inb1 = b.advance(nsteps, 0.9, want_t=True)
+    for qa, qb in zip(q0, ps.interiors(inb1)):
+        np.testing.assert_array_equal(qa, qb)
+    assert t0 == t1 and inb0 == inb1
     b.close()

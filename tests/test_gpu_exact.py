@@ -35,7 +35,7 @@ def gpu_solve(states32, seed_mode=mc.SEED_ADAPTIVE, net=None, tol=1e-8, max_iter
     us = torch.empty_like(ps)
     it = torch.empty(n, dtype=torch.uint8, device="cuda")
     fl = torch.empty_like(it)
-    stats = torch.zeros(6, dtype=torch.int64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.int64, device="cuda")
     mc.riemann_exact(n, gamma, [d.data_ptr() for d in dev], ps.data_ptr(), us.data_ptr(),
                      it.data_ptr(), fl.data_ptr(), seed_mode, net, tol, max_iter, stats.data_ptr())
     torch.cuda.synchronize()
@@ -140,3 +140,41 @@ def test_full_size_sampled():
     ref = oracle.exact_batch(GAMMA, *[a.astype(np.float64) for a in sub])
     compare(sub, ps[idx], us[idx], it[idx], fl[idx], ref)
     assert stats[0] == n and stats[3] == 0
+
+
+@pytest.mark.parametrize("mode", [mc.SEED_ADAPTIVE, mc.SEED_TR, mc.SEED_PVTR])
+def test_mixed_precision_newton_matches_oracle(mode):
+    """FP32 Newton stage then FP64 updates to the same |dp|/p < 1e-8 test:
+    p* and u* as the oracle's; the update counts are reported per stage (the
+    FP64 stage takes about two updates per interface)."""
+    st = f32_states(20011, seed=23)
+    ps, us, it, fl, stats = gpu_solve(st, mode | mc.NEWTON_MIXED)
+    ps_r, us_r, it_r, fl_r = oracle.exact_batch(GAMMA, *[a.astype(np.float64) for a in st],
+                                                seed_mode=ORACLE_SEED[mode])
+    np.testing.assert_array_equal(fl & mc.RS_VACUUM, fl_r & oracle.RS_VACUUM)
+    ok = (fl_r & oracle.RS_VACUUM) == 0
+    np.testing.assert_allclose(ps[ok], ps_r[ok].astype(np.float32), rtol=3e-7, atol=0)
+    assert np.all(np.abs(us[ok] - us_r[ok]) <= 1e-6 * (1.0 + np.abs(us_r[ok])))
+    assert (fl & mc.RS_NOCONV).sum() == 0
+    nonvac = stats[0] - stats[1]
+    assert stats[6] + stats[7] == stats[4] == int(it.sum())
+    f64_per = stats[7] / nonvac
+    print(f"mode {mode}: FP32 updates {stats[6] / nonvac:.3f}, FP64 updates {f64_per:.3f} per solve "
+          f"(all-FP64 oracle {it_r[ok].mean():.3f})")
+    assert 1.0 <= f64_per <= 2.5
+
+
+def test_mixed_precision_learned_seed():
+    """The learned seed with the FP32 stage: an untrained (zero) network
+    proposes p_TR, the stage and the FP64 finish still reach the oracle's p*."""
+    net = mc.SeedNet()
+    params = np.zeros(mc.MLP_NPARAM, dtype=np.float32)
+    params[mc.MLP_NWEIGHT + 10:] = 1.0
+    net.set_params(params.ctypes.data)
+    st = f32_states(8191, seed=29)
+    ps, us, it, fl, stats = gpu_solve(st, mc.SEED_MLP | mc.NEWTON_MIXED, net)
+    ps_r, us_r, it_r, fl_r = oracle.exact_batch(GAMMA, *[a.astype(np.float64) for a in st])
+    ok = (fl_r & oracle.RS_VACUUM) == 0
+    np.testing.assert_allclose(ps[ok], ps_r[ok].astype(np.float32), rtol=3e-7, atol=0)
+    assert stats[6] + stats[7] == stats[4]
+    net.close()

@@ -148,3 +148,33 @@ def test_params_round_trip():
     with pytest.raises(ValueError):
         net.set_params(np.zeros(10, dtype=np.float32))
     net.close()
+
+
+def test_training_is_deterministic():
+    """Two trainings from the same initial parameters, data and seed give
+    bitwise identical parameters and losses: the gradients are summed in a
+    fixed order (per warp, per CTA, then CTA by CTA), with no float atomics,
+    and so are the feature moments of the standardisation."""
+    st, ps = oracle_training_set(1 << 14, seed=13, offset=0)
+    n = st[0].size
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in st]
+    psd = torch.from_numpy(ps.astype(np.float32)).cuda()
+    feat = torch.empty((n, 10), dtype=torch.float32, device="cuda")
+    tgt = torch.empty(n, dtype=torch.float32, device="cuda")
+    mc.mlp_features(n, GAMMA, [d.data_ptr() for d in dev], psd.data_ptr(), feat.data_ptr(),
+                    tgt.data_ptr())
+    rng = np.random.default_rng(3)
+    params = np.zeros(mc.MLP_NPARAM, dtype=np.float32)
+    params[:mc.MLP_NWEIGHT] = random_params(rng)[:mc.MLP_NWEIGHT] * 0.5
+    params[mc.MLP_NWEIGHT + 10:] = 1.0
+    runs = []
+    for _ in range(2):
+        net = mc.SeedNet()
+        net.set_params(params.ctypes.data)
+        losses = np.zeros(4, dtype=np.float32)
+        net.train(n, feat.data_ptr(), tgt.data_ptr(), batch=2048, epochs=4, lr=3e-3, seed=9,
+                  fit_norm=True, loss_out=losses.ctypes.data)
+        runs.append((net.get_params().copy(), losses.copy()))
+        net.close()
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
