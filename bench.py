@@ -105,29 +105,51 @@ def replica_throughput(ms: float, world: int, units_per_step: int, steps: int) -
     return world * units_per_step * steps / (ms * 1e-3)
 
 
-def make_problem(mc, wl):
+def make_problem(mc, wl, mx=None, my=None, window=None):
+    """The workload's problem on an mx x my grid (n x n by default) and its
+    initial state, only the cells of `window` (i0, j0, nx, ny) if given."""
     from paper_1308_1464_gb300 import workloads
-    n = wl["n"]
+    mx = mx or wl["n"]
+    my = my or wl["n"]
     if wl["solver"] == "swe":
-        g = workloads.swe_dambreak(n, n)
+        g = workloads.swe_dambreak(mx, my, window=window)
         sid, param, bc = mc.SWE_ROE, (G, 0, 0, 0), mc.BC_WALL
     elif wl["solver"] in ("euler", "euler_godunov"):
-        g = workloads.euler_quadrants(n, n)
+        g = workloads.euler_quadrants(mx, my, window=window)
         sid = mc.EULER_ROE if wl["solver"] == "euler" else mc.EULER_GODUNOV
         param, bc = (GAMMA, 0, 0, 0), mc.BC_EXTRAP
     elif wl["solver"] == "advection":
-        g = workloads.advection_pulse(n, n)
+        g = workloads.advection_pulse(mx, my, window=window)
         sid, param, bc = mc.ADVECTION, (1.0, 0.6, 0, 0), mc.BC_PERIODIC
     elif wl["solver"] == "acoustics_var":
-        g = workloads.acoustics_layered(n, n)
+        g = workloads.acoustics_layered(mx, my, window=window)
         sid, param, bc = mc.ACOUSTICS_VAR, (0, 0, 0, 0), mc.BC_EXTRAP
     else:
-        g = workloads.acoustics_pulse(n, n)
+        g = workloads.acoustics_pulse(mx, my, window=window)
         sid, param, bc = mc.ACOUSTICS, (1.0, 4.0, 0, 0), mc.BC_PERIODIC
     dtype = mc.F64 if wl["dtype"] == "f64" else mc.F32
-    p = mc.Problem.make(sid, n, n, g.dx, g.dy, dtype=dtype, bc=(bc,) * 4, param=param,
+    p = mc.Problem.make(sid, mx, my, g.dx, g.dy, dtype=dtype, bc=(bc,) * 4, param=param,
                         limiter=wl.get("limiter", mc.LIM_MC), transverse=wl.get("transverse", 1))
     return p, g
+
+
+def sweep_kernels(mc, p) -> int:
+    """Kernels one fused-step call launches: the step kernel, plus the FP64
+    guard kernel of an FP32 Roe solver (shallow water, Euler) with the guard
+    on (param[3] >= 0)."""
+    guarded = (p.dtype == mc.F32 and p.solver in (mc.SWE_ROE, mc.EULER_ROE)
+               and float(p.param[3]) >= 0.0)
+    return 2 if guarded else 1
+
+
+def block_shape(world: int, spec: str = ""):
+    """px x py blocks: from spec "PXxPY", else the most nearly square
+    factorisation of world with px >= py."""
+    if spec:
+        px, py = (int(v) for v in spec.lower().split("x"))
+        return px, py
+    py = max(d for d in range(1, int(world ** 0.5) + 1) if world % d == 0)
+    return world // py, py
 
 
 class ClockSampler:
@@ -925,12 +947,12 @@ def bench_grid(args, wl, rank, world, sub=False):
     if lay.bytes < l2.l2_bytes:
         ms, nrej, clocks, kms, l2_note = time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh,
                                                          world)
-        launches = 2 * args.steps
+        launches = (1 + sweep_kernels(mc, p)) * args.steps
     else:
         ms, nrej, clocks, kms = time_large_grid(args, wl, ctx, a, b, q0, dt0, stream, sh, world)
         l2_note = "inputs larger than L2 (%.0f MB per state, %.0f MB L2)" % (lay.bytes / 1e6,
                                                                            l2.l2_bytes / 1e6)
-        launches = 3 * (args.steps + nrej)
+        launches = (2 + sweep_kernels(mc, p)) * (args.steps + nrej)
     del l2
     ms = max_over_ranks(ms, world, "cuda")
     value = replica_throughput(ms, world, n_cells, args.steps)
@@ -1028,6 +1050,153 @@ def bench_grid(args, wl, rank, world, sub=False):
 
 
 
+def bench_blocks(args, wl, rank, world):
+    """A decomposed grid: px x py blocks of n x n cells each (the workload's
+    n, so the work per block stays fixed as blocks are added: weak scaling),
+    one block per rank under torchrun, or all of them held by this process
+    with --blocks on one rank.  Each attempt of a step exchanges the two
+    ghost layers of every shared side (NCCL point-to-point of device strips,
+    or device copies within the process), runs the fused step with the
+    device dt, max-reduces the speed maximum on the device and applies the
+    dt rule on the device; the host reads the time-step state once per
+    advance call.  The timed region is K accepted steps of one call."""
+    import torch
+    import paper_1308_1464_gb300 as mc
+    from paper_1308_1464_gb300.blocks import (Block, Decomposition, DeviceBlockOps, DeviceStepper,
+                                              DistTransport)
+    from paper_1308_1464_gb300.state import DeviceState
+
+    px, py = block_shape(world, args.blocks)
+    if world > 1 and px * py != world:
+        raise SystemExit(f"--blocks {px}x{py} needs {px * py} ranks, not {world}")
+    n = wl["n"]
+    mx, my = px * n, py * n
+    glob, _ = make_problem(mc, wl, mx, my, window=(0, 0, 1, 1))
+    decomp = Decomposition(glob, px, py)
+    mine = [rank] if world > 1 else list(range(px * py))
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    blocks, qas, qbs, q0s, keep = [], [], [], [], []
+    for r in mine:
+        e = decomp.extent(r)
+        _, g = make_problem(mc, wl, mx, my, window=(e.i0, e.j0, e.mx, e.my))
+        ctx = mc.Context(decomp.local_problem(r))
+        b = Block(decomp, r, DeviceBlockOps(ctx, sh))
+        a, bb = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        npdt = np.float64 if glob.dtype == mc.F64 else np.float32
+        q0 = np.ascontiguousarray(g.q.astype(npdt))
+        a.upload(q0)
+        blocks.append(b)
+        qas.append(a.ptr)
+        qbs.append(bb.ptr)
+        q0s.append(q0)
+        keep.append((ctx, a, bb))
+    transport = DistTransport() if world > 1 else None
+    stepper = DeviceStepper(blocks, transport)
+    dt0 = wl["cfl"] / stepper.max_cell_speed(qas)
+
+    # warm-up, then the timed K steps from the warmed-up state
+    t_sim, dt, inb, _ = stepper.advance(qas, qbs, args.warmup, wl["cfl"], 1.0, 0.0, dt0)
+    cur_a, cur_b = (qbs, qas) if inb else (qas, qbs)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        t2, dt2, inb2, nrej = stepper.advance(cur_a, cur_b, args.steps, wl["cfl"], 1.0, t_sim, dt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    rdev = "cpu" if world > 1 and torch.distributed.get_backend() == "gloo" else "cuda"
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, rdev)
+    ncells = n * n * len(mine)
+    value = world * ncells * args.steps / (ms * 1e-3)
+
+    # kernel launches of one attempt on this process: per direction the
+    # packs, unpacks and the directional fill; the step's kernels; the dt rule
+    per_attempt = 0
+    for b in blocks:
+        for d in (0, 1):
+            sends, recvs = decomp.messages(b.rank, d)
+            per_attempt += len(sends) + len(recvs) + 1
+        per_attempt += sweep_kernels(mc, b.problem) + 1
+
+    # the fused step of the first held block alone (CUDA events on its stream)
+    ctx0 = keep[0][0]
+    q_in, q_out = (cur_b[0], cur_a[0]) if inb2 else (cur_a[0], cur_b[0])
+    ctx0.bc_fill(q_in, sh)
+    for _ in range(3):
+        ctx0.sweep(q_in, q_out, dt2, sh)
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    k0.record(stream)
+    for _ in range(reps):
+        ctx0.sweep(q_in, q_out, dt2, sh)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    lay = ctx0.layout
+    alg_bytes = 2 * n * n * glob.meqn * lay.elem_bytes
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
+                "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
+
+    # end to end: each block's state from pinned host memory, 100 steps,
+    # each block's state back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.from_numpy(q0).pin_memory() for q0 in q0s]
+        backs = [torch.empty_like(h).pin_memory() for h in hosts]
+        nsteps_e2e = 100
+
+        def e2e_once():
+            for (ctx, a, _), h in zip(keep, hosts):
+                ctx.upload(h.data_ptr(), a.ptr, sh)
+            _, _, ib, _ = stepper.advance(qas, qbs, nsteps_e2e, wl["cfl"], 1.0, 0.0, dt0)
+            for (ctx, a, bb), h in zip(keep, backs):
+                ctx.download((bb if ib else a).ptr, h.data_ptr(), sh)
+            torch.cuda.synchronize()
+
+        e2e_once()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        e2e_once()
+        el = max_over_ranks((time.perf_counter() - t0) * 1e3, world, rdev) * 1e-3
+        nbytes = sum(h.numel() * h.element_size() for h in hosts)
+        e2e = {"value": world * ncells * nsteps_e2e / el,
+               "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes / nsteps_e2e,
+               "d2h_bytes_per_step": nbytes / nsteps_e2e, "steps_per_call": nsteps_e2e,
+               "note": "per block: dense host state in (mc_upload), 100 decomposed steps "
+                       "(DeviceStepper), dense host state out (mc_download)"}
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+            "config": {"workload": wl["desc"].replace(f"{n}x{n}", f"{mx}x{my}")
+                       + f", {px}x{py} blocks of {n}x{n}",
+                       "mx": mx, "my": my, "blocks": [px, py],
+                       "parallelism": "blocks" if world > 1 else f"blocks ({px * py} on one GPU)",
+                       "transport": (DistTransport.__name__ + " " + torch.distributed.get_backend()
+                                     if world > 1 else "device copies"),
+                       "l2": "inputs larger than L2 (%.0f MB per block state)" % (lay.bytes / 1e6),
+                       "rejected_steps": nrej},
+            "roofline": roofline, "cpu_baseline": None, "e2e": e2e,
+            "gpu_launches": per_attempt * (args.steps + nrej), "clocks": clk.summary(),
+        }
+    for ctx, _, _ in keep:
+        ctx.close()
+    return line
+
+
 def compact(line, keep=("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype",
                          "riemann_solves_per_s", "roofline", "clocks", "gpu_launches")):
     out = {k: line[k] for k in keep if k in line}
@@ -1049,6 +1218,13 @@ def bench_configs(args):
         t0 = time.perf_counter()
         out[key] = compact(bench_grid(sub, WORKLOADS[name], 0, 1, sub=True))
         out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+    t0 = time.perf_counter()
+    bsub = copy.copy(sub)
+    bsub.blocks, bsub.no_e2e = "2x1", True
+    rec = compact(bench_blocks(bsub, WORKLOADS["swe32"], 0, 1))
+    rec["parallelism"] = "2x1 blocks of 4096x4096 on one GPU, halo strips by device copies"
+    rec["wall_s"] = round(time.perf_counter() - t0, 1)
+    out["swe_blocks_2x1_fp32"] = rec
     t0 = time.perf_counter()
     bl = bench_batch(sub, 0, 1)
     rec = compact(bl)
@@ -1085,8 +1261,15 @@ def main():
     ap.add_argument("--peaks-out", default="", help="with --peaks: also write the JSON to this file")
     ap.add_argument("--kernel-only", type=int, default=0, metavar="K",
                     help="profiling aid: run K stand-alone fused steps (mc_step) and exit")
-    ap.add_argument("--n", type=int, default=0,
-                    help="profiling aid: grid of n x n cells in place of the workload's (with --kernel-only)")
+    ap.add_argument("--size", type=int, default=0,
+                    help="a grid of n x n cells (per block with --blocks) in place of the workload's")
+    ap.add_argument("--blocks", default="",
+                    help="PXxPY: a grid workload decomposed into PX x PY blocks of n x n cells "
+                         "(under torchrun one block per rank, PX * PY = ranks; on one rank all "
+                         "blocks on this GPU); with several ranks the default is the most nearly "
+                         "square shape")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="torch.distributed backend of a multi-rank run")
     args = ap.parse_args()
     if args.peaks:
         return bench_peaks(args)
@@ -1118,16 +1301,25 @@ def main():
     from paper_1308_1464_gb300 import _build
 
     rank, world, local = dist_info()
-    torch.cuda.set_device(local)
+    # gloo ranks (a test of the multi-rank path) may share one GPU; NCCL ranks never do
+    torch.cuda.set_device(local if args.dist_backend == "nccl"
+                          else local % max(1, torch.cuda.device_count()))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(args.dist_backend)
     _build.build()
-    if args.n and args.kernel_only:
-        wl = dict(wl, n=args.n)
-    line = bench_grid(args, wl, rank, world)
-    if line is not None and args.workload == "swe32" and world == 1 and not args.no_configs:
+    if args.size:
+        wl = dict(wl, n=args.size, desc=wl["desc"].replace("%dx%d" % (wl["n"], wl["n"]),
+                                                           "%dx%d" % (args.size, args.size)))
+    if (world > 1 or args.blocks) and not args.kernel_only:
+        line = bench_blocks(args, wl, rank, world)
+    else:
+        line = bench_grid(args, wl, rank, world)
+    if (line is not None and args.workload == "swe32" and world == 1 and not args.no_configs
+            and not args.blocks):
         line["configs"] = bench_configs(args)
+        blk = line["configs"]["swe_blocks_2x1_fp32"]
+        blk["over_single_grid"] = round(blk["value"] / line["value"], 4)
     if rank == 0 and line is not None:
         print(json.dumps(line))
     if world > 1:

@@ -264,6 +264,38 @@ mc_status mc_halo_unpack(mc_ctx* ctx, const void* buf, int32_t side, void* q, vo
  * sides whose kind is not MC_BC_GIVEN.  dir 0 then dir 1 equals mc_bc_fill. */
 mc_status mc_bc_fill_dir(mc_ctx* ctx, void* q, int32_t dir, void* stream);
 
+/* A block stepped with its time-step state on the device (§1.2, Table 1,
+ * "dynamic time stepping", over a decomposed grid): between mc_block_begin
+ * and mc_block_end the context's device state holds dt, t, the buffer index
+ * cur (the state is qa when cur = 0, qb when 1) and the counters, so a rank
+ * enqueues attempt after attempt without reading anything back:
+ *   for direction x then y: mc_block_pack of the shared sides, exchange the
+ *     strips, mc_block_unpack, mc_block_fill_dir;
+ *   mc_block_sweep (q[cur] -> q[cur ^ 1] with the device dt; the speed
+ *     maximum of the step accumulates into *smax_dev, a uint64 holding the
+ *     bits of a non-negative double, so an integer max-reduction over ranks
+ *     is the maximum of the speeds);
+ *   the max-reduction of *smax_dev over the ranks, in place;
+ *   mc_block_dt_rule: the accept/reject rule of mc_advance on the reduced
+ *     maximum (reject above cfl_max and retake with cfl_desired / smax,
+ *     otherwise advance t, flip cur and propose cfl_desired / smax); it
+ *     zeroes *smax_dev for the next attempt.
+ * Every rank takes the same decisions.  mc_block_end synchronises and
+ * returns t, dt, cur and the accepted and rejected attempts; it reports
+ * MC_ENONPHYS / MC_ETIMEOUT / MC_EINVAL from the device status word.  All
+ * calls are asynchronous on `stream` except begin and end. */
+mc_status mc_block_begin(mc_ctx* ctx, double t, double dt, void* stream);
+mc_status mc_block_pack(mc_ctx* ctx, const void* qa, const void* qb, int32_t side, void* buf,
+                        void* stream);
+mc_status mc_block_unpack(mc_ctx* ctx, const void* buf, int32_t side, void* qa, void* qb,
+                          void* stream);
+mc_status mc_block_fill_dir(mc_ctx* ctx, void* qa, void* qb, int32_t dir, void* stream);
+mc_status mc_block_sweep(mc_ctx* ctx, void* qa, void* qb, uint64_t* smax_dev, void* stream);
+mc_status mc_block_dt_rule(mc_ctx* ctx, uint64_t* smax_dev, double cfl_desired, double cfl_max,
+                           void* stream);
+mc_status mc_block_end(mc_ctx* ctx, double* t, double* dt, int32_t* cur, int32_t* naccepted,
+                       int32_t* nrejected, void* stream);
+
 /* One unsplit step with explicit dt: fills q_in's ghosts, then writes the
  * updated interior of q_out (q_out's ghosts are left untouched; q_in and
  * q_out must not overlap).  The fused kernel performs, per tile, the normal

@@ -110,6 +110,13 @@ def lib():
         L.mc_halo_pack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
         L.mc_halo_unpack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
         L.mc_step.argtypes = [_VP, _VP, _VP, ctypes.c_double, _DP, _VP]
+        L.mc_block_begin.argtypes = [_VP, ctypes.c_double, ctypes.c_double, _VP]
+        L.mc_block_pack.argtypes = [_VP, _VP, _VP, ctypes.c_int32, _VP, _VP]
+        L.mc_block_unpack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP]
+        L.mc_block_fill_dir.argtypes = [_VP, _VP, _VP, ctypes.c_int32, _VP]
+        L.mc_block_sweep.argtypes = [_VP, _VP, _VP, _VP, _VP]
+        L.mc_block_dt_rule.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_double, _VP]
+        L.mc_block_end.argtypes = [_VP, _DP, _DP, _IP, _IP, _IP, _VP]
         L.mc_sweep.argtypes = [_VP, _VP, _VP, ctypes.c_double, _VP]
         L.mc_step_noalloc.argtypes = [P, _VP, _VP, ctypes.c_double, _DP, _VP]
         L.mc_peak_run.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP, _DP, _VP]
@@ -194,6 +201,34 @@ class Context:
         """Attach a SeedNet (or None) to the exact-solution Euler solver."""
         self._seed_net = net   # keep it alive while attached
         check(lib().mc_set_seed_net(self._h, net.handle if net is not None else None))
+
+    # ---- device-side block stepping (mc_block_*)
+    def block_begin(self, t: float, dt: float, stream: int = 0) -> None:
+        check(lib().mc_block_begin(self._h, float(t), float(dt), _VP(stream)))
+
+    def block_pack(self, qa: int, qb: int, side: int, buf: int, stream: int = 0) -> None:
+        check(lib().mc_block_pack(self._h, _VP(qa), _VP(qb), int(side), _VP(buf), _VP(stream)))
+
+    def block_unpack(self, buf: int, side: int, qa: int, qb: int, stream: int = 0) -> None:
+        check(lib().mc_block_unpack(self._h, _VP(buf), int(side), _VP(qa), _VP(qb), _VP(stream)))
+
+    def block_fill_dir(self, qa: int, qb: int, direction: int, stream: int = 0) -> None:
+        check(lib().mc_block_fill_dir(self._h, _VP(qa), _VP(qb), int(direction), _VP(stream)))
+
+    def block_sweep(self, qa: int, qb: int, smax_dev: int, stream: int = 0) -> None:
+        check(lib().mc_block_sweep(self._h, _VP(qa), _VP(qb), _VP(smax_dev), _VP(stream)))
+
+    def block_dt_rule(self, smax_dev: int, cfl_desired: float, cfl_max: float, stream: int = 0) -> None:
+        check(lib().mc_block_dt_rule(self._h, _VP(smax_dev), float(cfl_desired), float(cfl_max),
+                                     _VP(stream)))
+
+    def block_end(self, stream: int = 0):
+        """-> (t, dt, cur, naccepted, nrejected); synchronises."""
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        cur, na, nr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().mc_block_end(self._h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(cur),
+                                 ctypes.byref(na), ctypes.byref(nr), _VP(stream)))
+        return t.value, dt.value, cur.value, na.value, nr.value
 
     def guard_stats(self, reset: bool = True, stream: int = 0) -> int:
         """Interior edges the FP64 guard recomputed since the last reset."""

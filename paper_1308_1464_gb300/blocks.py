@@ -295,6 +295,17 @@ class DistTransport:
         dist.all_reduce(t, op=dist.ReduceOp.MAX, group=self.group)
         return float(t.item())
 
+    def max_tensor(self, t) -> None:
+        """In-place max-reduction of a one-element tensor over the ranks
+        (NCCL: on the device, no host read; gloo: through host memory)."""
+        dist = self.dist
+        if self.backend == "gloo" and t.is_cuda:
+            h = t.cpu()
+            dist.all_reduce(h, op=dist.ReduceOp.MAX, group=self.group)
+            t.copy_(h)
+        else:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX, group=self.group)
+
 
 class DeviceBlockOps:
     """A block's packing, unpacking, ghost fills and steps: the library's
@@ -331,3 +342,103 @@ class DeviceBlockOps:
 
     def max_speed(self, q: int) -> float:
         return self.ctx.max_cell_speed(q, self.stream)
+
+
+class DeviceStepper:
+    """Steps of a decomposed grid with the time-step state on the device
+    (mc_block_*): per attempt the two-phase halo exchange of the current
+    buffer, the fused step with the device dt, a max-reduction of the speed
+    maximum over the blocks, and the accept/reject rule on each block's
+    device; the host reads nothing back until the attempts are enqueued.
+    With a transport (one block per rank) the strips and the maximum travel
+    through it: NCCL moves device buffers and reduces the device scalar in
+    place; gloo stages them through host memory.  Without one, every block is
+    held by this process and the exchange and reduction are device copies.
+
+    Blocks must use DeviceBlockOps; states are passed as lists of the two
+    buffers of each block (qa, qb), the current one chosen on the device."""
+
+    def __init__(self, blocks, transport=None):
+        import torch
+        self.blocks = list(blocks)
+        self.transport = transport
+        if transport is not None and len(self.blocks) != 1:
+            raise ValueError("a transport serves one block per rank")
+        # the speed maximum of each block's attempt: int64 bits of a
+        # non-negative double (ordered like the doubles)
+        self.smax = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in self.blocks]
+
+    def _ctx(self, b):
+        return b.ops.ctx
+
+    def _exchange(self, qas, qbs) -> None:
+        for direction in (0, 1):
+            mail = {}
+            outs = []
+            for b, qa, qb in zip(self.blocks, qas, qbs):
+                sends, _ = b.decomp.messages(b.rank, direction)
+                out = []
+                for side, dst in sends:
+                    buf = b._send[side]
+                    self._ctx(b).block_pack(qa, qb, side, buf.data_ptr(), b.ops.stream)
+                    out.append((dst, side ^ 1, buf))
+                    mail[(b.rank, dst, side ^ 1)] = buf
+                outs.append(out)
+            if self.transport is None:
+                for b in self.blocks:
+                    for src, tag, buf in b.incoming(direction):
+                        b.ops.copy(mail.pop((src, b.rank, tag)), buf)
+                if mail:
+                    raise RuntimeError(f"unmatched halo messages: {sorted(mail)}")
+            else:
+                b = self.blocks[0]
+                self.transport.exchange(outs[0], b.incoming(direction))
+            for b, qa, qb in zip(self.blocks, qas, qbs):
+                _, recvs = b.decomp.messages(b.rank, direction)
+                for side, _src in recvs:
+                    self._ctx(b).block_unpack(b._recv[side].data_ptr(), side, qa, qb, b.ops.stream)
+                self._ctx(b).block_fill_dir(qa, qb, direction, b.ops.stream)
+
+    def _reduce_max(self) -> None:
+        if self.transport is None:
+            if len(self.smax) > 1:
+                m = self.smax[0]
+                for s in self.smax[1:]:
+                    m = m.maximum(s)
+                for s in self.smax:
+                    s.copy_(m)
+        else:
+            self.transport.max_tensor(self.smax[0])
+
+    def max_cell_speed(self, qas) -> float:
+        v = max(b.ops.max_speed(q) for b, q in zip(self.blocks, qas))
+        return v if self.transport is None else self.transport.max(v)
+
+    def advance(self, qas, qbs, nsteps: int, cfl_desired: float, cfl_max: float, t: float = 0.0,
+                dt: float | None = None):
+        """nsteps accepted steps from the states in qas; returns (t, dt,
+        result_in_b, nrejected), the same on every rank."""
+        if dt is None:
+            dt = cfl_desired / self.max_cell_speed(qas)
+        for b in self.blocks:
+            self._ctx(b).block_begin(t, dt, b.ops.stream)
+        attempts, total = nsteps, 0
+        res = None
+        while True:
+            for _ in range(attempts):
+                self._exchange(qas, qbs)
+                for b, qa, qb, sm in zip(self.blocks, qas, qbs, self.smax):
+                    self._ctx(b).block_sweep(qa, qb, sm.data_ptr(), b.ops.stream)
+                self._reduce_max()
+                for b, sm in zip(self.blocks, self.smax):
+                    self._ctx(b).block_dt_rule(sm.data_ptr(), cfl_desired, cfl_max, b.ops.stream)
+            total += attempts
+            res = [self._ctx(b).block_end(b.ops.stream) for b in self.blocks]
+            nacc = res[0][3]
+            if nacc >= nsteps:
+                break
+            if total > 100 * nsteps + 100:
+                raise McError(MC_EINVAL, "too many rejected steps")
+            attempts = nsteps - nacc
+        t, dt, cur, nacc, nrej = res[0]
+        return t, dt, bool(cur), nrej

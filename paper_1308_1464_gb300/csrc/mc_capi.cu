@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -173,10 +174,14 @@ cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void*
 // Courant number = dt * smax; reject (retake with dt = cfl_desired / smax)
 // above cfl_max, otherwise accept (advance t, flip the buffer index) and
 // propose dt = cfl_desired / smax.  Resets smax for the next attempt.
-__global__ void dt_update_kernel(DevState* st, double cfl_desired, double cfl_max)
+// The speed maximum is the context's own (smax_ext null) or a caller's
+// device scalar, e.g. the maximum over the blocks of a decomposed grid.
+__global__ void dt_update_kernel(DevState* st, double cfl_desired, double cfl_max,
+                                 unsigned long long* smax_ext)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double smax = __longlong_as_double((long long)st->smax_bits);
+    unsigned long long* sm = smax_ext ? smax_ext : &st->smax_bits;
+    const double smax = __longlong_as_double((long long)*sm);
     const double dt = st->dt, cfl = dt * smax;
     st->cfl_last = cfl;
     if (cfl > cfl_max) {
@@ -189,7 +194,7 @@ __global__ void dt_update_kernel(DevState* st, double cfl_desired, double cfl_ma
         if (cfl > st->cfl_maxseen) st->cfl_maxseen = cfl;
         if (smax > 0.0) st->dt = cfl_desired / smax;
     }
-    st->smax_bits = 0ull;
+    *sm = 0ull;
 }
 
 // Default rows per warp task: enough tasks to fill the GPU several times
@@ -695,7 +700,7 @@ static cudaError_t enqueue_attempts(mc_ctx* c, const CUtensorMap* ma, const CUte
         cudaError_t e = bc_launch(c->p, c->lay, qa, qb, &c->dev->cur, s);
         if (e == cudaSuccess) e = sweep_launch(L);
         if (e != cudaSuccess) return e;
-        dt_update_kernel<<<1, 32, 0, s>>>(c->dev, cfl_desired, cfl_max);
+        dt_update_kernel<<<1, 32, 0, s>>>(c->dev, cfl_desired, cfl_max, nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -799,6 +804,100 @@ mc_status mc_advance(mc_ctx* c, void* qa, void* qb, int nsteps, double cfl_desir
     *result_in_b = h.cur;
     if (nrejected) *nrejected = h.nrej;
     return MC_OK;
+}
+
+// ---- A block of a decomposed grid stepped with its time-step state on the
+// device: dt, t, the buffer index and the counters live in the context's
+// device state between mc_block_begin and mc_block_end, so a rank enqueues
+// attempt after attempt (halo exchange, step, a max-reduction of the speed
+// maximum over the ranks, the dt rule) without reading anything back.
+
+mc_status mc_block_begin(mc_ctx* c, double t, double dt, void* stream)
+{
+    if (!c) return set_error(MC_EINVAL, "NULL context");
+    if (!(dt > 0.0) || !isfinite(dt) || !isfinite(t)) return set_error(MC_EINVAL, "need finite t and dt > 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    h.dt = dt;
+    h.t = t;
+    // the counters of the other entry points stay as they were
+    cudaError_t e = cudaMemcpyAsync(c->dev, &h, offsetof(DevState, newton), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "block state upload");
+}
+
+mc_status mc_block_pack(mc_ctx* c, const void* qa, const void* qb, int32_t side, void* buf, void* stream)
+{
+    if (!c || !qa || !qb || !buf) return set_error(MC_EINVAL, "NULL argument");
+    if (side < 0 || side > 3) return set_error(MC_EINVAL, "side must be 0..3");
+    if (c->p.mx < 2 || c->p.my < 2) return set_error(MC_EINVAL, "halo strips need at least 2 x 2 cells");
+    cudaError_t e = halo_launch_cur(c->p, c->lay, const_cast<void*>(qa), const_cast<void*>(qb),
+                                    &c->dev->cur, buf, side, true, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "halo pack launch");
+}
+
+mc_status mc_block_unpack(mc_ctx* c, const void* buf, int32_t side, void* qa, void* qb, void* stream)
+{
+    if (!c || !qa || !qb || !buf) return set_error(MC_EINVAL, "NULL argument");
+    if (side < 0 || side > 3) return set_error(MC_EINVAL, "side must be 0..3");
+    if (c->p.mx < 2 || c->p.my < 2) return set_error(MC_EINVAL, "halo strips need at least 2 x 2 cells");
+    cudaError_t e = halo_launch_cur(c->p, c->lay, qa, qb, &c->dev->cur, const_cast<void*>(buf), side,
+                                    false, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "halo unpack launch");
+}
+
+mc_status mc_block_fill_dir(mc_ctx* c, void* qa, void* qb, int32_t dir, void* stream)
+{
+    if (!c || !qa || !qb) return set_error(MC_EINVAL, "NULL argument");
+    if (dir != 0 && dir != 1) return set_error(MC_EINVAL, "direction must be 0 (x) or 1 (y)");
+    cudaError_t e = bc_dir_launch(c->p, c->lay, qa, qb, &c->dev->cur, dir, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "directional ghost fill launch");
+}
+
+mc_status mc_block_sweep(mc_ctx* c, void* qa, void* qb, uint64_t* smax_dev, void* stream)
+{
+    if (!c || !qa || !qb || !smax_dev) return set_error(MC_EINVAL, "NULL argument");
+    if (qa == qb) return set_error(MC_EINVAL, "qa and qb must differ");
+    if (reinterpret_cast<uintptr_t>(qa) % 16 || reinterpret_cast<uintptr_t>(qb) % 16)
+        return set_error(MC_EINVAL, "states must be 16-byte aligned");
+    const CUtensorMap *ma, *mb;
+    mc_status st = get_map(c, qa, &ma);
+    if (st == MC_OK) st = get_map(c, qb, &mb);
+    if (st != MC_OK) return st;
+    SweepLaunch L{c->p, c->lay, ma, mb, qa, qb, &c->dev->cur, &c->dev->dt, 0.0,
+                  reinterpret_cast<unsigned long long*>(smax_dev), &c->dev->status, c->tile_rows, 0,
+                  static_cast<cudaStream_t>(stream)};
+    launch_extras(c, L);
+    cudaError_t e = sweep_launch(L);
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "sweep launch");
+}
+
+mc_status mc_block_dt_rule(mc_ctx* c, uint64_t* smax_dev, double cfl_desired, double cfl_max,
+                           void* stream)
+{
+    if (!c || !smax_dev) return set_error(MC_EINVAL, "NULL argument");
+    if (!(cfl_desired > 0.0) || !(cfl_max >= cfl_desired))
+        return set_error(MC_EINVAL, "need 0 < cfl_desired <= cfl_max");
+    dt_update_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+        c->dev, cfl_desired, cfl_max, reinterpret_cast<unsigned long long*>(smax_dev));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "dt rule launch");
+}
+
+mc_status mc_block_end(mc_ctx* c, double* t, double* dt, int32_t* cur, int32_t* naccepted,
+                       int32_t* nrejected, void* stream)
+{
+    if (!c) return set_error(MC_EINVAL, "NULL context");
+    DevState h;
+    mc_status st = read_status(c, &h, static_cast<cudaStream_t>(stream));
+    if (t) *t = h.t;
+    if (dt) *dt = h.dt;
+    if (cur) *cur = h.cur;
+    if (naccepted) *naccepted = h.nacc;
+    if (nrejected) *nrejected = h.nrej;
+    if (st != MC_OK) cudaMemsetAsync(&c->dev->status, 0, sizeof(int), static_cast<cudaStream_t>(stream));
+    return st;
 }
 
 mc_status mc_advance_host(mc_ctx* c, const void* host_q0, void* host_q, void* qa, void* qb,

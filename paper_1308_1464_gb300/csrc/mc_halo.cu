@@ -52,10 +52,13 @@ __device__ inline long long halo_cell(const HaloArgs& a, int side, bool ghost, l
     return (long long)m * a.ld_field + (long long)(j + 2) * a.ld_x + a.x_offset + i;
 }
 
+// The state is qa, or qb when cur is given and *cur == 1 (the buffer index a
+// block's device-side time-step loop keeps).
 template <typename T>
-__global__ void halo_pack_kernel(const T* __restrict__ q, T* __restrict__ buf, const HaloArgs a,
-                                 int side)
+__global__ void halo_pack_kernel(const T* qa, const T* qb, const int* cur, T* __restrict__ buf,
+                                 const HaloArgs a, int side)
 {
+    const T* __restrict__ q = (cur && *cur) ? qb : qa;
     const long long n = halo_count(a, side);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
@@ -63,9 +66,10 @@ __global__ void halo_pack_kernel(const T* __restrict__ q, T* __restrict__ buf, c
 }
 
 template <typename T>
-__global__ void halo_unpack_kernel(const T* __restrict__ buf, T* __restrict__ q, const HaloArgs a,
-                                   int side)
+__global__ void halo_unpack_kernel(const T* __restrict__ buf, T* qa, T* qb, const int* cur,
+                                   const HaloArgs a, int side)
 {
+    T* __restrict__ q = (cur && *cur) ? qb : qa;
     const long long n = halo_count(a, side);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
@@ -162,23 +166,35 @@ long long halo_elems(const mc_problem& p, int side)
     return halo_count(a, side);
 }
 
-cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* src, void* dst,
-                        int side, bool pack, cudaStream_t s)
+cudaError_t halo_launch_cur(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
+                            const int* cur_dev, void* buf, int side, bool pack, cudaStream_t s)
 {
     const HaloArgs a = halo_args(p, lay);
     const int blocks = grid_for(halo_count(a, side));
     if (p.dtype == MC_F64) {
         if (pack) halo_pack_kernel<double><<<blocks, 256, 0, s>>>(
-            static_cast<const double*>(src), static_cast<double*>(dst), a, side);
+            static_cast<const double*>(qa), static_cast<const double*>(qb), cur_dev,
+            static_cast<double*>(buf), a, side);
         else halo_unpack_kernel<double><<<blocks, 256, 0, s>>>(
-            static_cast<const double*>(src), static_cast<double*>(dst), a, side);
+            static_cast<const double*>(buf), static_cast<double*>(qa), static_cast<double*>(qb),
+            cur_dev, a, side);
     } else {
         if (pack) halo_pack_kernel<float><<<blocks, 256, 0, s>>>(
-            static_cast<const float*>(src), static_cast<float*>(dst), a, side);
+            static_cast<const float*>(qa), static_cast<const float*>(qb), cur_dev,
+            static_cast<float*>(buf), a, side);
         else halo_unpack_kernel<float><<<blocks, 256, 0, s>>>(
-            static_cast<const float*>(src), static_cast<float*>(dst), a, side);
+            static_cast<const float*>(buf), static_cast<float*>(qa), static_cast<float*>(qb),
+            cur_dev, a, side);
     }
     return cudaGetLastError();
+}
+
+cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* src, void* dst,
+                        int side, bool pack, cudaStream_t s)
+{
+    void* q = const_cast<void*>(pack ? src : static_cast<const void*>(dst));
+    void* buf = pack ? dst : const_cast<void*>(src);
+    return halo_launch_cur(p, lay, q, q, nullptr, buf, side, pack, s);
 }
 
 cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,

@@ -109,6 +109,9 @@ cudaError_t bc_launch(const mc_problem& p, const mc_layout& lay, void* qa, void*
 long long halo_elems(const mc_problem& p, int side);
 cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* src, void* dst,
                         int side, bool pack, cudaStream_t s);
+// the same on q[cur]: qa, or qb when *cur_dev == 1
+cudaError_t halo_launch_cur(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
+                            const int* cur_dev, void* buf, int side, bool pack, cudaStream_t s);
 cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
                           const int* cur_dev, int dir, cudaStream_t s);
 

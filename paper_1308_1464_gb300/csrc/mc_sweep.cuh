@@ -361,7 +361,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
 
     int newton_n = 0, newton_s = 0;   // Newton updates and solves of this lane (SEEDED solvers)
     int guard_n = 0;                  // interior edges this lane recomputed in FP64
-    bool task_flag = false;           // a near-sonic transonic edge met (GUARD_DETECT)
+    int hh = 0;                       // halves of this lane's edges with a near-sonic transonic
+                                      // speed, accumulated over the march (GUARD_DETECT)
     float g_lo = 3.0e38f, g_hi = 0.0f;   // range of the first field (GUARD_DETECT)
     for (int k = j0 - 3; k < jend; k++) {
         T qc2[NP], ql2[NP];
@@ -430,7 +431,6 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             f2 W2[NW][N], s2[NW], am2[N], ap2[N];
             typename RP::LinP L2;
             bool badx = false, bady = false;
-            int hh = 0;
             rp.template normal_pair<GUARD == GUARD_REDO>(QL, QR, W2, s2, am2, ap2, L2, badx, bady, hh);
             const bool trans1 = trans && !trans2;
             f2 Tm[N], Tp[N], Um[N], Up[N];
@@ -444,32 +444,26 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             // guarded or transonic edge is only marked (its speeds and flags
             // are left out, and the guard kernel recomputes it); the guard
             // kernel recomputes those edges in FP64
-            if constexpr (GUARD != GUARD_NONE) {
+            // (GUARD_DETECT: near-sonic edges accumulate in hh, near-dry
+            // ones show in the task's depth range; both are read at the end)
+            if constexpr (GUARD == GUARD_REDO) {
                 // only edges between cells of the ghosted grid: lanes of the
                 // last band past column mx + 1 hold no state (zeros), and
                 // would look near-dry
                 const bool gvalid = c >= -1 && c <= mx + 1;
-                if constexpr (GUARD == GUARD_DETECT) {
-                    // near-sonic transonic edges here; near-dry edges by the
-                    // task's depth range (below)
-                    if (gvalid && hh != 0) task_flag = true;
-                } else {
-                    const int gm = gvalid ? rp.guard_mask(QL, QR, L2) : 0;
-                    if (gm) {
-                        rp.guard_redo(QL, QR, gm, trans1, W2, s2, am2, ap2, L2, Tm, Tp, Um, Up, badx,
-                                      bady);
-                        // count each interior edge once: the x-edge c-1/2 of
-                        // row k+1 and the y-edge below row k+2 belong to the
-                        // task whose output lanes and rows hold column c and
-                        // that row (the grid's last edges to its last band
-                        // and tile)
-                        const bool own_c = lane >= 1 && lane <= BAND_W;
-                        const bool xown =
-                            ((own_c && c <= mx) || (lane == BAND_W + 1 && c == mx && i0 + BAND_W == mx)) &&
-                            k + 1 >= j0 && k + 1 < jend;
-                        const bool yown = own_c && c < mx && k + 2 >= j0 && (k + 2 < jend || k + 2 == my);
-                        guard_n += int((gm & 1) && xown) + int((gm & 2) && yown);
-                    }
+                const int gm = gvalid ? rp.guard_mask(QL, QR, L2) : 0;
+                if (gm) {
+                    rp.guard_redo(QL, QR, gm, trans1, W2, s2, am2, ap2, L2, Tm, Tp, Um, Up, badx, bady);
+                    // count each interior edge once: the x-edge c-1/2 of row
+                    // k+1 and the y-edge below row k+2 belong to the task
+                    // whose output lanes and rows hold column c and that row
+                    // (the grid's last edges to its last band and tile)
+                    const bool own_c = lane >= 1 && lane <= BAND_W;
+                    const bool xown =
+                        ((own_c && c <= mx) || (lane == BAND_W + 1 && c == mx && i0 + BAND_W == mx)) &&
+                        k + 1 >= j0 && k + 1 < jend;
+                    const bool yown = own_c && c < mx && k + 2 >= j0 && (k + 2 < jend || k + 2 == my);
+                    guard_n += int((gm & 1) && xown) + int((gm & 2) && yown);
                 }
             }
 #pragma unroll
@@ -748,7 +742,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 g_hi = fmaxf(g_hi, __shfl_xor_sync(0xffffffffu, g_hi, o));
             }
             const bool dry = rp.guard_on() && !(g_lo >= rp.gtau * g_hi);
-            *flagged = dry || __any_sync(0xffffffffu, task_flag && rp.guard_on());
+            const bool sonic = hh != 0 && c >= -1 && c <= mx + 1 && rp.guard_on();
+            *flagged = dry || __any_sync(0xffffffffu, sonic);
         }
     }
     if constexpr (GUARD == GUARD_REDO) {

@@ -52,9 +52,30 @@ def uniform(seed: int, stream: int, index) -> np.ndarray:
     return (_mix(z) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def _centres(n: int, lo: float, hi: float):
+def _centres(n: int, lo: float, hi: float, first: int = 0, count: int | None = None):
+    """Centres of cells first .. first + count - 1 of n cells on [lo, hi], and
+    the cell width."""
     d = (hi - lo) / n
-    return lo + (np.arange(n) + 0.5) * d, d
+    count = n - first if count is None else count
+    return lo + (np.arange(first, first + count) + 0.5) * d, d
+
+
+def _window(mx: int, my: int, window):
+    """(i0, j0, nx, ny) of a window of an mx x my grid (the whole grid for
+    None), checked to lie inside it."""
+    if window is None:
+        return 0, 0, mx, my
+    i0, j0, nx, ny = (int(v) for v in window)
+    if not (0 <= i0 and 0 <= j0 and nx > 0 and ny > 0 and i0 + nx <= mx and j0 + ny <= my):
+        raise ValueError(f"window {window} does not lie inside {mx} x {my} cells")
+    return i0, j0, nx, ny
+
+
+def _cell_index(mx: int, i0: int, j0: int, nx: int, ny: int) -> np.ndarray:
+    """Row-major global indices j * mx + i of the window's cells, shape (ny, nx)."""
+    j = np.arange(j0, j0 + ny, dtype=np.uint64)[:, None]
+    i = np.arange(i0, i0 + nx, dtype=np.uint64)[None, :]
+    return j * np.uint64(mx) + i
 
 
 @dataclass
@@ -67,67 +88,76 @@ class Grid:
     y_lo: float
 
 
-def acoustics_pulse(mx: int = 128, my: int = 128) -> Grid:
-    """Gaussian pressure pulse p = exp(-80 r^2) at (0.5, 0.5) on [0,1]^2, u = v = 0."""
-    x, dx = _centres(mx, 0.0, 1.0)
-    y, dy = _centres(my, 0.0, 1.0)
+def acoustics_pulse(mx: int = 128, my: int = 128, window=None) -> Grid:
+    """Gaussian pressure pulse p = exp(-80 r^2) at (0.5, 0.5) on [0,1]^2, u = v = 0.
+
+    ``window`` (i0, j0, nx, ny), here and in the generators below, returns
+    only those cells of the mx x my grid, equal to the same slice of the
+    whole grid (x_lo, y_lo then locate the window's first cell)."""
+    i0, j0, nx, ny = _window(mx, my, window)
+    x, dx = _centres(mx, 0.0, 1.0, i0, nx)
+    y, dy = _centres(my, 0.0, 1.0, j0, ny)
     X, Y = np.meshgrid(x, y)
-    q = np.zeros((3, my, mx))
+    q = np.zeros((3, ny, nx))
     q[0] = np.exp(-80.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2))
-    return Grid(q, dx, dy, 0.0, 0.0)
+    return Grid(q, dx, dy, i0 * dx, j0 * dy)
 
 
-def advection_pulse(mx: int = 4096, my: int = 4096) -> Grid:
+def advection_pulse(mx: int = 4096, my: int = 4096, window=None) -> Grid:
     """Scalar Gaussian q = exp(-80 r^2) at (0.5, 0.5) on [0,1]^2 plus a unit
     background, for constant-velocity advection on a periodic domain."""
-    x, dx = _centres(mx, 0.0, 1.0)
-    y, dy = _centres(my, 0.0, 1.0)
+    i0, j0, nx, ny = _window(mx, my, window)
+    x, dx = _centres(mx, 0.0, 1.0, i0, nx)
+    y, dy = _centres(my, 0.0, 1.0, j0, ny)
     X, Y = np.meshgrid(x, y)
     q = (1.0 + np.exp(-80.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2)))[None]
-    return Grid(q, dx, dy, 0.0, 0.0)
+    return Grid(q, dx, dy, i0 * dx, j0 * dy)
 
 
-def acoustics_layered(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED) -> Grid:
+def acoustics_layered(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED,
+                      window=None) -> Grid:
     """Pressure pulse in a layered medium on [0,1]^2 for variable-coefficient
     acoustics: planes (p, u, v, rho, c).  p = exp(-80 r^2) at (0.5, 0.3),
     u = v = 0; density 1 below y = 0.5 and 3 above, times 1 + U(-0.05, 0.05)
     per cell; sound speed 1 + x, times 1 + U(-0.05, 0.05) per cell."""
-    x, dx = _centres(mx, 0.0, 1.0)
-    y, dy = _centres(my, 0.0, 1.0)
+    i0, j0, nx, ny = _window(mx, my, window)
+    x, dx = _centres(mx, 0.0, 1.0, i0, nx)
+    y, dy = _centres(my, 0.0, 1.0, j0, ny)
     X, Y = np.meshgrid(x, y)
-    idx = np.arange(mx * my, dtype=np.uint64).reshape(my, mx)
-    q = np.zeros((5, my, mx))
+    idx = _cell_index(mx, i0, j0, nx, ny)
+    q = np.zeros((5, ny, nx))
     q[0] = np.exp(-80.0 * ((X - 0.5) ** 2 + (Y - 0.3) ** 2))
     q[3] = np.where(Y < 0.5, 1.0, 3.0) * (1.0 + 0.05 * (2.0 * uniform(seed, 21, idx) - 1.0))
     q[4] = (1.0 + X) * (1.0 + 0.05 * (2.0 * uniform(seed, 22, idx) - 1.0))
-    return Grid(q, dx, dy, 0.0, 0.0)
+    return Grid(q, dx, dy, i0 * dx, j0 * dy)
 
 
 def swe_dambreak(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED,
-                 noise: float = 1e-3) -> Grid:
+                 noise: float = 1e-3, window=None) -> Grid:
     """Radial dam break on [-1,1]^2: h = 2 for r < 0.5 else 1, plus U(-noise, noise)."""
-    x, dx = _centres(mx, -1.0, 1.0)
-    y, dy = _centres(my, -1.0, 1.0)
-    q = np.zeros((3, my, mx))
+    i0, j0, nx, ny = _window(mx, my, window)
+    x, dx = _centres(mx, -1.0, 1.0, i0, nx)
+    y, dy = _centres(my, -1.0, 1.0, j0, ny)
+    q = np.zeros((3, ny, nx))
     r2 = x[None, :] ** 2 + y[:, None] ** 2
     h = np.where(r2 < 0.25, 2.0, 1.0)
     if noise:
-        u = uniform(seed, S_NOISE_H, np.arange(mx * my, dtype=np.uint64)).reshape(my, mx)
-        h = h + noise * (2.0 * u - 1.0)
+        h = h + noise * (2.0 * uniform(seed, S_NOISE_H, _cell_index(mx, i0, j0, nx, ny)) - 1.0)
     q[0] = h
-    return Grid(q, dx, dy, -1.0, -1.0)
+    return Grid(q, dx, dy, -1.0 + i0 * dx, -1.0 + j0 * dy)
 
 
 def euler_quadrants(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED,
-                    noise: float = 1e-3, gamma: float = 1.4) -> Grid:
+                    noise: float = 1e-3, gamma: float = 1.4, window=None) -> Grid:
     """Four-quadrant Riemann data on [0,1]^2.
 
     Each quadrant (split at x = y = 0.5) draws rho, p ~ U[0.1, 2] and
     u, v ~ U[-1, 1]; every cell then gets U(-noise, noise) added to rho and p.
     The conserved energy is E = p/(gamma-1) + rho (u^2 + v^2)/2.
     """
-    x, dx = _centres(mx, 0.0, 1.0)
-    y, dy = _centres(my, 0.0, 1.0)
+    i0, j0, nx, ny = _window(mx, my, window)
+    x, dx = _centres(mx, 0.0, 1.0, i0, nx)
+    y, dy = _centres(my, 0.0, 1.0, j0, ny)
     d = uniform(seed, S_QUADRANT, np.arange(16, dtype=np.uint64)).reshape(4, 4)
     rho_q = 0.1 + 1.9 * d[:, 0]
     p_q = 0.1 + 1.9 * d[:, 1]
@@ -136,15 +166,15 @@ def euler_quadrants(mx: int = 4096, my: int = 4096, seed: int = DEFAULT_SEED,
     quad = (x[None, :] >= 0.5).astype(np.int64) + 2 * (y[:, None] >= 0.5).astype(np.int64)
     rho, p, u, v = rho_q[quad], p_q[quad], u_q[quad], v_q[quad]
     if noise:
-        k = np.arange(mx * my, dtype=np.uint64)
-        rho = rho + noise * (2.0 * uniform(seed, S_NOISE_RHO, k).reshape(my, mx) - 1.0)
-        p = p + noise * (2.0 * uniform(seed, S_NOISE_P, k).reshape(my, mx) - 1.0)
-    q = np.zeros((4, my, mx))
+        k = _cell_index(mx, i0, j0, nx, ny)
+        rho = rho + noise * (2.0 * uniform(seed, S_NOISE_RHO, k) - 1.0)
+        p = p + noise * (2.0 * uniform(seed, S_NOISE_P, k) - 1.0)
+    q = np.zeros((4, ny, nx))
     q[0] = rho
     q[1] = rho * u
     q[2] = rho * v
     q[3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
-    return Grid(q, dx, dy, 0.0, 0.0)
+    return Grid(q, dx, dy, i0 * dx, j0 * dy)
 
 
 @dataclass

@@ -30,7 +30,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_max_time():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1]
@@ -55,3 +55,13 @@ def test_exact_draw_blocks_are_disjoint():
     blocks.sort()
     assert all(a1 <= b0 for (a0, a1), (b0, b1) in zip(blocks, blocks[1:]))
     assert bench.exact_offset(0, n) == 0
+
+
+def test_block_shape():
+    """Ranks of a decomposed-grid run form the most nearly square px x py
+    (px >= py) unless a shape is given."""
+    import bench
+    assert [bench.block_shape(w) for w in (1, 2, 3, 4, 6, 8, 9, 12)] == \
+        [(1, 1), (2, 1), (3, 1), (2, 2), (3, 2), (4, 2), (3, 3), (4, 3)]
+    assert bench.block_shape(4, "4x1") == (4, 1)
+    assert bench.block_shape(1, "2X1") == (2, 1)

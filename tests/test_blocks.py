@@ -228,7 +228,7 @@ def test_gloo_ranks_equal_single_grid(solver, bc, px, py):
     import torch.multiprocessing as mp
     mx, my, nsteps = 12, 10, 3
     world = px * py
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_rank, args=(world, _free_port(), (solver, bc, px, py, mx, my, nsteps), out),
              nprocs=world, join=True)
@@ -272,3 +272,22 @@ def test_patch_subset_matches_whole_set():
     for k, p in zip([3, 17, 39], some):
         assert (p.nx, p.ny) == (whole[k].nx, whole[k].ny)
         np.testing.assert_array_equal(p.grid.q, whole[k].grid.q)
+
+
+@pytest.mark.parametrize("name", ["swe_dambreak", "euler_quadrants", "advection_pulse",
+                                  "acoustics_layered", "acoustics_pulse"])
+def test_grid_window_matches_whole_grid(name):
+    """A block's window of a seeded grid equals that slice of the whole grid
+    (same counter-based draws, same cell centres), and its x_lo, y_lo locate
+    the window's first cell."""
+    from paper_1308_1464_gb300 import workloads
+    f = getattr(workloads, name)
+    whole = f(37, 29)
+    for i0, j0, nx, ny in ((0, 0, 37, 29), (5, 3, 17, 11), (36, 28, 1, 1), (0, 20, 37, 9)):
+        part = f(37, 29, window=(i0, j0, nx, ny))
+        np.testing.assert_array_equal(part.q, whole.q[:, j0:j0 + ny, i0:i0 + nx])
+        assert (part.dx, part.dy) == (whole.dx, whole.dy)
+        assert part.x_lo == pytest.approx(whole.x_lo + i0 * whole.dx)
+        assert part.y_lo == pytest.approx(whole.y_lo + j0 * whole.dy)
+    with pytest.raises(ValueError):
+        f(37, 29, window=(30, 0, 8, 4))

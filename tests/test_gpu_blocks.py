@@ -213,7 +213,7 @@ def _rank(rank, world, port, args, out):
 def test_gloo_ranks_on_one_gpu_equal_single_grid():
     import torch.multiprocessing as mp
     solver, dtype, bc, px, py, mx, my, nsteps = "swe", mc.F32, (P, P, W, W), 2, 1, 64, 40, 3
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that holds a CUDA context
     out = mgr.dict()
     mp.spawn(_rank, args=(2, _free_port(), (solver, dtype, bc, px, py, mx, my, nsteps), out),
              nprocs=2, join=True)
@@ -227,3 +227,136 @@ def test_gloo_ranks_on_one_gpu_equal_single_grid():
         got[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx] = out[r][0]
         assert out[r][1] == t_want
     np.testing.assert_array_equal(got, want)
+
+
+def decomposed_device(p, q, px, py, nsteps, cfl=0.8, dt0=None):
+    """The decomposed run with the time-step state on the device
+    (DeviceStepper over mc_block_*), all blocks in this process."""
+    from paper_1308_1464_gb300.blocks import DeviceStepper
+    d = Decomposition(p, px, py)
+    ctxs = [mc.Context(d.local_problem(r)) for r in range(d.nblocks)]
+    blocks = [Block(d, r, DeviceBlockOps(c)) for r, c in enumerate(ctxs)]
+    qa, qb = [], []
+    for r, c in enumerate(ctxs):
+        e = d.extent(r)
+        a, b = DeviceState(c).zero_(), DeviceState(c).zero_()
+        a.upload(q[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx])
+        qa.append(a)
+        qb.append(b)
+    t, dt, in_b, nrej = DeviceStepper(blocks).advance([s.ptr for s in qa], [s.ptr for s in qb],
+                                                      nsteps, cfl, 1.0, dt=dt0)
+    out = np.zeros(q.shape, dtype=qa[0].np_dtype)
+    for r in range(d.nblocks):
+        e = d.extent(r)
+        out[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx] = (qb[r] if in_b else qa[r]).download()
+    for c in ctxs:
+        c.close()
+    return out, t, dt, nrej
+
+
+@pytest.mark.parametrize("solver,dtype,bc,px,py", [("swe", mc.F32, (W, W, W, W), 2, 2),
+                                                   ("euler", mc.F64, (P, P, X, X), 3, 2)])
+def test_device_stepper_equals_single_grid(solver, dtype, bc, px, py):
+    """The device-side loop (halo exchange of the current buffer, step with
+    the device dt, max-reduction, accept/reject on the device) equals the
+    single-grid mc_advance bit for bit, a rejected first attempt included."""
+    mx, my, nsteps = 75, 61, 5
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, _ = problems(solver, mx, my, dx, dy, dtype, bc)
+    qin = q.astype(np.float64 if dtype == mc.F64 else np.float32)
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin)
+        dt0 = 3.0 * 0.8 / ctx.max_cell_speed(a.ptr)          # rejected, then retaken
+        t_w, dt_w, inb_w, nrej_w = ctx.advance(a.ptr, b.ptr, nsteps, 0.8, 1.0, 0.0, dt0)
+        want = (b if inb_w else a).download()
+    got, t, dt, nrej = decomposed_device(p, qin, px, py, nsteps, dt0=dt0)
+    assert nrej == nrej_w >= 1
+    assert t == t_w and dt == dt_w
+    np.testing.assert_array_equal(got, want)
+
+
+def _rank_device(rank, world, port, args, out):
+    import torch.distributed as dist
+    from paper_1308_1464_gb300.blocks import DeviceStepper
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    solver, dtype, bc, px, py, mx, my, nsteps = args
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, _ = problems(solver, mx, my, dx, dy, dtype, bc)
+    qin = q.astype(np.float64 if dtype == mc.F64 else np.float32)
+    d = Decomposition(p, px, py)
+    e = d.extent(rank)
+    with mc.Context(d.local_problem(rank)) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx])
+        st = DeviceStepper([Block(d, rank, DeviceBlockOps(ctx))], DistTransport())
+        t, dt, in_b, nrej = st.advance([a.ptr], [b.ptr], nsteps, 0.8, 1.0)
+        out[rank] = ((b if in_b else a).download(), t)
+    dist.destroy_process_group()
+
+
+def test_gloo_ranks_device_stepper_equal_single_grid():
+    """Two gloo ranks on this one GPU run the device-side loop; strips and the
+    speed maximum go through host memory (gloo), decisions stay on the
+    device.  No kernel waits on another rank's: every exchange happens
+    between launches."""
+    import torch.multiprocessing as mp
+    solver, dtype, bc, px, py, mx, my, nsteps = "swe", mc.F32, (P, P, W, W), 2, 1, 64, 40, 3
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that holds a CUDA context
+    out = mgr.dict()
+    mp.spawn(_rank_device, args=(2, _free_port(), (solver, dtype, bc, px, py, mx, my, nsteps), out),
+             nprocs=2, join=True)
+    q, dx, dy = initial_state(solver, mx, my, seed=9)
+    p, _ = problems(solver, mx, my, dx, dy, dtype, bc)
+    want, t_want = single_grid(p, q.astype(np.float32), nsteps)
+    d = Decomposition(p, px, py)
+    got = np.zeros_like(want)
+    for r in range(2):
+        e = d.extent(r)
+        got[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx] = out[r][0]
+        assert out[r][1] == t_want
+    np.testing.assert_array_equal(got, want)
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench_line(cmd, timeout=900):
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable] + cmd, cwd=ROOT, capture_output=True, text=True,
+                       timeout=timeout)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert lines, r.stdout[-2000:]
+    return json.loads(lines[-1])
+
+
+def test_bench_blocks_in_one_process():
+    """bench.py's decomposed-grid path with every block on this GPU: 2 x 2
+    blocks of 256^2 cells, K accepted steps, launches counted per attempt."""
+    line = _bench_line(["bench.py", "--blocks", "2x2", "--size", "256", "--steps", "6",
+                        "--warmup", "3", "--no-e2e"])
+    assert line["config"]["blocks"] == [2, 2] and line["config"]["mx"] == 512
+    assert line["value"] > 0 and line["steps"] == 6
+    # per attempt and block: 2 directions x (1 pack + 1 unpack + 1 fill), the
+    # step kernel and the guard kernel of FP32 shallow water, the dt rule
+    assert line["gpu_launches"] == 4 * (2 * 3 + 2 + 1) * (6 + line["config"]["rejected_steps"])
+
+
+def test_bench_blocks_two_gloo_ranks():
+    """The multi-rank path of bench.py (torchrun, one block per rank) with
+    two gloo ranks sharing this GPU: strips and the speed maximum are staged
+    through host memory between launches, so no kernel waits on the other
+    rank.  Rank 0 prints one line for the whole job."""
+    port = _free_port()
+    line = _bench_line(["-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
+                        "--dist-backend", "gloo", "--size", "192", "--steps", "4", "--warmup", "3"])
+    assert line["n_gpus"] == 2 and line["config"]["blocks"] == [2, 1]
+    assert line["config"]["parallelism"] == "blocks"
+    assert line["value"] > 0 and line["e2e"]["value"] > 0
