@@ -736,15 +736,16 @@ def exact_record(args, out, e2e, world, n, ntrain, epochs, train_s, losses, clk)
     # |dp|/p < 1e-8 test in FP64)
     ms = out["learned_mixed"]["ms"]
     cnt = ncu_exact()
-    if cnt is not None and "learned" in cnt:
+    if cnt is not None and "learned_mixed" in cnt:
         # FP64-pipe bound: flops counted by ncu on these sources over the live time
-        c = cnt["learned"]
+        c = cnt["learned_mixed"]
         achieved = c["fp64_flops_per_launch"] / (ms * 1e-3) / 1e12
         pk64, pk64_src = fp64_peak()
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": pk64,
                     "unit": "TFLOP/s", "frac": round(achieved / pk64, 4),
-                    "traffic": c["dram_bytes_per_launch"], "kernel": "exact_kernel<true>",
+                    "traffic": c["dram_bytes_per_launch"], "kernel": "exact_kernel<1, 1>",
                     "fp64_pipe_active_pct": c["fp64_pipe_active_pct"],
+                    "fp32_flops_per_launch": c["fp32_flops_per_launch"],
                     "peak_source": pk64_src,
                     "flops_source": "FP64 thread instructions of one launch counted by ncu on "
                                     "these sources (FMA = 2 flops, add and multiply = 1)"}
@@ -752,7 +753,7 @@ def exact_record(args, out, e2e, world, n, ntrain, epochs, train_s, losses, clk)
         roofline = {"bound": "hbm", "achieved": round(34 * n / (ms * 1e-3) / 1e9, 1),
                     "peak": peak, "unit": "GB/s",
                     "frac": round(34 * n / (ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
-                    "kernel": "exact_kernel<true>", "note": "FP64-ALU bound; bytes not binding"}
+                    "kernel": "exact_kernel<1, 1>", "note": "FP64-ALU bound; bytes not binding"}
     return {
         "metric": "Riemann solves/s", "value": out["learned_mixed"]["solves_per_s"],
         "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
