@@ -226,6 +226,16 @@ mc_status mc_guard_stats(mc_ctx* ctx, int64_t* edges, int32_t reset, void* strea
 mc_status mc_upload(mc_ctx* ctx, const void* host_dense, void* q_dev, void* stream);
 mc_status mc_download(mc_ctx* ctx, const void* q_dev, void* host_dense, void* stream);
 
+/* Device-side repacking of a whole interior between the dense order of
+ * mc_upload (meqn x my x mx, x fastest) and the library layout: to_layout
+ * != 0 reads dense src and writes the interior of the state dst (ghosts and
+ * padding untouched), 0 the reverse.  Both are device pointers to buffers of
+ * the caller that must not overlap (a dense copy needs meqn*my*mx elements;
+ * a spare state buffer holds one).  With it a host transfer moves one
+ * contiguous block instead of one row at a time.  Asynchronous on stream;
+ * MC_EINVAL for NULL or equal pointers. */
+mc_status mc_repack(mc_ctx* ctx, const void* src, void* dst, int32_t to_layout, void* stream);
+
 /* Fills the ghost layers of the device state q from its interior: periodic
  * wrap, zero-order extrapolation, or a reflecting wall (mirror with the
  * wall-normal momentum negated), per side (LeVeque 2002, ch. 7 and §21.8).
@@ -372,7 +382,11 @@ mc_status mc_advance(mc_ctx* ctx, void* qa, void* qb, int nsteps, double cfl_des
 
 /* End-to-end form with host buffers: uploads host_q0 (dense interior) into
  * qa, runs mc_advance, downloads the result into host_q (dense interior),
- * synchronising. */
+ * synchronising.  Each transfer moves one contiguous block: the upload lands
+ * densely in qb and a kernel repacks it into qa's layout; the result is
+ * repacked densely into the buffer that does not hold it and copied out.
+ * Both buffers' previous contents are overwritten; qa and qb must differ
+ * (MC_EINVAL).  host buffers in pinned memory give the full transfer rate. */
 mc_status mc_advance_host(mc_ctx* ctx, const void* host_q0, void* host_q, void* qa, void* qb,
                           int nsteps, double cfl_desired, double cfl_max, double* t_inout,
                           double* dt_inout, int* nrejected, void* stream);

@@ -103,6 +103,7 @@ def lib():
                                       ctypes.c_int32, _VP]
         L.mc_guard_stats.argtypes = [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, _VP]
         L.mc_upload.argtypes = [_VP, _VP, _VP, _VP]
+        L.mc_repack.argtypes = [_VP, _VP, _VP, ctypes.c_int32, _VP]
         L.mc_download.argtypes = [_VP, _VP, _VP, _VP]
         L.mc_bc_fill.argtypes = [_VP, _VP, _VP]
         L.mc_bc_fill_dir.argtypes = [_VP, _VP, ctypes.c_int32, _VP]
@@ -247,6 +248,9 @@ class Context:
 
     def download(self, q_dev: int, host_dense_ptr: int, stream: int = 0) -> None:
         check(lib().mc_download(self._h, _VP(q_dev), _VP(host_dense_ptr), _VP(stream)))
+
+    def repack(self, src_dev: int, dst_dev: int, to_layout: bool, stream: int = 0) -> None:
+        check(lib().mc_repack(self._h, _VP(src_dev), _VP(dst_dev), int(bool(to_layout)), _VP(stream)))
 
     def bc_fill(self, q_dev: int, stream: int = 0) -> None:
         check(lib().mc_bc_fill(self._h, _VP(q_dev), _VP(stream)))

@@ -180,21 +180,7 @@ __global__ void dt_update_kernel(DevState* st, double cfl_desired, double cfl_ma
                                  unsigned long long* smax_ext)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long* sm = smax_ext ? smax_ext : &st->smax_bits;
-    const double smax = __longlong_as_double((long long)*sm);
-    const double dt = st->dt, cfl = dt * smax;
-    st->cfl_last = cfl;
-    if (cfl > cfl_max) {
-        st->nrej++;
-        if (smax > 0.0) st->dt = cfl_desired / smax;
-    } else {
-        st->t += dt;
-        st->cur ^= 1;
-        st->nacc++;
-        if (cfl > st->cfl_maxseen) st->cfl_maxseen = cfl;
-        if (smax > 0.0) st->dt = cfl_desired / smax;
-    }
-    *sm = 0ull;
+    dt_rule_apply(st, cfl_desired, cfl_max, smax_ext ? smax_ext : &st->smax_bits);
 }
 
 // Default rows per warp task: enough tasks to fill the GPU several times
@@ -525,6 +511,15 @@ mc_status mc_download(mc_ctx* c, const void* q_dev, void* host_dense, void* stre
     return copy_dense(c, q_dev, host_dense, false, static_cast<cudaStream_t>(stream));
 }
 
+mc_status mc_repack(mc_ctx* c, const void* src, void* dst, int32_t to_layout, void* stream)
+{
+    if (!c || !src || !dst) return set_error(MC_EINVAL, "NULL argument");
+    if (src == dst) return set_error(MC_EINVAL, "src and dst must differ");
+    cudaError_t e = dense_repack_launch(c->p, c->lay, src, dst, to_layout != 0,
+                                        c->sms > 0 ? c->sms : 152, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MC_OK : cuda_error(e, "repack launch");
+}
+
 mc_status mc_bc_fill(mc_ctx* c, void* q, void* stream)
 {
     if (!c || !q) return set_error(MC_EINVAL, "NULL argument");
@@ -696,13 +691,22 @@ static cudaError_t enqueue_attempts(mc_ctx* c, const CUtensorMap* ma, const CUte
     SweepLaunch L{c->p, c->lay, ma, mb, qa, qb, &c->dev->cur, &c->dev->dt, 0.0,
                   &c->dev->smax_bits, &c->dev->status, c->tile_rows, 0, s};
     launch_extras(c, L);
+    // where the FP64 guard's kernel follows the step, it applies the rule
+    // (one launch fewer per attempt)
+    bool folded = false;
+    L.dt_state = c->dev;
+    L.cfl_desired = cfl_desired;
+    L.cfl_max = cfl_max;
+    L.dt_folded = &folded;
     for (int k = 0; k < attempts; k++) {
         cudaError_t e = bc_launch(c->p, c->lay, qa, qb, &c->dev->cur, s);
         if (e == cudaSuccess) e = sweep_launch(L);
         if (e != cudaSuccess) return e;
-        dt_update_kernel<<<1, 32, 0, s>>>(c->dev, cfl_desired, cfl_max, nullptr);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if (!folded) {
+            dt_update_kernel<<<1, 32, 0, s>>>(c->dev, cfl_desired, cfl_max, nullptr);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -904,17 +908,26 @@ mc_status mc_advance_host(mc_ctx* c, const void* host_q0, void* host_q, void* qa
                           int nsteps, double cfl_desired, double cfl_max, double* t_inout,
                           double* dt_inout, int* nrejected, void* stream)
 {
-    if (!c || !host_q0 || !host_q) return set_error(MC_EINVAL, "NULL argument");
+    if (!c || !host_q0 || !host_q || !qa || !qb) return set_error(MC_EINVAL, "NULL argument");
+    if (qa == qb) return set_error(MC_EINVAL, "qa and qb must differ");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    mc_status st = copy_dense(c, host_q0, qa, true, s);
-    if (st != MC_OK) return st;
+    // The buffer that does not hold the state stages it densely, so each
+    // direction moves one contiguous block over the host link (a row-pitched
+    // copy moves one row at a time) and a kernel repacks it on the device.
+    const size_t dense = (size_t)c->lay.meqn * c->p.mx * c->p.my * c->lay.elem_bytes;
+    const int sms = c->sms > 0 ? c->sms : 152;
+    cudaError_t e = cudaMemcpyAsync(qb, host_q0, dense, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = dense_repack_launch(c->p, c->lay, qb, qa, true, sms, s);
+    if (e != cudaSuccess) return cuda_error(e, "upload");
     int inb = 0;
-    st = mc_advance(c, qa, qb, nsteps, cfl_desired, cfl_max, t_inout, dt_inout, &inb, nrejected,
-                    stream);
+    mc_status st = mc_advance(c, qa, qb, nsteps, cfl_desired, cfl_max, t_inout, dt_inout, &inb,
+                              nrejected, stream);
     if (st != MC_OK) return st;
-    st = copy_dense(c, inb ? qb : qa, host_q, false, s);
-    if (st != MC_OK) return st;
-    cudaError_t e = cudaStreamSynchronize(s);
+    void* res = inb ? qb : qa;
+    void* spare = inb ? qa : qb;
+    e = dense_repack_launch(c->p, c->lay, res, spare, false, sms, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_q, spare, dense, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? MC_OK : cuda_error(e, "download");
 }
 

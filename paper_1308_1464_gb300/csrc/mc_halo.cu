@@ -11,7 +11,10 @@
 // (the x ghost columns included).  This file holds the kernels of those
 // phases: packing a side's two interior layers into a dense strip,
 // unpacking a received strip into the ghost layers, and the directional
-// fill of the sides whose kind is a physical boundary.
+// fill of the sides whose kind is a physical boundary.  It also holds the
+// repacking of a whole interior between the dense [meqn][my][mx] order and
+// the padded layout, which lets a host transfer of a state move one
+// contiguous block.
 #include "mc_internal.h"
 
 namespace mc {
@@ -195,6 +198,63 @@ cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* s
     void* q = const_cast<void*>(pack ? src : static_cast<const void*>(dst));
     void* buf = pack ? dst : const_cast<void*>(src);
     return halo_launch_cur(p, lay, q, q, nullptr, buf, side, pack, s);
+}
+
+namespace {
+
+// One interior row (m, j) per loop step: dense row m * my + j holds
+// row_words words, the layout row starts at word lay_base(m, j).  Word W is
+// 16 bytes when every row start is 16-byte aligned on both sides, else one
+// element.
+template <typename W>
+__global__ void dense_repack_kernel(const W* __restrict__ src, W* __restrict__ dst, int my,
+                                    int rows, long long row_words, long long ld_x_w,
+                                    long long ld_field_w, long long x_offset_w, bool to_layout)
+{
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int m = r / my, j = r - m * my;
+        const long long dense0 = (long long)r * row_words;
+        const long long lay0 = (long long)m * ld_field_w + (long long)(j + 2) * ld_x_w + x_offset_w;
+        const W* s = src + (to_layout ? dense0 : lay0);
+        W* d = dst + (to_layout ? lay0 : dense0);
+        for (long long i = threadIdx.x; i < row_words; i += blockDim.x) d[i] = s[i];
+    }
+}
+
+template <typename W>
+cudaError_t repack_as(const void* src, void* dst, int my, int rows, long long row_words,
+                      long long ld_x_w, long long ld_field_w, long long x_offset_w, bool to_layout,
+                      int sms, cudaStream_t s)
+{
+    const int blocks = rows < 8 * sms ? rows : 8 * sms;
+    dense_repack_kernel<W><<<blocks, 256, 0, s>>>(static_cast<const W*>(src), static_cast<W*>(dst), my,
+                                                 rows, row_words, ld_x_w, ld_field_w, x_offset_w,
+                                                 to_layout);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t dense_repack_launch(const mc_problem& p, const mc_layout& lay, const void* src,
+                                void* dst, bool to_layout, int sms, cudaStream_t s)
+{
+    const long long es = lay.elem_bytes;
+    const int rows = lay.meqn * p.my;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst);
+    // 16-byte words when the row length, both bases and every layout row
+    // start are multiples of 16 bytes
+    const bool v16 = (p.mx * es) % 16 == 0 && a % 16 == 0 && (lay.ld_x * es) % 16 == 0 &&
+                     (lay.ld_field * es) % 16 == 0 && ((lay.x_offset + 2 * lay.ld_x) * es) % 16 == 0;
+    if (v16) {
+        const long long k = 16 / es;
+        return repack_as<uint4>(src, dst, p.my, rows, p.mx / k, lay.ld_x / k, lay.ld_field / k,
+                                lay.x_offset / k, to_layout, sms, s);
+    }
+    if (es == 8)
+        return repack_as<unsigned long long>(src, dst, p.my, rows, p.mx, lay.ld_x, lay.ld_field,
+                                             lay.x_offset, to_layout, sms, s);
+    return repack_as<unsigned int>(src, dst, p.my, rows, p.mx, lay.ld_x, lay.ld_field, lay.x_offset,
+                                   to_layout, sms, s);
 }
 
 cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,

@@ -46,6 +46,13 @@ struct SweepLaunch {
     unsigned long long* guard = nullptr;       // FP64-guard edge counter, or null
     void* gq = nullptr;                        // GuardQueue of the FP64 guard, or null (no guard)
     int* gq_tasks = nullptr;                   // its task list (ntasks entries), or null: all tasks
+    // A loop of attempts may fold its time-step rule into the guard kernel:
+    // dt_state (the context's DevState) and the CFL pair.  The rule is applied
+    // there only when the guard kernel runs; the launch reports in *dt_folded
+    // (if given) whether it was, so that the caller applies it otherwise.
+    DevState* dt_state = nullptr;
+    double cfl_desired = 0.0, cfl_max = 0.0;
+    bool* dt_folded = nullptr;
     int sms = 0;                               // SMs of the device (0: unknown, full CTAs)
 };
 
@@ -112,6 +119,10 @@ cudaError_t halo_launch(const mc_problem& p, const mc_layout& lay, const void* s
 // the same on q[cur]: qa, or qb when *cur_dev == 1
 cudaError_t halo_launch_cur(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
                             const int* cur_dev, void* buf, int side, bool pack, cudaStream_t s);
+// Copies a whole interior between the dense [meqn][my][mx] order (src or
+// dst, device memory) and the padded layout; the two must not overlap.
+cudaError_t dense_repack_launch(const mc_problem& p, const mc_layout& lay, const void* src,
+                                void* dst, bool to_layout, int sms, cudaStream_t s);
 cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, void* qb,
                           const int* cur_dev, int dir, cudaStream_t s);
 

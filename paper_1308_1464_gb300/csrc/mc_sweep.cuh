@@ -56,6 +56,43 @@ struct GuardQueue {
     unsigned count, done;
 };
 
+// ------------------------------------------------------------------ time step
+
+struct DevState {
+    unsigned long long smax_bits;
+    double dt, t, cfl_last, cfl_maxseen;
+    int cur, nacc, nrej, status;
+    unsigned long long newton[2];   // Newton updates and normal solves (exact-solution solver)
+    unsigned long long guard;       // interior edges of FP32 steps recomputed in FP64
+    GuardQueue gq;                  // tasks queued for the FP64 guard's recompute
+};
+
+// The time-step rule of one attempt (paper §1.2, "dynamic time stepping"),
+// applied by one thread once the attempt's speed maximum *sm is complete:
+// Courant number = dt * smax; above cfl_max the attempt is rejected and
+// retaken with dt = cfl_desired / smax, otherwise it is accepted (t advances,
+// the buffer index flips) and proposes dt = cfl_desired / smax.  Resets *sm
+// for the next attempt.
+__device__ __forceinline__ void dt_rule_apply(DevState* st, double cfl_desired, double cfl_max,
+                                              unsigned long long* sm)
+{
+    // a volatile read: other blocks' atomics may have completed it in this kernel
+    const double smax = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long*>(sm));
+    const double dt = st->dt, cfl = dt * smax;
+    st->cfl_last = cfl;
+    if (cfl > cfl_max) {
+        st->nrej++;
+        if (smax > 0.0) st->dt = cfl_desired / smax;
+    } else {
+        st->t += dt;
+        st->cur ^= 1;
+        st->nacc++;
+        if (cfl > st->cfl_maxseen) st->cfl_maxseen = cfl;
+        if (smax > 0.0) st->dt = cfl_desired / smax;
+    }
+    *sm = 0ull;
+}
+
 template <class RP>
 struct SweepArgs {
     using T = typename RP::real;
@@ -77,6 +114,11 @@ struct SweepArgs {
     unsigned long long* guard_edges;      // edges recomputed in FP64 (FP32 pair solvers), or null
     GuardQueue* gq;                       // tasks the FP64 guard recomputes, or null (no guard)
     int* gq_tasks;                        // their indices (capacity ntasks), or null: all tasks
+    // the attempt's time-step rule, applied by the guard kernel once the
+    // speed maximum is complete (a loop of attempts that folds it there), or
+    // null: the caller applies it
+    DevState* dt_state;
+    double cfl_desired, cfl_max;
 };
 
 // Solvers that take each state's 1/sqrt(h) from the caller (RS_CACHE):
@@ -886,7 +928,12 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
 {
     using T = typename RP::real;
     const unsigned n = a.gq->count;
-    if (n == 0) return;
+    if (n == 0) {
+        // nothing queued: the step kernel's speed maximum is complete
+        if (a.dt_state && blockIdx.x == 0 && threadIdx.x == 0)
+            dt_rule_apply(a.dt_state, a.cfl_desired, a.cfl_max, a.smax_bits);
+        return;
+    }
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpRing W = warp_ring(smem, sizeof(T), RP::NPLANE);
@@ -924,13 +971,16 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) atomic_max_nonneg(a.smax_bits, v);
-    // the last block to finish empties the queue for the next step
+    // the last block to finish empties the queue for the next step and, when
+    // asked, applies the time-step rule to the now complete speed maximum
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(&a.gq->done, 1u) == gridDim.x - 1) {
+            __threadfence();
             a.gq->count = 0;
             a.gq->done = 0;
+            if (a.dt_state) dt_rule_apply(a.dt_state, a.cfl_desired, a.cfl_max, a.smax_bits);
             __threadfence();
         }
     }
@@ -995,17 +1045,6 @@ __global__ void bc_fill_kernel(const BcArgs<T> a)
         }
     }
 }
-
-// ------------------------------------------------------------------ time step
-
-struct DevState {
-    unsigned long long smax_bits;
-    double dt, t, cfl_last, cfl_maxseen;
-    int cur, nacc, nrej, status;
-    unsigned long long newton[2];   // Newton updates and normal solves (exact-solution solver)
-    unsigned long long guard;       // interior edges of FP32 steps recomputed in FP64
-    GuardQueue gq;                  // tasks queued for the FP64 guard's recompute
-};
 
 // ------------------------------------------------------------------ cell speeds
 

@@ -56,6 +56,14 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.guard_edges = RP::PAIRED ? L.guard : nullptr;
     a.gq = RP::PAIRED ? static_cast<GuardQueue*>(L.gq) : nullptr;
     a.gq_tasks = RP::PAIRED ? L.gq_tasks : nullptr;
+    // the guard kernel applies the time-step rule only where it runs
+    a.dt_state = nullptr;
+    if constexpr (RP::PAIRED) {
+        if (a.gq && a.rp.guard_on()) a.dt_state = L.dt_state;
+    }
+    a.cfl_desired = L.cfl_desired;
+    a.cfl_max = L.cfl_max;
+    if (L.dt_folded) *L.dt_folded = a.dt_state != nullptr;
 
     const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (a.net ? seednet_smem_bytes() : 0);
     // a grid with fewer tasks than SWEEP_WARPS per SM gets smaller CTAs, so

@@ -68,20 +68,28 @@ def test_rejection_and_retake(dtype):
     assert scaled_error("swe", got, want[:, 2:-2, 2:-2]) <= (1e-11 if dtype == mc.F64 else 1e-4)
 
 
-def test_advance_host_matches_device_path():
-    g = workloads.swe_dambreak(96, 80)
+@pytest.mark.parametrize("mx,my,dtype", [(96, 80, mc.F32), (37, 23, mc.F32), (64, 50, mc.F64),
+                                         (37, 23, mc.F64), (5, 3, mc.F32)])
+def test_advance_host_matches_device_path(mx, my, dtype):
+    """The host-buffer form (one contiguous transfer each way, repacked on the
+    device: 16-byte words where rows allow, elements otherwise) gives the
+    device path's bits; its buffers start with garbage, so every interior
+    cell must come from the upload."""
+    g = workloads.swe_dambreak(mx, my)
     W = mc.BC_WALL
-    p, _ = problems("swe", 96, 80, g.dx, g.dy, mc.F32, (W, W, W, W))
-    q32 = g.q.astype(np.float32)
+    p, _ = problems("swe", mx, my, g.dx, g.dy, dtype, (W, W, W, W))
+    qin = g.q.astype(np.float64 if dtype == mc.F64 else np.float32)
     dt0 = 0.9 * g.dx / (2.0 + np.sqrt(9.81 * 2.0))
     with mc.Context(p) as ctx:
         a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
-        a.upload(q32)
+        a.upload(qin)
         t1, dt1, inb, _ = ctx.advance(a.ptr, b.ptr, 7, 0.9, 1.0, 0.0, dt0)
         dev = (b if inb else a).download()
-        a2, b2 = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
-        host = np.zeros_like(q32)
-        t2, dt2, _ = ctx.advance_host(q32.ctypes.data, host.ctypes.data, a2.ptr, b2.ptr, 7, 0.9,
+        a2, b2 = DeviceState(ctx), DeviceState(ctx)
+        a2.buf.fill_(0x7F)
+        b2.buf.fill_(0x3C)
+        host = np.zeros_like(qin)
+        t2, dt2, _ = ctx.advance_host(qin.ctypes.data, host.ctypes.data, a2.ptr, b2.ptr, 7, 0.9,
                                       1.0, 0.0, dt0)
     assert t1 == t2 and dt1 == dt2
     np.testing.assert_array_equal(dev, host)
@@ -156,3 +164,36 @@ def test_degenerate_waves(dtype):
             np.testing.assert_array_equal(got[0], want[0])
             assert np.abs(got[1:] - want[1:]).max() <= 1e-12 * 1e-60
             assert np.abs(got[1]).max() > 1e-61
+
+
+@pytest.mark.parametrize("mx,my,dtype", [(64, 20, mc.F32), (37, 23, mc.F32), (37, 23, mc.F64),
+                                         (1, 1, mc.F64)])
+def test_repack_moves_exactly_the_interior(mx, my, dtype):
+    """mc_repack: dense -> layout writes the interior cells and nothing else
+    (ghosts and padding keep their bytes), and layout -> dense reads back the
+    same array that mc_download gives."""
+    W = mc.BC_WALL
+    p, _ = problems("swe", mx, my, 1.0 / mx, 1.0 / my, dtype, (W, W, W, W))
+    npdt = np.float64 if dtype == mc.F64 else np.float32
+    rng = np.random.default_rng(mx * 100 + my)
+    q = (1.0 + rng.uniform(size=(3, my, mx))).astype(npdt)
+    with mc.Context(p) as ctx:
+        s = DeviceState(ctx)
+        s.buf.fill_(0x5A)
+        before = s.buf.cpu().numpy().copy()
+        dense = torch.from_numpy(q.ravel().copy()).cuda()
+        ctx.repack(dense.data_ptr(), s.ptr, True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(s.download(), q)
+        after = s.buf.cpu().numpy()
+        # every byte outside the interior is untouched
+        ref = DeviceState(ctx)
+        ref.buf.copy_(torch.from_numpy(before).cuda())
+        ref.upload(q)
+        np.testing.assert_array_equal(after, ref.buf.cpu().numpy())
+        back = torch.zeros_like(dense)
+        ctx.repack(s.ptr, back.data_ptr(), False)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(back.cpu().numpy().reshape(q.shape), q)
+        with pytest.raises(mc.McError):
+            ctx.repack(s.ptr, s.ptr, False)
