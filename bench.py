@@ -915,7 +915,7 @@ def time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh, world):
     return total, 0, clk.summary(), kms / reps, note
 
 
-def bench_grid(args, wl, rank, world, sub=False):
+def bench_grid(args, wl, rank, world, sub=False, key=None):
     """One grid workload: K time steps in one timed region (graph-captured
     mc_advance) or runs of a few steps after an L2 flush for a state smaller
     than the L2, plus the fused step alone; with sub, the record of a further
@@ -924,6 +924,7 @@ def bench_grid(args, wl, rank, world, sub=False):
     import paper_1308_1464_gb300 as mc
     from paper_1308_1464_gb300.state import DeviceState
 
+    key = key or args.workload      # the workload's name in WORKLOADS (its ncu records)
     p, g = make_problem(mc, wl)
     n_cells = p.mx * p.my
     ctx = mc.Context(p)
@@ -964,10 +965,10 @@ def bench_grid(args, wl, rank, world, sub=False):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(args.workload),
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(key),
                 "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
                 "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
-    f64 = ncu_fp64(args.workload) if p.dtype == mc.F64 else None
+    f64 = ncu_fp64(key) if p.dtype == mc.F64 else None
     if f64 is not None:
         # an FP64 step is bound by the FP64 pipe: counted FP64 flops over the
         # live kernel time, against the nominal FP64 rate
@@ -1143,8 +1144,11 @@ def bench_blocks(args, wl, rank, world):
     alg_bytes = 2 * n * n * glob.meqn * lay.elem_bytes
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kms * 1e-3) / 1e9
+    # a block runs the single grid's kernel at the same size: its counters apply
+    same_size = args.workload in WORKLOADS and WORKLOADS[args.workload]["n"] == n
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(args.workload) if same_size else None,
                 "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
                 "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
 
@@ -1227,7 +1231,7 @@ def bench_configs(args):
     for key, name in (("acoustics_128_fp64", "acoustics"), ("swe_4096_fp64", "swe64"),
                       ("euler_4096_fp32", "euler32")):
         t0 = time.perf_counter()
-        out[key] = compact(bench_grid(sub, WORKLOADS[name], 0, 1, sub=True))
+        out[key] = compact(bench_grid(sub, WORKLOADS[name], 0, 1, sub=True, key=name))
         out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
     t0 = time.perf_counter()
     bsub = copy.copy(sub)
