@@ -898,37 +898,44 @@ struct EulerRP {
 
         f2 k0 = p_min0(sm), k2 = p_min0(sp);
         if (efix) {
-            // the tests of normal() for both halves, free of branches: for a
-            // state q, e = gamma (gamma-1) rho^2 e_int, m its normal momentum;
-            // u < c <=> m <= 0 or m^2 < e, u > c <=> m > 0 and m^2 > e, and the
-            // mirror tests for u + c (each also needs rho > 0 and e > 0)
+            // the tests of normal() for both halves: for a state q, e = gamma
+            // (gamma-1) rho^2 e_int, m its normal momentum; u < c <=> m <= 0 or
+            // m^2 < e, u > c <=> m > 0 and m^2 > e, and the mirror tests for
+            // u + c (each also needs rho > 0 and e > 0)
             f2 qm0[NEQ], qm2[NEQ];
 #pragma unroll
             for (int m = 0; m < NEQ; m++) {
                 qm0[m] = p_add(ql[m], W[0][m]);
                 qm2[m] = p_sub(qr[m], W[2][m]);
             }
-            const f2 e_l = g_rho2e_pair(ql), e_m0 = g_rho2e_pair(qm0);
-            const f2 e_m2 = g_rho2e_pair(qm2), e_r = g_rho2e_pair(qr);
-            const f2 ml2 = p_mul(ql[1], ql[1]), mm02 = p_mul(qm0[1], qm0[1]);
-            const f2 mm22 = p_mul(qm2[1], qm2[1]), mr2 = p_mul(qr[1], qr[1]);
-            bool t0[2], t2[2];
+            // a wave can be transonic only if its middle state moves faster
+            // than sound (rightward for the 1-wave, leftward for the 3-wave):
+            // those tests come first, the outer states' only where one holds
+            const f2 e_m0 = g_rho2e_pair(qm0), e_m2 = g_rho2e_pair(qm2);
+            const f2 mm02 = p_mul(qm0[1], qm0[1]), mm22 = p_mul(qm2[1], qm2[1]);
+            bool m_fast[2], m_neg[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                const bool ok_l = (half(ql[0], h) > 0.f) & (half(e_l, h) > 0.f);
                 const bool ok_m0 = (half(qm0[0], h) > 0.f) & (half(e_m0, h) > 0.f);
                 const bool ok_m2 = (half(qm2[0], h) > 0.f) & (half(e_m2, h) > 0.f);
-                const bool ok_r = (half(qr[0], h) > 0.f) & (half(e_r, h) > 0.f);
-                // wave 1: u - c < 0 on the left, u - c > 0 in the middle state
-                const bool l_slow = ok_l & ((half(ql[1], h) <= 0.f) | (half(ml2, h) < half(e_l, h)));
-                const bool m_fast = ok_m0 & (half(qm0[1], h) > 0.f) & (half(mm02, h) > half(e_m0, h));
-                // wave 3: u + c < 0 in the middle state, u + c > 0 on the right
-                const bool m_neg = ok_m2 & (half(qm2[1], h) < 0.f) & (half(mm22, h) > half(e_m2, h));
-                const bool r_pos = ok_r & ((half(qr[1], h) >= 0.f) | (half(mr2, h) < half(e_r, h)));
-                t0[h] = l_slow & m_fast;
-                t2[h] = m_neg & r_pos;
+                // wave 1: u - c > 0 in the middle state; wave 3: u + c < 0 there
+                m_fast[h] = ok_m0 & (half(qm0[1], h) > 0.f) & (half(mm02, h) > half(e_m0, h));
+                m_neg[h] = ok_m2 & (half(qm2[1], h) < 0.f) & (half(mm22, h) > half(e_m2, h));
             }
-            if (t0[0] | t0[1] | t2[0] | t2[1]) {
+            if (m_fast[0] | m_fast[1] | m_neg[0] | m_neg[1]) {
+                const f2 e_l = g_rho2e_pair(ql), e_r = g_rho2e_pair(qr);
+                const f2 ml2 = p_mul(ql[1], ql[1]), mr2 = p_mul(qr[1], qr[1]);
+                bool t0[2], t2[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const bool ok_l = (half(ql[0], h) > 0.f) & (half(e_l, h) > 0.f);
+                    const bool ok_r = (half(qr[0], h) > 0.f) & (half(e_r, h) > 0.f);
+                    // wave 1: u - c < 0 on the left; wave 3: u + c > 0 on the right
+                    const bool l_slow = ok_l & ((half(ql[1], h) <= 0.f) | (half(ml2, h) < half(e_l, h)));
+                    const bool r_pos = ok_r & ((half(qr[1], h) >= 0.f) | (half(mr2, h) < half(e_r, h)));
+                    t0[h] = l_slow & m_fast[h];
+                    t2[h] = m_neg[h] & r_pos;
+                }
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     float qa[NEQ], qb[NEQ];
