@@ -405,14 +405,17 @@ struct SweRP {
             // square root or division (u < c  <=>  hu <= 0 or (hu)^2 < g h^3);
             // only a transonic wave pays for the speeds themselves.  A
             // non-positive intermediate depth leaves the wave unfixed.
+            // The test of the intermediate state (faster than sound) comes
+            // first: it rarely holds, and the outer state's test is then
+            // skipped.
             const T hul = ql[un], hum = ql[un] + W[0][un], hm = hl + W[0][0];
-            const bool l_neg = hul <= T(0) || hul * hul < g * hl * hl * hl;
-            const bool r_pos = hm > T(0) && hum > T(0) && hum * hum > g * hm * hm * hm;
-            if (l_neg && r_pos) hh_fix(hl, hul, hm, hum, T(-1), s[0], c, k0);
+            if (hm > T(0) && hum > T(0) && hum * hum > g * hm * hm * hm) {
+                if (hul <= T(0) || hul * hul < g * hl * hl * hl) hh_fix(hl, hul, hm, hum, T(-1), s[0], c, k0);
+            }
             const T hur = qr[un], hun = qr[un] - W[2][un], hn = hr - W[2][0];
-            const bool n_neg = hn > T(0) && hun < T(0) && hun * hun > g * hn * hn * hn;
-            const bool rr_pos = hur >= T(0) || hur * hur < g * hr * hr * hr;
-            if (n_neg && rr_pos) hh_fix(hn, hun, hr, hur, T(1), s[2], c, k2);
+            if (hn > T(0) && hun < T(0) && hun * hun > g * hn * hn * hn) {
+                if (hur >= T(0) || hur * hur < g * hr * hr * hr) hh_fix(hn, hun, hr, hur, T(1), s[2], c, k2);
+            }
         }
         // A-dQ = sum_p k_p W^p, A+dQ = sum_p (s^p - k_p) W^p (k_p = min(s^p, 0)
         // unless the entropy fix replaced it), over the non-zero components
@@ -799,7 +802,8 @@ struct EulerRP {
             T qm[NEQ];
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = ql[m] + W[0][m];
-            if (slower_than_sound<DIR>(ql, false) && faster_than_sound<DIR>(qm, true))
+            // the intermediate state's test first: it rarely holds
+            if (faster_than_sound<DIR>(qm, true) && slower_than_sound<DIR>(ql, false))
                 hh_fix<DIR>(ql, qm, T(-1), s[0], c, k0);
 #pragma unroll
             for (int m = 0; m < NEQ; m++) qm[m] = qr[m] - W[2][m];
