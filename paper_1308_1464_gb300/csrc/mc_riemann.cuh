@@ -420,8 +420,21 @@ struct SweRP {
         // A-dQ = sum_p k_p W^p, A+dQ = sum_p (s^p - k_p) W^p (k_p = min(s^p, 0)
         // unless the entropy fix replaced it), over the non-zero components
         const T k1 = tmin0(s[1]);
-        const T m1 = k0 * a1, m2 = k1 * a2, m3 = k2 * a3;
-        const T p1 = (s[0] - k0) * a1, p2 = (s[1] - k1) * a2, p3 = (s[2] - k2) * a3;
+        const T m2 = k1 * a2, p2 = (s[1] - k1) * a2;
+        if (k0 == s[0] && k2 == T(0) && s[2] > T(0)) {
+            // subsonic, no fix: wave 1 is all left-going, wave 3 all
+            // right-going; the sums below without their zero terms
+            const T m1 = k0 * a1, p3 = s[2] * a3;
+            amdq[0] = m1;
+            amdq[un] = m1 * (u - c);
+            amdq[ut] = m1 * v + m2;
+            apdq[0] = p3;
+            apdq[un] = p3 * (u + c);
+            apdq[ut] = p3 * v + p2;
+            return;
+        }
+        const T m1 = k0 * a1, m3 = k2 * a3;
+        const T p1 = (s[0] - k0) * a1, p3 = (s[2] - k2) * a3;
         amdq[0] = m1 + m3;
         amdq[un] = m1 * (u - c) + m3 * (u + c);
         amdq[ut] = (m1 + m3) * v + m2;
@@ -609,6 +622,20 @@ struct SweRP {
         const T b2 = a[vt] - v * a[0];
         const T b3 = (a[vn] - (u - c) * a[0]) * L.r2c;
         const T l1 = u - c, l2 = u, l3 = u + c;
+        if (l1 < T(0) && l3 > T(0)) {
+            // subsonic across the split direction (the common case): B-
+            // takes wave 1, B+ wave 3, the shear wave goes with the sign of
+            // u; the same sums as below without their zero terms
+            const T m1 = l1 * b1, p3 = l3 * b3;
+            const T m2 = tmin0(l2) * b2, p2 = tmax0(l2) * b2;
+            bm[0] = m1;
+            bm[vn] = m1 * l1;
+            bm[vt] = m1 * v + m2;
+            bp[0] = p3;
+            bp[vn] = p3 * l3;
+            bp[vt] = p3 * v + p2;
+            return;
+        }
         const T m1 = tmin0(l1) * b1, m2 = tmin0(l2) * b2, m3 = tmin0(l3) * b3;
         const T p1 = tmax0(l1) * b1, p2 = tmax0(l2) * b2, p3 = tmax0(l3) * b3;
         bm[0] = m1 + m3;
