@@ -554,8 +554,22 @@ struct SweRP {
         const f2 b1 = p_mul(p_fma(p_neg(l3), a[0], a[2]), p_neg(L.r2c));
         const f2 b2 = p_fma(p_neg(v), a[0], a[1]);
         const f2 b3 = p_mul(p_fma(p_neg(l1), a[0], a[2]), L.r2c);
-        const f2 m1 = p_mul(p_min0(l1), b1), m2 = p_mul(p_min0(u), b2), m3 = p_mul(p_min0(l3), b3);
-        const f2 q1 = p_mul(p_max0(l1), b1), q2 = p_mul(p_max0(u), b2), q3 = p_mul(p_max0(l3), b3);
+        const f2 m2 = p_mul(p_min0(u), b2), q2 = p_mul(p_max0(u), b2);
+        if ((l1.x < 0.f) & (l1.y < 0.f) & (l3.x > 0.f) & (l3.y > 0.f)) {
+            // both halves subsonic across the split direction (the common
+            // case): wave 1 all to B-, wave 3 all to B+; the sums below
+            // without their zero terms
+            const f2 m1 = p_mul(l1, b1), q3 = p_mul(l3, b3);
+            bm[0] = m1;
+            bm[2] = p_mul(m1, l1);
+            bm[1] = p_fma(m1, v, m2);
+            bp[0] = q3;
+            bp[2] = p_mul(q3, l3);
+            bp[1] = p_fma(q3, v, q2);
+            return;
+        }
+        const f2 m1 = p_mul(p_min0(l1), b1), m3 = p_mul(p_min0(l3), b3);
+        const f2 q1 = p_mul(p_max0(l1), b1), q3 = p_mul(p_max0(l3), b3);
         bm[0] = p_add(m1, m3);
         bm[2] = p_fma(m1, l1, p_mul(m3, l3));
         bm[1] = p_fma(bm[0], v, m2);
