@@ -544,6 +544,9 @@ struct SweRP {
         apdq[2] = p_fma(apdq[0], v, q2);
     }
 
+    // SUB: the subsonic form below (a caller near its register cap may
+    // leave it out)
+    template <bool SUB = true>
     __device__ __forceinline__ void transverse_pair(const LinP& L, const f2* a, f2* bm, f2* bp) const
     {
         // transverse<0> in the edge-normal frame: split direction normal
@@ -555,7 +558,7 @@ struct SweRP {
         const f2 b2 = p_fma(p_neg(v), a[0], a[1]);
         const f2 b3 = p_mul(p_fma(p_neg(l1), a[0], a[2]), L.r2c);
         const f2 m2 = p_mul(p_min0(u), b2), q2 = p_mul(p_max0(u), b2);
-        if ((l1.x < 0.f) & (l1.y < 0.f) & (l3.x > 0.f) & (l3.y > 0.f)) {
+        if (SUB && (l1.x < 0.f) & (l1.y < 0.f) & (l3.x > 0.f) & (l3.y > 0.f)) {
             // both halves subsonic across the split direction (the common
             // case): wave 1 all to B-, wave 3 all to B+; the sums below
             // without their zero terms
@@ -1014,6 +1017,7 @@ struct EulerRP {
         }
     }
 
+    template <bool SUB = true>   // the shallow-water form's flag; no subsonic form here
     __device__ __forceinline__ void transverse_pair(const LinP& L, const f2* a, f2* bm, f2* bp) const
     {
         // transverse<0> in the edge-normal frame: split direction normal

@@ -477,8 +477,11 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             const bool trans1 = trans && !trans2;
             f2 Tm[N], Tp[N], Um[N], Up[N];
             if (trans1) {
-                rp.transverse_pair(L2, am2, Tm, Tp);
-                rp.transverse_pair(L2, ap2, Um, Up);
+                // the wall-ghost form (the batched kernel) keeps the general
+                // split: the subsonic one's code would push it past its
+                // register cap into spills
+                rp.template transverse_pair<!WALL_GHOSTS>(L2, am2, Tm, Tp);
+                rp.template transverse_pair<!WALL_GHOSTS>(L2, ap2, Um, Up);
             }
             const bool yin = ye_lane && k + 2 >= 0 && k + 2 <= my;
             const bool xin = xe_lane && k + 1 >= 0 && k + 1 < my;
