@@ -639,7 +639,9 @@ struct SweRP {
         const T b2 = a[vt] - v * a[0];
         const T b3 = (a[vn] - (u - c) * a[0]) * L.r2c;
         const T l1 = u - c, l2 = u, l3 = u + c;
-        if (l1 < T(0) && l3 > T(0)) {
+        // FP64 only: in FP32 (transverse option 2) the extra code measured
+        // slower than the zero terms it saves
+        if (sizeof(T) == 8 && l1 < T(0) && l3 > T(0)) {
             // subsonic across the split direction (the common case): B-
             // takes wave 1, B+ wave 3, the shear wave goes with the sign of
             // u; the same sums as below without their zero terms

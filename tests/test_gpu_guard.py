@@ -198,3 +198,32 @@ def test_guard_quiet_on_the_bench_dambreak():
     got, want, nguard, _ = step("swe", g.q, (W, W, W, W), 0.0, dx=g.dx)
     assert nguard == 0
     assert scaled_error("swe", got, want) <= TOL[mc.F32]
+
+
+def test_advance_with_queued_tasks():
+    """mc_advance of an FP32 run whose steps queue tasks for the FP64 guard:
+    the guard kernel then recomputes them and, in the graph-captured loop,
+    applies the time-step rule once the speed maximum is complete (its last
+    block).  An initial dt three times too large is rejected and retaken;
+    times, step sizes, the rejection count and the state follow the oracle's
+    driver as for an unguarded run."""
+    mx, my, nsteps = 70, 45, 6
+    q32 = near_dry_dambreak(mx, my, seed=7).astype(np.float32)
+    dx = 1.0 / 64
+    p = mc.Problem.make(mc.SWE_ROE, mx, my, dx, dx, dtype=mc.F32, bc=(W, W, W, W),
+                        param=(G, 0, 0, 0))
+    op = oracle.Problem(oracle.SWE, mx, my, dx, dx, bc=(W, W, W, W), param=(G, 0, 0, 0))
+    qo = embed(op, q32.astype(np.float64))
+    dt0 = 3.0 * 0.9 / oracle.max_cell_speed(op, oracle.bc_fill(op, qo))
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(q32)
+        ctx.guard_stats(reset=True)
+        t, dt, inb, nrej = ctx.advance(a.ptr, b.ptr, nsteps, 0.9, 1.0, 0.0, dt0)
+        got = (b if inb else a).download().astype(np.float64)
+        nguard = ctx.guard_stats(reset=True)
+    want, t_ref, dt_ref, nrej_ref, _ = oracle.advance(op, qo, nsteps, 0.9, 1.0, 0.0, dt0)
+    assert nguard > 0
+    assert nrej == nrej_ref >= 1
+    assert t == pytest.approx(t_ref, rel=1e-5) and dt == pytest.approx(dt_ref, rel=1e-5)
+    assert scaled_error("swe", got, want[:, 2:-2, 2:-2]) <= 1e-4
