@@ -45,6 +45,18 @@ int ntasks_for(const mc_problem& p, int tile_rows, int* nbands)
     return nb * nr;
 }
 
+int ntasks_split(const mc_problem& p, int tile_rows, int split, int* nbands, int* nbig)
+{
+    if (split <= 0) {
+        *nbig = 0;
+        return ntasks_for(p, tile_rows, nbands);
+    }
+    const int nb = (p.mx + BAND_W - 1) / BAND_W;
+    *nbands = nb;
+    *nbig = nb * (split / (TALL_TILES * tile_rows));
+    return *nbig + nb * ((p.my - split + tile_rows - 1) / tile_rows);
+}
+
 static int meqn_of(int solver) { return solver_meqn(solver); }
 
 static mc_status validate(const mc_problem* p)
@@ -206,6 +218,25 @@ static int default_tile_rows(const mc_problem& p)
     return rows;
 }
 
+// Rows [0, split) of the default layout go in tasks of TALL_TILES tiles
+// (fewer halo rows re-read: a task of r rows marches r + 3), the rest in
+// tasks of tile rows, launched last: on a grid with several waves of tasks
+// the last wave is then made of short tasks, so the SMs finish together.
+// The short part holds about one wave (SWEEP_WARPS warps on each SM, three
+// CTAs each, the occupancy of the FP32 steps); grids of fewer than four
+// such waves keep uniform tiles (split 0).
+static int default_tile_split(const mc_problem& p, int rows, int sms)
+{
+    const long long nb = (p.mx + BAND_W - 1) / BAND_W;
+    const long long wave = 3LL * (sms > 0 ? sms : 152) * SWEEP_WARPS;
+    if (nb * ((p.my + rows - 1) / rows) < 4 * wave) return 0;
+    long long shortr = (wave * rows + nb - 1) / nb;            // rows of about one wave
+    shortr = (shortr + rows - 1) / rows * rows;
+    long long split = (long long)p.my - shortr;
+    split = split / (TALL_TILES * rows) * (TALL_TILES * rows);
+    return split > 0 ? int(split) : 0;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -233,6 +264,7 @@ struct mc_ctx {
     mc_problem p;
     mc_layout lay;
     int tile_rows;
+    int tile_split;                // rows in tasks of TALL_TILES tiles (default layout), or 0
     DevState* dev;                 // device scratch: time-step scalars and status
     CUtensorMap* dmaps;            // device array of MAP_SLOTS tensor maps
     cudaStream_t capture;          // private stream used to capture graphs
@@ -258,8 +290,8 @@ static bool has_guard(const mc_problem& p)
 static void ensure_guard_list(mc_ctx* c)
 {
     if (!has_guard(c->p)) return;
-    int nb = 0;
-    const int need = ntasks_for(c->p, c->tile_rows, &nb);
+    int nb = 0, nbig = 0;
+    const int need = ntasks_split(c->p, c->tile_rows, c->tile_split, &nb, &nbig);
     if (need <= c->gq_cap) return;
     if (c->gq_tasks) cudaFree(c->gq_tasks);
     c->gq_tasks = nullptr;
@@ -279,6 +311,7 @@ static void launch_extras(const mc_ctx* c, SweepLaunch& L)
         L.gq_tasks = c->gq_tasks;
     }
     L.sms = c->sms;
+    L.tile_split = c->tile_split;
 }
 
 static void drop_graphs(mc_ctx* c)
@@ -382,6 +415,7 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
             cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             c->sms = 0;
     }
+    c->tile_split = default_tile_split(*p, c->tile_rows, c->sms);
     cudaError_t e = cudaMalloc(&c->dev, sizeof(DevState));
     if (e != cudaSuccess) {
         delete c;
@@ -433,10 +467,15 @@ mc_status mc_destroy(mc_ctx* c)
 mc_status mc_set_tile_rows(mc_ctx* c, int rows)
 {
     if (!c) return set_error(MC_EINVAL, "context is NULL");
-    if (rows == 0) rows = default_tile_rows(c->p);
+    int split = 0;
+    if (rows == 0) {
+        rows = default_tile_rows(c->p);
+        split = default_tile_split(c->p, rows, c->sms);
+    }
     if (rows < 1 || rows > 4096) return set_error(MC_EINVAL, "tile rows %d out of range", rows);
-    if (rows != c->tile_rows) drop_graphs(c);
+    if (rows != c->tile_rows || split != c->tile_split) drop_graphs(c);
     c->tile_rows = rows;
+    c->tile_split = split;
     ensure_guard_list(c);
     return MC_OK;
 }

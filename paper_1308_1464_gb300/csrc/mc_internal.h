@@ -53,6 +53,7 @@ struct SweepLaunch {
     DevState* dt_state = nullptr;
     double cfl_desired = 0.0, cfl_max = 0.0;
     bool* dt_folded = nullptr;
+    int tile_split = 0;                        // rows in tasks of TALL_TILES tiles, launched first (0: none)
     int sms = 0;                               // SMs of the device (0: unknown, full CTAs)
 };
 
@@ -127,6 +128,9 @@ cudaError_t bc_dir_launch(const mc_problem& p, const mc_layout& lay, void* qa, v
                           const int* cur_dev, int dir, cudaStream_t s);
 
 int ntasks_for(const mc_problem& p, int tile_rows, int* nbands);
+// tasks of the layout with rows [0, split) in tiles of TALL_TILES tile_rows
+// (nbig of them, first) and the rest in tiles of tile_rows; split 0: uniform
+int ntasks_split(const mc_problem& p, int tile_rows, int split, int* nbands, int* nbig);
 
 // error reporting
 mc_status set_error(mc_status st, const char* fmt, ...);

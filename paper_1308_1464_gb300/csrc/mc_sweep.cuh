@@ -107,6 +107,7 @@ struct SweepArgs {
     long long ld_x, ld_field, x_offset;
     int limiter, order, transverse;
     int nbands, ntasks, tile_rows;
+    int split, nbig;                 // rows [0, split) in the first nbig tasks, TALL_TILES tiles each
     unsigned long long* smax_bits;
     int* status;
     const MlpDev* net;                    // pressure-seed network, or null (solvers with SEEDED)
@@ -839,6 +840,24 @@ __device__ __forceinline__ WarpRing warp_ring(unsigned char* smem, int es, int n
 // The fused step over one grid.  The tensor maps of the two state buffers
 // live in device global memory (64-byte aligned, written by the host before
 // the launch); the kernel takes plain pointers to them.
+// The band and rows of a warp task: the first nbig tasks cut rows
+// [0, split) in tiles of TALL_TILES * tile_rows, the others the rows from
+// split on in tiles of tile_rows; bands vary fastest.
+template <class A>
+__device__ __forceinline__ void task_extent(const A& a, int task, int& i0, int& j0, int& jend)
+{
+    if (task < a.nbig) {
+        i0 = (task % a.nbands) * BAND_W;
+        j0 = (task / a.nbands) * (TALL_TILES * a.tile_rows);
+        jend = j0 + TALL_TILES * a.tile_rows;
+    } else {
+        const int t = task - a.nbig;
+        i0 = (t % a.nbands) * BAND_W;
+        j0 = a.split + (t / a.nbands) * a.tile_rows;
+        jend = min(j0 + a.tile_rows, a.my);
+    }
+}
+
 template <class RP, int MODE>
 __global__ void __launch_bounds__(SWEEP_WARPS * 32, min_ctas<RP>::value)
     ctu_sweep_kernel(const CUtensorMap* map_a, const CUtensorMap* map_b, const SweepArgs<RP> a)
@@ -889,9 +908,8 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32, min_ctas<RP>::value)
     constexpr int GD = RP::PAIRED ? GUARD_DETECT : GUARD_NONE;
     for (int task = blockIdx.x * nw + warp; task < a.ntasks && !failed && map_ok;
          task += gridDim.x * nw) {
-        const int i0 = (task % a.nbands) * BAND_W;
-        const int j0 = (task / a.nbands) * a.tile_rows;
-        const int jend = min(j0 + a.tile_rows, a.my);
+        int i0, j0, jend;
+        task_extent(a, task, i0, j0, jend);
         bool fl = false, tb = false;
         T tx = T(0), ty = T(0);
         failed = !sweep_task<RP, false, MODE, GD>(a.rp, map, qout, a.mx, a.my, a.ld_x, a.ld_field,
@@ -957,9 +975,8 @@ __global__ void __launch_bounds__(SWEEP_WARPS * 32)
     T smx = T(0), smy = T(0);
     for (int idx = blockIdx.x * nw + warp; idx < total && !failed && map_ok; idx += gridDim.x * nw) {
         const int task = a.gq_tasks ? a.gq_tasks[idx] : idx;
-        const int i0 = (task % a.nbands) * BAND_W;
-        const int j0 = (task / a.nbands) * a.tile_rows;
-        const int jend = min(j0 + a.tile_rows, a.my);
+        int i0, j0, jend;
+        task_extent(a, task, i0, j0, jend);
         failed = !sweep_task<RP, false, MODE, GUARD_REDO>(a.rp, map, qout, a.mx, a.my, a.ld_x,
                                                           a.ld_field, a.x_offset, i0, j0, jend, nux,
                                                           nuy, a.limiter, second, a.transverse, W,

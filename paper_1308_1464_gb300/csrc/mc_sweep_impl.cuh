@@ -48,7 +48,8 @@ cudaError_t sweep_launch_t(const SweepLaunch& L)
     a.order = L.prob.order;
     a.transverse = L.prob.transverse;
     a.tile_rows = L.tile_rows;
-    a.ntasks = ntasks_for(L.prob, L.tile_rows, &a.nbands);
+    a.split = L.tile_split;
+    a.ntasks = ntasks_split(L.prob, L.tile_rows, L.tile_split, &a.nbands, &a.nbig);
     a.smax_bits = L.smax_bits;
     a.status = L.status;
     a.net = RP::SEEDED ? static_cast<const MlpDev*>(L.seed_net) : nullptr;

@@ -71,3 +71,27 @@ def test_ten_steps_full_size(solver, dtype, bc, cfl):
         tol = TOL[mc.F32] * NSTEPS
     err = scaled_error(solver, got, want[:, 2:-2, 2:-2])
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("solver,bc", [("swe", (W, W, W, W)), ("euler", (X, X, X, X))])
+def test_default_layout_equals_uniform_tiles(solver, bc):
+    """On a 4096^2 grid the default layout cuts most rows in 128-row tasks,
+    launched first, and the last wave's worth in 64-row tasks; one step with
+    it gives the bits of uniform 64-row tasks (and of uniform 32-row ones),
+    speed maximum included."""
+    n = 4096
+    g = workloads.swe_dambreak(n, n) if solver == "swe" else workloads.euler_quadrants(n, n)
+    p, _ = problems(solver, n, n, g.dx, g.dy, mc.F32, bc)
+    qin = np.ascontiguousarray(g.q.astype(np.float32))
+    outs = []
+    with mc.Context(p) as ctx:
+        a, b = DeviceState(ctx).zero_(), DeviceState(ctx).zero_()
+        a.upload(qin)
+        dt = 0.8 / ctx.max_cell_speed(a.ptr)
+        for rows in (0, 64, 32):
+            ctx.set_tile_rows(rows)
+            smax = ctx.step(a.ptr, b.ptr, dt)
+            outs.append((b.download(), smax))
+    for q, smax in outs[1:]:
+        assert smax == outs[0][1]
+        np.testing.assert_array_equal(q, outs[0][0])
