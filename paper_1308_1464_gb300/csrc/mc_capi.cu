@@ -136,6 +136,26 @@ static cudaError_t sweep_prepare(const mc_problem& p)
     }
 }
 
+// resident CTAs per SM of the problem's fused step (1 if unknown)
+static int sweep_ctas_per_sm(const mc_problem& p)
+{
+    int ctas = 0;
+    cudaError_t e;
+    switch (p.solver) {
+    case MC_ACOUSTICS: e = sweep_occupancy_acoustics(p, &ctas); break;
+    case MC_SWE_ROE: e = sweep_occupancy_swe(p, &ctas); break;
+    case MC_ADVECTION: e = sweep_occupancy_advection(p, &ctas); break;
+    case MC_ACOUSTICS_VAR: e = sweep_occupancy_acoustics_var(p, &ctas); break;
+    case MC_EULER_GODUNOV: e = sweep_occupancy_euler_godunov(p, &ctas); break;
+    default: e = sweep_occupancy_euler(p, &ctas); break;
+    }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    return ctas > 0 ? ctas : 1;
+}
+
 static cudaError_t maxspeed_launch(const mc_problem& p, const mc_layout& lay, const void* q,
                                    unsigned long long* out, cudaStream_t s)
 {
@@ -222,13 +242,12 @@ static int default_tile_rows(const mc_problem& p)
 // (fewer halo rows re-read: a task of r rows marches r + 3), the rest in
 // tasks of tile rows, launched last: on a grid with several waves of tasks
 // the last wave is then made of short tasks, so the SMs finish together.
-// The short part holds about one wave (SWEEP_WARPS warps on each SM, three
-// CTAs each, the occupancy of the FP32 steps); grids of fewer than four
-// such waves keep uniform tiles (split 0).
-static int default_tile_split(const mc_problem& p, int rows, int sms)
+// The short part holds about one wave (the kernel's resident warps on every
+// SM); grids of fewer than four waves keep uniform tiles (split 0).
+static int default_tile_split(const mc_problem& p, int rows, int sms, int ctas_per_sm)
 {
     const long long nb = (p.mx + BAND_W - 1) / BAND_W;
-    const long long wave = 3LL * (sms > 0 ? sms : 152) * SWEEP_WARPS;
+    const long long wave = (long long)ctas_per_sm * (sms > 0 ? sms : 152) * SWEEP_WARPS;
     if (nb * ((p.my + rows - 1) / rows) < 4 * wave) return 0;
     long long shortr = (wave * rows + nb - 1) / nb;            // rows of about one wave
     shortr = (shortr + rows - 1) / rows * rows;
@@ -264,7 +283,8 @@ struct mc_ctx {
     mc_problem p;
     mc_layout lay;
     int tile_rows;
-    int tile_split;                // rows in tasks of TALL_TILES tiles (default layout), or 0
+    int tile_split = 0;            // rows in tasks of TALL_TILES tiles (default layout), or 0
+    int ctas_per_sm = 1;           // resident CTAs of the fused step's kernel
     DevState* dev;                 // device scratch: time-step scalars and status
     CUtensorMap* dmaps;            // device array of MAP_SLOTS tensor maps
     cudaStream_t capture;          // private stream used to capture graphs
@@ -415,7 +435,7 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
             cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             c->sms = 0;
     }
-    c->tile_split = default_tile_split(*p, c->tile_rows, c->sms);
+
     cudaError_t e = cudaMalloc(&c->dev, sizeof(DevState));
     if (e != cudaSuccess) {
         delete c;
@@ -436,6 +456,8 @@ mc_status mc_create(const mc_problem* p, mc_ctx** out)
         delete c;
         return cuda_error(e, "context set-up");
     }
+    c->ctas_per_sm = sweep_ctas_per_sm(c->p);
+    c->tile_split = default_tile_split(c->p, c->tile_rows, c->sms, c->ctas_per_sm);
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
@@ -470,7 +492,7 @@ mc_status mc_set_tile_rows(mc_ctx* c, int rows)
     int split = 0;
     if (rows == 0) {
         rows = default_tile_rows(c->p);
-        split = default_tile_split(c->p, rows, c->sms);
+        split = default_tile_split(c->p, rows, c->sms, c->ctas_per_sm);
     }
     if (rows < 1 || rows > 4096) return set_error(MC_EINVAL, "tile rows %d out of range", rows);
     if (rows != c->tile_rows || split != c->tile_split) drop_graphs(c);

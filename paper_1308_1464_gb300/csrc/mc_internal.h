@@ -96,6 +96,13 @@ cudaError_t sweep_prepare_euler(int dtype);
 cudaError_t sweep_prepare_advection(int dtype);
 cudaError_t sweep_prepare_acoustics_var(int dtype);
 cudaError_t sweep_prepare_euler_godunov(int dtype);
+// resident CTAs per SM of the problem's fused-step kernel (after its prepare)
+cudaError_t sweep_occupancy_acoustics(const mc_problem& p, int* ctas);
+cudaError_t sweep_occupancy_swe(const mc_problem& p, int* ctas);
+cudaError_t sweep_occupancy_euler(const mc_problem& p, int* ctas);
+cudaError_t sweep_occupancy_advection(const mc_problem& p, int* ctas);
+cudaError_t sweep_occupancy_acoustics_var(const mc_problem& p, int* ctas);
+cudaError_t sweep_occupancy_euler_godunov(const mc_problem& p, int* ctas);
 cudaError_t maxspeed_launch_acoustics(const mc_problem& p, const mc_layout& lay, const void* q,
                                       unsigned long long* out, cudaStream_t s);
 cudaError_t maxspeed_launch_swe(const mc_problem& p, const mc_layout& lay, const void* q,

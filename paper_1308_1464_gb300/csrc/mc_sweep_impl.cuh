@@ -212,6 +212,26 @@ cudaError_t batch_init_t(const BatchLaunch& L)
     return cudaGetLastError();
 }
 
+// CTAs of the fused step's kernel (the problem's compiled scheme) resident
+// on one SM; the kernel's shared-memory limit must be raised already
+template <class RP>
+cudaError_t sweep_occupancy_t(const mc_problem& p, int* ctas)
+{
+    using T = typename RP::real;
+    const int smem = sweep_smem_bytes(sizeof(T), RP::NPLANE) + (RP::SEEDED ? seednet_smem_bytes() : 0);
+    switch (scheme_mode(p)) {
+    case MODE_FAST:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, ctu_sweep_kernel<RP, MODE_FAST>,
+                                                             SWEEP_WARPS * 32, smem);
+    case MODE_TRANS2:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, ctu_sweep_kernel<RP, MODE_TRANS2>,
+                                                             SWEEP_WARPS * 32, smem);
+    default:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, ctu_sweep_kernel<RP, MODE_GENERAL>,
+                                                             SWEEP_WARPS * 32, smem);
+    }
+}
+
 template <class RP>
 cudaError_t batch_occupancy_t(int* ctas)
 {
@@ -289,6 +309,11 @@ cudaError_t multi_launch_t(const MultiLaunch& L)
     cudaError_t sweep_prepare_##NAME(int dtype)                                                \
     {                                                                                          \
         return dtype == MC_F64 ? sweep_prepare_t<RPT<double>>() : sweep_prepare_t<RPT<float>>(); \
+    }                                                                                          \
+    cudaError_t sweep_occupancy_##NAME(const mc_problem& p, int* ctas)                         \
+    {                                                                                          \
+        return p.dtype == MC_F64 ? sweep_occupancy_t<RPT<double>>(p, ctas)                     \
+                                 : sweep_occupancy_t<RPT<float>>(p, ctas);                     \
     }                                                                                          \
     cudaError_t batch_launch_##NAME(const BatchLaunch& L)                                      \
     {                                                                                          \
