@@ -16,6 +16,7 @@
 // the padded layout, which lets a host transfer of a state move one
 // contiguous block.
 #include "mc_internal.h"
+#include "mc_tile.h"
 
 namespace mc {
 
@@ -141,11 +142,15 @@ __global__ void bc_dir_kernel(const DirArgs<T> a, int dir)
         const long long dst = (long long)(j + 2) * h.ld_x + h.x_offset + i;
         const long long src = (long long)(sj + 2) * h.ld_x + h.x_offset + si;
         const int fm = dir == 0 ? 1 : 2;  // normal momentum of the side
-        for (int m = 0; m < h.meqn; m++) {
-            T v = q[m * h.ld_field + src];
-            if (flip && m == fm) v = -v;
-            q[m * h.ld_field + dst] = v;
-        }
+        // all planes' loads first, so their latencies overlap (a ghost's
+        // source is never a ghost this phase writes)
+        T v[BC_MAX_PLANES];
+#pragma unroll
+        for (int m = 0; m < BC_MAX_PLANES; m++)
+            if (m < h.meqn) v[m] = q[m * h.ld_field + src];
+#pragma unroll
+        for (int m = 0; m < BC_MAX_PLANES; m++)
+            if (m < h.meqn) q[m * h.ld_field + dst] = (flip && m == fm) ? -v[m] : v[m];
     }
 }
 

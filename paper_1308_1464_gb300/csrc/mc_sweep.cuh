@@ -1058,11 +1058,15 @@ __global__ void bc_fill_kernel(const BcArgs<T> a)
         const int sj = bc_map(j, a.my, a.bc[2], a.bc[3], fy);
         const long long dst = (long long)(j + 2) * a.ld_x + a.x_offset + i;
         const long long src = (long long)(sj + 2) * a.ld_x + a.x_offset + si;
-        for (int m = 0; m < a.meqn; m++) {
-            T v = q[m * a.ld_field + src];
-            if ((m == 1 && fx) || (m == 2 && fy)) v = -v;
-            q[m * a.ld_field + dst] = v;
-        }
+        // all planes' loads first (at most BC_MAX_PLANES), so their latencies
+        // overlap, then the stores
+        T v[BC_MAX_PLANES];
+#pragma unroll
+        for (int m = 0; m < BC_MAX_PLANES; m++)
+            if (m < a.meqn) v[m] = q[m * a.ld_field + src];
+#pragma unroll
+        for (int m = 0; m < BC_MAX_PLANES; m++)
+            if (m < a.meqn) q[m * a.ld_field + dst] = ((m == 1 && fx) || (m == 2 && fy)) ? -v[m] : v[m];
     }
 }
 

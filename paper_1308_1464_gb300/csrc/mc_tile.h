@@ -39,6 +39,8 @@ __host__ __device__ constexpr int sweep_smem_bytes(int es, int neq)
 // compile-time schemes of the fused step (see sweep_task)
 constexpr int MODE_GENERAL = 0, MODE_TRANS2 = 1, MODE_FAST = 2;
 constexpr int DEFAULT_TILE_ROWS = 64;
+// state planes of any solver (Euler 4, variable-coefficient acoustics 5)
+constexpr int BC_MAX_PLANES = 5;
 // the default layout's long tasks: this many tiles of rows each (a task of r
 // rows marches r + 3 rows, so longer ones re-read fewer halo rows)
 constexpr int TALL_TILES = 2;
