@@ -407,6 +407,8 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
     int hh = 0;                       // halves of this lane's edges with a near-sonic transonic
                                       // speed, accumulated over the march (GUARD_DETECT)
     float g_lo = 3.0e38f, g_hi = 0.0f;   // range of the first field (GUARD_DETECT)
+    // this lane's output cell of row k (from k = j0 on), advanced one row at a time
+    T* orow = qout + (long long)(j0 + 2) * ld_x + x_offset + c;
     for (int k = j0 - 3; k < jend; k++) {
         T qc2[NP], ql2[NP];
         // material of cell (c-1, k), the neighbour below where A-dQ of x-edge
@@ -725,7 +727,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             if (RP::POSITIVE) bad |= out_lane && !(qn[0] > T(0));
             else bad |= out_lane && qn[0] != qn[0];
             if (out_lane) {
-                T* o = qout + (long long)(k + 2) * ld_x + x_offset + c;
+                T* o = orow;
 #pragma unroll
                 for (int m = 0; m < N; m++) o[m * ld_field] = qn[m];
 #pragma unroll
@@ -747,6 +749,7 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
             }
         }
 
+        if (k >= j0) orow += ld_x;
         // ---- rotate
 #pragma unroll
         for (int m = 0; m < NP; m++) {
