@@ -1237,7 +1237,8 @@ def bench_configs(args):
     bsub = copy.copy(sub)
     bsub.blocks, bsub.no_e2e = "2x1", True
     rec = compact(bench_blocks(bsub, WORKLOADS["swe32"], 0, 1))
-    rec["parallelism"] = "2x1 blocks of 4096x4096 on one GPU, halo strips by device copies"
+    rec["parallelism"] = ("2x1 blocks of 4096x4096 on one GPU, halo strips by device copies, "
+                          "each attempt replayed from a CUDA graph")
     rec["wall_s"] = round(time.perf_counter() - t0, 1)
     out["swe_blocks_2x1_fp32"] = rec
     t0 = time.perf_counter()

@@ -353,12 +353,15 @@ class DeviceStepper:
     With a transport (one block per rank) the strips and the maximum travel
     through it: NCCL moves device buffers and reduces the device scalar in
     place; gloo stages them through host memory.  Without one, every block is
-    held by this process and the exchange and reduction are device copies.
+    held by this process and the exchange and reduction are device copies;
+    an attempt is then captured once into a CUDA graph (graph=True) and
+    replayed, since every launch of it reads the device state alone.
 
-    Blocks must use DeviceBlockOps; states are passed as lists of the two
-    buffers of each block (qa, qb), the current one chosen on the device."""
+    Blocks must use DeviceBlockOps, all on one stream; states are passed as
+    lists of the two buffers of each block (qa, qb), the current one chosen
+    on the device."""
 
-    def __init__(self, blocks, transport=None):
+    def __init__(self, blocks, transport=None, graph: bool = True):
         import torch
         self.blocks = list(blocks)
         self.transport = transport
@@ -367,11 +370,13 @@ class DeviceStepper:
         # the speed maximum of each block's attempt: int64 bits of a
         # non-negative double (ordered like the doubles)
         self.smax = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in self.blocks]
+        self.graph = graph and transport is None
+        self._graphs = {}
 
     def _ctx(self, b):
         return b.ops.ctx
 
-    def _exchange(self, qas, qbs) -> None:
+    def _exchange(self, qas, qbs, stream) -> None:
         for direction in (0, 1):
             mail = {}
             outs = []
@@ -380,7 +385,7 @@ class DeviceStepper:
                 out = []
                 for side, dst in sends:
                     buf = b._send[side]
-                    self._ctx(b).block_pack(qa, qb, side, buf.data_ptr(), b.ops.stream)
+                    self._ctx(b).block_pack(qa, qb, side, buf.data_ptr(), stream)
                     out.append((dst, side ^ 1, buf))
                     mail[(b.rank, dst, side ^ 1)] = buf
                 outs.append(out)
@@ -396,8 +401,8 @@ class DeviceStepper:
             for b, qa, qb in zip(self.blocks, qas, qbs):
                 _, recvs = b.decomp.messages(b.rank, direction)
                 for side, _src in recvs:
-                    self._ctx(b).block_unpack(b._recv[side].data_ptr(), side, qa, qb, b.ops.stream)
-                self._ctx(b).block_fill_dir(qa, qb, direction, b.ops.stream)
+                    self._ctx(b).block_unpack(b._recv[side].data_ptr(), side, qa, qb, stream)
+                self._ctx(b).block_fill_dir(qa, qb, direction, stream)
 
     def _reduce_max(self) -> None:
         if self.transport is None:
@@ -410,6 +415,30 @@ class DeviceStepper:
         else:
             self.transport.max_tensor(self.smax[0])
 
+    def _attempt(self, qas, qbs, cfl_desired: float, cfl_max: float, stream) -> None:
+        self._exchange(qas, qbs, stream)
+        for b, qa, qb, sm in zip(self.blocks, qas, qbs, self.smax):
+            self._ctx(b).block_sweep(qa, qb, sm.data_ptr(), stream)
+        self._reduce_max()
+        for b, sm in zip(self.blocks, self.smax):
+            self._ctx(b).block_dt_rule(sm.data_ptr(), cfl_desired, cfl_max, stream)
+
+    def _attempt_graph(self, qas, qbs, cfl_desired: float, cfl_max: float):
+        """The captured attempt for these buffers and CFL numbers, captured
+        after an eager attempt has encoded the buffers' tensor maps; the
+        attempt with the two buffers' roles exchanged is captured with it
+        (capturing runs nothing), so a later call that starts from the other
+        buffer finds its graph ready."""
+        import torch
+        key = (tuple(qas), tuple(qbs), float(cfl_desired), float(cfl_max))
+        if key not in self._graphs:
+            for a, b in ((qas, qbs), (qbs, qas)):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self._attempt(a, b, cfl_desired, cfl_max, torch.cuda.current_stream().cuda_stream)
+                self._graphs[(tuple(a), tuple(b), float(cfl_desired), float(cfl_max))] = g
+        return self._graphs[key]
+
     def max_cell_speed(self, qas) -> float:
         v = max(b.ops.max_speed(q) for b, q in zip(self.blocks, qas))
         return v if self.transport is None else self.transport.max(v)
@@ -420,18 +449,22 @@ class DeviceStepper:
         result_in_b, nrejected), the same on every rank."""
         if dt is None:
             dt = cfl_desired / self.max_cell_speed(qas)
+        stream = self.blocks[0].ops.stream
         for b in self.blocks:
             self._ctx(b).block_begin(t, dt, b.ops.stream)
         attempts, total = nsteps, 0
         res = None
         while True:
-            for _ in range(attempts):
-                self._exchange(qas, qbs)
-                for b, qa, qb, sm in zip(self.blocks, qas, qbs, self.smax):
-                    self._ctx(b).block_sweep(qa, qb, sm.data_ptr(), b.ops.stream)
-                self._reduce_max()
-                for b, sm in zip(self.blocks, self.smax):
-                    self._ctx(b).block_dt_rule(sm.data_ptr(), cfl_desired, cfl_max, b.ops.stream)
+            if attempts > 0:
+                self._attempt(qas, qbs, cfl_desired, cfl_max, stream)
+                if attempts > 1:
+                    if self.graph:
+                        g = self._attempt_graph(qas, qbs, cfl_desired, cfl_max)
+                        for _ in range(attempts - 1):
+                            g.replay()
+                    else:
+                        for _ in range(attempts - 1):
+                            self._attempt(qas, qbs, cfl_desired, cfl_max, stream)
             total += attempts
             res = [self._ctx(b).block_end(b.ops.stream) for b in self.blocks]
             nacc = res[0][3]
