@@ -734,16 +734,19 @@ __device__ __forceinline__ bool sweep_task(const RP& rp, const CUtensorMap* map,
                 for (int m = N; m < NP; m++) o[m * ld_field] = qc0[m];   // material, unchanged
                 if (WALL_GHOSTS) {
                     const bool hx = c < 2 || c >= mx - 2, hy = k < 2 || k >= my - 2;
-                    const int gi = c < 2 ? -1 - c : 2 * mx - 1 - c;
-                    const int gj = k < 2 ? -1 - k : 2 * my - 1 - k;
-                    T* base = qout + x_offset;
+                    if (hx || hy) {
+                        // mirrors of this cell, addressed from its own slot o
+                        const int gi = c < 2 ? -1 - c : 2 * mx - 1 - c;
+                        const int gj = k < 2 ? -1 - k : 2 * my - 1 - k;
+                        T* ox = o + (gi - c);
+                        T* oy = o + (long long)(gj - k) * ld_x;
+                        T* oxy = oy + (gi - c);
 #pragma unroll
-                    for (int m = 0; m < N; m++) {
-                        if (hx) base[m * ld_field + (long long)(k + 2) * ld_x + gi] = m == 1 ? -qn[m] : qn[m];
-                        if (hy) base[m * ld_field + (long long)(gj + 2) * ld_x + c] = m == 2 ? -qn[m] : qn[m];
-                        if (hx && hy)
-                            base[m * ld_field + (long long)(gj + 2) * ld_x + gi] =
-                                (m == 1 || m == 2) ? -qn[m] : qn[m];
+                        for (int m = 0; m < N; m++) {
+                            if (hx) ox[m * ld_field] = m == 1 ? -qn[m] : qn[m];
+                            if (hy) oy[m * ld_field] = m == 2 ? -qn[m] : qn[m];
+                            if (hx && hy) oxy[m * ld_field] = (m == 1 || m == 2) ? -qn[m] : qn[m];
+                        }
                     }
                 }
             }
