@@ -248,6 +248,19 @@ def sweep_source_hash():
     return h.hexdigest()[:16]
 
 
+def batch_source_hash():
+    """Sources of the batched kernel: its own files and the fused step's."""
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1308_1464_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if (name.startswith("mc_sweep") or name.startswith("mc_batch")
+                or name in ("mc_riemann.cuh", "mc_device.cuh", "mc_tile.h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def exact_source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1308_1464_gb300", "csrc")
@@ -295,6 +308,21 @@ def ncu_traffic(workload: str):
         e = d.get(workload)
         if e and e.get("source_hash") == sweep_source_hash():
             return e["dram_bytes_per_launch"]
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def ncu_batch():
+    """DRAM bytes of one persistent launch of the batched kernel (20 steps
+    over the 2000 patches) from the committed ncu summary, if it was taken
+    on the current sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            d = json.load(f)
+        e = d.get("batch2000")
+        if e and e.get("source_hash") == batch_source_hash():
+            return e
     except (OSError, ValueError):
         pass
     return None
@@ -483,6 +511,7 @@ def bench_batch(args, rank, world):
     value = cells_all * K / (ms * 1e-3)
     alg = 2 * cells * 3 * 4 * K     # this rank's bytes (the roofline is per GPU)
     peak, kind = measured_peaks()
+    nb = ncu_batch() if world == 1 else None
     b.close()
     return {
         "metric": "cell-updates/s", "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -506,7 +535,10 @@ def bench_batch(args, rank, world):
         "batched_over_plain": ms_plain / ms,
         "roofline": {"bound": "hbm", "achieved": round(alg / (ms * 1e-3) / 1e9, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
-                     "traffic": None, "kernel": "batch_sweep_kernel",
+                     "traffic": nb["dram_bytes_per_launch"] if nb else None,
+                     "kernel": "batch_sweep_kernel",
+                     "algorithmic_bytes_per_launch": 2 * cells * 3 * 4 * per_launch,
+                     "timed": "each persistent launch with its initial speed scan",
                      "peak_source": f"{kind} HBM copy"},
         # per persistent launch: the per-patch initial speed scan and the sweep
         "gpu_launches": 2 * launches, "clocks": clk.summary(),
