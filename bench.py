@@ -1293,6 +1293,36 @@ def bench_configs(args):
     return out
 
 
+def bench_next_rows(args):
+    """The step's further forms, each timed briefly on this GPU like the
+    further configurations: the van Leer limiter with transverse option 2
+    (f1), advection and variable-coefficient acoustics (f2), Euler with the
+    exact-solution normal solve and the learned pressure seed (f3), and
+    refined patches with refluxing against the uniformly fine grid (f4)."""
+    import copy
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.light = 20, 5, True
+    out = {}
+    for key, name in (("f1_swe_vanleer_trans2_4096_fp32", "swe32t2"),
+                      ("f2_advection_8192_fp32", "adv32"),
+                      ("f2_acoustics_var_4096_fp32", "acvar32"),
+                      ("f3_euler_godunov_4096_fp32", "eulg32")):
+        t0 = time.perf_counter()
+        line = bench_grid(sub, WORKLOADS[name], 0, 1, sub=True, key=name)
+        rec = compact(line)
+        if "pressure_seed" in line:
+            rec["pressure_seed"] = line["pressure_seed"]
+        rec["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[key] = rec
+    t0 = time.perf_counter()
+    am = bench_amr(sub, 0, 1)
+    rec = compact(am)
+    rec["uniform_fine"] = am["uniform_fine"]
+    rec["wall_s"] = round(time.perf_counter() - t0, 1)
+    out["f4_amr_dambreak_4096_fp32"] = rec
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1303,7 +1333,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the records of the further configurations in the default run")
+                    help="skip the records of the further configurations and forms in the default run")
     ap.add_argument("--peaks", action="store_true",
                     help="time the execution-unit microbenchmarks (FFMA, FFMA2, DFMA, MUFU, issue) and exit")
     ap.add_argument("--peaks-out", default="", help="with --peaks: also write the JSON to this file")
@@ -1368,6 +1398,7 @@ def main():
         line["configs"] = bench_configs(args)
         blk = line["configs"]["swe_blocks_2x1_fp32"]
         blk["over_single_grid"] = round(blk["value"] / line["value"], 4)
+        line["next_rows"] = bench_next_rows(args)
     if rank == 0 and line is not None:
         print(json.dumps(line))
     if world > 1:
