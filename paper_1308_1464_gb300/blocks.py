@@ -23,6 +23,7 @@ for every block held by one process, through ``exchange_local``.
 """
 from __future__ import annotations
 
+import contextlib
 import copy
 from dataclasses import dataclass
 
@@ -199,6 +200,17 @@ def exchange_local(blocks, qs) -> None:
             raise RuntimeError(f"unmatched halo messages: {sorted(mail)}")
 
 
+def _on_stream(blocks):
+    """Torch's current stream set to the blocks' stream for device blocks (a
+    transport's collectives and tensor copies then queue behind their
+    kernels); nothing for host blocks."""
+    s = getattr(blocks[0].ops, "torch_stream", None) if blocks else None
+    if s is None:
+        return contextlib.nullcontext()
+    import torch
+    return torch.cuda.stream(s)
+
+
 class Stepper:
     """Steps of a decomposed grid with one global time step.
 
@@ -228,8 +240,9 @@ class Stepper:
     def step(self, qs_in, qs_out, dt: float) -> float:
         """One step of every block with dt; returns the global smax of the
         step's waves (Courant number = dt * smax)."""
-        self.fill(qs_in)
-        return self._max([b.ops.step(qi, qo, dt) for b, qi, qo in zip(self.blocks, qs_in, qs_out)])
+        with _on_stream(self.blocks):
+            self.fill(qs_in)
+            return self._max([b.ops.step(qi, qo, dt) for b, qi, qo in zip(self.blocks, qs_in, qs_out)])
 
     def advance(self, qa, qb, nsteps: int, cfl_desired: float, cfl_max: float, t: float = 0.0,
                 dt: float | None = None):
@@ -317,6 +330,10 @@ class DeviceBlockOps:
         self.ctx = ctx
         self.stream = stream
         self.dtype = torch.float64 if ctx.layout.elem_bytes == 8 else torch.float32
+        # the same stream as torch sees it: tensor copies, reductions and
+        # collectives issued for this block queue behind its kernels there
+        self.torch_stream = (torch.cuda.default_stream() if stream == 0
+                             else torch.cuda.ExternalStream(stream))
 
     def halo_elems(self, side: int) -> int:
         return self.ctx.halo_elems(side)
@@ -326,6 +343,8 @@ class DeviceBlockOps:
         return torch.empty(int(n), dtype=self.dtype, device="cuda")
 
     def copy(self, src, dst) -> None:
+        # on torch's current stream: the steppers make it this block's
+        # stream (or, while an attempt is captured, the capturing stream)
         dst.copy_(src)
 
     def pack(self, q: int, side: int, buf) -> None:
@@ -367,6 +386,8 @@ class DeviceStepper:
         self.transport = transport
         if transport is not None and len(self.blocks) != 1:
             raise ValueError("a transport serves one block per rank")
+        if len({b.ops.stream for b in self.blocks}) != 1:
+            raise ValueError("the blocks' operations must share one stream")
         # the speed maximum of each block's attempt: int64 bits of a
         # non-negative double (ordered like the doubles)
         self.smax = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in self.blocks]
@@ -446,7 +467,13 @@ class DeviceStepper:
     def advance(self, qas, qbs, nsteps: int, cfl_desired: float, cfl_max: float, t: float = 0.0,
                 dt: float | None = None):
         """nsteps accepted steps from the states in qas; returns (t, dt,
-        result_in_b, nrejected), the same on every rank."""
+        result_in_b, nrejected), the same on every rank.  The reductions,
+        copies, collectives and graph replays go to the blocks' stream."""
+        import torch
+        with torch.cuda.stream(self.blocks[0].ops.torch_stream):
+            return self._advance(qas, qbs, nsteps, cfl_desired, cfl_max, t, dt)
+
+    def _advance(self, qas, qbs, nsteps, cfl_desired, cfl_max, t, dt):
         if dt is None:
             dt = cfl_desired / self.max_cell_speed(qas)
         stream = self.blocks[0].ops.stream

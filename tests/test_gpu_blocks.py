@@ -229,13 +229,15 @@ def test_gloo_ranks_on_one_gpu_equal_single_grid():
     np.testing.assert_array_equal(got, want)
 
 
-def decomposed_device(p, q, px, py, nsteps, cfl=0.8, dt0=None):
+def decomposed_device(p, q, px, py, nsteps, cfl=0.8, dt0=None, stream=None, graph=True):
     """The decomposed run with the time-step state on the device
-    (DeviceStepper over mc_block_*), all blocks in this process."""
+    (DeviceStepper over mc_block_*), all blocks in this process, on the
+    given torch stream (default: the default stream)."""
     from paper_1308_1464_gb300.blocks import DeviceStepper
     d = Decomposition(p, px, py)
     ctxs = [mc.Context(d.local_problem(r)) for r in range(d.nblocks)]
-    blocks = [Block(d, r, DeviceBlockOps(c)) for r, c in enumerate(ctxs)]
+    sh = stream.cuda_stream if stream is not None else 0
+    blocks = [Block(d, r, DeviceBlockOps(c, sh)) for r, c in enumerate(ctxs)]
     qa, qb = [], []
     for r, c in enumerate(ctxs):
         e = d.extent(r)
@@ -243,8 +245,10 @@ def decomposed_device(p, q, px, py, nsteps, cfl=0.8, dt0=None):
         a.upload(q[:, e.j0: e.j0 + e.my, e.i0: e.i0 + e.mx])
         qa.append(a)
         qb.append(b)
-    t, dt, in_b, nrej = DeviceStepper(blocks).advance([s.ptr for s in qa], [s.ptr for s in qb],
-                                                      nsteps, cfl, 1.0, dt=dt0)
+    torch.cuda.synchronize()
+    t, dt, in_b, nrej = DeviceStepper(blocks, graph=graph).advance(
+        [s.ptr for s in qa], [s.ptr for s in qb], nsteps, cfl, 1.0, dt=dt0)
+    torch.cuda.synchronize()
     out = np.zeros(q.shape, dtype=qa[0].np_dtype)
     for r in range(d.nblocks):
         e = d.extent(r)
@@ -273,6 +277,22 @@ def test_device_stepper_equals_single_grid(solver, dtype, bc, px, py):
     got, t, dt, nrej = decomposed_device(p, qin, px, py, nsteps, dt0=dt0)
     assert nrej == nrej_w >= 1
     assert t == t_w and dt == dt_w
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_device_stepper_on_a_side_stream(graph):
+    """Blocks whose operations run on a stream other than torch's current
+    one: the halo copies, the max-reduction and the graph replays queue on
+    that stream too, so the run equals the default-stream run bit for bit."""
+    mx, my, nsteps = 75, 61, 6
+    q, dx, dy = initial_state("swe", mx, my, seed=4)
+    p, _ = problems("swe", mx, my, dx, dy, mc.F32, (W, W, W, W))
+    qin = q.astype(np.float32)
+    want, t_w, dt_w, nrej_w = decomposed_device(p, qin, 2, 2, nsteps, graph=graph)
+    got, t, dt, nrej = decomposed_device(p, qin, 2, 2, nsteps, stream=torch.cuda.Stream(),
+                                         graph=graph)
+    assert (t, dt, nrej) == (t_w, dt_w, nrej_w)
     np.testing.assert_array_equal(got, want)
 
 
