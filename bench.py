@@ -957,6 +957,8 @@ def bench_grid(args, wl, rank, world, sub=False, key=None):
     from paper_1308_1464_gb300.state import DeviceState
 
     key = key or args.workload      # the workload's name in WORKLOADS (its ncu records)
+    # the committed ncu counts were taken at the workload's own size
+    same_size = key in WORKLOADS and WORKLOADS[key]["n"] == wl["n"]
     p, g = make_problem(mc, wl)
     n_cells = p.mx * p.my
     ctx = mc.Context(p)
@@ -997,10 +999,11 @@ def bench_grid(args, wl, rank, world, sub=False, key=None):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(key),
+                "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(key) if same_size else None,
                 "kernel": "ctu_sweep_kernel", "kernel_ms": round(kms, 4),
                 "algorithmic_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} HBM copy"}
-    f64 = ncu_fp64(key) if p.dtype == mc.F64 else None
+    f64 = ncu_fp64(key) if p.dtype == mc.F64 and same_size else None
     if f64 is not None:
         # an FP64 step is bound by the FP64 pipe: counted FP64 flops over the
         # live kernel time, against the nominal FP64 rate
