@@ -901,15 +901,17 @@ def time_large_grid(args, wl, ctx, a, b, q0, dt0, stream, sh, world):
     return ms, nrej, clk.summary(), k0.elapsed_time(k1) / reps
 
 
-def time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh, world):
-    """A state smaller than the L2 (the small fixed-dt case): runs of
+def time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh, world, dt0):
+    """A state smaller than the L2 (the small fixed-dt case, or a grid
+    workload run at a small --size with half its initial dt held fixed, so
+    that the Courant number stays below one as the waves speed up): runs of
     iter_steps steps (ghost fill + fused step each, mc_step without a
     read-back), each run timed by CUDA events after an L2 flush; the fused
     step alone is timed the same way, one flushed launch at a time.  The
     host enqueues while the flush runs, so the events see GPU time only."""
     import torch
-    dt = wl["fixed_dt"]
-    it_steps = wl["iter_steps"]
+    dt = wl.get("fixed_dt", 0.5 * dt0)
+    it_steps = wl.get("iter_steps", 10)
     assert args.steps % it_steps == 0, f"steps must be a multiple of {it_steps}"
     qa, qb = a, b
     for _ in range(args.warmup):
@@ -982,7 +984,7 @@ def bench_grid(args, wl, rank, world, sub=False, key=None):
     l2 = L2Flush(torch)
     if lay.bytes < l2.l2_bytes:
         ms, nrej, clocks, kms, l2_note = time_small_grid(args, wl, ctx, a, b, q0, l2, stream, sh,
-                                                         world)
+                                                         world, dt0)
         launches = (1 + sweep_kernels(mc, p)) * args.steps
     else:
         ms, nrej, clocks, kms = time_large_grid(args, wl, ctx, a, b, q0, dt0, stream, sh, world)
